@@ -1,0 +1,302 @@
+"""ctypes wrapper around the C oracle (test infrastructure only).
+
+Every function mirrors one C entry point in gpbo_oracle.c and works in float64
+numpy arrays.  Nothing here imports the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build_oracle import build
+
+_lib = None
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_L = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        _lib = C.CDLL(path)
+        L = _lib
+        L.orc_splitmix64.restype = C.c_uint64
+        L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_uniform24.restype = C.c_double
+        L.orc_uniform24.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_normal.restype = C.c_double
+        L.orc_normal.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_uniform_points.argtypes = [C.c_uint64, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _D]
+        L.orc_block_value.restype = C.c_double
+        L.orc_block_value.argtypes = [C.c_int, _D, C.c_int]
+        L.orc_objective.argtypes = [C.c_int, _I, _I, _D, _D, _D]
+        L.orc_matern52.restype = C.c_double
+        L.orc_matern52.argtypes = [C.c_double]
+        L.orc_kmat.argtypes = [_D, C.c_int, C.c_int, _D, C.c_double, C.c_double, _D]
+        L.orc_cholesky.restype = C.c_int
+        L.orc_cholesky.argtypes = [_D, C.c_int, _D]
+        L.orc_forward.argtypes = [_D, C.c_int, _D, _D]
+        L.orc_backward_t.argtypes = [_D, C.c_int, _D, _D]
+        L.orc_tri_inverse.argtypes = [_D, C.c_int, _D]
+        L.orc_gp_fit.restype = C.c_int
+        L.orc_gp_fit.argtypes = [_D, _D, C.c_int, C.c_int, _D, C.c_double, C.c_double, _D, _D, _D]
+        L.orc_posterior.argtypes = [_D, C.c_int, C.c_int, _D, C.c_double, _D, _D, _D, C.c_int64, _D, _D]
+        L.orc_ei.restype = C.c_double
+        L.orc_ei.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.orc_ei_batch.argtypes = [_D, _D, C.c_int64, C.c_double, C.c_double, _D]
+        L.orc_argmax.restype = C.c_int64
+        L.orc_argmax.argtypes = [_D, C.c_int64]
+        L.orc_standardize.argtypes = [_D, C.c_int, _D, _D, _D]
+        L.orc_search_step.restype = C.c_int
+        L.orc_search_step.argtypes = [_D, _D, C.c_int, C.c_int, _D, C.c_double, C.c_double, _D, C.c_int64,
+                                      C.c_uint64, C.c_double, _D, _D, _L, _D, _D, _D]
+        L.orc_screen_pairwise.restype = C.c_int
+        L.orc_screen_pairwise.argtypes = [C.c_int, _I, _I, C.c_double, C.c_uint64, C.c_int, C.c_int,
+                                          C.c_double, _D, _D]
+        L.orc_screen_routine.restype = C.c_int
+        L.orc_screen_routine.argtypes = [C.c_int, _I, _I, C.c_double, C.c_uint64, C.c_int, C.c_int,
+                                         C.c_double, _D]
+        L.orc_partition_pairwise.restype = C.c_int
+        L.orc_partition_pairwise.argtypes = [_D, C.c_int, C.c_double, C.c_int, _D, _I, _I, _I]
+        L.orc_partition_routine.restype = C.c_int
+        L.orc_partition_routine.argtypes = [_D, C.c_int, C.c_int, _I, C.c_double, C.c_int, _I, _I, _I]
+        if hasattr(L, "orc_mlp_forward"):
+            _bind_mlp(L)
+    return _lib
+
+
+def _bind_mlp(L):
+    L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.orc_mlp_backward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
+                                   _D, _D, _D, _D, _D, _D, _D]
+    L.orc_gelu.restype = C.c_double
+    L.orc_gelu.argtypes = [C.c_double]
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_I)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle status {code}")
+        self.code = code
+
+
+def _check(st):
+    if st != 0:
+        raise OracleError(st)
+
+
+# ------------------------------------------------------------------ wrappers
+def splitmix64(seed, stream, counter):
+    return int(lib().orc_splitmix64(seed, stream, counter))
+
+
+def uniform24(seed, stream, counter):
+    return float(lib().orc_uniform24(seed, stream, counter))
+
+
+def normal(seed, stream, counter):
+    return float(lib().orc_normal(seed, stream, counter))
+
+
+def uniform_points(seed, stream, count, d, first=0):
+    out = np.empty((count, d))
+    lib().orc_uniform_points(seed, stream, first, count, d, out.ctypes.data_as(_D))
+    return out
+
+
+def block_value(fn, x01):
+    x, px = _d(x01)
+    return float(lib().orc_block_value(fn, px, x.shape[-1]))
+
+
+def objective(block_dim, block_fn, x):
+    bd, pbd = _i(block_dim)
+    bf, pbf = _i(block_fn)
+    xx, px = _d(x)
+    fr = np.empty(len(bd))
+    ft = np.empty(1)
+    lib().orc_objective(len(bd), pbd, pbf, px, fr.ctypes.data_as(_D), ft.ctypes.data_as(_D))
+    return float(ft[0]), fr
+
+
+def matern52(r):
+    return float(lib().orc_matern52(float(r)))
+
+
+def kmat(X, ls, s2, sn2):
+    X, pX = _d(X)
+    n, d = X.shape
+    ls, pls = _d(np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,)))
+    K = np.empty((n, n))
+    lib().orc_kmat(pX, n, d, pls, s2, sn2, K.ctypes.data_as(_D))
+    return K
+
+
+def cholesky(K):
+    K, pK = _d(K)
+    n = K.shape[0]
+    Lm = np.empty((n, n))
+    _check(lib().orc_cholesky(pK, n, Lm.ctypes.data_as(_D)))
+    return Lm
+
+
+def forward(Lm, b):
+    Lm, pL = _d(Lm)
+    b, pb = _d(b)
+    x = np.empty_like(b)
+    lib().orc_forward(pL, Lm.shape[0], pb, x.ctypes.data_as(_D))
+    return x
+
+
+def backward_t(Lm, b):
+    Lm, pL = _d(Lm)
+    b, pb = _d(b)
+    x = np.empty_like(b)
+    lib().orc_backward_t(pL, Lm.shape[0], pb, x.ctypes.data_as(_D))
+    return x
+
+
+def tri_inverse(Lm):
+    Lm, pL = _d(Lm)
+    n = Lm.shape[0]
+    out = np.empty((n, n))
+    lib().orc_tri_inverse(pL, n, out.ctypes.data_as(_D))
+    return out
+
+
+def gp_fit(X, y, ls, s2, sn2):
+    X, pX = _d(X)
+    y, py = _d(y)
+    n, d = X.shape
+    ls, pls = _d(np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,)))
+    K = np.empty((n, n))
+    Lm = np.empty((n, n))
+    alpha = np.empty(n)
+    _check(lib().orc_gp_fit(pX, py, n, d, pls, s2, sn2, K.ctypes.data_as(_D), Lm.ctypes.data_as(_D),
+                            alpha.ctypes.data_as(_D)))
+    return K, Lm, alpha
+
+
+def posterior(X, ls, s2, Lm, alpha, Xc):
+    X, pX = _d(X)
+    n, d = X.shape
+    ls, pls = _d(np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,)))
+    Lm, pL = _d(Lm)
+    alpha, pa = _d(alpha)
+    Xc, pXc = _d(Xc)
+    M = Xc.shape[0]
+    mu = np.empty(M)
+    sg = np.empty(M)
+    lib().orc_posterior(pX, n, d, pls, s2, pL, pa, pXc, M, mu.ctypes.data_as(_D), sg.ctypes.data_as(_D))
+    return mu, sg
+
+
+def ei(mu, sigma, tau, xi=0.0):
+    return float(lib().orc_ei(mu, sigma, tau, xi))
+
+
+def ei_batch(mu, sigma, tau, xi=0.0):
+    mu, pm = _d(mu)
+    sg, ps = _d(sigma)
+    out = np.empty_like(mu)
+    lib().orc_ei_batch(pm, ps, mu.shape[0], tau, xi, out.ctypes.data_as(_D))
+    return out
+
+
+def argmax(v):
+    v, pv = _d(v)
+    return int(lib().orc_argmax(pv, v.shape[0]))
+
+
+def standardize(y):
+    y, py = _d(y)
+    ys = np.empty_like(y)
+    m = np.empty(1)
+    s = np.empty(1)
+    lib().orc_standardize(py, y.shape[0], ys.ctypes.data_as(_D), m.ctypes.data_as(_D), s.ctypes.data_as(_D))
+    return ys, float(m[0]), float(s[0])
+
+
+def search_step(X, y, ls, s2, sn2, M=None, seed=0, Xc=None, xi=0.0, want_arrays=False):
+    X, pX = _d(X)
+    y, py = _d(y)
+    n, d = X.shape
+    ls, pls = _d(np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,)))
+    if Xc is not None:
+        Xc, pXc = _d(Xc)
+        M = Xc.shape[0]
+    else:
+        pXc = C.cast(None, _D)
+    x_next = np.empty(d)
+    ei_max = np.empty(1)
+    am = np.empty(1, dtype=np.int64)
+    arrs = [np.empty(M) for _ in range(3)] if want_arrays else None
+    ptrs = [a.ctypes.data_as(_D) for a in arrs] if want_arrays else [C.cast(None, _D)] * 3
+    _check(lib().orc_search_step(pX, py, n, d, pls, s2, sn2, pXc, M, seed, xi, x_next.ctypes.data_as(_D),
+                                 ei_max.ctypes.data_as(_D), am.ctypes.data_as(_L), *ptrs))
+    out = {"x_next": x_next, "ei_max": float(ei_max[0]), "argmax": int(am[0])}
+    if want_arrays:
+        out.update(mu=arrs[0], sigma=arrs[1], ei=arrs[2])
+    return out
+
+
+def screen_pairwise(block_dim, block_fn, noise_sd, seed, n_base, h):
+    bd, pbd = _i(block_dim)
+    bf, pbf = _i(block_fn)
+    d = int(bd.sum())
+    score = np.empty((d, d))
+    sens = np.empty(d)
+    _check(lib().orc_screen_pairwise(len(bd), pbd, pbf, noise_sd, seed, d, n_base, h,
+                                     score.ctypes.data_as(_D), sens.ctypes.data_as(_D)))
+    return score, sens
+
+
+def screen_routine(block_dim, block_fn, noise_sd, seed, n_base, h):
+    bd, pbd = _i(block_dim)
+    bf, pbf = _i(block_fn)
+    d = int(bd.sum())
+    S = np.empty((len(bd), d))
+    _check(lib().orc_screen_routine(len(bd), pbd, pbf, noise_sd, seed, d, n_base, h, S.ctypes.data_as(_D)))
+    return S
+
+
+def partition_pairwise(score, cutoff, max_dims, influence):
+    score, ps = _d(score)
+    d = score.shape[0]
+    infl, pi = _d(influence)
+    g = np.empty(d, dtype=np.int32)
+    ng = np.empty(1, dtype=np.int32)
+    fx = np.empty(d, dtype=np.int32)
+    _check(lib().orc_partition_pairwise(ps, d, cutoff, max_dims, pi, g.ctypes.data_as(_I),
+                                        ng.ctypes.data_as(_I), fx.ctypes.data_as(_I)))
+    return g, int(ng[0]), fx
+
+
+def partition_routine(S, owner, cutoff, max_dims):
+    S, pS = _d(S)
+    R, d = S.shape
+    ow, pow_ = _i(owner)
+    g = np.empty(d, dtype=np.int32)
+    ng = np.empty(1, dtype=np.int32)
+    fx = np.empty(d, dtype=np.int32)
+    _check(lib().orc_partition_routine(pS, R, d, pow_, cutoff, max_dims, g.ctypes.data_as(_I),
+                                       ng.ctypes.data_as(_I), fx.ctypes.data_as(_I)))
+    return g, int(ng[0]), fx
+
+
+def block_owner(block_dim):
+    return np.repeat(np.arange(len(block_dim)), block_dim).astype(np.int32)

@@ -1,0 +1,302 @@
+"""Benchmark of the GP-BO hot path on one B300 (or N replicas under torchrun).
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+  * the pairwise interdependence screen of the 20-parameter five-block function
+    (190 pairs x 32 base points), its cut-off, merge and 10-parameter cap, and
+  * one BO iteration at n = 4096 observations, d = 20: standardise, FP64 fit
+    (kernel matrix, Cholesky, refined alpha, L^-1), cross-kernel + mean, variance on
+    tensor cores, EI and argmax over M = 2^20 candidates drawn on the device.
+Metric: EI candidates scored per second (M per step time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f16|bf16|f32] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_OBS, D, M_CAND = 4096, 20, 1 << 20
+METRIC = "EI candidates scored/sec at n=4096,d=20 (chosen vs plain, same B300, err<=2e-3)"
+UNIT = "candidates/s"
+WORKLOAD = ("one BO step: pairwise screen of the 20-D five-block Ackley/Rastrigin function (190 pairs x 32 bases) "
+            "+ GP fit n=4096 d=20 (FP64) + posterior/EI/argmax over M=2^20 device-drawn candidates")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2403_08131_b300 import gpbo, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gpbo.Context(local, stream)
+    w = W.config4(n=N_OBS, M=M_CAND, prec=args.prec)
+    sw = W.screen_config2()
+    o = sw.objective
+    seed = w.seed + 1000 * rank
+    Xd = torch.from_numpy(w.X).to(dev)
+    yd = torch.from_numpy(w.y).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(prec):
+        g = ctx.screen(o.block_dim, o.block_fn, o.noise_sd, sw.seed, sw.n_base, sw.h, sw.cutoff, sw.max_dims)
+        r = ctx.search_step(Xd, yd, w.lengthscale, 1.0, w.noise_var, M=M_CAND, seed=seed, prec=prec)
+        return g, r
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(prec, steps, warmup, trace=False):
+        for _ in range(warmup):
+            step(prec)
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        l0 = ctx.launches
+        if trace:
+            ctx.trace(True)
+        for i in range(steps):
+            flush.fill_(i & 0xFF)                     # evict L2 (256 MiB > 126 MB) between steps
+            ev[i][0].record(stream)
+            res = step(prec)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        tr = ctx.trace_read() if trace else None
+        if trace:
+            ctx.trace(False)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        return ms, ctx.launches - l0, tr, res
+
+    with ClockSampler(local) as clk:
+        ms, launches, tr, (g, r) = timed(args.prec, args.steps, args.warmup, trace=True)
+    clocks = clk.summary()
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * M_CAND * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    Xh = torch.from_numpy(w.X).pin_memory().numpy()
+    yh = torch.from_numpy(w.y).pin_memory().numpy()
+
+    def step_e2e():
+        ctx.screen(o.block_dim, o.block_fn, o.noise_sd, sw.seed, sw.n_base, sw.h, sw.cutoff, sw.max_dims)
+        return ctx.search_step(Xh, yh, w.lengthscale, 1.0, w.noise_var, M=M_CAND, seed=seed, prec=args.prec)
+
+    step_e2e()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize(dev)
+        step_e2e()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    h2d = w.X.nbytes + w.y.nbytes
+    d2h = D * 8 + 8 + 8 + (D * D + D) * 8 + 2 * D * 4 + 4
+
+    out = None
+    if rank == 0:
+        peaks, src = measured_peaks()
+        var = tr["variance"]
+        achieved = var["flops"] / (var["ms"] / 1e3) / 1e12 if var["ms"] > 0 else 0.0
+        peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
+        phases = {k: {"ms_per_step": v["ms"] / args.steps, "launch_groups": v["intervals"] // max(args.steps, 1),
+                      "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None}
+                  for k, v in tr.items()}
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f16": "f16", "bf16": "bf16", "f32": "f32"}[args.prec],
+            "data": "synthetic (seeded SplitMix64 draws; objectives evaluated in the input generator)",
+            "config": {"workload": WORKLOAD, "n": N_OBS, "d": D, "M": M_CAND, "variance_operands": args.prec,
+                       "accumulate": "f32 (tensor memory)" if args.prec != "f32" else "f32",
+                       "fit": "f64", "l2": "flushed between steps (256 MiB write)", "parallelism": f"replica x{world}"},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "tensor", "kernel": "k_var_ei_tc" if args.prec != "f32" else "k_var_simt",
+                         "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "peak_source": f"bf16_tflops_sustained ({src})",
+                         "flops_per_candidate": N_OBS * (N_OBS + 1), "traffic": None},
+            "phases": phases,
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "e2e": {"value": round(world * M_CAND * args.steps / e2e_s, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "result": {"argmax": r["argmax"], "ei_max": r["ei_max"], "n_groups": g["n_groups"]},
+        }
+        if not args.no_plain and args.prec != "f32":
+            pms, _, ptr, _ = timed("f32", 1, 1, trace=True)
+            out["plain"] = {"value": round(M_CAND / (pms / 1e3), 1), "unit": UNIT, "dtype": "f32",
+                            "ms_per_step": round(pms, 3),
+                            "variance_tflops": round(ptr["variance"]["flops"] / (ptr["variance"]["ms"] / 1e3) / 1e12, 3)}
+            out["speedup_vs_plain"] = round(out["value"] / out["plain"]["value"], 2)
+    ctx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------- oracle
+def oracle_sample(n_cand=1024):
+    """The FP64 oracle as it stands on this host: the fit at n=4096 plus a bounded
+    sample of candidates; returns (cand/s extrapolated to M=2^20 per step, detail)."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_2403_08131_b300 import workloads as W
+
+    w = W.config4(n=N_OBS, M=M_CAND)
+    t0 = time.perf_counter()
+    ys, _, _ = orc.standardize(w.y)
+    _, Lo, ao = orc.gp_fit(w.X, ys, w.lengthscale, 1.0, w.noise_var)
+    t_fit = time.perf_counter() - t0
+    Xc = w.candidates(n_cand).astype(np.float64)
+    t0 = time.perf_counter()
+    mu, sg = orc.posterior(w.X, w.lengthscale, 1.0, Lo, ao, Xc)
+    orc.argmax(orc.ei_batch(mu, sg, ys.min()))
+    t_c = (time.perf_counter() - t0) / n_cand
+    value = M_CAND / (t_fit + M_CAND * t_c)
+    return value, t_fit, t_c
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    total, vals = 0.0, []
+    for i in range(args.warmup + args.steps):
+        v, t_fit, t_c = oracle_sample()
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(M_CAND / value * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_OBS, "d": D, "M": M_CAND},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: FP64 fit at n=4096 + 1024 scored candidates; value = 2^20 / "
+                                       "(fit s + 2^20 x s per candidate); the screen (<0.1% of the step) is not timed"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        if world == 1 and not args.no_cpu:
+            v, t_fit, t_c = oracle_sample()
+            out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"FP64 oracle fit at n=4096 ({t_fit:.1f} s) + 1024 candidates "
+                                             f"({t_c * 1e3:.2f} ms each); value = 2^20 / (fit + 2^20 x per-candidate)"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * gpbo.h -- C ABI of libgpbo.so, the B300 (sm_103a) hot path of the GP-BO tuning loop
+ * in "Cost-Effective Methodology for Complex Tuning Searches in HPC" (arXiv 2403.08131).
+ *
+ * The paper runs Bayesian optimisation (a surrogate trained on the evaluated
+ * configurations, an acquisition function choosing the next one; §III-A) inside every
+ * independent or merged sub-search, after an interdependence analysis decides which
+ * routines' parameters are searched together (§IV-B..D).  This library computes, on one
+ * GPU, the step every sub-search repeats and the screen that forms the sub-searches:
+ *
+ *   gp_fit           Matern-5/2 ARD kernel matrix, FP64 Cholesky, refined alpha = K^-1 y,
+ *                    and the triangular inverse used to score candidates;
+ *   gp_posterior_ei  posterior mean and standard deviation of many candidates, expected
+ *                    improvement and its argmax, fused;
+ *   interdep_screen  pairwise or per-routine perturbation screen, cut-off, merge, 10-cap;
+ *   search_step      one BO iteration: standardise, fit, score, return the next point.
+ *
+ * Conventions for every call:
+ *   - Every function returns a gpbo_status; no C++ exception crosses the ABI.
+ *   - Outputs are left untouched when the status is not GPBO_OK.
+ *   - Array arguments are DEVICE pointers on the context's device unless `flags`
+ *     contains GPBO_HOST_PTRS, in which case they are host pointers and the call copies
+ *     them in and out itself.  Small per-call scalars and vectors named "host" below are
+ *     always host pointers.
+ *   - The caller owns every array it passes.  The library owns gpbo_ctx and gp_model.
+ *   - Work is ordered on the context's stream.  Calls that return host scalars
+ *     synchronise that stream before returning.
+ *   - One context per host thread; contexts are independent.
+ *   - Limits: 1 <= d <= 64, 1 <= n <= 16384, 1 <= M < 2^31.
+ *   - The library never falls back to the CPU; without a usable GPU, gpbo_create fails.
+ */
+#ifndef GPBO_H
+#define GPBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPBO_MAX_D 64
+#define GPBO_MAX_N 16384
+
+typedef struct gpbo_ctx gpbo_ctx; /* opaque: stream, workspace arena, device properties */
+typedef struct gp_model gp_model; /* opaque: device copies of X, L, L^-1, alpha, hyperparameters */
+
+typedef enum gpbo_status {
+    GPBO_OK = 0,
+    GPBO_EINVAL = 1,   /* bad size, null pointer, d or n out of range */
+    GPBO_ENOTSPD = 2,  /* a Cholesky pivot was not positive */
+    GPBO_ENAN = 3,     /* NaN or Inf in X, y or a candidate */
+    GPBO_ENOMEM = 4,   /* device allocation failed */
+    GPBO_ECUDA = 5,    /* a CUDA runtime call failed */
+    GPBO_ETIMEOUT = 6, /* a bounded device-side wait gave up; the kernel exited cleanly */
+    GPBO_ENOTSUP = 7   /* the device is not sm_103 or the request needs a missing feature */
+} gpbo_status;
+
+/* Scoring precision of the posterior variance (the fit is FP64 in every case).
+ *   F64  : all of the scoring in FP64 on CUDA cores.
+ *   F32  : cross-kernel and variance products in FP32 on CUDA cores.
+ *   BF16 : variance operands L^-1 and K* rounded to BF16, tcgen05 tensor cores with
+ *          FP32 accumulation in tensor memory; mean and EI in FP32 from FP32 K*.
+ *   F16  : as BF16 with IEEE half operands (same tensor rate, 3 more mantissa bits). */
+typedef enum gpbo_prec {
+    GPBO_PREC_F64 = 0,
+    GPBO_PREC_F32 = 1,
+    GPBO_PREC_BF16 = 2,
+    GPBO_PREC_F16 = 3
+} gpbo_prec;
+
+#define GPBO_HOST_PTRS 0x1u /* array arguments are host pointers (copied in/out by the call) */
+#define GPBO_JITTER 0x2u    /* on a failed Cholesky, retry with noise_var x10, at most 3 times */
+
+/* Fixed GP hyperparameters (the paper leaves the surrogate to GPTune; these are the
+ * Matern nu=5/2 ARD covariance's parameters, Rasmussen & Williams 2006 eq. 4.17):
+ *   k(a, b) = signal_var * m(r),  r^2 = sum_k ((a_k - b_k) / lengthscale[k])^2,
+ *   m(r) = (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r),
+ * plus noise_var on the diagonal of the training covariance.
+ * lengthscale: host array of d positive values. */
+typedef struct gp_hyper {
+    int d;
+    const double *lengthscale;
+    double signal_var;
+    double noise_var;
+} gp_hyper;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to order work
+ * on, or NULL for a stream the context creates and owns.  Fails with GPBO_ENOTSUP on a
+ * device that is not compute capability 10.3. */
+int gpbo_create(gpbo_ctx **out, int device, void *cuda_stream);
+int gpbo_destroy(gpbo_ctx *ctx);
+/* Re-target the context at another stream (NULL = its own). */
+int gpbo_set_stream(gpbo_ctx *ctx, void *cuda_stream);
+/* Static string for a status code. */
+const char *gpbo_strerror(int status);
+/* Kernels the context has launched since creation (for launch accounting). */
+int64_t gpbo_launch_count(const gpbo_ctx *ctx);
+/* Per-phase device timing with CUDA events recorded on the context's stream around each
+ * phase's kernels (phases: 0 fit, 1 cross-kernel + mean, 2 variance + EI + argmax,
+ * 3 screen).  gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
+ * gpbo_trace_read synchronises, then writes for each of the first nphase phases the total
+ * milliseconds, the number of timed intervals, and the algorithmic flops the phase's
+ * kernels were asked to do (variance: n(n+1) per candidate; cross-kernel: 3nd + 2n). */
+int gpbo_trace_enable(gpbo_ctx *ctx, int on);
+int gpbo_trace_read(gpbo_ctx *ctx, int nphase, double *ms, int64_t *intervals, double *flops);
+/* Upper bound, in bytes, of the scratch arena the context may grow to (default 2 GiB).
+ * Candidate scoring works through the pool in chunks that fit in this bound. */
+int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes);
+
+/* ------------------------------------------------------------------ fit (§III-A)
+ * Train the surrogate on n evaluated configurations (§III-A: the surrogate is trained
+ * on the configurations evaluated so far; §IV-D: GP training is O(N^3)).
+ *   X : n x d row-major FP64, the configurations scaled into [0,1]^d.
+ *   y : n FP64 objective values, used as given (zero prior mean).
+ * Computes K, L with K = L L^T in FP64, alpha = K^-1 y by FP64 blocked substitution
+ * with one refinement step r = y - K alpha, alpha += K^-1 r, and L^-1 in the scoring
+ * precision's working type (FP64 for F64, FP32 otherwise).
+ * flags: GPBO_HOST_PTRS, GPBO_JITTER.  On success *out owns the model; free it with
+ * gp_model_free.  GPBO_ENOTSPD when a pivot is not positive (after any jitter retries). */
+int gp_fit(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp,
+           gpbo_prec prec, unsigned flags, gp_model **out);
+int gp_model_free(gp_model *model);
+/* Shape and the noise variance actually used (differs from hyp->noise_var after jitter). */
+int gp_model_info(const gp_model *model, int *n, int *d, int *prec, double *noise_var_used);
+/* Copy the FP64 factor L (n x n row-major, zeros above the diagonal) or alpha (n) to host
+ * memory.  Either pointer may be NULL.  Synchronises. */
+int gp_model_read(const gp_model *model, double *L_host, double *alpha_host);
+
+/* ------------------------------------------------------------------ score (§III-A)
+ * Posterior of the latent objective at M candidates and expected improvement below the
+ * incumbent y_best (minimisation; Jones et al. 1998), fused with its argmax:
+ *   mu_c    = sum_i k(x_c, x_i) alpha_i
+ *   sigma_c = sqrt(max(signal_var - |L^-1 k_c|^2, 0))
+ *   EI_c    = (y_best - mu_c - xi) Phi(z) + sigma_c phi(z),  z = (y_best - mu_c - xi)/sigma_c,
+ *             and max(y_best - mu_c - xi, 0) where sigma_c = 0.
+ * Xc : M x d row-major FP32 candidates in [0,1]^d, or NULL to draw them on the device
+ *      from `seed` (SplitMix64 counter stream 2, 24-bit uniforms; gpbo_gen_candidates).
+ * mu, sigma, ei : M-element outputs, each may be NULL.  Element type is double for a
+ *      GPBO_PREC_F64 model and float otherwise.
+ * argmax, ei_max : host scalars, required.  Ties go to the lowest index.
+ * flags : GPBO_HOST_PTRS applies to Xc, mu, sigma and ei.  Synchronises. */
+int gp_posterior_ei(gpbo_ctx *ctx, const gp_model *model, const float *Xc, int64_t M, uint64_t seed,
+                    double y_best, double xi, unsigned flags, void *mu, void *sigma, void *ei,
+                    int64_t *argmax, double *ei_max);
+
+/* Candidate c, coordinate k = uniform24(seed, stream 2, (first + c) * d + k) for
+ * c < M, written as FP32 into the device array out (M x d).  SplitMix64 (Steele, Lea,
+ * Flood 2014), output number `counter` of the generator seeded with
+ * seed ^ (stream * 0x9E3779B97F4A7C15), top 24 bits scaled by 2^-24. */
+int gpbo_gen_candidates(gpbo_ctx *ctx, uint64_t seed, int64_t first, int64_t M, int d, float *out);
+
+/* ------------------------------------------------------------------ screen (§IV-B..D)
+ * Built-in synthetic objectives: additive blocks, block b owns the next block_dim[b]
+ * inputs, each mapped from [0,1] onto the function's usual domain (Ackley
+ * [-32.768, 32.768], Rastrigin [-5.12, 5.12], chained Rosenbrock [-2, 2]).  The block
+ * values are the "routine" outputs (§III-C: groups of a synthetic function stand for
+ * routines of an application).  Each evaluation adds noise_sd * N(0,1) from counter
+ * stream 4 of `seed` (Box-Muller).
+ * Host black box instead: set fn (non-NULL); it is called on the host with one point
+ * and must write f_total and, in ROUTINE mode, n_routines routine outputs; nonzero
+ * return = failed evaluation (the screen then fails with GPBO_EINVAL).  param_owner[i]
+ * (host, d entries) names the routine that owns parameter i in ROUTINE mode. */
+typedef enum gpbo_fn { GPBO_FN_ACKLEY = 0, GPBO_FN_RASTRIGIN = 1, GPBO_FN_ROSENBROCK = 2 } gpbo_fn;
+typedef int (*gpbo_host_fn)(const double *x, int d, double *f_total, double *f_routines, void *user);
+typedef struct gpbo_objective {
+    int n_blocks;
+    const int *block_dim;   /* host, n_blocks entries */
+    const int *block_fn;    /* host, n_blocks gpbo_fn codes */
+    double noise_sd;
+    uint64_t seed;
+    gpbo_host_fn fn;        /* NULL = built-in blocks */
+    int n_routines;         /* host black box only */
+    const int *param_owner; /* host black box only, ROUTINE mode */
+    void *user;
+} gpbo_objective;
+
+typedef enum gpbo_screen_mode { GPBO_SCREEN_PAIRWISE = 0, GPBO_SCREEN_ROUTINE = 1 } gpbo_screen_mode;
+/* n_base base points b_k = (1-h) u, u uniform in [0,1)^d (stream 3); step h along each axis.
+ * PAIRWISE: score_ij = mean_k |f(b+he_i+he_j) - f(b+he_i) - f(b+he_j) + f(b)|
+ *                      / (mean_k(|f(b+he_i) - f(b)| + |f(b+he_j) - f(b)|) + 1e-12),
+ *           edge i-j when score_ij > cutoff; influence_i = mean_k |f(b+he_i)-f(b)|/(|f(b)|+1e-12).
+ * ROUTINE:  score_gi = mean_k |(f_g(b_k) - f_g(b_k + h e_i)) / f_g(b_k)| (§IV-B's score with
+ *           V = n_base), routine g linked to the owner of parameter i when score_gi > cutoff
+ *           (§IV-C); influence_i = max_g score_gi.
+ * Linked parameters (PAIRWISE) or routines (ROUTINE) merge (union-find); a group's label is
+ * its smallest parameter index.  A group with more than max_dims members keeps its max_dims
+ * most influential ones and marks the rest fixed (§IV-D; max_dims <= 0 disables the cap).
+ * Noise counters: PAIRWISE evaluation e of base k uses k*E + e, E = 1 + d + d(d-1)/2, with
+ * e = 0 the base, 1+i the step along i, 1+d+p the double step of the p-th pair i<j in
+ * lexicographic order.  ROUTINE output g of evaluation e (0 base, 1+i step) uses
+ * (k*(1+d) + e)*R + g. */
+typedef struct screen_opts {
+    int mode;
+    int n_base;
+    double h;
+    double cutoff;
+    int max_dims;
+    uint64_t seed;
+} screen_opts;
+
+/* score: host, d x d (PAIRWISE) or R x d (ROUTINE; R = n_blocks or n_routines) FP64.
+ * influence, group_of, fixed: host, d entries each.  n_groups: host scalar.
+ * Any output may be NULL except group_of and n_groups.  Synchronises. */
+int interdep_screen(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opts *opts,
+                    double *score, double *influence, int *group_of, int *n_groups, int *fixed);
+
+/* ------------------------------------------------------------------ one BO step (§III-A)
+ * z-score y (population std, 1 when zero), fit on (X, y'), score the M candidates (Xc, or
+ * drawn from seed when Xc is NULL) with EI below tau = min y', and return the EI argmax:
+ * x_next (host, d doubles), ei_max (host, standardised units), argmax (host, may be NULL).
+ * flags: GPBO_HOST_PTRS applies to X, y and Xc.  Synchronises. */
+int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp,
+                const float *Xc, int64_t M, uint64_t seed, double xi, gpbo_prec prec, unsigned flags,
+                double *x_next, double *ei_max, int64_t *argmax);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPBO_H */

@@ -349,8 +349,8 @@ int orc_search_step(const double *X, const double *y, int n, int d, const double
 }
 
 /* ------------------------------------------------------------------ screens
- * Base points b_k: uniform in [0, 0.9]^d (stream 3), b_k,t = 0.9 * u(k*d + t), so that
- * b + h e_i + h e_j stays in the unit box for h = 0.1.
+ * Base points b_k: b_k,t = (1 - h) * u(k*d + t) with u uniform on stream 3, so that
+ * b + h e_i + h e_j stays in the unit box.
  * Pairwise evaluation e of base k: e = 0 base; e = 1+i single step along i;
  * e = 1+d+p(i,j) double step along i and j (p = lexicographic pair index, i<j).
  * Noise (stream 4): total f of evaluation e at base k adds noise_sd * N(counter k*E + e),
@@ -380,7 +380,7 @@ int orc_screen_pairwise(int nb, const int *bdim, const int *bfn, double noise_sd
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < n_base; ++k) {
         double b[64], x[64];
-        for (int t = 0; t < d; ++t) b[t] = 0.9 * orc_uniform24(seed, 3, (uint64_t)k * d + t);
+        for (int t = 0; t < d; ++t) b[t] = (1.0 - h) * orc_uniform24(seed, 3, (uint64_t)k * d + t);
         for (int64_t e = 0; e < E; ++e) {
             int i = -1, j = -1;
             if (e >= 1 && e <= d) i = (int)e - 1;
@@ -439,7 +439,7 @@ int orc_screen_routine(int nb, const int *bdim, const int *bfn, double noise_sd,
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < n_base; ++k) {
         double b[64], x[64];
-        for (int t = 0; t < d; ++t) b[t] = 0.9 * orc_uniform24(seed, 3, (uint64_t)k * d + t);
+        for (int t = 0; t < d; ++t) b[t] = (1.0 - h) * orc_uniform24(seed, 3, (uint64_t)k * d + t);
         for (int e = 0; e < E; ++e) {
             screen_point(b, d, e - 1, -1, h, x);
             double *fr = fv + ((size_t)k * E + e) * R;

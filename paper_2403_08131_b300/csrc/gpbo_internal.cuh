@@ -1,0 +1,202 @@
+// Internal declarations shared by the CUDA sources of libgpbo.so.
+// Nothing here is part of the public ABI (include/gpbo.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <cstdio>
+
+#include "../../include/gpbo.h"
+
+namespace gpbo {
+
+// Block size of the FP64 factorisation and of the padded square layouts.
+constexpr int NB = 64;
+// The tensor-core variance kernel works on L^-1 in row chunks of this many outputs,
+// so tensor-core models pad n to a multiple of it.
+constexpr int TC_NCHUNK = 256;
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+inline int64_t round_up64(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+void note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+#define GPBO_CUDA_TRY(expr)                                                    \
+    do {                                                                       \
+        cudaError_t e_ = (expr);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            gpbo::note_cuda_error(e_, #expr, __FILE__, __LINE__);              \
+            return e_ == cudaErrorMemoryAllocation ? GPBO_ENOMEM : GPBO_ECUDA; \
+        }                                                                      \
+    } while (0)
+
+#define GPBO_LAUNCH_CHECK(ctx)                                            \
+    do {                                                                  \
+        (ctx)->launches++;                                                \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) {                                          \
+            gpbo::note_cuda_error(e_, "kernel launch", __FILE__, __LINE__); \
+            return GPBO_ECUDA;                                            \
+        }                                                                 \
+    } while (0)
+
+#define GPBO_TRY(expr)                \
+    do {                              \
+        int s_ = (expr);              \
+        if (s_ != GPBO_OK) return s_; \
+    } while (0)
+
+// Device-side error word bits (gpbo_ctx::dev_status).
+enum : unsigned {
+    DEV_NOTSPD = 1u,
+    DEV_TIMEOUT = 2u,
+    DEV_NAN = 4u,
+};
+
+}  // namespace gpbo
+
+namespace gpbo {
+constexpr int TRACE_PHASES = 4;
+enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3 };
+struct TraceRec {
+    int phase;
+    cudaEvent_t a, b;
+    double flops;
+};
+}  // namespace gpbo
+
+struct gpbo_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t launches = 0;
+    int64_t ws_limit = (int64_t)2 << 30;
+    void *ws = nullptr;              // grow-only scratch arena
+    size_t ws_size = 0;
+    unsigned *dev_status = nullptr;  // device error word (cleared by each call)
+    void *pinned = nullptr;          // small pinned host staging buffer
+    bool trace = false;              // per-phase event timing (gpbo_trace_enable)
+    gpbo::TraceRec *trace_recs = nullptr;
+    int trace_n = 0, trace_cap = 0;
+};
+
+struct gp_model {
+    gpbo_ctx *ctx = nullptr;
+    int n = 0, d = 0, n_pad = 0;
+    int prec = GPBO_PREC_F64;
+    double s2 = 1.0, sn2 = 0.0;
+    double ls[GPBO_MAX_D];
+    // device buffers (n_pad x n_pad squares are row-major; padding rows/cols hold the
+    // identity on the diagonal of K and L and zero elsewhere)
+    double *X = nullptr;        // n x d FP64 as given
+    double *Xs64 = nullptr;     // d x n_pad FP64, x / l, zero padding
+    float *Xs32 = nullptr;      // d x n_pad FP32, x / l
+    double *K = nullptr;        // n_pad x n_pad kernel matrix (kept for the refinement residual)
+    double *L = nullptr;        // n_pad x n_pad factor, lower
+    double *Dinv = nullptr;     // n_pad/NB blocks of NB x NB: inverses of L's diagonal blocks
+    double *alpha64 = nullptr;  // n_pad, zero padding
+    float *alpha32 = nullptr;   // n_pad
+    double *Linv64 = nullptr;   // F64 scoring: L^-1
+    float *Linv32 = nullptr;    // F32 and tensor-core scoring: L^-1 in FP32
+    void *Linv16 = nullptr;     // BF16/F16 scoring: L^-1 rounded to the operand type
+};
+
+namespace gpbo {
+
+// capi.cu
+int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out);
+// Open / close a timed interval of `phase` on the context's stream (no-ops unless tracing).
+int trace_begin(gpbo_ctx *ctx, int phase, double flops);
+int trace_end(gpbo_ctx *ctx);
+int take_device_status(gpbo_ctx *ctx, unsigned *bits_out);
+
+// fit.cu
+int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_dev);
+int standardize_dev(gpbo_ctx *ctx, const double *y, int n, double *ys, double *tau_dev);
+
+// score.cu
+int score_model(gpbo_ctx *ctx, const gp_model *m, const float *Xc_dev, int64_t M, uint64_t seed,
+                double y_best, const double *tau_dev, double xi, void *mu, void *sigma, void *ei,
+                int64_t *argmax, double *ei_max);
+int gen_candidates(gpbo_ctx *ctx, uint64_t seed, int64_t first, int64_t M, int d, float *out);
+
+// score_tc.cu: one chunk of C candidates whose K* (C x n_pad, 16-bit) and mu are ready.
+int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t C, int64_t c0,
+                   const float *mu, double y_best, const double *tau_dev, double xi, float *sigma_out,
+                   float *ei_out, float *part_ei, int64_t *part_idx, int *n_parts);
+
+// screen.cu
+int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opts *o, double *score,
+               double *influence, int *group_of, int *n_groups, int *fixed);
+
+// 1 / lengthscale per dimension, passed by value to kernels.
+struct Lengthscales_inv {
+    double inv[GPBO_MAX_D];
+};
+
+// ------------------------------------------------------------------ device helpers
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t stream, uint64_t counter)
+{
+    // SplitMix64 output number `counter` of the generator seeded with seed ^ stream*gamma.
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    uint64_t z = (seed ^ (stream * gamma)) + (counter + 1ull) * gamma;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline float uniform24f(uint64_t seed, uint64_t stream, uint64_t counter)
+{
+    return (float)(splitmix64(seed, stream, counter) >> 40) * (1.0f / 16777216.0f);
+}
+
+__host__ __device__ inline double uniform24d(uint64_t seed, uint64_t stream, uint64_t counter)
+{
+    return (double)(splitmix64(seed, stream, counter) >> 40) * (1.0 / 16777216.0);
+}
+
+constexpr double SQRT5 = 2.23606797749978969641;
+
+// Matern nu=5/2 shape (1 + sqrt5 r + 5 r^2/3) exp(-sqrt5 r), from the squared distance.
+__device__ __forceinline__ double matern52_r2(double r2)
+{
+    double r = sqrt(r2);
+    double t = SQRT5 * r;
+    return (1.0 + t + (5.0 / 3.0) * r2) * exp(-t);
+}
+
+__device__ __forceinline__ float matern52_r2f(float r2)
+{
+    float r = sqrtf(r2);
+    float t = 2.2360680f * r;
+    return (1.0f + t + 1.6666666f * r2) * __expf(-t);
+}
+
+// Expected improvement below tau for minimisation (Jones, Schonlau, Welch 1998).
+__device__ __forceinline__ double ei_min(double mu, double sigma, double tau, double xi)
+{
+    double imp = tau - mu - xi;
+    if (!(sigma > 0.0)) return imp > 0.0 ? imp : 0.0;
+    double z = imp / sigma;
+    return imp * (0.5 * erfc(-z * 0.70710678118654752440)) + sigma * (0.39894228040143267794 * exp(-0.5 * z * z));
+}
+
+__device__ __forceinline__ float ei_minf(float mu, float sigma, float tau, float xi)
+{
+    float imp = tau - mu - xi;
+    if (!(sigma > 0.0f)) return imp > 0.0f ? imp : 0.0f;
+    float z = imp / sigma;
+    return imp * (0.5f * erfcf(-z * 0.70710678f)) + sigma * (0.39894228f * expf(-0.5f * z * z));
+}
+
+// Argmax tie rule: larger value wins, then the lower index.
+template <typename T>
+__device__ __forceinline__ bool better(T v, int64_t i, T bv, int64_t bi)
+{
+    return v > bv || (v == bv && i < bi);
+}
+
+}  // namespace gpbo

@@ -1,0 +1,437 @@
+// Posterior variance, EI and argmax on the 5th-generation tensor cores (tcgen05).
+//
+// For a chunk of C candidates whose cross-kernel rows K* (C x n_pad, BF16 or FP16,
+// observation index contiguous) and means are ready, computes
+//     V = K* (L^-1)^T             (C x n_pad; only the lower triangle of L^-1 is read)
+//     sigma_c^2 = s2 - sum_i V_ci^2,  EI_c, and the chunk's (EI, index) winners.
+// This is the triangular solve v = L^-1 k* of the GP posterior variance (Rasmussen &
+// Williams 2006, Alg. 2.1) written as a GEMM with many right-hand sides, so that it is a
+// dense contraction and belongs on the tensor cores.
+//
+// Kernel shape (one CTA per SM, persistent over 128-candidate tiles):
+//   warp 0      TMA producer: K* tile (128 x 64) and L^-1 tile (256 x 64) per stage,
+//               128-byte swizzle, 4 stages of 48 KiB in shared memory
+//   warp 1      allocates 512 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
+//               K=16, FP32 accumulate) into one of two 256-column accumulators
+//   warps 2..5  epilogue: tcgen05.ld the accumulator, square and sum into the candidate's
+//               running |v|^2 (one TMEM lane = one candidate = one thread), then sigma,
+//               EI and the per-CTA argmax
+// For output chunk q (L^-1 rows 256q .. 256q+255) only K columns < 256(q+1) are read:
+// the triangle's zero blocks are never loaded or multiplied.
+//
+// Every mbarrier wait is bounded (about 2 s of SM clock).  On timeout the kernel sets
+// DEV_TIMEOUT in the context's status word, every role leaves its loop, the producer
+// waits (bounded) for copies it issued, the MMA issuer drains its MMAs, and the
+// allocating warp frees TMEM before the CTA exits.
+#include "gpbo_internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+namespace gpbo {
+
+namespace tc {
+
+constexpr int BM = 128;        // candidates per tile (MMA M, TMEM lanes)
+constexpr int BN = TC_NCHUNK;  // L^-1 rows per output chunk (MMA N)
+constexpr int BK = 64;         // K elements per stage (128 bytes of 16-bit values)
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 512;
+constexpr long long TIMEOUT_CYCLES = 4000000000ll;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+struct Shared {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float best_v[4];
+    int64_t best_i[4];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Gives up (returning false) when another role has aborted, or after
+// TIMEOUT_CYCLES, in which case it raises the abort flag and the device status bit.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *status,
+                                       bool honour_abort = true)
+{
+    long long t0 = clock64();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (honour_abort && *abort_flag) return false;
+            if (clock64() - t0 > TIMEOUT_CYCLES) {
+                *abort_flag = 1;
+                atomicOr(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with 128-byte
+// swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc(const void *p)
+{
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;          // start address
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A/B format (0 = F16, 1 = BF16),
+// both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct Params {
+    int64_t C;        // candidates in this chunk
+    int64_t c0;       // pool index of the chunk's first candidate
+    int n_pad;
+    int num_tiles;
+    float s2;
+    float xi;
+    double y_best;
+    const double *tau_dev;
+    const float *mu;  // pool-indexed
+    float *sigma_out; // pool-indexed, may be null
+    float *ei_out;    // pool-indexed, may be null
+    float *part_ei;   // one per CTA
+    int64_t *part_idx;
+    unsigned *status;
+    uint32_t idesc;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_var_ei_tc(const __grid_constant__ CUtensorMap map_k, const __grid_constant__ CUtensorMap map_l, Params P)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char *tiles = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    Shared *sh = (Shared *)(tiles + (size_t)STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nq = P.n_pad / BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sh->acc_full[a], 1);
+            mbar_init(&sh->acc_empty[a], 4);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort_flag = &sh->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_k) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];
+            uint32_t armed_par[STAGES];
+            for (int s = 0; s < STAGES; ++s) armed[s] = 0, armed_par[s] = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+                for (int q = 0; ok && q < nq; ++q) {
+                    const int ksteps = (q + 1) * (BN / BK);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                        unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
+                        unsigned char *b = a + A_BYTES;
+                        mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
+                        armed[stage] = 1;
+                        armed_par[stage] = phase;
+                        tma_load_2d(a, &map_k, ks * BK, t * BM, &sh->full[stage]);
+                        tma_load_2d(b, &map_l, ks * BK, q * BN, &sh->full[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
+            // leave no copy in flight: wait for the last arming of every stage
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s]) mbar_wait(&sh->full[s], armed_par[s], abort_flag, P.status, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+                for (int q = 0; ok && q < nq; ++q) {
+                    if (!mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+                    const int ksteps = (q + 1) * (BN / BK);
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        tc_fence_after();
+                        const unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
+                        const unsigned char *b = a + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_f16(d_tmem, smem_desc(a + kk * 32), smem_desc(b + kk * 32), P.idesc,
+                                    (ks > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(&sh->empty[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&sh->acc_full[acc]);
+                    if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+                }
+            }
+            // drain every MMA this thread issued before TMEM is released
+            mma_commit(&sh->drain);
+            mbar_wait(&sh->drain, 0, abort_flag, P.status, false);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        const float tau = P.tau_dev ? (float)*P.tau_dev : (float)P.y_best;
+        float best_v = -1.0f;
+        int64_t best_i = INT64_MAX;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+            float ss = 0.0f;
+            for (int q = 0; q < nq; ++q) {
+                // every lane waits; the warp leaves together so tcgen05.ld stays warp-uniform
+                const bool got = mbar_wait(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
+                if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll 1
+                for (int cb = 0; cb < BN / 32; ++cb) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_addr + (uint32_t)(acc * BN + cb * 32), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) ss = fmaf(v[j], v[j], ss);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
+                if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+            }
+            if (!ok) break;
+            const int64_t cl = (int64_t)t * BM + row;
+            if (cl < P.C) {
+                const int64_t c = P.c0 + cl;
+                const float var = P.s2 - ss;
+                const float sg = var > 0.0f ? sqrtf(var) : 0.0f;
+                const float e = ei_minf(P.mu[c], sg, tau, P.xi);
+                if (P.sigma_out) P.sigma_out[c] = sg;
+                if (P.ei_out) P.ei_out[c] = e;
+                if (better(e, c, best_v, best_i)) { best_v = e; best_i = c; }
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            float ov = __shfl_xor_sync(0xffffffffu, best_v, o);
+            int64_t oi = __shfl_xor_sync(0xffffffffu, best_i, o);
+            if (better(ov, oi, best_v, best_i)) { best_v = ov; best_i = oi; }
+        }
+        if (lane == 0) {
+            sh->best_v[warp - 2] = best_v;
+            sh->best_i[warp - 2] = best_i;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x == 0) {
+        float bv = sh->best_v[0];
+        int64_t bi = sh->best_i[0];
+        for (int w = 1; w < 4; ++w)
+            if (better(sh->best_v[w], sh->best_i[w], bv, bi)) { bv = sh->best_v[w]; bi = sh->best_i[w]; }
+        P.part_ei[blockIdx.x] = bv;
+        P.part_idx[blockIdx.x] = bi;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace tc
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder()
+{
+    if (g_encode) return GPBO_OK;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    GPBO_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return GPBO_ENOTSUP;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return GPBO_OK;
+}
+
+// 2-D row-major 16-bit matrix (rows x cols, cols contiguous), box = box_rows x 64 cols.
+static int encode_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t rows, uint64_t cols,
+                     uint32_t box_rows)
+{
+    GPBO_TRY(get_encoder());
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(map, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        fprintf(stderr, "gpbo: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
+        return GPBO_ECUDA;
+    }
+    return GPBO_OK;
+}
+
+int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t C, int64_t c0, const float *mu,
+                   double y_best, const double *tau_dev, double xi, float *sigma_out, float *ei_out, float *part_ei,
+                   int64_t *part_idx, int *n_parts)
+{
+    if (m->n_pad % tc::BN != 0 || C <= 0 || C > 0x7fffffffll) return GPBO_EINVAL;
+    if (((uintptr_t)Kstar & 15) || ((uintptr_t)m->Linv16 & 15)) return GPBO_EINVAL;
+    const CUtensorMapDataType dt =
+        m->prec == GPBO_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUtensorMap mk, ml;
+    GPBO_TRY(encode_2d(&mk, dt, Kstar, (uint64_t)C, (uint64_t)m->n_pad, tc::BM));
+    GPBO_TRY(encode_2d(&ml, dt, m->Linv16, (uint64_t)m->n_pad, (uint64_t)m->n_pad, tc::BN));
+    static bool attr = false;
+    if (!attr) {
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(tc::k_var_ei_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc::SMEM_BYTES));
+        attr = true;
+    }
+    tc::Params P;
+    P.C = C;
+    P.c0 = c0;
+    P.n_pad = m->n_pad;
+    P.num_tiles = (int)cdiv64(C, tc::BM);
+    P.s2 = (float)m->s2;
+    P.xi = (float)xi;
+    P.y_best = y_best;
+    P.tau_dev = tau_dev;
+    P.mu = mu;
+    P.sigma_out = sigma_out;
+    P.ei_out = ei_out;
+    P.part_ei = part_ei;
+    P.part_idx = part_idx;
+    P.status = ctx->dev_status;
+    P.idesc = tc::instr_desc(m->prec == GPBO_PREC_BF16 ? 1u : 0u);
+    const int grid = std::min(P.num_tiles, ctx->sm_count);
+    tc::k_var_ei_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, ctx->stream>>>(mk, ml, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    *n_parts = grid;
+    return GPBO_OK;
+}
+
+}  // namespace gpbo

@@ -1,0 +1,296 @@
+"""Python binding of libgpbo.so (include/gpbo.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  PyTorch provides device
+buffers and the stream; numpy arrays are passed as host buffers with GPBO_HOST_PTRS.
+Importing this module fails loudly when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpbo.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2403_08131_b300.build`")
+
+_lib = C.CDLL(LIB_PATH)
+
+GPBO_OK, GPBO_EINVAL, GPBO_ENOTSPD, GPBO_ENAN, GPBO_ENOMEM, GPBO_ECUDA, GPBO_ETIMEOUT, GPBO_ENOTSUP = range(8)
+PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+HOST_PTRS = 0x1
+JITTER = 0x2
+SCREEN_PAIRWISE, SCREEN_ROUTINE = 0, 1
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_L = C.POINTER(C.c_int64)
+
+
+class GpHyper(C.Structure):
+    _fields_ = [("d", C.c_int), ("lengthscale", _D), ("signal_var", C.c_double), ("noise_var", C.c_double)]
+
+
+HOST_FN = C.CFUNCTYPE(C.c_int, _D, C.c_int, _D, _D, C.c_void_p)
+
+
+class GpboObjective(C.Structure):
+    _fields_ = [("n_blocks", C.c_int), ("block_dim", _I), ("block_fn", _I), ("noise_sd", C.c_double),
+                ("seed", C.c_uint64), ("fn", HOST_FN), ("n_routines", C.c_int), ("param_owner", _I),
+                ("user", C.c_void_p)]
+
+
+class ScreenOpts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("n_base", C.c_int), ("h", C.c_double), ("cutoff", C.c_double),
+                ("max_dims", C.c_int), ("seed", C.c_uint64)]
+
+
+def _sig(name, restype, argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    return f
+
+
+_create = _sig("gpbo_create", C.c_int, [C.POINTER(_P), C.c_int, _P])
+_destroy = _sig("gpbo_destroy", C.c_int, [_P])
+_set_stream = _sig("gpbo_set_stream", C.c_int, [_P, _P])
+_strerror = _sig("gpbo_strerror", C.c_char_p, [C.c_int])
+_launches = _sig("gpbo_launch_count", C.c_int64, [_P])
+_ws_limit = _sig("gpbo_set_workspace_limit", C.c_int, [_P, C.c_int64])
+_trace_en = _sig("gpbo_trace_enable", C.c_int, [_P, C.c_int])
+_trace_rd = _sig("gpbo_trace_read", C.c_int, [_P, C.c_int, _D, _L, _D])
+PHASES = ("fit", "xkern", "variance", "screen")
+_fit = _sig("gp_fit", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_int, C.c_uint,
+                                 C.POINTER(_P)])
+_model_free = _sig("gp_model_free", C.c_int, [_P])
+_model_info = _sig("gp_model_info", C.c_int, [_P, _I, _I, _I, _D])
+_model_read = _sig("gp_model_read", C.c_int, [_P, _P, _P])
+_posterior = _sig("gp_posterior_ei", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double, C.c_double, C.c_uint,
+                                               _P, _P, _P, _L, _D])
+_gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
+_screen = _sig("interdep_screen", C.c_int, [_P, C.POINTER(GpboObjective), C.c_int, C.POINTER(ScreenOpts), _P, _P,
+                                             _P, _I, _P])
+_step = _sig("search_step", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), _P, C.c_int64, C.c_uint64,
+                                       C.c_double, C.c_int, C.c_uint, _P, _D, _L])
+
+
+class GpboError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {_strerror(code).decode()} ({code})")
+
+
+def check(code, where=""):
+    if code != GPBO_OK:
+        raise GpboError(code, where)
+
+
+def strerror(code):
+    return _strerror(code).decode()
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _is_host(a):
+    return a is None or isinstance(a, np.ndarray)
+
+
+def _hyper(lengthscale, signal_var, noise_var):
+    ls = np.ascontiguousarray(lengthscale, dtype=np.float64)
+    h = GpHyper(len(ls), ls.ctypes.data_as(_D), float(signal_var), float(noise_var))
+    return h, ls
+
+
+class Context:
+    """A gpbo_ctx on one device, ordered on `stream` (a torch.cuda.Stream, a raw
+    cudaStream_t as int, or None for a stream the library owns)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = _P()
+        check(_create(C.byref(self._h), device, _stream_handle(stream)), "gpbo_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            _destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        check(_set_stream(self._h, _stream_handle(stream)), "gpbo_set_stream")
+
+    def set_workspace_limit(self, nbytes: int):
+        check(_ws_limit(self._h, int(nbytes)), "gpbo_set_workspace_limit")
+
+    @property
+    def launches(self) -> int:
+        return int(_launches(self._h))
+
+    def trace(self, on: bool):
+        """Start (clearing) or stop per-phase CUDA-event timing on the context's stream."""
+        check(_trace_en(self._h, 1 if on else 0), "gpbo_trace_enable")
+
+    def trace_read(self):
+        n = len(PHASES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        fl = (C.c_double * n)()
+        check(_trace_rd(self._h, n, ms, cnt, fl), "gpbo_trace_read")
+        return {p: {"ms": ms[i], "intervals": int(cnt[i]), "flops": fl[i]} for i, p in enumerate(PHASES)}
+
+    # ------------------------------------------------------------ fit / score
+    def fit(self, X, y, lengthscale, signal_var, noise_var, prec="f64", jitter=False):
+        """X (n x d) and y (n): both torch float64 CUDA tensors, or both numpy arrays."""
+        host = _is_host(X)
+        if host:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        n, d = X.shape
+        h, keep = _hyper(lengthscale, signal_var, noise_var)
+        flags = (HOST_PTRS if host else 0) | (JITTER if jitter else 0)
+        out = _P()
+        check(_fit(self._h, _ptr(X), _ptr(y), n, d, C.byref(h), PREC[prec], flags, C.byref(out)), "gp_fit")
+        return Model(self, out, prec)
+
+    def posterior_ei(self, model, Xc=None, M=None, seed=0, y_best=0.0, xi=0.0, mu=None, sigma=None, ei=None):
+        """Xc: M x d float32 torch CUDA tensor / numpy array, or None with M and seed.
+        mu/sigma/ei: preallocated outputs of the same kind (or None).  Returns (argmax, ei_max)."""
+        host = Xc is not None and _is_host(Xc) or any(isinstance(a, np.ndarray) for a in (mu, sigma, ei))
+        if Xc is not None:
+            if isinstance(Xc, np.ndarray):
+                Xc = np.ascontiguousarray(Xc, dtype=np.float32)
+            M = Xc.shape[0]
+        am = C.c_int64(-1)
+        em = C.c_double(0.0)
+        check(_posterior(self._h, model._h, _ptr(Xc), int(M), int(seed), float(y_best), float(xi),
+                         HOST_PTRS if host else 0, _ptr(mu), _ptr(sigma), _ptr(ei), C.byref(am), C.byref(em)),
+              "gp_posterior_ei")
+        return int(am.value), float(em.value)
+
+    def gen_candidates(self, out, seed, first=0):
+        M, d = out.shape
+        check(_gen(self._h, int(seed), int(first), int(M), int(d), _ptr(out)), "gpbo_gen_candidates")
+        return out
+
+    def search_step(self, X, y, lengthscale, signal_var, noise_var, Xc=None, M=None, seed=0, xi=0.0, prec="f64",
+                    jitter=False):
+        host = _is_host(X)
+        if host:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            if Xc is not None:
+                Xc = np.ascontiguousarray(Xc, dtype=np.float32)
+        n, d = X.shape
+        if Xc is not None:
+            M = Xc.shape[0]
+        h, keep = _hyper(lengthscale, signal_var, noise_var)
+        x_next = np.empty(d)
+        em = C.c_double(0.0)
+        am = C.c_int64(-1)
+        flags = (HOST_PTRS if host else 0) | (JITTER if jitter else 0)
+        check(_step(self._h, _ptr(X), _ptr(y), n, d, C.byref(h), _ptr(Xc), int(M), int(seed), float(xi), PREC[prec],
+                    flags, x_next.ctypes.data, C.byref(em), C.byref(am)), "search_step")
+        return {"x_next": x_next, "ei_max": float(em.value), "argmax": int(am.value)}
+
+    # ------------------------------------------------------------ screen
+    def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,
+               max_dims=10, mode=SCREEN_PAIRWISE, host_fn=None, d=None, n_routines=0, param_owner=None):
+        """Built-in block objective (block_dim, block_fn) or a host black box
+        host_fn(x: np.ndarray) -> (f_total, routines) with d / n_routines / param_owner."""
+        keep = []
+        if host_fn is None:
+            bd = np.ascontiguousarray(block_dim, dtype=np.int32)
+            bf = np.ascontiguousarray(block_fn, dtype=np.int32)
+            keep += [bd, bf]
+            d = int(bd.sum())
+            obj = GpboObjective(len(bd), bd.ctypes.data_as(_I), bf.ctypes.data_as(_I), float(noise_sd), int(seed),
+                                HOST_FN(), 0, C.cast(None, _I), None)
+            R = len(bd)
+        else:
+            def tramp(xp, dd, ft, fr, user):
+                try:
+                    x = np.ctypeslib.as_array(xp, shape=(dd,)).copy()
+                    tot, rout = host_fn(x)
+                    ft[0] = float(tot)
+                    for g in range(n_routines):
+                        fr[g] = float(rout[g])
+                    return 0
+                except Exception:
+                    return 1
+            cb = HOST_FN(tramp)
+            keep.append(cb)
+            ow = np.ascontiguousarray(param_owner if param_owner is not None else np.zeros(d), dtype=np.int32)
+            keep.append(ow)
+            obj = GpboObjective(0, C.cast(None, _I), C.cast(None, _I), 0.0, int(seed), cb, int(n_routines),
+                                ow.ctypes.data_as(_I), None)
+            R = n_routines
+        opts = ScreenOpts(int(mode), int(n_base), float(h), float(cutoff), int(max_dims), int(seed))
+        rows = d if mode == SCREEN_PAIRWISE else R
+        score = np.zeros((rows, d))
+        infl = np.zeros(d)
+        group = np.zeros(d, dtype=np.int32)
+        fixed = np.zeros(d, dtype=np.int32)
+        ng = C.c_int(0)
+        check(_screen(self._h, C.byref(obj), d, C.byref(opts), score.ctypes.data, infl.ctypes.data,
+                      group.ctypes.data, C.byref(ng), fixed.ctypes.data), "interdep_screen")
+        return {"score": score, "influence": infl, "group_of": group, "n_groups": int(ng.value), "fixed": fixed}
+
+
+class Model:
+    def __init__(self, ctx, handle, prec):
+        self.ctx = ctx
+        self._h = handle
+        self.prec = prec
+
+    def free(self):
+        if self._h:
+            _model_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self):
+        n, d, p = C.c_int(), C.c_int(), C.c_int()
+        sn2 = C.c_double()
+        check(_model_info(self._h, C.byref(n), C.byref(d), C.byref(p), C.byref(sn2)), "gp_model_info")
+        return {"n": n.value, "d": d.value, "prec": p.value, "noise_var": sn2.value}
+
+    def read(self):
+        inf = self.info()
+        n = inf["n"]
+        Lm = np.empty((n, n))
+        alpha = np.empty(n)
+        check(_model_read(self._h, Lm.ctypes.data, alpha.ctypes.data), "gp_model_read")
+        return Lm, alpha
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream

@@ -18,3 +18,16 @@ def orc():
     from oracle import oracle
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_08131_b300 import build
+    build.build()
+    from paper_2403_08131_b300 import gpbo
+    c = gpbo.Context(0, torch.cuda.current_stream())
+    yield c
+    c.close()

@@ -1,0 +1,66 @@
+"""GPU fit (kernel matrix, FP64 Cholesky, refined alpha) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2403_08131_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _obs(n, d, seed):
+    X = W.uniform_points(seed, W.STREAM_OBS, n, d)
+    obj = W.Objective([d], [W.FN_ACKLEY], 0.0, seed)
+    y = obj(X)
+    return X, (y - y.mean()) / (y.std() or 1.0)
+
+
+@pytest.mark.parametrize("n,d", [(1, 3), (3, 2), (64, 4), (100, 20), (257, 7), (513, 20)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_fit_factor_and_alpha_match_oracle(ctx, orc, n, d, prec):
+    from tests._util import to_dev
+    X, y = _obs(n, d, 1000 + n)
+    ls = W.lengthscale_rule(d)
+    m = ctx.fit(to_dev(X), to_dev(y), ls, 1.0, 1e-4, prec=prec)
+    Lg, ag = m.read()
+    _, Lo, ao = orc.gp_fit(X, y, ls, 1.0, 1e-4)
+    assert np.abs(Lg - Lo).max() <= 1e-11 * np.abs(Lo).max()
+    assert np.abs(ag - ao).max() <= 1e-9 * (np.abs(ao).max() + 1)
+    assert np.all(np.triu(Lg, 1) == 0)
+    m.free()
+
+
+def test_fit_host_pointers_equal_device(ctx):
+    from tests._util import to_dev
+    X, y = _obs(200, 5, 7)
+    ls = W.lengthscale_rule(5)
+    a = ctx.fit(X, y, ls, 1.0, 1e-6).read()
+    b = ctx.fit(to_dev(X), to_dev(y), ls, 1.0, 1e-6).read()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_fit_not_spd_and_jitter(ctx, orc):
+    from paper_2403_08131_b300 import gpbo
+    X = np.array([[0.1, 0.2], [0.1, 0.2], [0.7, 0.4]])
+    y = np.array([1.0, 1.0, -1.0])
+    with pytest.raises(gpbo.GpboError) as e:
+        ctx.fit(X, y, [0.3, 0.3], 1.0, 0.0)
+    assert e.value.code == gpbo.GPBO_ENOTSPD
+    with pytest.raises(orc.OracleError) as e2:
+        orc.gp_fit(X, y, 0.3, 1.0, 0.0)
+    assert e2.value.code == 2
+    m = ctx.fit(X, y, [0.3, 0.3], 1.0, 0.0, jitter=True)
+    assert m.info()["noise_var"] > 0
+
+
+def test_fit_rejects_bad_arguments(ctx):
+    from paper_2403_08131_b300 import gpbo
+    X, y = _obs(10, 3, 1)
+    for ls in ([0.3, -1.0, 0.3], [0.3, 0.3]):
+        with pytest.raises(gpbo.GpboError) as e:
+            ctx.fit(X, y, ls, 1.0, 1e-6)
+        assert e.value.code == gpbo.GPBO_EINVAL
+    Xn = X.copy()
+    Xn[3, 1] = np.nan
+    with pytest.raises(gpbo.GpboError) as e:
+        ctx.fit(Xn, y, [0.3] * 3, 1.0, 1e-6)
+    assert e.value.code == gpbo.GPBO_ENAN

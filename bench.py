@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="M",
+                    help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
     return ap.parse_args()
 
 
@@ -276,8 +278,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    import torch
+
+    from paper_2403_08131_b300 import gpbo, workloads as W
+
+    w = W.config4(n=N_OBS, M=args.profile_case, prec=args.prec)
+    ctx = gpbo.Context(0, torch.cuda.current_stream())
+    ys = (w.y - w.y.mean()) / w.y.std()
+    m = ctx.fit(torch.from_numpy(w.X).cuda(), torch.from_numpy(ys).cuda(), w.lengthscale, 1.0, w.noise_var,
+                prec=args.prec)
+    am, em = ctx.posterior_ei(m, None, M=args.profile_case, seed=w.seed, y_best=float(ys.min()))
+    torch.cuda.synchronize()
+    print(f"profile case: prec={args.prec} n={N_OBS} M={args.profile_case} argmax={am} ei_max={em:.6g}")
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

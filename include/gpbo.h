@@ -58,9 +58,11 @@ typedef enum gpbo_status {
 /* Scoring precision of the posterior variance (the fit is FP64 in every case).
  *   F64  : all of the scoring in FP64 on CUDA cores.
  *   F32  : cross-kernel and variance products in FP32 on CUDA cores.
- *   BF16 : variance operands L^-1 and K* rounded to BF16, tcgen05 tensor cores with
- *          FP32 accumulation in tensor memory; mean and EI in FP32 from FP32 K*.
- *   F16  : as BF16 with IEEE half operands (same tensor rate, 3 more mantissa bits). */
+ *   BF16 : variance operands on tcgen05 tensor cores with FP32 accumulation in tensor
+ *          memory: K* rounded to BF16, L^-1 carried as two BF16 terms (hi + lo) so that its
+ *          rounding cancels (twice the tensor work of F16); mean and EI in FP32 from FP32 K*.
+ *   F16  : K* and L^-1 rounded to IEEE half, one tensor-core pass (same rate as BF16,
+ *          3 more mantissa bits; the fast accurate path). */
 typedef enum gpbo_prec {
     GPBO_PREC_F64 = 0,
     GPBO_PREC_F32 = 1,
@@ -121,6 +123,7 @@ int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes);
  * gp_model_free.  GPBO_ENOTSPD when a pivot is not positive (after any jitter retries). */
 int gp_fit(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp,
            gpbo_prec prec, unsigned flags, gp_model **out);
+/* Free a model.  Models must be freed before the context they were fitted on. */
 int gp_model_free(gp_model *model);
 /* Shape and the noise variance actually used (differs from hyp->noise_var after jitter). */
 int gp_model_info(const gp_model *model, int *n, int *d, int *prec, double *noise_var_used);

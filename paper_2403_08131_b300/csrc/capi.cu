@@ -120,7 +120,8 @@ static int alloc_model(gp_model *m)
     GPBO_TRY(dalloc(&m->alpha32, m->n_pad));
     if (m->prec == GPBO_PREC_F64) GPBO_TRY(dalloc(&m->Linv64, sq));
     else GPBO_TRY(dalloc(&m->Linv32, sq));
-    if (m->prec == GPBO_PREC_BF16 || m->prec == GPBO_PREC_F16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 2));
+    if (m->prec == GPBO_PREC_F16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 2));
+    if (m->prec == GPBO_PREC_BF16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 4));  // hi then lo
     return GPBO_OK;
 }
 
@@ -140,16 +141,17 @@ static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int 
     for (int k = 0; k < d; ++k) m->ls[k] = hyp->lengthscale[k];
     int st = alloc_model(m);
     const int tries = (flags & GPBO_JITTER) ? 4 : 1;
-    for (int t = 0; st == GPBO_OK && t < tries; ++t) {
+    for (int t = 0; st == GPBO_OK || st == GPBO_ENOTSPD; ++t) {
+        if (t == tries) break;
+        if (t > 0) m->sn2 = m->sn2 > 0 ? m->sn2 * 10.0 : 1e-10;  // jitter escalation
         const double nn = (double)n;
         st = trace_begin(ctx, PH_FIT, nn * nn * nn / 3.0);
-        if (st == GPBO_OK) st = fit_model(ctx, m, X, y);
-        if (st == GPBO_OK || st == GPBO_ENOTSPD) {
-            int s2 = trace_end(ctx);
-            if (st == GPBO_OK) st = s2;
-        }
-        if (st != GPBO_ENOTSPD) break;
-        m->sn2 = m->sn2 > 0 ? m->sn2 * 10.0 : 1e-10;
+        if (st != GPBO_OK) break;
+        st = fit_model(ctx, m, X, y);
+        if (st != GPBO_OK && st != GPBO_ENOTSPD) break;
+        const int s2 = trace_end(ctx);
+        if (s2 != GPBO_OK) { st = s2; break; }
+        if (st == GPBO_OK) break;
     }
     if (st != GPBO_OK) {
         cudaStreamSynchronize(ctx->stream);

@@ -367,6 +367,18 @@ __global__ void k_cast(const Tin *__restrict__ in, int64_t count, Tout *__restri
     if (t < count) out[t] = convert_to<Tout>((double)in[t]);
 }
 
+// BF16 operands with a compensated inverse: hi = bf16(L^-1), lo = bf16(L^-1 - hi).
+__global__ void k_split_bf16(const float *__restrict__ in, int64_t count, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const float v = in[t];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[t] = h;
+    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 // Bottom-up block recursion: at level l the runs of 2^l diagonal blocks are inverted; runs
 // 2j and 2j+1 merge by X21 = -X22 (L21 X11).  Ls is L in the working type T.
 template <typename T>
@@ -506,7 +518,8 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs, host));
         if (m->prec == GPBO_PREC_BF16) {
-            k_cast<float, __nv_bfloat16><<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, (__nv_bfloat16 *)m->Linv16);
+            __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;
+            k_split_bf16<<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, hi, hi + sq);
             GPBO_LAUNCH_CHECK(ctx);
         } else if (m->prec == GPBO_PREC_F16) {
             k_cast<float, __half><<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, (__half *)m->Linv16);

@@ -101,7 +101,7 @@ struct gp_model {
     float *alpha32 = nullptr;   // n_pad
     double *Linv64 = nullptr;   // F64 scoring: L^-1
     float *Linv32 = nullptr;    // F32 and tensor-core scoring: L^-1 in FP32
-    void *Linv16 = nullptr;     // BF16/F16 scoring: L^-1 rounded to the operand type
+    void *Linv16 = nullptr;     // F16: L^-1 rounded; BF16: hi = bf16(L^-1) then lo = bf16(L^-1 - hi)
 };
 
 namespace gpbo {

@@ -18,6 +18,9 @@
 //               EI and the per-CTA argmax
 // For output chunk q (L^-1 rows 256q .. 256q+255) only K columns < 256(q+1) are read:
 // the triangle's zero blocks are never loaded or multiplied.
+// BF16 models carry a compensated inverse, hi = bf16(L^-1) and lo = bf16(L^-1 - hi); the
+// K loop then runs twice (hi, then lo) into the same accumulator, so only K*'s rounding
+// remains (twice the MMA work).  FP16 models run a single pass.
 //
 // Every mbarrier wait is bounded (about 2 s of SM clock).  On timeout the kernel sets
 // DEV_TIMEOUT in the context's status word, every role leaves its loop, the producer
@@ -189,10 +192,12 @@ struct Params {
     int64_t *part_idx;
     unsigned *status;
     uint32_t idesc;
+    int split;        // 1: V = K* hi^T + K* lo^T (compensated BF16 inverse), 0: single pass
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_var_ei_tc(const __grid_constant__ CUtensorMap map_k, const __grid_constant__ CUtensorMap map_l, Params P)
+    k_var_ei_tc(const __grid_constant__ CUtensorMap map_k, const __grid_constant__ CUtensorMap map_l,
+                const __grid_constant__ CUtensorMap map_l2, Params P)
 {
     extern __shared__ unsigned char smraw[];
     unsigned char *tiles = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -231,6 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // ---------------- TMA producer
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_k) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l) : "memory");
+            if (P.split) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l2) : "memory");
             int stage = 0;
             uint32_t phase = 0;
             int armed[STAGES];
@@ -240,7 +246,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
                 for (int q = 0; ok && q < nq; ++q) {
                     const int ksteps = (q + 1) * (BN / BK);
-                    for (int ks = 0; ks < ksteps; ++ks) {
+                    // the compensated form runs the K loop twice: hi operand, then lo
+                    for (int ks2 = 0; ks2 < ksteps * (1 + P.split); ++ks2) {
+                        const int ks = ks2 < ksteps ? ks2 : ks2 - ksteps;
                         if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                         unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                         unsigned char *b = a + A_BYTES;
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         armed[stage] = 1;
                         armed_par[stage] = phase;
                         tma_load_2d(a, &map_k, ks * BK, t * BM, &sh->full[stage]);
-                        tma_load_2d(b, &map_l, ks * BK, q * BN, &sh->full[stage]);
+                        tma_load_2d(b, ks2 < ksteps ? &map_l : &map_l2, ks * BK, q * BN, &sh->full[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                 }
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (!mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-                    const int ksteps = (q + 1) * (BN / BK);
+                    const int ksteps = (q + 1) * (BN / BK) * (1 + P.split);
                     for (int ks = 0; ks < ksteps; ++ks) {
                         if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
@@ -402,9 +410,13 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
     if (((uintptr_t)Kstar & 15) || ((uintptr_t)m->Linv16 & 15)) return GPBO_EINVAL;
     const CUtensorMapDataType dt =
         m->prec == GPBO_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    CUtensorMap mk, ml;
+    CUtensorMap mk, ml, ml2;
+    const int split = m->prec == GPBO_PREC_BF16 ? 1 : 0;
+    const size_t sq = (size_t)m->n_pad * m->n_pad;
     GPBO_TRY(encode_2d(&mk, dt, Kstar, (uint64_t)C, (uint64_t)m->n_pad, tc::BM));
     GPBO_TRY(encode_2d(&ml, dt, m->Linv16, (uint64_t)m->n_pad, (uint64_t)m->n_pad, tc::BN));
+    GPBO_TRY(encode_2d(&ml2, dt, (const uint16_t *)m->Linv16 + (split ? sq : 0), (uint64_t)m->n_pad,
+                       (uint64_t)m->n_pad, tc::BN));
     static bool attr = false;
     if (!attr) {
         GPBO_CUDA_TRY(cudaFuncSetAttribute(tc::k_var_ei_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -427,8 +439,9 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
     P.part_idx = part_idx;
     P.status = ctx->dev_status;
     P.idesc = tc::instr_desc(m->prec == GPBO_PREC_BF16 ? 1u : 0u);
+    P.split = split;
     const int grid = std::min(P.num_tiles, ctx->sm_count);
-    tc::k_var_ei_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, ctx->stream>>>(mk, ml, P);
+    tc::k_var_ei_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, ctx->stream>>>(mk, ml, ml2, P);
     GPBO_LAUNCH_CHECK(ctx);
     *n_parts = grid;
     return GPBO_OK;

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -122,11 +123,15 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None):
         self._h = _P()
+        self._models = weakref.WeakSet()
         check(_create(C.byref(self._h), device, _stream_handle(stream)), "gpbo_create")
         self.device = device
 
     def close(self):
+        """Free every live model of this context, then the context itself."""
         if self._h:
+            for m in list(self._models):
+                m.free()
             _destroy(self._h)
             self._h = _P()
 
@@ -170,7 +175,9 @@ class Context:
         flags = (HOST_PTRS if host else 0) | (JITTER if jitter else 0)
         out = _P()
         check(_fit(self._h, _ptr(X), _ptr(y), n, d, C.byref(h), PREC[prec], flags, C.byref(out)), "gp_fit")
-        return Model(self, out, prec)
+        m = Model(self, out, prec)
+        self._models.add(m)
+        return m
 
     def posterior_ei(self, model, Xc=None, M=None, seed=0, y_best=0.0, xi=0.0, mu=None, sigma=None, ei=None):
         """Xc: M x d float32 torch CUDA tensor / numpy array, or None with M and seed.

@@ -52,7 +52,8 @@ typedef enum gpbo_status {
     GPBO_ENOMEM = 4,   /* device allocation failed */
     GPBO_ECUDA = 5,    /* a CUDA runtime call failed */
     GPBO_ETIMEOUT = 6, /* a bounded device-side wait gave up; the kernel exited cleanly */
-    GPBO_ENOTSUP = 7   /* the device is not sm_103 or the request needs a missing feature */
+    GPBO_ENOTSUP = 7,  /* the device is not sm_103 or the request needs a missing feature */
+    GPBO_ESCRATCH = 8  /* the problem does not fit the fixed scratch of gp_posterior_ei_noalloc */
 } gpbo_status;
 
 /* Scoring precision of the posterior variance (the fit is FP64 in every case).
@@ -147,6 +148,32 @@ int gp_model_read(const gp_model *model, double *L_host, double *alpha_host);
 int gp_posterior_ei(gpbo_ctx *ctx, const gp_model *model, const float *Xc, int64_t M, uint64_t seed,
                     double y_best, double xi, unsigned flags, void *mu, void *sigma, void *ei,
                     int64_t *argmax, double *ei_max);
+
+/* Allocation-free scoring (no counterpart in the paper; a deployment convenience).
+ * Same results as gp_posterior_ei for an FP32 or FP64 model, but the call allocates no
+ * memory at all: no cudaMalloc, no cudaFree, no allocating library routine.  It is meant
+ * for callers that must not allocate device memory while they run -- a serving loop whose
+ * memory is owned by a pooling allocator (PyTorch's caching allocator, an arena sized at
+ * start-up), a process running under a hard device-memory cap, or code that already holds
+ * every buffer it will ever use.  Its scratch space is one fixed array of
+ * GPBO_NOALLOC_SCRATCH_BYTES (4 MiB) in the library's device memory, which every GPU that
+ * loads the library holds until the process exits.
+ *   - Xc, mu, sigma, ei are DEVICE pointers (no GPBO_HOST_PTRS); argmax, ei_max are host.
+ *     Xc may be NULL to draw the candidates from `seed` as gp_posterior_ei does.
+ *   - The model must be GPBO_PREC_F32 or GPBO_PREC_F64 (GPBO_ENOTSUP otherwise).
+ *   - The pool is scored in chunks that fit the scratch; a model whose padded size is
+ *     too large for even 64 candidates per chunk (FP32: n_pad > 16320; FP64: n_pad > 8128)
+ *     is rejected with GPBO_ESCRATCH before any work is queued.
+ *   - The first call on a device looks up the scratch array's device address (once per
+ *     device, with that device current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; each call
+ *     clears what it needs.  Calls that overlap on the GPU (several streams or host
+ *     threads at once on one device) race on the scratch: order them on one stream.
+ *   - Synchronises the context's stream (to return argmax and ei_max). */
+#define GPBO_NOALLOC_SCRATCH_BYTES (4u << 20)
+int gp_posterior_ei_noalloc(gpbo_ctx *ctx, const gp_model *model, const float *Xc, int64_t M, uint64_t seed,
+                            double y_best, double xi, void *mu, void *sigma, void *ei, int64_t *argmax,
+                            double *ei_max);
 
 /* Candidate c, coordinate k = uniform24(seed, stream 2, (first + c) * d + k) for
  * c < M, written as FP32 into the device array out (M x d).  SplitMix64 (Steele, Lea,

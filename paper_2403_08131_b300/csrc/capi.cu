@@ -190,6 +190,7 @@ const char *gpbo_strerror(int s)
     case GPBO_ECUDA: return "CUDA runtime error";
     case GPBO_ETIMEOUT: return "bounded device wait timed out";
     case GPBO_ENOTSUP: return "unsupported device or feature";
+    case GPBO_ESCRATCH: return "problem too large for the allocation-free scratch (4 MiB)";
     }
     return "unknown status";
 }

@@ -19,6 +19,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
 
 namespace gpbo {
 
@@ -376,4 +378,144 @@ int score_model(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t M, ui
     return GPBO_EINVAL;
 }
 
+// ------------------------------------------------------------------ allocation-free scoring
+// gp_posterior_ei_noalloc: the CUDA-core scoring path with its scratch (K* chunk, per-CTA
+// argmax partials, running best) in one fixed file-scope device array instead of the
+// context's workspace, so that a call allocates nothing.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GPBO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_dev[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on `device` (which must be current).  In host code the
+// array's name is only a stand-in for the symbol, never a usable address.
+int noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return GPBO_ENOTSUP;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[device]) {
+        void *p = nullptr;
+        GPBO_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_dev[device] = (unsigned char *)p;
+    }
+    *out = g_noalloc_dev[device];
+    return GPBO_OK;
+}
+}  // namespace
+
+__global__ void k_noalloc_reset(double *best_ei, int64_t *best_idx)
+{
+    *best_ei = -2.0;
+    *best_idx = INT64_MAX;
+}
+
+// Reduce one chunk's per-CTA partials and merge them into the running best.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_noalloc_merge(const T *__restrict__ part_ei, const int64_t *__restrict__ part_idx,
+                                                        int np, double *best_ei, int64_t *best_idx)
+{
+    __shared__ double sv[1024];
+    __shared__ int64_t si[1024];
+    double bv = -2.0;
+    int64_t bi = INT64_MAX;
+    for (int p = threadIdx.x; p < np; p += blockDim.x)
+        if (better((double)part_ei[p], part_idx[p], bv, bi)) { bv = (double)part_ei[p]; bi = part_idx[p]; }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s; s >>= 1) {
+        if (threadIdx.x < s && better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && better(sv[0], si[0], *best_ei, *best_idx)) {
+        *best_ei = sv[0];
+        *best_idx = si[0];
+    }
+}
+
+template <typename T>
+static int score_noalloc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t M, uint64_t seed, double y_best,
+                         double xi, T *mu_out, T *sigma_out, T *ei_out, int64_t *argmax, double *ei_max)
+{
+    const int n_pad = m->n_pad;
+    const size_t per_cand = (size_t)n_pad * sizeof(T);
+    // layout: [0,256) running best | partials (ei T, idx int64) | mu chunk (if needed) | K* chunk
+    const size_t head = 256;
+    auto need = [&](int64_t C) {
+        const size_t np = (size_t)cdiv64(C, 64);
+        size_t b = head + np * (sizeof(T) + sizeof(int64_t)) + 256;
+        b += (mu_out ? 0 : (size_t)C * sizeof(T)) + 256;
+        return b + (size_t)C * per_cand;
+    };
+    int64_t C = (int64_t)(GPBO_NOALLOC_SCRATCH_BYTES / (per_cand + sizeof(T) + 1)) / 64 * 64;
+    while (C >= 64 && need(C) > GPBO_NOALLOC_SCRATCH_BYTES) C -= 64;
+    if (C < 64) return GPBO_ESCRATCH;
+    C = std::min<int64_t>(C, round_up64(M, 64));
+    unsigned char *base = nullptr;
+    GPBO_TRY(noalloc_scratch(ctx->device, &base));
+    double *best_ei = (double *)base;
+    int64_t *best_idx = (int64_t *)(base + 8);
+    const int64_t np = cdiv64(C, 64);
+    int64_t *pidx = (int64_t *)(base + head);
+    T *pei = (T *)(base + head + np * sizeof(int64_t));
+    unsigned char *p = (unsigned char *)(((uintptr_t)(pei + np) + 255) & ~(uintptr_t)255);
+    T *mu_chunk = nullptr;
+    if (!mu_out) {
+        mu_chunk = (T *)p;
+        p = (unsigned char *)(((uintptr_t)(mu_chunk + C) + 255) & ~(uintptr_t)255);
+    }
+    T *Kst = (T *)p;
+    const T *Xs = nullptr, *alpha = nullptr, *Linv = nullptr;
+    if constexpr (sizeof(T) == 8) { Xs = m->Xs64; alpha = m->alpha64; Linv = m->Linv64; }
+    else { Xs = m->Xs32; alpha = m->alpha32; Linv = m->Linv32; }
+    k_noalloc_reset<<<1, 1, 0, ctx->stream>>>(best_ei, best_idx);
+    GPBO_LAUNCH_CHECK(ctx);
+    for (int64_t c0 = 0; c0 < M; c0 += C) {
+        const int64_t Cc = std::min(C, M - c0);
+        // the kernels index mu by pool position; the chunk buffer stands in for [c0, c0 + Cc)
+        T *mu = mu_out ? mu_out : mu_chunk - c0;
+        GPBO_TRY((launch_xkern<T, T>(ctx, m, Xc, seed, c0, Cc, Xs, alpha, Kst, mu)));
+        const unsigned g = (unsigned)cdiv64(Cc, 64);
+        k_var_simt<T><<<g, 256, 0, ctx->stream>>>(Kst, Cc, c0, n_pad, Linv, mu, (T)m->s2, y_best, nullptr, (T)xi,
+                                                  sigma_out, ei_out, pei, pidx, 0);
+        GPBO_LAUNCH_CHECK(ctx);
+        k_noalloc_merge<T><<<1, 1024, 0, ctx->stream>>>(pei, pidx, (int)g, best_ei, best_idx);
+        GPBO_LAUNCH_CHECK(ctx);
+    }
+    GPBO_CUDA_TRY(cudaMemcpyAsync(ctx->pinned, base, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *ei_max = ((double *)ctx->pinned)[0];
+    *argmax = ((int64_t *)ctx->pinned)[1];
+    return GPBO_OK;
+}
+
 }  // namespace gpbo
+
+extern "C" int gp_posterior_ei_noalloc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t M, uint64_t seed,
+                                       double y_best, double xi, void *mu, void *sigma, void *ei, int64_t *argmax,
+                                       double *ei_max)
+{
+    using namespace gpbo;
+    if (!ctx || !m || !argmax || !ei_max || M < 1 || M > 0x7fffffffll) return GPBO_EINVAL;
+    if (!std::isfinite(y_best) || !std::isfinite(xi)) return GPBO_EINVAL;
+    if (m->prec != GPBO_PREC_F32 && m->prec != GPBO_PREC_F64) return GPBO_ENOTSUP;
+    GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
+    int64_t am = -1;
+    double em = 0.0;
+    int st = m->prec == GPBO_PREC_F64
+                 ? score_noalloc<double>(ctx, m, Xc, M, seed, y_best, xi, (double *)mu, (double *)sigma, (double *)ei,
+                                         &am, &em)
+                 : score_noalloc<float>(ctx, m, Xc, M, seed, y_best, xi, (float *)mu, (float *)sigma, (float *)ei,
+                                        &am, &em);
+    if (st != GPBO_OK) return st;
+    *argmax = am;
+    *ei_max = em;
+    return GPBO_OK;
+}
+

@@ -21,7 +21,8 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
-GPBO_OK, GPBO_EINVAL, GPBO_ENOTSPD, GPBO_ENAN, GPBO_ENOMEM, GPBO_ECUDA, GPBO_ETIMEOUT, GPBO_ENOTSUP = range(8)
+GPBO_OK, GPBO_EINVAL, GPBO_ENOTSPD, GPBO_ENAN, GPBO_ENOMEM, GPBO_ECUDA, GPBO_ETIMEOUT, GPBO_ENOTSUP, GPBO_ESCRATCH = \
+    range(9)
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 HOST_PTRS = 0x1
 JITTER = 0x2
@@ -74,6 +75,8 @@ _model_info = _sig("gp_model_info", C.c_int, [_P, _I, _I, _I, _D])
 _model_read = _sig("gp_model_read", C.c_int, [_P, _P, _P])
 _posterior = _sig("gp_posterior_ei", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double, C.c_double, C.c_uint,
                                                _P, _P, _P, _L, _D])
+_posterior_noalloc = _sig("gp_posterior_ei_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double,
+                                                               C.c_double, _P, _P, _P, _L, _D])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
 _screen = _sig("interdep_screen", C.c_int, [_P, C.POINTER(GpboObjective), C.c_int, C.POINTER(ScreenOpts), _P, _P,
                                              _P, _I, _P])
@@ -192,6 +195,18 @@ class Context:
         check(_posterior(self._h, model._h, _ptr(Xc), int(M), int(seed), float(y_best), float(xi),
                          HOST_PTRS if host else 0, _ptr(mu), _ptr(sigma), _ptr(ei), C.byref(am), C.byref(em)),
               "gp_posterior_ei")
+        return int(am.value), float(em.value)
+
+    def posterior_ei_noalloc(self, model, Xc=None, M=None, seed=0, y_best=0.0, xi=0.0, mu=None, sigma=None,
+                             ei=None):
+        """Allocation-free scoring of an FP32/FP64 model: the library allocates nothing
+        during the call.  Every array is a device tensor the caller already owns."""
+        if Xc is not None:
+            M = Xc.shape[0]
+        am = C.c_int64(-1)
+        em = C.c_double(0.0)
+        check(_posterior_noalloc(self._h, model._h, _ptr(Xc), int(M), int(seed), float(y_best), float(xi), _ptr(mu),
+                                 _ptr(sigma), _ptr(ei), C.byref(am), C.byref(em)), "gp_posterior_ei_noalloc")
         return int(am.value), float(em.value)
 
     def gen_candidates(self, out, seed, first=0):

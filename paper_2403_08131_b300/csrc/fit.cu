@@ -34,40 +34,55 @@ __global__ void k_scale_x(const double *__restrict__ X, int n, int d, int n_pad,
     if (Xs32) Xs32[t] = (float)v;
 }
 
-// K_ij = s2 m(r_ij) + sn2 [i == j] over the real block, identity on the padding.
+// K_ij = s2 m(r_ij) + sn2 [i == j] over the real block, identity on the padding.  Each
+// thread of the lower half (i >= j, by 32 x 32 tiles) writes K_ij and its mirror K_ji.
 __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, double s2, double sn2,
                        double *__restrict__ K)
 {
-    int j = blockIdx.x * 32 + threadIdx.x;
-    int i = blockIdx.y * 8 + threadIdx.y;
-    if (i >= n_pad || j >= n_pad) return;
-    double v;
-    if (i < n && j < n) {
-        double r2 = 0.0;
-        for (int k = 0; k < d; ++k) {
-            double t = Xs[(int64_t)k * n_pad + i] - Xs[(int64_t)k * n_pad + j];
-            r2 = fma(t, t, r2);
+    const int tj = blockIdx.x, ti = blockIdx.y;
+    if (tj > ti) return;
+    __shared__ double tile[32][33];
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = ti * 32 + r, j = tj * 32 + threadIdx.x;
+        double v;
+        if (i < n && j < n) {
+            double r2 = 0.0;
+            for (int k = 0; k < d; ++k) {
+                double t = Xs[(int64_t)k * n_pad + i] - Xs[(int64_t)k * n_pad + j];
+                r2 = fma(t, t, r2);
+            }
+            v = s2 * matern52_r2(r2) + (i == j ? sn2 : 0.0);
+        } else {
+            v = i == j ? 1.0 : 0.0;
         }
-        v = s2 * matern52_r2(r2) + (i == j ? sn2 : 0.0);
-    } else {
-        v = i == j ? 1.0 : 0.0;
+        K[(int64_t)i * n_pad + j] = v;
+        tile[r][threadIdx.x] = v;
     }
-    K[(int64_t)i * n_pad + j] = v;
+    if (ti == tj) return;
+    __syncthreads();
+    // mirror: K[j][i] for the transposed tile, coalesced along i
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = tj * 32 + r, i = ti * 32 + threadIdx.x;
+        K[(int64_t)j * n_pad + i] = tile[threadIdx.x][r];
+    }
 }
 
 // ------------------------------------------------------------------ Cholesky
 // Diagonal block k: unblocked right-looking factorisation in shared memory, then the
 // inverse of the factor (column j solves L x = e_j).  Writes L_kk (zeros above) and Dinv_k.
+// Pivots use one reciprocal square root: L_jj = p * rsqrt(p), 1/L_jj = rsqrt(p), so the
+// column scaling and the inverse multiply instead of divide.  The inverse gives each
+// column four threads (a lane quad) that split every dot product and combine by shuffles.
 __global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status)
 {
     extern __shared__ double sm[];
     double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
     double(*inv)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
+    __shared__ double rdiag[NB];
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = A[base + (int64_t)(e / NB) * n_pad + e % NB];
-    __shared__ double piv_s;
     for (int j = 0; j < NB; ++j) {
         __syncthreads();
         if (tid == 0) {
@@ -76,69 +91,68 @@ __global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ A, int n
                 atomicOr(status, DEV_NOTSPD);
                 p = 1.0;
             }
-            piv_s = sqrt(p);
-            a[j][j] = piv_s;
+            const double r = rsqrt(p);
+            a[j][j] = p * r;
+            rdiag[j] = r;
         }
         __syncthreads();
-        const double piv = piv_s;
-        for (int r = j + 1 + tid; r < NB; r += blockDim.x) a[r][j] /= piv;
+        const double r = rdiag[j];
+        for (int i = j + 1 + tid; i < NB; i += blockDim.x) a[i][j] *= r;
         __syncthreads();
         const int cnt = NB - 1 - j;
         for (int e = tid; e < cnt * cnt; e += blockDim.x) {
-            int r = j + 1 + e / cnt, c = j + 1 + e % cnt;
-            if (c <= r) a[r][c] -= a[r][j] * a[c][j];
+            int i = j + 1 + e / cnt, c = j + 1 + e % cnt;
+            if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
         }
     }
     __syncthreads();
-    if (tid < NB) {
-        const int j = tid;
-        for (int i = 0; i < j; ++i) inv[i][j] = 0.0;
-        inv[j][j] = 1.0 / a[j][j];
+    {
+        const int j = tid >> 2, sub = tid & 3;
+        const unsigned mask = 0xFu << (threadIdx.x & 28);
+        for (int i = sub; i < j; i += 4) inv[i][j] = 0.0;
+        if (sub == 0) inv[j][j] = rdiag[j];
+        __syncwarp(mask);
         for (int i = j + 1; i < NB; ++i) {
             double s = 0.0;
-            for (int t = j; t < i; ++t) s = fma(a[i][t], inv[t][j], s);
-            inv[i][j] = -s / a[i][i];
+            for (int t = j + sub; t < i; t += 4) s = fma(a[i][t], inv[t][j], s);
+            s += __shfl_xor_sync(mask, s, 1);
+            s += __shfl_xor_sync(mask, s, 2);
+            if (sub == 0) inv[i][j] = -s * rdiag[i];
+            __syncwarp(mask);
         }
     }
     __syncthreads();
     double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e / NB, c = e % NB;
-        A[base + (int64_t)r * n_pad + c] = c <= r ? a[r][c] : 0.0;
-        D[e] = inv[r][c];
+        int i = e / NB, c = e % NB;
+        A[base + (int64_t)i * n_pad + c] = c <= i ? a[i][c] : 0.0;
+        D[e] = inv[i][c];
     }
 }
 
-// Panel: L_ik = A_ik L_kk^-T for the block rows i > k (one CTA per block row).
+// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, one CTA per 16-row slab so that
+// the short panels at the end of the factorisation still spread over many SMs.
 __global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv)
 {
-    extern __shared__ double sm[];
-    double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    double(*dv)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
-    const int ib = kb + 1 + blockIdx.x;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int64_t base = (int64_t)ib * NB * n_pad + (int64_t)kb * NB;
+    __shared__ double a[16][NB + 1];
+    __shared__ double dv[NB][NB + 1];
+    const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)blockIdx.x * 16;
+    const int tid = threadIdx.x, tx = tid % 64, ty = tid / 64;
     const double *D = Dinv + (int64_t)kb * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        a[e / NB][e % NB] = A[base + (int64_t)(e / NB) * n_pad + e % NB];
-        dv[e / NB][e % NB] = D[e];
-    }
+    for (int e = tid; e < 16 * NB; e += blockDim.x)
+        a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
+    for (int e = tid; e < NB * NB; e += blockDim.x) dv[e / NB][e % NB] = D[e];
     __syncthreads();
-    double acc[4][4] = {};
-    for (int t = 0; t < NB; ++t) {
-        double x[4], y[4];
+    // thread (ty, tx): rows ty, ty+4, ty+8, ty+12; column tx; L_kk^-T is lower, so t <= tx
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = 0; t <= tx; ++t) {
+        const double y = dv[tx][t];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) { x[u] = a[ty + 16 * u][t]; y[u] = dv[tx + 16 * u][t]; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+        for (int u = 0; u < 4; ++u) acc[u] = fma(a[ty + 4 * u][t], y, acc[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) A[base + (int64_t)(ty + 16 * u) * n_pad + tx + 16 * v] = acc[u][v];
+    for (int u = 0; u < 4; ++u) A[(row0 + ty + 4 * u) * n_pad + (int64_t)kb * NB + tx] = acc[u];
 }
 
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.
@@ -196,15 +210,22 @@ __global__ void __launch_bounds__(256) k_fwd_step(const double *__restrict__ L, 
                                                   int n_pad, int b, double *__restrict__ w, double *__restrict__ z)
 {
     __shared__ double wb[NB], zb[NB];
+    __shared__ double D[NB][NB + 1];
     const int tid = threadIdx.x;
+    const double *Db = Dinv + (int64_t)b * NB * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Db[e];
     if (tid < NB) wb[tid] = w[b * NB + tid];
     __syncthreads();
-    const double *D = Dinv + (int64_t)b * NB * NB;
-    if (tid < NB) {
+    {   // z_b = Dinv_b w_b: four threads per row
+        const int r = tid >> 2, sub = tid & 3;
         double s = 0.0;
-        for (int t = 0; t <= tid; ++t) s = fma(D[tid * NB + t], wb[t], s);
-        zb[tid] = s;
-        if (blockIdx.x == 0) z[b * NB + tid] = s;
+        for (int t = sub; t <= r; t += 4) s = fma(D[r][t], wb[t], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (sub == 0) {
+            zb[r] = s;
+            if (blockIdx.x == 0) z[b * NB + r] = s;
+        }
     }
     __syncthreads();
     const int rb = b + 1 + blockIdx.x;
@@ -224,15 +245,22 @@ __global__ void __launch_bounds__(256) k_bwd_step(const double *__restrict__ L, 
                                                   int n_pad, int b, double *__restrict__ w, double *__restrict__ x)
 {
     __shared__ double wb[NB], xb[NB], red[4][NB];
+    __shared__ double D[NB][NB + 1];
     const int tid = threadIdx.x;
+    const double *Db = Dinv + (int64_t)b * NB * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Db[e];
     if (tid < NB) wb[tid] = w[b * NB + tid];
     __syncthreads();
-    const double *D = Dinv + (int64_t)b * NB * NB;
-    if (tid < NB) {
+    {   // x_b = Dinv_b^T w_b: four threads per output
+        const int r = tid >> 2, sub = tid & 3;
         double s = 0.0;
-        for (int t = tid; t < NB; ++t) s = fma(D[t * NB + tid], wb[t], s);
-        xb[tid] = s;
-        if (blockIdx.x == 0) x[b * NB + tid] = s;
+        for (int t = r + sub; t < NB; t += 4) s = fma(D[t][r], wb[t], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (sub == 0) {
+            xb[r] = s;
+            if (blockIdx.x == 0) x[b * NB + r] = s;
+        }
     }
     __syncthreads();
     const int cb = blockIdx.x;
@@ -380,51 +408,68 @@ __global__ void k_split_bf16(const float *__restrict__ in, int64_t count, __nv_b
 }
 
 // Bottom-up block recursion: at level l the runs of 2^l diagonal blocks are inverted; runs
-// 2j and 2j+1 merge by X21 = -X22 (L21 X11).  Ls is L in the working type T.
-template <typename T>
-static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev,
-                        std::vector<GemmProb> &host)
+// 2j and 2j+1 merge by X21 = -X22 (L21 X11).  Ls is L in the working type T.  Every level's
+// problem list goes to the device in one copy up front, so no host sync sits between levels.
+static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int> &level_first,
+                       std::vector<int> &level_count, std::vector<int2> &level_maxmn)
 {
     const int nblk = n_pad / NB;
+    probs.clear();
+    level_first.clear();
+    level_count.clear();
+    level_maxmn.clear();
     for (int run = 1; run < nblk; run *= 2) {
-        host.clear();
+        const int first = (int)probs.size();
         int maxm = 0, maxn = 0;
         for (int b0 = 0; b0 + run < nblk; b0 += 2 * run) {
-            const int r0 = (b0 + run) * NB;               // first row of the right run
-            const int sl = run * NB;                       // left run size (always full)
+            const int r0 = (b0 + run) * NB;
+            const int sl = run * NB;
             const int sr = std::min(run, nblk - b0 - run) * NB;
-            GemmProb p;
-            p.a_off = (int64_t)r0 * n_pad + (int64_t)b0 * NB;   // L21
-            p.b_off = (int64_t)b0 * NB * n_pad + (int64_t)b0 * NB;  // X11
-            p.c_off = (int64_t)r0 * n_pad + (int64_t)b0 * NB;   // T (in tmp, same indexing)
+            GemmProb p;                                           // T = L21 X11
+            p.a_off = (int64_t)r0 * n_pad + (int64_t)b0 * NB;
+            p.b_off = (int64_t)b0 * NB * n_pad + (int64_t)b0 * NB;
+            p.c_off = (int64_t)r0 * n_pad + (int64_t)b0 * NB;
             p.m = sr;
             p.n = sl;
             p.k = sl;
-            host.push_back(p);
+            probs.push_back(p);
             maxm = std::max(maxm, sr);
             maxn = std::max(maxn, sl);
         }
-        const int np = (int)host.size();
-        GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, host.data(), sizeof(GemmProb) * np, cudaMemcpyHostToDevice,
-                                      ctx->stream));
-        dim3 grid((maxn + 63) / 64, (maxm + 63) / 64, np);
-        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Ls, Linv, tmp, n_pad, n_pad, n_pad, probs_dev, T(1), 0, 1);
-        GPBO_LAUNCH_CHECK(ctx);
-        // second product: C = -X22 * T, with A = X22 (lower), B = T
-        for (auto &p : host) {
-            int64_t r0 = p.a_off / n_pad;
-            p.b_off = p.c_off;                                // T
-            p.a_off = r0 * n_pad + r0;                        // X22
+        const int cnt = (int)probs.size() - first;
+        for (int q = 0; q < cnt; ++q) {                           // X21 = -X22 T
+            GemmProb p = probs[first + q];
+            const int64_t r0 = p.a_off / n_pad;
+            p.b_off = p.c_off;
+            p.a_off = r0 * n_pad + r0;
             p.k = p.m;
+            probs.push_back(p);
         }
-        GemmProb *probs2 = probs_dev + np;
-        GPBO_CUDA_TRY(cudaMemcpyAsync(probs2, host.data(), sizeof(GemmProb) * np, cudaMemcpyHostToDevice,
-                                      ctx->stream));
-        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Linv, tmp, Linv, n_pad, n_pad, n_pad, probs2, T(-1), 1, 0);
+        level_first.push_back(first);
+        level_count.push_back(cnt);
+        level_maxmn.push_back(make_int2(maxm, maxn));
+    }
+}
+
+template <typename T>
+static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev)
+{
+    std::vector<GemmProb> probs;
+    std::vector<int> first, count;
+    std::vector<int2> mm;
+    trtri_plan(n_pad, probs, first, count, mm);
+    if (probs.empty()) return GPBO_OK;
+    // the host vector dies at return: copy synchronously with respect to it (pageable memory)
+    GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, probs.data(), sizeof(GemmProb) * probs.size(), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    for (size_t l = 0; l < first.size(); ++l) {
+        dim3 grid((mm[l].y + 63) / 64, (mm[l].x + 63) / 64, count[l]);
+        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Ls, Linv, tmp, n_pad, n_pad, n_pad, probs_dev + first[l],
+                                                         T(1), 0, 1);
         GPBO_LAUNCH_CHECK(ctx);
-        // the host vector is reused next level; the copies above are stream-ordered, so
-        // wait for them before the host buffer changes
-        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Linv, tmp, Linv, n_pad, n_pad, n_pad,
+                                                         probs_dev + first[l] + count[l], T(-1), 1, 0);
+        GPBO_LAUNCH_CHECK(ctx);
     }
     return GPBO_OK;
 }
@@ -457,7 +502,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     k_scale_x<<<blocks_for((int64_t)d * n_pad), 256, 0, st>>>(m->X, n, d, n_pad, ls, m->Xs64, m->Xs32);
     GPBO_LAUNCH_CHECK(ctx);
     {
-        dim3 grid(n_pad / 32, n_pad / 8);
+        dim3 grid(n_pad / 32, n_pad / 32);
         k_kmat<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, n, d, n_pad, m->s2, m->sn2, m->K);
         GPBO_LAUNCH_CHECK(ctx);
     }
@@ -468,7 +513,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         const int T = nblk - kb - 1;
         if (T > 0) {
-            k_chol_panel<<<T, 256, smem2, st>>>(m->L, n_pad, kb, m->Dinv);
+            k_chol_panel<<<T * (NB / 16), 256, 0, st>>>(m->L, n_pad, kb, m->Dinv);
             GPBO_LAUNCH_CHECK(ctx);
             k_chol_update<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, smem2, st>>>(m->L, n_pad, kb, nblk);
             GPBO_LAUNCH_CHECK(ctx);
@@ -495,8 +540,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_LAUNCH_CHECK(ctx);
 
     // L^-1 for scoring
-    std::vector<GemmProb> host;
-    const int max_probs = nblk + 2;
+    const int max_probs = 2 * nblk + 2;
     GemmProb *probs = nullptr;
     const int64_t sq = (int64_t)n_pad * n_pad;
     if (m->prec == GPBO_PREC_F64) {
@@ -506,7 +550,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         probs = (GemmProb *)(tmp + sq);
         k_linv_init<double><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv64);
         GPBO_LAUNCH_CHECK(ctx);
-        GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs, host));
+        GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs));
     } else {
         void *w2 = nullptr;
         GPBO_TRY(ws_reserve(ctx, sizeof(float) * 2 * sq + sizeof(GemmProb) * 2 * max_probs, &w2));
@@ -516,7 +560,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         k_linv_init<float><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv32);
         GPBO_LAUNCH_CHECK(ctx);
-        GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs, host));
+        GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs));
         if (m->prec == GPBO_PREC_BF16) {
             __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;
             k_split_bf16<<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, hi, hi + sq);
@@ -587,7 +631,6 @@ void fit_set_smem_limits()
 {
     const int smem2 = (int)(sizeof(double) * 2 * NB * (NB + 1));
     cudaFuncSetAttribute(k_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
-    cudaFuncSetAttribute(k_chol_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
     cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
 }
 

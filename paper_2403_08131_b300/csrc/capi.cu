@@ -94,7 +94,8 @@ static bool finite_all(const double *a, int64_t n)
 static void free_model(gp_model *m)
 {
     if (!m) return;
-    void *ptrs[] = {m->X, m->Xs64, m->Xs32, m->K, m->L, m->Dinv, m->alpha64, m->alpha32, m->Linv64, m->Linv32, m->Linv16};
+    void *ptrs[] = {m->X,       m->Xs64,    m->Xs32,   m->K,      m->L,      m->Dinv,
+                    m->alpha64, m->alpha32, m->Linv64, m->Linv32, m->Linv16, m->Zsplit, m->nb32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -122,6 +123,10 @@ static int alloc_model(gp_model *m)
     else GPBO_TRY(dalloc(&m->Linv32, sq));
     if (m->prec == GPBO_PREC_F16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 2));
     if (m->prec == GPBO_PREC_BF16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 4));  // hi then lo
+    if ((m->prec == GPBO_PREC_BF16 || m->prec == GPBO_PREC_F16) && m->d <= 32) {
+        GPBO_CUDA_TRY(cudaMalloc(&m->Zsplit, (size_t)m->n_pad * 128 * 2));
+        GPBO_TRY(dalloc(&m->nb32, m->n_pad));
+    }
     return GPBO_OK;
 }
 

@@ -501,6 +501,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaMemcpyAsync(m->X, X_dev, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, st));
     k_scale_x<<<blocks_for((int64_t)d * n_pad), 256, 0, st>>>(m->X, n, d, n_pad, ls, m->Xs64, m->Xs32);
     GPBO_LAUNCH_CHECK(ctx);
+    if (m->Zsplit) GPBO_TRY(xkern_tc_prepare(ctx, m));
     {
         dim3 grid(n_pad / 32, n_pad / 32);
         k_kmat<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, n, d, n_pad, m->s2, m->sn2, m->K);

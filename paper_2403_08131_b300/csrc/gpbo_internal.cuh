@@ -102,6 +102,8 @@ struct gp_model {
     double *Linv64 = nullptr;   // F64 scoring: L^-1
     float *Linv32 = nullptr;    // F32 and tensor-core scoring: L^-1 in FP32
     void *Linv16 = nullptr;     // F16: L^-1 rounded; BF16: hi = bf16(L^-1) then lo = bf16(L^-1 - hi)
+    void *Zsplit = nullptr;     // 16-bit models, d <= 32: n_pad x 128 FP16 [hi | lo | hi | 0] of (x - 1/2) / l
+    float *nb32 = nullptr;      // 16-bit models: |(x_i - 1/2) / l|^2
 };
 
 namespace gpbo {
@@ -127,6 +129,12 @@ int gen_candidates(gpbo_ctx *ctx, uint64_t seed, int64_t first, int64_t M, int d
 int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t C, int64_t c0,
                    const float *mu, double y_best, const double *tau_dev, double xi, float *sigma_out,
                    float *ei_out, float *part_ei, int64_t *part_idx, int *n_parts);
+
+// xkern_tc.cu: the cross-kernel on tensor cores for 16-bit models with d <= 32.
+int xkern_tc_prepare(gpbo_ctx *ctx, gp_model *m);
+bool xkern_tc_usable(const gp_model *m);
+int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
+             float *mu);
 
 // screen.cu
 int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opts *o, double *score,

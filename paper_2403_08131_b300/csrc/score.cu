@@ -122,6 +122,103 @@ __global__ void __launch_bounds__(256) k_xkern(const float *__restrict__ Xc, uin
     }
 }
 
+// FP32 cross-kernel and mean (F32, BF16 and F16 models): same results as k_xkern<float, Out>
+// up to the last bits of r = sqrt(r^2) and exp, with fewer instructions per K* element.
+// CTA = 256 threads = 8 warps x 8 candidates; each lane owns 4 consecutive observations of a
+// 128-observation chunk, read as one float4 per dimension straight from L1/L2; K* leaves as
+// one 8- or 16-byte store per candidate and chunk.
+template <typename Out> struct Pack4;
+template <> struct Pack4<float> {
+    using T = float4;
+    __device__ static T make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <> struct Pack4<__half> {
+    using T = uint2;
+    __device__ static T make(float a, float b, float c, float d)
+    {
+        __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
+        return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
+    }
+};
+template <> struct Pack4<__nv_bfloat16> {
+    using T = uint2;
+    __device__ static T make(float a, float b, float c, float d)
+    {
+        __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+        return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
+    }
+};
+
+// s2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r) with r = r2 rsqrt(r2) (r = 0 at coincidence).
+__device__ __forceinline__ float matern_fast(float r2, float s2)
+{
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float e = __expf(-2.2360680f * r);
+    return s2 * fmaf(1.6666666f, r2, fmaf(2.2360680f, r, 1.0f)) * e;
+}
+
+template <typename Out>
+__global__ void __launch_bounds__(256) k_xkern32(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
+                                                 int d, const float *__restrict__ Xs, const float *__restrict__ alpha,
+                                                 int n, int n_pad, float s2, Lengthscales_inv ls, Out *__restrict__ Kst,
+                                                 float *__restrict__ mu)
+{
+    constexpr int CW = 8;                 // candidates per warp
+    extern __shared__ float cs[];         // [64][d]
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    const int64_t cbase = blockIdx.x * 64ll;
+    for (int e = tid; e < 64 * d; e += 256) {
+        const int r = e / d, k = e - (e / d) * d;
+        const int64_t c = c0 + cbase + r;
+        const float x = Xc ? (cbase + r < C ? Xc[c * d + k] : 0.0f) : uniform24f(seed, 2, (uint64_t)(c * d + k));
+        cs[e] = x * (float)ls.inv[k];
+    }
+    __syncthreads();
+    const float *cw = cs + warp * CW * d;
+    float mp[CW];
+#pragma unroll
+    for (int a = 0; a < CW; ++a) mp[a] = 0.0f;
+    for (int i0 = 0; i0 < n_pad; i0 += 128) {
+        const int i = i0 + 4 * lane;
+        if (i >= n_pad) break;
+        float r2[CW][4];
+#pragma unroll
+        for (int a = 0; a < CW; ++a) r2[a][0] = r2[a][1] = r2[a][2] = r2[a][3] = 0.0f;
+        for (int k = 0; k < d; ++k) {
+            const float4 o = *reinterpret_cast<const float4 *>(Xs + (size_t)k * n_pad + i);
+#pragma unroll
+            for (int a = 0; a < CW; ++a) {
+                const float cv = cw[a * d + k];
+                const float t0 = cv - o.x, t1 = cv - o.y, t2 = cv - o.z, t3 = cv - o.w;
+                r2[a][0] = fmaf(t0, t0, r2[a][0]);
+                r2[a][1] = fmaf(t1, t1, r2[a][1]);
+                r2[a][2] = fmaf(t2, t2, r2[a][2]);
+                r2[a][3] = fmaf(t3, t3, r2[a][3]);
+            }
+        }
+        const float4 al = *reinterpret_cast<const float4 *>(alpha + i);
+        const bool v0 = i < n, v1 = i + 1 < n, v2 = i + 2 < n, v3 = i + 3 < n;
+#pragma unroll
+        for (int a = 0; a < CW; ++a) {
+            const float k0 = v0 ? matern_fast(r2[a][0], s2) : 0.0f;
+            const float k1 = v1 ? matern_fast(r2[a][1], s2) : 0.0f;
+            const float k2 = v2 ? matern_fast(r2[a][2], s2) : 0.0f;
+            const float k3 = v3 ? matern_fast(r2[a][3], s2) : 0.0f;
+            mp[a] = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mp[a]))));
+            const int64_t cl = cbase + warp * CW + a;
+            if (cl < C)
+                *reinterpret_cast<typename Pack4<Out>::T *>(Kst + cl * n_pad + i) = Pack4<Out>::make(k0, k1, k2, k3);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < CW; ++a) {
+        float v = mp[a];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t cl = cbase + warp * CW + a;
+        if (lane == 0 && cl < C) mu[c0 + cl] = v;
+    }
+}
+
 // Variance, EI and per-CTA argmax on CUDA cores.  CTA = 64 candidates; it walks the
 // lower triangle of L^-1 in 64-row blocks (outputs) and 16-wide K steps.
 template <typename T>
@@ -247,6 +344,14 @@ static int launch_xkern(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint6
 {
     Lengthscales_inv ls;
     for (int k = 0; k < m->d; ++k) ls.inv[k] = 1.0 / m->ls[k];
+    if constexpr (sizeof(Acc) == 4) {
+        // FP32 models: the register-tiled kernel (n_pad is a multiple of 64, so every float4 is in bounds)
+        const size_t smem = sizeof(float) * 64 * (size_t)m->d;
+        k_xkern32<Out><<<(unsigned)cdiv64(C, 64), 256, smem, ctx->stream>>>(Xc, seed, c0, C, m->d, Xs, alpha, m->n,
+                                                                             m->n_pad, (float)m->s2, ls, Kst, mu);
+        GPBO_LAUNCH_CHECK(ctx);
+        return GPBO_OK;
+    }
     const size_t smem = sizeof(Acc) * ((size_t)32 * m->d + (size_t)m->d * 128 + 128);
     static int attr_bytes = 0;  // one per template instance
     if ((int)smem > attr_bytes) {
@@ -337,7 +442,10 @@ static int score_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t M
         const int64_t Cc = std::min(C, M - c0);
         const double nn = (double)m->n;
         GPBO_TRY(trace_begin(ctx, PH_XKERN, (double)Cc * (3.0 * nn * m->d + 2.0 * nn)));
-        GPBO_TRY((launch_xkern<float, Out>(ctx, m, Xc, seed, c0, Cc, m->Xs32, m->alpha32, Kst, mu)));
+        if (xkern_tc_usable(m))
+            GPBO_TRY(xkern_tc(ctx, m, Xc, seed, c0, Cc, Kst, mu));
+        else
+            GPBO_TRY((launch_xkern<float, Out>(ctx, m, Xc, seed, c0, Cc, m->Xs32, m->alpha32, Kst, mu)));
         GPBO_TRY(trace_end(ctx));
         int used = 0;
         GPBO_TRY(trace_begin(ctx, PH_VAR, (double)Cc * nn * (nn + 1.0)));

@@ -407,6 +407,15 @@ __global__ void k_split_bf16(const float *__restrict__ in, int64_t count, __nv_b
     lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Zero rows n..n_pad-1 of a 16-bit L^-1 (count rows of width n_pad), so that the cross-kernel
+// values of padded observations never reach the variance.
+__global__ void k_zero_pad_rows(uint16_t *__restrict__ A, int n, int n_pad)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t cnt = (int64_t)(n_pad - n) * n_pad;
+    if (t < cnt) A[(int64_t)n * n_pad + t] = 0;
+}
+
 // Bottom-up block recursion: at level l the runs of 2^l diagonal blocks are inverted; runs
 // 2j and 2j+1 merge by X21 = -X22 (L21 X11).  Ls is L in the working type T.  Every level's
 // problem list goes to the device in one copy up front, so no host sync sits between levels.
@@ -566,9 +575,21 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
             __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;
             k_split_bf16<<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, hi, hi + sq);
             GPBO_LAUNCH_CHECK(ctx);
+            if (n_pad > n) {
+                for (int part = 0; part < 2; ++part) {
+                    k_zero_pad_rows<<<blocks_for((int64_t)(n_pad - n) * n_pad), 256, 0, st>>>(
+                        (uint16_t *)(hi + part * sq), n, n_pad);
+                    GPBO_LAUNCH_CHECK(ctx);
+                }
+            }
         } else if (m->prec == GPBO_PREC_F16) {
             k_cast<float, __half><<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, (__half *)m->Linv16);
             GPBO_LAUNCH_CHECK(ctx);
+            if (n_pad > n) {
+                k_zero_pad_rows<<<blocks_for((int64_t)(n_pad - n) * n_pad), 256, 0, st>>>((uint16_t *)m->Linv16, n,
+                                                                                          n_pad);
+                GPBO_LAUNCH_CHECK(ctx);
+            }
         }
     }
     GPBO_TRY(take_device_status(ctx, &bits));

@@ -10,13 +10,14 @@
 // significant bits, the accuracy of an FP32 dot product.  Centring the coordinates at 1/2
 // keeps |z|^2 small, so the subtraction |z_c|^2 + |z_i|^2 - 2 z_c . z_i cancels little.
 // The Matern evaluation, the mean and the 16-bit rounding of K* run in the epilogue, where
-// each thread owns one candidate (one TMEM lane) and half of a 256-observation chunk.
+// each thread owns one candidate (one TMEM lane) and a quarter of a 256-observation chunk.
 //
-// Roles (one CTA per SM, persistent over 128-candidate tiles, 320 threads):
+// Roles (one CTA per SM, persistent over 128-candidate tiles, 576 threads):
 //   warp 0     TMA: B' chunk (256 observations x 128) per stage, 2 stages of 64 KiB
 //   warp 1     TMEM (512 columns); one lane issues 8 MMAs (M=128, N=256, K=16) per chunk
 //              into one of two 256-column accumulators
-//   warps 2-9  epilogue: warp w reads TMEM lane quadrant w % 4 and column half (w-2) / 4;
+//   warps 2-17 epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4
+//              (64 of each chunk's 256 columns);
 //              warps 2-5 also build A' for the next tile (two smem slots) and its |z_c|^2;
 //              a slot is rebuilt only after its MMAs completed and all 8 warps read its |z_c|^2
 // Every wait is bounded; on timeout the kernel raises DEV_TIMEOUT, drains and exits.
@@ -37,7 +38,8 @@ constexpr int BN = 256;
 constexpr int KB = 128;                    // split width: [hi|hi|lo|0] x 32 for A', [hi|lo|hi|0] for B'
 constexpr int DMAX = 32;
 constexpr int STAGES = 2;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;             // 4 lane quadrants x 4 column groups of 64
+constexpr int GROUPS = EPI_WARPS / 4;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr int TMEM_COLS = 512;
 constexpr int A_TILE = BM * 128;           // bytes of one 64-column K tile of A'
@@ -57,8 +59,8 @@ struct Shared {
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
-    float na[2][BM];        // |z_c|^2 per A' slot
-    float mu_half[2][BM];   // column-half-1 partial means per slot
+    float na[2][BM];                 // |z_c|^2 per A' slot
+    float mu_part[2][GROUPS - 1][BM]; // column groups 1..3: partial means per slot
 };
 
 inline size_t smem_bytes() { return (size_t)2 * A_SLOT + (size_t)STAGES * B_STAGE + 1024 + sizeof(Shared); }
@@ -96,11 +98,14 @@ template <> struct Pack8<__nv_bfloat16> {
     }
 };
 
-__device__ __forceinline__ float matern_s2(float r2, float s2)
+// s2 (1 + sqrt5 r + 5 r^2/3) exp(-sqrt5 r) with r = sqrt.approx(r2) (0 at 0) and
+// exp via ex2.approx; c1 = s2 sqrt5, c2 = s2 5/3 are folded in by the caller.
+__device__ __forceinline__ float matern_folded(float r2, float s2, float c1, float c2)
 {
-    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
-    const float e = __expf(-2.2360680f * r);
-    return s2 * fmaf(1.6666666f, r2, fmaf(2.2360680f, r, 1.0f)) * e;
+    float r, e;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(r2));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-3.2259460f * r));  // -sqrt5 / ln 2
+    return fmaf(c2, r2, fmaf(c1, r, s2)) * e;
 }
 
 // Build A' row `r` of tile `t` into slot base `a` (128B-swizzled K-major, two 64-column tiles).
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             mbar_init(&sh->acc_empty[a], EPI_WARPS);
             mbar_init(&sh->a_full[a], 4);
             mbar_init(&sh->a_empty[a], 1 + EPI_WARPS);  // MMA commit + every epilogue warp read |z_c|^2
-            mbar_init(&sh->mu_ready[a], 4);
+            mbar_init(&sh->mu_ready[a], 4 * (GROUPS - 1));
             mbar_init(&sh->mu_free[a], 4);
         }
         mbar_init(&sh->drain, 1);
@@ -252,9 +257,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
         // ---------------- epilogue (+ A' builders in warps 2..5)
         const int ew = warp - 2;
         const int quad = warp & 3;
-        const int half = ew >> 2;
+        const int grp = ew >> 2;                // column group: 64 of the chunk's 256 columns
         const int row = quad * 32 + lane;
-        const bool builder = half == 0;
+        const bool builder = grp == 0;
+        const float s2 = P.s2, c1 = P.s2 * 2.2360680f, c2 = P.s2 * 1.6666666f;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         Out *Kst = (Out *)P.Kst;
         int acc = 0;
@@ -294,25 +300,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
-                for (int cb = 0; cb < 4; ++cb) {
+                for (int cb = 0; cb < 2; ++cb) {
                     float v[32];
-                    tmem_ld32(tmem + lane_addr + (uint32_t)(acc * BN + half * 128 + cb * 32), v);
-                    const int i0 = q * BN + half * 128 + cb * 32;
+                    tmem_ld32(tmem + lane_addr + (uint32_t)(acc * BN + grp * 64 + cb * 32), v);
+                    const int i0 = q * BN + grp * 64 + cb * 32;
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
                         const float4 nb = *reinterpret_cast<const float4 *>(P.nb + i0 + j);
                         const float4 al = *reinterpret_cast<const float4 *>(P.alpha + i0 + j);
-                        float kv[4];
-                        const float nbv[4] = {nb.x, nb.y, nb.z, nb.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float r2 = fmaxf(fmaf(-2.0f, v[j + u], na + nbv[u]), 0.0f);
-                            kv[u] = i0 + j + u < P.n ? matern_s2(r2, P.s2) : 0.0f;
-                        }
-                        mu = fmaf(kv[0], al.x, fmaf(kv[1], al.y, fmaf(kv[2], al.z, fmaf(kv[3], al.w, mu))));
-                        pk[j / 2] = Pack8<Out>::two(kv[0], kv[1]);
-                        pk[j / 2 + 1] = Pack8<Out>::two(kv[2], kv[3]);
+                        // padded observations: alpha = 0 and the 16-bit L^-1 rows are zero there,
+                        // so their (finite) K* values never reach mu or sigma
+                        const float k0 = matern_folded(fmaxf(fmaf(-2.0f, v[j], na + nb.x), 0.0f), s2, c1, c2);
+                        const float k1 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 1], na + nb.y), 0.0f), s2, c1, c2);
+                        const float k2 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 2], na + nb.z), 0.0f), s2, c1, c2);
+                        const float k3 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 3], na + nb.w), 0.0f), s2, c1, c2);
+                        mu = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mu))));
+                        pk[j / 2] = Pack8<Out>::two(k0, k1);
+                        pk[j / 2 + 1] = Pack8<Out>::two(k2, k3);
                     }
                     if (cl < P.C) {
                         uint4 *dst = reinterpret_cast<uint4 *>(Kst + cl * P.n_pad + i0);
@@ -327,18 +332,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                 if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
             }
             if (!ok) break;
-            // combine the two column halves of the mean
+            // combine the column groups' partial means (group 0 writes the result)
             const uint32_t use = (uint32_t)(k >> 1) & 1u;
             if (!builder) {
                 const bool g = mbar_wait(&sh->mu_free[slot], use ^ 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
-                sh->mu_half[slot][row] = mu;
+                sh->mu_part[slot][grp - 1][row] = mu;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->mu_ready[slot]);
             } else {
                 const bool g = mbar_wait(&sh->mu_ready[slot], use, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
-                const float m = mu + sh->mu_half[slot][row];
+                float m = mu;
+#pragma unroll
+                for (int gg = 0; gg < GROUPS - 1; ++gg) m += sh->mu_part[slot][gg][row];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->mu_free[slot]);
                 if (cl < P.C) P.mu[P.c0 + cl] = m;

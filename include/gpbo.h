@@ -105,9 +105,14 @@ int64_t gpbo_launch_count(const gpbo_ctx *ctx);
  * 3 screen).  gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
  * gpbo_trace_read synchronises, then writes for each of the first nphase phases the total
  * milliseconds, the number of timed intervals, and the algorithmic flops the phase's
- * kernels were asked to do (variance: n(n+1) per candidate; cross-kernel: 3nd + 2n). */
+ * kernels were asked to do (variance: n(n+1) per candidate; cross-kernel: 3nd + 2n;
+ * trailing updates: 2 * 64^3 per updated 64 x 64 tile). */
 int gpbo_trace_enable(gpbo_ctx *ctx, int on);
 int gpbo_trace_read(gpbo_ctx *ctx, int nphase, double *ms, int64_t *intervals, double *flops);
+/* Measured CUDA-core FMA throughput of the context's device, for roofline denominators:
+ * kind 0 = FP64 DFMA, 1 = FP32 FFMA.  Runs a short in-bounds FMA-chain kernel (about 50 ms)
+ * and writes TFLOP/s (2 flops per FMA) to *tflops.  Synchronises. */
+int gpbo_probe_fma(gpbo_ctx *ctx, int kind, double *tflops);
 /* Upper bound, in bytes, of the scratch arena the context may grow to (default 2 GiB).
  * Candidate scoring works through the pool in chunks that fit in this bound. */
 int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes);

@@ -12,6 +12,7 @@
 namespace gpbo {
 
 void fit_set_smem_limits();
+int probe_fma(gpbo_ctx *ctx, int kind, double *tflops);
 
 void note_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
@@ -296,6 +297,13 @@ int gpbo_trace_read(gpbo_ctx *ctx, int nphase, double *ms, int64_t *intervals, d
         if (flops) flops[t.phase] += t.flops;
     }
     return GPBO_OK;
+}
+
+int gpbo_probe_fma(gpbo_ctx *ctx, int kind, double *tflops)
+{
+    if (!ctx || !tflops || (kind != 0 && kind != 1)) return GPBO_EINVAL;
+    GPBO_TRY(set_device(ctx));
+    return probe_fma(ctx, kind, tflops);
 }
 
 int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes)

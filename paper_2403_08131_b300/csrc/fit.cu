@@ -525,8 +525,11 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (T > 0) {
             k_chol_panel<<<T * (NB / 16), 256, 0, st>>>(m->L, n_pad, kb, m->Dinv);
             GPBO_LAUNCH_CHECK(ctx);
-            k_chol_update<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, smem2, st>>>(m->L, n_pad, kb, nblk);
+            const int64_t tiles = (int64_t)T * (T + 1) / 2;
+            GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
+            k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk);
             GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trace_end(ctx));
         }
     }
     k_zero_upper_blocks<<<blocks_for((int64_t)n_pad * n_pad), 256, 0, st>>>(m->L, n_pad);
@@ -656,4 +659,50 @@ void fit_set_smem_limits()
     cudaFuncSetAttribute(k_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
 }
 
+// ------------------------------------------------------------------ FMA throughput probe
+// Each thread runs 8 independent FMA chains; one store per thread keeps the work alive.
+template <typename T>
+__global__ void k_fma_probe(T *out, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (T)(threadIdx.x + j);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;
+}
+
+int probe_fma(gpbo_ctx *ctx, int kind, double *tflops)
+{
+    const int blocks = ctx->sm_count * 8, threads = 256;
+    const int64_t n = (int64_t)blocks * threads;
+    const int iters = kind == 0 ? 2000 : 40000;
+    void *w = nullptr;
+    GPBO_TRY(ws_reserve(ctx, sizeof(double) * n, &w));
+    cudaEvent_t a, b;
+    GPBO_CUDA_TRY(cudaEventCreate(&a));
+    GPBO_CUDA_TRY(cudaEventCreate(&b));
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        GPBO_CUDA_TRY(cudaEventRecord(a, ctx->stream));
+        if (kind == 0) k_fma_probe<double><<<blocks, threads, 0, ctx->stream>>>((double *)w, iters, 0.999, 1e-3);
+        else k_fma_probe<float><<<blocks, threads, 0, ctx->stream>>>((float *)w, iters, 0.999f, 1e-3f);
+        GPBO_LAUNCH_CHECK(ctx);
+        GPBO_CUDA_TRY(cudaEventRecord(b, ctx->stream));
+        GPBO_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0.f;
+        GPBO_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *tflops = 2.0 * 8.0 * iters * (double)n / (best * 1e-3) / 1e12;
+    return GPBO_OK;
+}
+
 }  // namespace gpbo
+

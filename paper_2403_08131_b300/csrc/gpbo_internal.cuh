@@ -58,8 +58,8 @@ enum : unsigned {
 }  // namespace gpbo
 
 namespace gpbo {
-constexpr int TRACE_PHASES = 4;
-enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3 };
+constexpr int TRACE_PHASES = 5;
+enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3, PH_CHOL_UPDATE = 4 };
 struct TraceRec {
     int phase;
     cudaEvent_t a, b;

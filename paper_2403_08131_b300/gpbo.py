@@ -67,7 +67,8 @@ _launches = _sig("gpbo_launch_count", C.c_int64, [_P])
 _ws_limit = _sig("gpbo_set_workspace_limit", C.c_int, [_P, C.c_int64])
 _trace_en = _sig("gpbo_trace_enable", C.c_int, [_P, C.c_int])
 _trace_rd = _sig("gpbo_trace_read", C.c_int, [_P, C.c_int, _D, _L, _D])
-PHASES = ("fit", "xkern", "variance", "screen")
+PHASES = ("fit", "xkern", "variance", "screen", "chol_update")
+_probe = _sig("gpbo_probe_fma", C.c_int, [_P, C.c_int, _D])
 _fit = _sig("gp_fit", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_int, C.c_uint,
                                  C.POINTER(_P)])
 _model_free = _sig("gp_model_free", C.c_int, [_P])
@@ -157,6 +158,12 @@ class Context:
     def trace(self, on: bool):
         """Start (clearing) or stop per-phase CUDA-event timing on the context's stream."""
         check(_trace_en(self._h, 1 if on else 0), "gpbo_trace_enable")
+
+    def probe_fma(self, kind: str) -> float:
+        """Measured FMA throughput in TFLOP/s: kind "f64" (DFMA) or "f32" (FFMA)."""
+        v = C.c_double(0.0)
+        check(_probe(self._h, 0 if kind == "f64" else 1, C.byref(v)), "gpbo_probe_fma")
+        return float(v.value)
 
     def trace_read(self):
         n = len(PHASES)

@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP32 plain-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
                     help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
     return ap.parse_args()
@@ -108,6 +109,38 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows), "reasons": reasons,
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------- batched form
+def batched_form(ctx, W, dev, steps=3):
+    """64 independent sub-searches (d in U{2..12}, n in U{32..1024}, M = 16384 each, FP32
+    scoring) in one graph launch per step, against 64 sequential search_step calls."""
+    import torch
+
+    subs = W.batched_config3(G=64, M=16384)
+    probs = [dict(X=torch.from_numpy(w.X).to(dev), y=torch.from_numpy(w.y).to(dev), lengthscale=w.lengthscale,
+                  signal_var=1.0, noise_var=w.noise_var, M=16384, seed=w.seed) for w in subs]
+    ctx.search_step_batched(probs)                      # builds arenas and captures the graph
+    ctx.search_step_batched(probs)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.search_step_batched(probs)
+    torch.cuda.synchronize(dev)
+    tb = (time.perf_counter() - t0) / steps
+    for pb in probs[:2]:                                # warm the single-problem path
+        ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=16384, seed=pb["seed"], prec="f32")
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for pb in probs:
+        ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=16384, seed=pb["seed"], prec="f32")
+    torch.cuda.synchronize(dev)
+    ts = time.perf_counter() - t0
+    flops = sum(w.n * (w.n + 1) for w in subs) * 16384
+    return {"workload": "64 GPs, d in U{2..12}, n in U{32..1024}, M=16384 each, FP32 scoring, one graph launch",
+            "value": round(64 * 16384 / tb, 1), "unit": "candidates/s", "ms_per_step": round(tb * 1e3, 3),
+            "sequential_ms": round(ts * 1e3, 3), "speedup_vs_sequential": round(ts / tb, 2),
+            "variance_tflops": round(flops / tb / 1e12, 3), "timing": "host wall clock around synchronised calls"}
 
 
 # ---------------------------------------------------------------------------- ours
@@ -238,6 +271,8 @@ def run_ours(args, rank, world, local):
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "result": {"argmax": r["argmax"], "ei_max": r["ei_max"], "n_groups": g["n_groups"]},
         }
+        if not args.no_batched:
+            out["forms"] = {"batched": batched_form(ctx, W, dev)}
         if not args.no_plain and args.prec != "f32":
             pms, _, ptr, _ = timed("f32", 1, 1, trace=True)
             out["plain"] = {"value": round(M_CAND / (pms / 1e3), 1), "unit": UNIT, "dtype": "f32",

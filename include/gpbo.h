@@ -250,6 +250,24 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
                 const float *Xc, int64_t M, uint64_t seed, double xi, gpbo_prec prec, unsigned flags,
                 double *x_next, double *ei_max, int64_t *argmax);
 
+/* ------------------------------------------------------------------ batched step (§IV-D)
+ * G independent sub-searches -- the paper runs the independent and merged searches its
+ * analysis produces in parallel (§IV-D) -- each of its own dimension d[g], size n[g] and
+ * hyperparameters hyp[g], in one graph launch: every kernel of search_step covers all G
+ * problems at once, with the same device code, so problem g's result equals search_step
+ * on it bit for bit.  FP32 scoring only (GPBO_ENOTSUP otherwise); M[g] candidates are
+ * drawn on the device from seed[g].
+ *   X, y : host arrays of G pointers; the pointed-to data are device arrays (n[g] x d[g]
+ *          and n[g]) unless flags has GPBO_HOST_PTRS.
+ *   x_next : host, G x 64 doubles; row g holds the d[g] coordinates of problem g's pick.
+ *   ei_max : host, G.  argmax : host, G, may be NULL.
+ * The first call for a set of shapes (G, n, d, M, hyperparameters, xi) builds device arenas
+ * and captures the step into a CUDA graph held by the context; later calls with the same
+ * shapes copy the new X, y and seeds and replay the graph.  Synchronises. */
+int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const double *const *y, const int *n,
+                        const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
+                        gpbo_prec prec, unsigned flags, double *x_next, double *ei_max, int64_t *argmax);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,518 @@
+// Batched BO step: G independent sub-searches of uneven dimension and size in one graph
+// launch.  The paper runs the independent and merged searches that its interdependence
+// analysis produces in parallel (§IV-D, "which can be conducted in parallel"); here every
+// kernel of the step covers all G problems at once (blockIdx.y = problem), with the same
+// device bodies as the single-problem path, so each problem's results are bit-identical to
+// a search_step call on it.  The whole sequence is captured once per set of shapes into a
+// CUDA graph; later calls copy the new inputs and replay it.
+//
+// Work per step: standardise y, kernel matrix, blocked FP64 Cholesky (step k for every
+// problem with more than k blocks), refined alpha, FP32 L^-1 (one merged recursion plan),
+// FP32 cross-kernel + mean, FP32 variance + EI, per-problem argmax and x_next.
+#include "fit_kernels.cuh"
+#include "score_kernels.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace gpbo {
+
+struct BProb {
+    int n, d, n_pad, nblk;
+    int64_t M;
+    uint64_t seed;
+    double s2, sn2;
+    int64_t off_X, off_y, off_xs, off_sq, off_dinv, off_vec, off_kst, off_mu, off_part;
+    int part_count;
+};
+
+struct BatchPlan {
+    // key
+    int G = 0;
+    std::vector<int> n, d;
+    std::vector<int64_t> M;
+    std::vector<double> key_hyp;
+    double xi = 0.0;     // baked into the captured graph
+    // arenas
+    BProb *probs_dev = nullptr;
+    std::vector<BProb> probs;
+    double *dX = nullptr, *dy = nullptr, *dys = nullptr, *tau = nullptr;
+    double *Xs64 = nullptr, *K = nullptr, *L = nullptr, *Dinv = nullptr, *vec = nullptr, *lsinv = nullptr;
+    float *Xs32 = nullptr, *alpha32 = nullptr, *L32 = nullptr, *Linv32 = nullptr, *tmp = nullptr, *Kst = nullptr;
+    float *mu = nullptr, *pei = nullptr;
+    int64_t *pidx = nullptr;
+    double *best_ei = nullptr;
+    int64_t *best_idx = nullptr;
+    float *xnext = nullptr;
+    GemmProb *gemm_dev = nullptr;
+    std::vector<int> lvl_first, lvl_count;
+    std::vector<int2> lvl_mm;
+    int64_t sum_vec = 0;
+    int max_npad = 0, max_nblk = 0, max_tiles64 = 0;
+    int64_t max_sq = 0, max_dn = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void *> allocs;
+};
+
+// ------------------------------------------------------------------ batched kernels
+__device__ __forceinline__ Lengthscales_inv ls_of(const double *lsinv, int g, int d)
+{
+    Lengthscales_inv ls;
+    for (int k = 0; k < d; ++k) ls.inv[k] = lsinv[g * GPBO_MAX_D + k];
+    return ls;
+}
+
+__global__ void __launch_bounds__(1024) b_standardize(const BProb *P, const double *y, double *ys, double *tau)
+{
+    const BProb &p = P[blockIdx.x];
+    k_standardize_body(y + p.off_y, p.n, ys + p.off_y, tau + blockIdx.x, 0, 0);
+}
+
+__global__ void b_scale_x(const BProb *P, const double *X, const double *lsinv, double *Xs64, float *Xs32)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.d * p.n_pad) return;
+    k_scale_x_body(X + p.off_X, p.n, p.d, p.n_pad, ls_of(lsinv, blockIdx.y, p.d), Xs64 + p.off_xs, Xs32 + p.off_xs,
+                   blockIdx.x, 0);
+}
+
+__global__ void b_kmat(const BProb *P, const double *Xs64, double *K)
+{
+    const BProb &p = P[blockIdx.z];
+    const int nt = p.n_pad / 32;
+    if ((int)blockIdx.x >= nt || (int)blockIdx.y >= nt) return;
+    k_kmat_body(Xs64 + p.off_xs, p.n, p.d, p.n_pad, p.s2, p.sn2, K + p.off_sq, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) b_chol_diag(const BProb *P, double *L, double *Dinv, int kb, unsigned *status)
+{
+    const BProb &p = P[blockIdx.y];
+    if (kb >= p.nblk) return;
+    k_chol_diag_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, status, 0, 0);
+}
+
+__global__ void __launch_bounds__(256) b_chol_panel(const BProb *P, double *L, const double *Dinv, int kb)
+{
+    const BProb &p = P[blockIdx.y];
+    const int T = p.nblk - kb - 1;
+    if (T <= 0 || (int)blockIdx.x >= T * (NB / 16)) return;
+    k_chol_panel_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x, 0);
+}
+
+__global__ void __launch_bounds__(256) b_chol_update(const BProb *P, double *L, int kb)
+{
+    const BProb &p = P[blockIdx.y];
+    const int T = p.nblk - kb - 1;
+    if (T <= 0 || (int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
+    k_chol_update_body(L + p.off_sq, p.n_pad, kb, p.nblk, blockIdx.x, 0);
+}
+
+__global__ void b_zero_upper(const BProb *P, double *L)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
+    k_zero_upper_blocks_body(L + p.off_sq, p.n_pad, blockIdx.x, 0);
+}
+
+// vec arena per problem: [alpha64 | ypad | work (2 n_pad) | r | dlt]
+__global__ void b_pad_copy(const BProb *P, const double *ys, double *vec)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int)(blockIdx.x * blockDim.x) >= p.n_pad) return;
+    k_pad_copy_body(ys + p.off_y, p.n, p.n_pad, vec + p.off_vec + p.n_pad, blockIdx.x, 0);
+}
+
+__global__ void b_copy_vec(const BProb *P, double *vec, int src_slot, int dst_slot)
+{
+    const BProb &p = P[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n_pad) vec[p.off_vec + (int64_t)dst_slot * p.n_pad + i] = vec[p.off_vec + (int64_t)src_slot * p.n_pad + i];
+}
+
+__global__ void __launch_bounds__(256) b_fwd_step(const BProb *P, const double *L, const double *Dinv, double *vec,
+                                                  int b)
+{
+    const BProb &p = P[blockIdx.y];
+    if (b >= p.nblk || (int)blockIdx.x >= max(1, p.nblk - b - 1)) return;
+    double *work = vec + p.off_vec + 2 * (int64_t)p.n_pad;
+    k_fwd_step_body(L + p.off_sq, Dinv + p.off_dinv, p.n_pad, b, work, work + p.n_pad, blockIdx.x, 0);
+}
+
+__global__ void __launch_bounds__(256) b_bwd_step(const BProb *P, const double *L, const double *Dinv, double *vec,
+                                                  int s, int out_slot)
+{
+    const BProb &p = P[blockIdx.y];
+    const int b = p.nblk - 1 - s;
+    if (b < 0 || (int)blockIdx.x >= max(1, b)) return;
+    double *work = vec + p.off_vec + 2 * (int64_t)p.n_pad;
+    k_bwd_step_body(L + p.off_sq, Dinv + p.off_dinv, p.n_pad, b, work + p.n_pad,
+                    vec + p.off_vec + (int64_t)out_slot * p.n_pad, blockIdx.x, 0);
+}
+
+__global__ void b_residual(const BProb *P, const double *K, double *vec)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int)(blockIdx.x * (blockDim.x / 32)) >= p.n_pad) return;
+    double *v = vec + p.off_vec;
+    k_residual_body(K + p.off_sq, v, v + p.n_pad, p.n_pad, v + 4 * (int64_t)p.n_pad, blockIdx.x, 0);
+}
+
+__global__ void b_axpy_cast(const BProb *P, double *vec, float *alpha32)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int)(blockIdx.x * blockDim.x) >= p.n_pad) return;
+    double *v = vec + p.off_vec;
+    k_axpy_cast_body(v, v + 5 * (int64_t)p.n_pad, p.n_pad, alpha32 + p.off_vec / 6, blockIdx.x, 0);
+}
+
+__global__ void b_cast_L(const BProb *P, const double *L, float *L32)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
+    k_cast_body<double, float>(L + p.off_sq, (int64_t)p.n_pad * p.n_pad, L32 + p.off_sq, blockIdx.x, 0);
+}
+
+__global__ void b_linv_init(const BProb *P, const double *Dinv, float *Linv)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
+    k_linv_init_body<float>(Dinv + p.off_dinv, p.n_pad, Linv + p.off_sq, blockIdx.x, 0);
+}
+
+// The recursion's GEMMs: problems in blockIdx.z, shared body with the single-problem path.
+__global__ void __launch_bounds__(256) b_gemm(const float *A, const float *B, float *Cc, const GemmProb *probs, float alpha,
+                                              int tri_a, int tri_b)
+{
+    k_gemm_batched_body<float>(A, B, Cc, 0, 0, 0, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) b_xkern(const BProb *P, const float *Xs32, const float *alpha32, const double *lsinv,
+                                               float *Kst, float *mu)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * 64 >= p.M) return;
+    k_xkern32_body<float>(nullptr, p.seed, 0, p.M, p.d, Xs32 + p.off_xs, alpha32 + p.off_vec / 6, p.n, p.n_pad,
+                          (float)p.s2, ls_of(lsinv, blockIdx.y, p.d), Kst + p.off_kst, mu + p.off_mu, blockIdx.x, 0, 0);
+}
+
+__global__ void __launch_bounds__(256) b_var(const BProb *P, const float *Kst, const float *Linv, const float *mu,
+                                             const double *tau, float xi, float *pei, int64_t *pidx)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int64_t)blockIdx.x * 64 >= p.M) return;
+    k_var_simt_body<float>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
+                           tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0, blockIdx.x,
+                           0, 0);
+}
+
+__global__ void __launch_bounds__(1024) b_argmax(const BProb *P, const float *pei, const int64_t *pidx, double *best_ei,
+                                                 int64_t *best_idx)
+{
+    const BProb &p = P[blockIdx.x];
+    k_argmax_final_body<float>(pei + p.off_part, pidx + p.off_part, p.part_count, best_ei + blockIdx.x,
+                               best_idx + blockIdx.x, 0, 0, 0);
+}
+
+// x_next of problem g: its argmax candidate, redrawn from the counter stream.
+__global__ void b_gather(const BProb *P, const int64_t *best_idx, float *xnext)
+{
+    const BProb &p = P[blockIdx.x];
+    const int k = threadIdx.x;
+    if (k < p.d) xnext[blockIdx.x * GPBO_MAX_D + k] = uniform24f(p.seed, 2, (uint64_t)(best_idx[blockIdx.x] * p.d + k));
+}
+
+// ------------------------------------------------------------------ plan
+static void free_plan(BatchPlan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    for (void *p : pl->allocs) cudaFree(p);
+    delete pl;
+}
+
+template <typename T>
+static int arena(BatchPlan *pl, T **out, int64_t count)
+{
+    void *p = nullptr;
+    GPBO_CUDA_TRY(cudaMalloc(&p, sizeof(T) * std::max<int64_t>(count, 1)));
+    pl->allocs.push_back(p);
+    *out = (T *)p;
+    return GPBO_OK;
+}
+
+static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
+{
+    const int G = pl->G;
+    pl->probs.resize(G);
+    int64_t sX = 0, sy = 0, sxs = 0, ssq = 0, sdinv = 0, svec = 0, skst = 0, smu = 0, spart = 0;
+    std::vector<double> lsinv((size_t)G * GPBO_MAX_D, 0.0);
+    for (int g = 0; g < G; ++g) {
+        BProb &p = pl->probs[g];
+        p.n = pl->n[g];
+        p.d = pl->d[g];
+        p.n_pad = round_up(p.n, NB);
+        p.nblk = p.n_pad / NB;
+        p.M = pl->M[g];
+        p.seed = 0;
+        p.s2 = hyp[g].signal_var;
+        p.sn2 = hyp[g].noise_var;
+        for (int k = 0; k < p.d; ++k) lsinv[(size_t)g * GPBO_MAX_D + k] = 1.0 / hyp[g].lengthscale[k];
+        p.off_X = sX;     sX += (int64_t)p.n * p.d;
+        p.off_y = sy;     sy += p.n;
+        p.off_xs = sxs;   sxs += (int64_t)p.d * p.n_pad;
+        p.off_sq = ssq;   ssq += (int64_t)p.n_pad * p.n_pad;
+        p.off_dinv = sdinv; sdinv += (int64_t)p.n_pad * NB;
+        p.off_vec = svec; svec += 6 * (int64_t)p.n_pad;
+        p.off_kst = skst; skst += p.M * p.n_pad;
+        p.off_mu = smu;   smu += p.M;
+        p.part_count = (int)cdiv64(p.M, 64);
+        p.off_part = spart; spart += p.part_count;
+        pl->max_npad = std::max(pl->max_npad, p.n_pad);
+        pl->max_nblk = std::max(pl->max_nblk, p.nblk);
+        pl->max_tiles64 = std::max<int>(pl->max_tiles64, (int)cdiv64(p.M, 64));
+        pl->max_sq = std::max<int64_t>(pl->max_sq, (int64_t)p.n_pad * p.n_pad);
+        pl->max_dn = std::max<int64_t>(pl->max_dn, (int64_t)p.d * p.n_pad);
+    }
+    // alpha32 shares the vec offsets divided by 6 (one float per padded row)
+    GPBO_TRY(arena(pl, &pl->probs_dev, G));
+    GPBO_TRY(arena(pl, &pl->dX, sX));
+    GPBO_TRY(arena(pl, &pl->dy, sy));
+    GPBO_TRY(arena(pl, &pl->dys, sy));
+    GPBO_TRY(arena(pl, &pl->tau, G));
+    GPBO_TRY(arena(pl, &pl->Xs64, sxs));
+    GPBO_TRY(arena(pl, &pl->Xs32, sxs));
+    GPBO_TRY(arena(pl, &pl->K, ssq));
+    GPBO_TRY(arena(pl, &pl->L, ssq));
+    GPBO_TRY(arena(pl, &pl->Dinv, sdinv));
+    GPBO_TRY(arena(pl, &pl->vec, svec));
+    GPBO_TRY(arena(pl, &pl->alpha32, svec / 6));
+    GPBO_TRY(arena(pl, &pl->lsinv, (int64_t)G * GPBO_MAX_D));
+    GPBO_TRY(arena(pl, &pl->L32, ssq));
+    GPBO_TRY(arena(pl, &pl->Linv32, ssq));
+    GPBO_TRY(arena(pl, &pl->tmp, ssq));
+    GPBO_TRY(arena(pl, &pl->Kst, skst));
+    GPBO_TRY(arena(pl, &pl->mu, smu));
+    GPBO_TRY(arena(pl, &pl->pei, spart));
+    GPBO_TRY(arena(pl, &pl->pidx, spart));
+    GPBO_TRY(arena(pl, &pl->best_ei, G));
+    GPBO_TRY(arena(pl, &pl->best_idx, G));
+    GPBO_TRY(arena(pl, &pl->xnext, (int64_t)G * GPBO_MAX_D));
+    GPBO_CUDA_TRY(cudaMemcpy(pl->lsinv, lsinv.data(), sizeof(double) * lsinv.size(), cudaMemcpyHostToDevice));
+    // merged triangular-inverse plan: level l gathers every problem's runs of 2^l blocks
+    std::vector<GemmProb> all;
+    for (int run = 1; run < pl->max_nblk; run *= 2) {
+        std::vector<GemmProb> first, second;
+        int maxm = 0, maxn = 0;
+        for (int g = 0; g < G; ++g) {
+            const BProb &p = pl->probs[g];
+            for (int b0 = 0; b0 + run < p.nblk; b0 += 2 * run) {
+                const int r0 = (b0 + run) * NB, sl = run * NB, sr = std::min(run, p.nblk - b0 - run) * NB;
+                GemmProb q;
+                q.a_off = p.off_sq + (int64_t)r0 * p.n_pad + (int64_t)b0 * NB;
+                q.b_off = p.off_sq + (int64_t)b0 * NB * p.n_pad + (int64_t)b0 * NB;
+                q.c_off = q.a_off;
+                q.m = sr;
+                q.n = sl;
+                q.k = sl;
+                q.ld = p.n_pad;
+                first.push_back(q);
+                GemmProb q2 = q;
+                q2.b_off = q.c_off;
+                q2.a_off = p.off_sq + (int64_t)r0 * p.n_pad + r0;
+                q2.k = sr;
+                second.push_back(q2);
+                maxm = std::max(maxm, sr);
+                maxn = std::max(maxn, sl);
+            }
+        }
+        if (first.empty()) continue;
+        pl->lvl_first.push_back((int)all.size());
+        pl->lvl_count.push_back((int)first.size());
+        pl->lvl_mm.push_back(make_int2(maxm, maxn));
+        all.insert(all.end(), first.begin(), first.end());
+        all.insert(all.end(), second.begin(), second.end());
+    }
+    GPBO_TRY(arena(pl, &pl->gemm_dev, (int64_t)all.size()));
+    if (!all.empty())
+        GPBO_CUDA_TRY(cudaMemcpy(pl->gemm_dev, all.data(), sizeof(GemmProb) * all.size(), cudaMemcpyHostToDevice));
+    GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
+    return GPBO_OK;
+}
+
+static unsigned gb(int64_t count, int threads = 256) { return (unsigned)std::max<int64_t>(1, cdiv64(count, threads)); }
+
+// The batched step's kernels, in order, on stream st (captured into the plan's graph).
+static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
+{
+    const int G = pl->G;
+    const BProb *P = pl->probs_dev;
+    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1);
+    b_standardize<<<G, 1024, 0, st>>>(P, pl->dy, pl->dys, pl->tau);
+    b_scale_x<<<dim3(gb(pl->max_dn), G), 256, 0, st>>>(P, pl->dX, pl->lsinv, pl->Xs64, pl->Xs32);
+    b_kmat<<<dim3(pl->max_npad / 32, pl->max_npad / 32, G), dim3(32, 8), 0, st>>>(P, pl->Xs64, pl->K);
+    GPBO_CUDA_TRY(cudaMemcpyAsync(pl->L, pl->K, sizeof(double) * (size_t)(pl->probs.back().off_sq + pl->probs.back().n_pad *
+                                  (int64_t)pl->probs.back().n_pad), cudaMemcpyDeviceToDevice, st));
+    for (int kb = 0; kb < pl->max_nblk; ++kb) {
+        b_chol_diag<<<dim3(1, G), 256, smem2, st>>>(P, pl->L, pl->Dinv, kb, ctx->dev_status);
+        const int T = pl->max_nblk - kb - 1;
+        if (T > 0) {
+            b_chol_panel<<<dim3(T * (NB / 16), G), 256, 0, st>>>(P, pl->L, pl->Dinv, kb);
+            b_chol_update<<<dim3((unsigned)((int64_t)T * (T + 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb);
+        }
+    }
+    b_zero_upper<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L);
+    // alpha = K^-1 y' with one refinement step; vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 dlt
+    b_pad_copy<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->dys, pl->vec);
+    for (int pass = 0; pass < 2; ++pass) {
+        b_copy_vec<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->vec, pass == 0 ? 1 : 4, 2);
+        for (int b = 0; b < pl->max_nblk; ++b)
+            b_fwd_step<<<dim3(std::max(1, pl->max_nblk - b - 1), G), 256, 0, st>>>(P, pl->L, pl->Dinv, pl->vec, b);
+        for (int s = 0; s < pl->max_nblk; ++s)
+            b_bwd_step<<<dim3(std::max(1, pl->max_nblk - 1 - s), G), 256, 0, st>>>(P, pl->L, pl->Dinv, pl->vec, s,
+                                                                                 pass == 0 ? 0 : 5);
+        if (pass == 0) b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, st>>>(P, pl->K, pl->vec);
+    }
+    b_axpy_cast<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->vec, pl->alpha32);
+    // FP32 L^-1
+    b_cast_L<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L, pl->L32);
+    b_linv_init<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->Dinv, pl->Linv32);
+    for (size_t l = 0; l < pl->lvl_first.size(); ++l) {
+        dim3 grid((pl->lvl_mm[l].y + 63) / 64, (pl->lvl_mm[l].x + 63) / 64, pl->lvl_count[l]);
+        b_gemm<<<grid, 256, 0, st>>>(pl->L32, pl->Linv32, pl->tmp, pl->gemm_dev + pl->lvl_first[l], 1.0f, 0, 1);
+        b_gemm<<<grid, 256, 0, st>>>(pl->Linv32, pl->tmp, pl->Linv32, pl->gemm_dev + pl->lvl_first[l] + pl->lvl_count[l],
+                                     -1.0f, 1, 0);
+    }
+    // scoring
+    b_xkern<<<dim3(pl->max_tiles64, G), 256, sizeof(float) * 64 * GPBO_MAX_D, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,
+                                                                                    pl->Kst, pl->mu);
+    b_var<<<dim3(pl->max_tiles64, G), 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    b_argmax<<<G, 1024, 0, st>>>(P, pl->pei, pl->pidx, pl->best_ei, pl->best_idx);
+    b_gather<<<G, GPBO_MAX_D, 0, st>>>(P, pl->best_idx, pl->xnext);
+    GPBO_CUDA_TRY(cudaGetLastError());
+    return GPBO_OK;
+}
+
+// Kernels one graph replay launches (for launch accounting).
+static int64_t plan_launches(const BatchPlan *pl)
+{
+    int64_t k = 3 + 1;  // standardise, scale, kmat, + (memcpy node not counted) zero_upper
+    for (int kb = 0; kb < pl->max_nblk; ++kb) k += (pl->max_nblk - kb - 1 > 0) ? 3 : 1;
+    k += 1 + 2 * (1 + 2 * (int64_t)pl->max_nblk) + 1 + 1;  // pad, passes, residual, axpy
+    k += 2 + 2 * (int64_t)pl->lvl_first.size() + 4;
+    return k;
+}
+
+static bool same_key(const BatchPlan *pl, int G, const int *n, const int *d, const int64_t *M, const gp_hyper *hyp,
+                     double xi)
+{
+    if (!pl || pl->G != G || pl->xi != xi) return false;
+    std::vector<double> kh;
+    for (int g = 0; g < G; ++g) {
+        if (pl->n[g] != n[g] || pl->d[g] != d[g] || pl->M[g] != M[g]) return false;
+        kh.push_back(hyp[g].signal_var);
+        kh.push_back(hyp[g].noise_var);
+        for (int k = 0; k < d[g]; ++k) kh.push_back(hyp[g].lengthscale[k]);
+    }
+    return kh == pl->key_hyp;
+}
+
+}  // namespace gpbo
+
+using namespace gpbo;
+
+static BatchPlan *g_last_plan_for_ctx(gpbo_ctx *ctx) { return (BatchPlan *)ctx->batch_plan; }
+
+extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const double *const *y, const int *n,
+                                   const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
+                                   gpbo_prec prec, unsigned flags, double *x_next, double *ei_max, int64_t *argmax)
+{
+    if (!ctx || G < 1 || G > 4096 || !X || !y || !n || !d || !hyp || !M || !seed || !x_next || !ei_max) return GPBO_EINVAL;
+    if (prec != GPBO_PREC_F32) return GPBO_ENOTSUP;
+    for (int g = 0; g < G; ++g) {
+        if (!X[g] || !y[g] || n[g] < 1 || n[g] > GPBO_MAX_N || d[g] < 1 || d[g] > GPBO_MAX_D || M[g] < 1 ||
+            M[g] > 0x7fffffffll || hyp[g].d != d[g] || !hyp[g].lengthscale || !(hyp[g].signal_var > 0) ||
+            !(hyp[g].noise_var >= 0))
+            return GPBO_EINVAL;
+        for (int k = 0; k < d[g]; ++k)
+            if (!(hyp[g].lengthscale[k] > 0)) return GPBO_EINVAL;
+    }
+    GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
+    BatchPlan *pl = g_last_plan_for_ctx(ctx);
+    if (!same_key(pl, G, n, d, M, hyp, xi)) {
+        cudaStreamSynchronize(ctx->stream);
+        free_plan(pl);
+        ctx->batch_plan = nullptr;
+        pl = new BatchPlan();
+        pl->G = G;
+        pl->xi = xi;
+        pl->n.assign(n, n + G);
+        pl->d.assign(d, d + G);
+        pl->M.assign(M, M + G);
+        for (int g = 0; g < G; ++g) {
+            pl->key_hyp.push_back(hyp[g].signal_var);
+            pl->key_hyp.push_back(hyp[g].noise_var);
+            for (int k = 0; k < d[g]; ++k) pl->key_hyp.push_back(hyp[g].lengthscale[k]);
+        }
+        int st = build_plan(ctx, pl, hyp);
+        if (st != GPBO_OK) {
+            free_plan(pl);
+            return st;
+        }
+        ctx->batch_plan = pl;
+    }
+    // this call's inputs and seeds
+    const cudaMemcpyKind kind = (flags & GPBO_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int g = 0; g < G; ++g) {
+        BProb &p = pl->probs[g];
+        p.seed = seed[g];
+        GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dX + p.off_X, X[g], sizeof(double) * p.n * p.d, kind, ctx->stream));
+        GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dy + p.off_y, y[g], sizeof(double) * p.n, kind, ctx->stream));
+    }
+    GPBO_CUDA_TRY(cudaMemcpyAsync(pl->probs_dev, pl->probs.data(), sizeof(BProb) * G, cudaMemcpyHostToDevice, ctx->stream));
+    if (!pl->exec) {
+        // capture the step once; the probe table and arenas keep their addresses from here on
+        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * 2 * NB * (NB + 1))));
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * 2 * NB * (NB + 1))));
+        GPBO_CUDA_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+        int st = enqueue_step(ctx, pl, pl->cap, (float)xi);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(pl->cap, &graph);
+        if (st != GPBO_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            note_cuda_error(e, "batched capture", __FILE__, __LINE__);
+            return st != GPBO_OK ? st : GPBO_ECUDA;
+        }
+        pl->graph = graph;
+        GPBO_CUDA_TRY(cudaGraphInstantiate(&pl->exec, graph, 0));
+    }
+    GPBO_CUDA_TRY(cudaGraphLaunch(pl->exec, ctx->stream));
+    ctx->launches += plan_launches(pl);
+    std::vector<double> be(G);
+    std::vector<int64_t> bi(G);
+    std::vector<float> xn((size_t)G * GPBO_MAX_D);
+    GPBO_CUDA_TRY(cudaMemcpyAsync(be.data(), pl->best_ei, sizeof(double) * G, cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(bi.data(), pl->best_idx, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(xn.data(), pl->xnext, sizeof(float) * xn.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    unsigned bits = 0;
+    GPBO_TRY(take_device_status(ctx, &bits));
+    if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
+    for (int g = 0; g < G; ++g) {
+        ei_max[g] = be[g];
+        if (argmax) argmax[g] = bi[g];
+        for (int k = 0; k < GPBO_MAX_D; ++k) x_next[(size_t)g * GPBO_MAX_D + k] = k < d[g] ? (double)xn[(size_t)g * GPBO_MAX_D + k] : 0.0;
+    }
+    return GPBO_OK;
+}
+
+namespace gpbo {
+void batch_plan_free(void *p) { free_plan((BatchPlan *)p); }
+}  // namespace gpbo

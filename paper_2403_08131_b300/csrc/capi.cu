@@ -49,9 +49,12 @@ int take_device_status(gpbo_ctx *ctx, unsigned *bits_out)
     return GPBO_OK;
 }
 
+// Trace intervals may nest (the Cholesky updates inside the fit): begin takes the next
+// record and pushes its index, end pops it.
 int trace_begin(gpbo_ctx *ctx, int phase, double flops)
 {
     if (!ctx->trace) return GPBO_OK;
+    if (ctx->trace_depth >= (int)(sizeof(ctx->trace_stack) / sizeof(ctx->trace_stack[0]))) return GPBO_EINVAL;
     if (ctx->trace_n == ctx->trace_cap) {
         int cap = ctx->trace_cap ? ctx->trace_cap * 2 : 256;
         TraceRec *r = (TraceRec *)realloc(ctx->trace_recs, sizeof(TraceRec) * cap);
@@ -62,11 +65,13 @@ int trace_begin(gpbo_ctx *ctx, int phase, double flops)
         ctx->trace_recs = r;
         ctx->trace_cap = cap;
     }
-    TraceRec &t = ctx->trace_recs[ctx->trace_n];
+    const int idx = ctx->trace_n++;
+    TraceRec &t = ctx->trace_recs[idx];
     if (!t.a) GPBO_CUDA_TRY(cudaEventCreate(&t.a));
     if (!t.b) GPBO_CUDA_TRY(cudaEventCreate(&t.b));
     t.phase = phase;
     t.flops = flops;
+    ctx->trace_stack[ctx->trace_depth++] = idx;
     GPBO_CUDA_TRY(cudaEventRecord(t.a, ctx->stream));
     return GPBO_OK;
 }
@@ -74,8 +79,9 @@ int trace_begin(gpbo_ctx *ctx, int phase, double flops)
 int trace_end(gpbo_ctx *ctx)
 {
     if (!ctx->trace) return GPBO_OK;
-    GPBO_CUDA_TRY(cudaEventRecord(ctx->trace_recs[ctx->trace_n].b, ctx->stream));
-    ctx->trace_n++;
+    if (ctx->trace_depth <= 0) return GPBO_EINVAL;
+    const int idx = ctx->trace_stack[--ctx->trace_depth];
+    GPBO_CUDA_TRY(cudaEventRecord(ctx->trace_recs[idx].b, ctx->stream));
     return GPBO_OK;
 }
 
@@ -236,6 +242,7 @@ int gpbo_destroy(gpbo_ctx *ctx)
     if (!ctx) return GPBO_EINVAL;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->batch_plan) batch_plan_free(ctx->batch_plan);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dev_status) cudaFree(ctx->dev_status);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -274,6 +281,7 @@ int gpbo_trace_enable(gpbo_ctx *ctx, int on)
     if (!ctx) return GPBO_EINVAL;
     ctx->trace = on != 0;
     if (on) ctx->trace_n = 0;
+    ctx->trace_depth = 0;
     return GPBO_OK;
 }
 

@@ -11,7 +11,7 @@
 // Padding: n is padded to n_pad (a multiple of 64, or of 256 for tensor-core models).
 // Padded rows/columns of K are the identity, so L and L^-1 are the identity there, the
 // padded right-hand side is zero, and alpha is zero there.  No kernel needs a ragged tail.
-#include "gpbo_internal.cuh"
+#include "fit_kernels.cuh"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -21,296 +21,68 @@
 
 namespace gpbo {
 
-// ------------------------------------------------------------------ inputs
-// Xs64[k][i] = X[i][k] / l_k for i < n, 0 for padding; Xs32 is its FP32 rounding.
+// Single-problem kernels: thin wrappers over the bodies in fit_kernels.cuh.
 __global__ void k_scale_x(const double *__restrict__ X, int n, int d, int n_pad, Lengthscales_inv ls,
                           double *__restrict__ Xs64, float *__restrict__ Xs32)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)d * n_pad) return;
-    int k = (int)(t / n_pad), i = (int)(t % n_pad);
-    double v = i < n ? X[(int64_t)i * d + k] * ls.inv[k] : 0.0;
-    Xs64[t] = v;
-    if (Xs32) Xs32[t] = (float)v;
+    k_scale_x_body(X, n, d, n_pad, ls, Xs64, Xs32, blockIdx.x, blockIdx.y);
 }
 
-// K_ij = s2 m(r_ij) + sn2 [i == j] over the real block, identity on the padding.  Each
-// thread of the lower half (i >= j, by 32 x 32 tiles) writes K_ij and its mirror K_ji.
 __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, double s2, double sn2,
                        double *__restrict__ K)
 {
-    const int tj = blockIdx.x, ti = blockIdx.y;
-    if (tj > ti) return;
-    __shared__ double tile[32][33];
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int i = ti * 32 + r, j = tj * 32 + threadIdx.x;
-        double v;
-        if (i < n && j < n) {
-            double r2 = 0.0;
-            for (int k = 0; k < d; ++k) {
-                double t = Xs[(int64_t)k * n_pad + i] - Xs[(int64_t)k * n_pad + j];
-                r2 = fma(t, t, r2);
-            }
-            v = s2 * matern52_r2(r2) + (i == j ? sn2 : 0.0);
-        } else {
-            v = i == j ? 1.0 : 0.0;
-        }
-        K[(int64_t)i * n_pad + j] = v;
-        tile[r][threadIdx.x] = v;
-    }
-    if (ti == tj) return;
-    __syncthreads();
-    // mirror: K[j][i] for the transposed tile, coalesced along i
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int j = tj * 32 + r, i = ti * 32 + threadIdx.x;
-        K[(int64_t)j * n_pad + i] = tile[threadIdx.x][r];
-    }
+    k_kmat_body(Xs, n, d, n_pad, s2, sn2, K, blockIdx.x, blockIdx.y);
 }
 
-// ------------------------------------------------------------------ Cholesky
-// Diagonal block k: unblocked right-looking factorisation in shared memory, then the
-// inverse of the factor (column j solves L x = e_j).  Writes L_kk (zeros above) and Dinv_k.
-// Pivots use one reciprocal square root: L_jj = p * rsqrt(p), 1/L_jj = rsqrt(p), so the
-// column scaling and the inverse multiply instead of divide.  The inverse gives each
-// column four threads (a lane quad) that split every dot product and combine by shuffles.
 __global__ void __launch_bounds__(256) k_chol_diag(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status)
 {
-    extern __shared__ double sm[];
-    double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    double(*inv)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
-    __shared__ double rdiag[NB];
-    const int tid = threadIdx.x;
-    const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = A[base + (int64_t)(e / NB) * n_pad + e % NB];
-    for (int j = 0; j < NB; ++j) {
-        __syncthreads();
-        if (tid == 0) {
-            double p = a[j][j];
-            if (!(p > 0.0)) {
-                atomicOr(status, DEV_NOTSPD);
-                p = 1.0;
-            }
-            const double r = rsqrt(p);
-            a[j][j] = p * r;
-            rdiag[j] = r;
-        }
-        __syncthreads();
-        const double r = rdiag[j];
-        for (int i = j + 1 + tid; i < NB; i += blockDim.x) a[i][j] *= r;
-        __syncthreads();
-        const int cnt = NB - 1 - j;
-        for (int e = tid; e < cnt * cnt; e += blockDim.x) {
-            int i = j + 1 + e / cnt, c = j + 1 + e % cnt;
-            if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-        }
-    }
-    __syncthreads();
-    {
-        const int j = tid >> 2, sub = tid & 3;
-        const unsigned mask = 0xFu << (threadIdx.x & 28);
-        for (int i = sub; i < j; i += 4) inv[i][j] = 0.0;
-        if (sub == 0) inv[j][j] = rdiag[j];
-        __syncwarp(mask);
-        for (int i = j + 1; i < NB; ++i) {
-            double s = 0.0;
-            for (int t = j + sub; t < i; t += 4) s = fma(a[i][t], inv[t][j], s);
-            s += __shfl_xor_sync(mask, s, 1);
-            s += __shfl_xor_sync(mask, s, 2);
-            if (sub == 0) inv[i][j] = -s * rdiag[i];
-            __syncwarp(mask);
-        }
-    }
-    __syncthreads();
-    double *D = Dinv + (int64_t)kb * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, c = e % NB;
-        A[base + (int64_t)i * n_pad + c] = c <= i ? a[i][c] : 0.0;
-        D[e] = inv[i][c];
-    }
+    k_chol_diag_body(A, n_pad, kb, Dinv, status, blockIdx.x, blockIdx.y);
 }
 
-// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, one CTA per 16-row slab so that
-// the short panels at the end of the factorisation still spread over many SMs.
 __global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv)
 {
-    __shared__ double a[16][NB + 1];
-    __shared__ double dv[NB][NB + 1];
-    const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)blockIdx.x * 16;
-    const int tid = threadIdx.x, tx = tid % 64, ty = tid / 64;
-    const double *D = Dinv + (int64_t)kb * NB * NB;
-    for (int e = tid; e < 16 * NB; e += blockDim.x)
-        a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
-    for (int e = tid; e < NB * NB; e += blockDim.x) dv[e / NB][e % NB] = D[e];
-    __syncthreads();
-    // thread (ty, tx): rows ty, ty+4, ty+8, ty+12; column tx; L_kk^-T is lower, so t <= tx
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = 0; t <= tx; ++t) {
-        const double y = dv[tx][t];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(a[ty + 4 * u][t], y, acc[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) A[(row0 + ty + 4 * u) * n_pad + (int64_t)kb * NB + tx] = acc[u];
+    k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y);
 }
 
-// Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.
 __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int n_pad, int kb, int nblk)
 {
-    extern __shared__ double sm[];
-    double(*li)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    double(*lj)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
-    const int64_t p = blockIdx.x;
-    int ii = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= p) ++ii;
-    while ((int64_t)ii * (ii + 1) / 2 > p) --ii;
-    const int jj = (int)(p - (int64_t)ii * (ii + 1) / 2);
-    const int ib = kb + 1 + ii, jb = kb + 1 + jj;
-    if (ib >= nblk || jb > ib) return;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int64_t bi = (int64_t)ib * NB * n_pad + (int64_t)kb * NB;
-    const int64_t bj = (int64_t)jb * NB * n_pad + (int64_t)kb * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int r = e / NB, c = e % NB;
-        li[r][c] = A[bi + (int64_t)r * n_pad + c];
-        lj[r][c] = A[bj + (int64_t)r * n_pad + c];
-    }
-    __syncthreads();
-    double acc[4][4] = {};
-    for (int t = 0; t < NB; ++t) {
-        double x[4], y[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { x[u] = li[ty + 16 * u][t]; y[u] = lj[tx + 16 * u][t]; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-    }
-    const int64_t bo = (int64_t)ib * NB * n_pad + (int64_t)jb * NB;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) A[bo + (int64_t)(ty + 16 * u) * n_pad + tx + 16 * v] -= acc[u][v];
+    k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y);
 }
 
-// Zero the strictly upper blocks (they still hold K after the in-place factorisation).
 __global__ void k_zero_upper_blocks(double *__restrict__ A, int n_pad)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n_pad * n_pad) return;
-    int i = (int)(t / n_pad), j = (int)(t % n_pad);
-    if (j / NB > i / NB) A[t] = 0.0;
+    k_zero_upper_blocks_body(A, n_pad, blockIdx.x, blockIdx.y);
 }
 
-// ------------------------------------------------------------------ triangular solves
-// Forward step b of L z = w: z_b = Dinv_b w_b (every CTA recomputes it), CTA 0 stores it,
-// and each CTA updates one later block of w: w_r -= L_rb z_b.
 __global__ void __launch_bounds__(256) k_fwd_step(const double *__restrict__ L, const double *__restrict__ Dinv,
                                                   int n_pad, int b, double *__restrict__ w, double *__restrict__ z)
 {
-    __shared__ double wb[NB], zb[NB];
-    __shared__ double D[NB][NB + 1];
-    const int tid = threadIdx.x;
-    const double *Db = Dinv + (int64_t)b * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Db[e];
-    if (tid < NB) wb[tid] = w[b * NB + tid];
-    __syncthreads();
-    {   // z_b = Dinv_b w_b: four threads per row
-        const int r = tid >> 2, sub = tid & 3;
-        double s = 0.0;
-        for (int t = sub; t <= r; t += 4) s = fma(D[r][t], wb[t], s);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        if (sub == 0) {
-            zb[r] = s;
-            if (blockIdx.x == 0) z[b * NB + r] = s;
-        }
-    }
-    __syncthreads();
-    const int rb = b + 1 + blockIdx.x;
-    if (rb * NB >= n_pad) return;
-    const int row = rb * NB + (tid >> 2), part = tid & 3;
-    const double *Lr = L + (int64_t)row * n_pad + (int64_t)b * NB + part * 16;
-    double s = 0.0;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) s = fma(Lr[t], zb[part * 16 + t], s);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0) w[row] -= s;
+    k_fwd_step_body(L, Dinv, n_pad, b, w, z, blockIdx.x, blockIdx.y);
 }
 
-// Backward step b of L^T x = w: x_b = Dinv_b^T w_b; each CTA c < b updates w_c -= L_bc^T x_b.
 __global__ void __launch_bounds__(256) k_bwd_step(const double *__restrict__ L, const double *__restrict__ Dinv,
                                                   int n_pad, int b, double *__restrict__ w, double *__restrict__ x)
 {
-    __shared__ double wb[NB], xb[NB], red[4][NB];
-    __shared__ double D[NB][NB + 1];
-    const int tid = threadIdx.x;
-    const double *Db = Dinv + (int64_t)b * NB * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Db[e];
-    if (tid < NB) wb[tid] = w[b * NB + tid];
-    __syncthreads();
-    {   // x_b = Dinv_b^T w_b: four threads per output
-        const int r = tid >> 2, sub = tid & 3;
-        double s = 0.0;
-        for (int t = r + sub; t < NB; t += 4) s = fma(D[t][r], wb[t], s);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        if (sub == 0) {
-            xb[r] = s;
-            if (blockIdx.x == 0) x[b * NB + r] = s;
-        }
-    }
-    __syncthreads();
-    const int cb = blockIdx.x;
-    if (cb >= b) return;
-    const int col = tid & 63, part = tid >> 6;
-    const double *Lb = L + (int64_t)(b * NB + part * 16) * n_pad + (int64_t)cb * NB + col;
-    double s = 0.0;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) s = fma(Lb[(int64_t)t * n_pad], xb[part * 16 + t], s);
-    red[part][col] = s;
-    __syncthreads();
-    if (tid < NB) w[cb * NB + tid] -= red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
+    k_bwd_step_body(L, Dinv, n_pad, b, w, x, blockIdx.x, blockIdx.y);
 }
 
-// r = y - K alpha (one warp per row).
 __global__ void k_residual(const double *__restrict__ K, const double *__restrict__ alpha,
                            const double *__restrict__ y, int n_pad, double *__restrict__ r)
 {
-    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (row >= n_pad) return;
-    const double *Kr = K + (int64_t)row * n_pad;
-    double s = 0.0;
-    for (int j = lane; j < n_pad; j += 32) s = fma(Kr[j], alpha[j], s);
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) r[row] = y[row] - s;
+    k_residual_body(K, alpha, y, n_pad, r, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_axpy_cast(double *__restrict__ a, const double *__restrict__ dlt, int n, float *__restrict__ a32)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double v = dlt ? a[i] + dlt[i] : a[i];
-    a[i] = v;
-    if (a32) a32[i] = (float)v;
+    k_axpy_cast_body(a, dlt, n, a32, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_pad_copy(const double *__restrict__ y, int n, int n_pad, double *__restrict__ out)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_pad) out[i] = i < n ? y[i] : 0.0;
+    k_pad_copy_body(y, n, n_pad, out, blockIdx.x, blockIdx.y);
 }
-
-// ------------------------------------------------------------------ triangular inverse
-// Batched SIMT GEMM C = alpha * A * B on row-major tiles; each problem in `probs` has its own
-// operand offsets and shape.  tri_a: A is lower triangular (skip k > row block end);
-// tri_b: B is lower triangular (skip k < column block start).
-struct GemmProb {
-    int64_t a_off, b_off, c_off;
-    int m, n, k;
-};
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_batched(const T *__restrict__ Abase, const T *__restrict__ Bbase,
@@ -318,102 +90,36 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const T *__restrict__ Abas
                                                       const GemmProb *__restrict__ probs, T alpha, int tri_a,
                                                       int tri_b)
 {
-    constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ T As[BK][BM + 1];
-    __shared__ T Bs[BK][BN + 1];
-    const GemmProb pr = probs[blockIdx.z];
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    if (m0 >= pr.m || n0 >= pr.n) return;
-    const T *A = Abase + pr.a_off;
-    const T *B = Bbase + pr.b_off;
-    T *C = Cbase + pr.c_off;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    int kbeg = 0, kend = pr.k;
-    if (tri_a) kend = min(kend, m0 + BM);
-    if (tri_b) kbeg = (n0 / BK) * BK;
-    T acc[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += 256) {
-            int r = e / BK, c = e % BK;
-            int gr = m0 + r, gc = k0 + c;
-            As[c][r] = (gr < pr.m && gc < pr.k) ? A[(int64_t)gr * lda + gc] : T(0);
-        }
-        for (int e = tid; e < BK * BN; e += 256) {
-            int r = e / BN, c = e % BN;
-            int gr = k0 + r, gc = n0 + c;
-            Bs[r][c] = (gr < pr.k && gc < pr.n) ? B[(int64_t)gr * ldb + gc] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < BK; ++t) {
-            T x[4], y[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { x[u] = As[t][ty + 16 * u]; y[u] = Bs[t][tx + 16 * u]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += x[u] * y[v];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            int gr = m0 + ty + 16 * u, gc = n0 + tx + 16 * v;
-            if (gr < pr.m && gc < pr.n) C[(int64_t)gr * ldc + gc] = alpha * acc[u][v];
-        }
+    k_gemm_batched_body<T>(Abase, Bbase, Cbase, lda, ldb, ldc, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y);
 }
 
-// Linv's diagonal blocks from Dinv (rounded to T); everything else zero.
 template <typename T>
 __global__ void k_linv_init(const double *__restrict__ Dinv, int n_pad, T *__restrict__ Linv)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n_pad * n_pad) return;
-    int i = (int)(t / n_pad), j = (int)(t % n_pad);
-    T v = T(0);
-    if (i / NB == j / NB) {
-        int b = i / NB;
-        v = (T)Dinv[(int64_t)b * NB * NB + (i % NB) * NB + (j % NB)];
-    }
-    Linv[t] = v;
+    k_linv_init_body<T>(Dinv, n_pad, Linv, blockIdx.x, blockIdx.y);
 }
-
-template <typename T> __device__ __forceinline__ T convert_to(double v) { return (T)v; }
-template <> __device__ __forceinline__ __nv_bfloat16 convert_to<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
-template <> __device__ __forceinline__ __half convert_to<__half>(double v) { return __float2half_rn((float)v); }
 
 template <typename Tin, typename Tout>
 __global__ void k_cast(const Tin *__restrict__ in, int64_t count, Tout *__restrict__ out)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < count) out[t] = convert_to<Tout>((double)in[t]);
+    k_cast_body<Tin, Tout>(in, count, out, blockIdx.x, blockIdx.y);
 }
 
-// BF16 operands with a compensated inverse: hi = bf16(L^-1), lo = bf16(L^-1 - hi).
 __global__ void k_split_bf16(const float *__restrict__ in, int64_t count, __nv_bfloat16 *__restrict__ hi,
                              __nv_bfloat16 *__restrict__ lo)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const float v = in[t];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[t] = h;
-    lo[t] = __float2bfloat16_rn(v - __bfloat162float(h));
+    k_split_bf16_body(in, count, hi, lo, blockIdx.x, blockIdx.y);
 }
 
-// Zero rows n..n_pad-1 of a 16-bit L^-1 (count rows of width n_pad), so that the cross-kernel
-// values of padded observations never reach the variance.
 __global__ void k_zero_pad_rows(uint16_t *__restrict__ A, int n, int n_pad)
 {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t cnt = (int64_t)(n_pad - n) * n_pad;
-    if (t < cnt) A[(int64_t)n * n_pad + t] = 0;
+    k_zero_pad_rows_body(A, n, n_pad, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(1024) k_standardize(const double *__restrict__ y, int n, double *__restrict__ ys,
+                                                      double *__restrict__ tau)
+{
+    k_standardize_body(y, n, ys, tau, blockIdx.x, blockIdx.y);
 }
 
 // Bottom-up block recursion: at level l the runs of 2^l diagonal blocks are inverted; runs
@@ -441,6 +147,7 @@ static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int>
             p.m = sr;
             p.n = sl;
             p.k = sl;
+            p.ld = n_pad;
             probs.push_back(p);
             maxm = std::max(maxm, sr);
             maxn = std::max(maxn, sl);
@@ -598,51 +305,6 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
     return GPBO_OK;
-}
-
-// ------------------------------------------------------------------ standardisation
-// ys = (y - mean) / std (population std; 1 when zero), tau = min ys.  One CTA.
-__global__ void __launch_bounds__(1024) k_standardize(const double *__restrict__ y, int n, double *__restrict__ ys,
-                                                      double *__restrict__ tau)
-{
-    __shared__ double red[32];
-    __shared__ double bc;
-    const int tid = threadIdx.x, lane = tid % 32, wid = tid / 32;
-    auto block_sum = [&](double v) {
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            v = lane < (int)(blockDim.x / 32) ? red[lane] : 0.0;
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) bc = v;
-        }
-        __syncthreads();
-        double r = bc;
-        __syncthreads();
-        return r;
-    };
-    double s = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) s += y[i];
-    const double mean = block_sum(s) / n;
-    double v = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) v += (y[i] - mean) * (y[i] - mean);
-    double sd = sqrt(block_sum(v) / n);
-    if (!(sd > 0.0)) sd = 1.0;
-    double mn = INFINITY;
-    for (int i = tid; i < n; i += blockDim.x) {
-        double t = (y[i] - mean) / sd;
-        ys[i] = t;
-        mn = fmin(mn, t);
-    }
-    for (int o = 16; o; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if (lane == 0) red[wid] = mn;
-    __syncthreads();
-    if (tid == 0) {
-        double m = red[0];
-        for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmin(m, red[w]);
-        *tau = m;
-    }
 }
 
 int standardize_dev(gpbo_ctx *ctx, const double *y, int n, double *ys, double *tau_dev)

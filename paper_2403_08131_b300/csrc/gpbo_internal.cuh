@@ -81,6 +81,9 @@ struct gpbo_ctx {
     bool trace = false;              // per-phase event timing (gpbo_trace_enable)
     gpbo::TraceRec *trace_recs = nullptr;
     int trace_n = 0, trace_cap = 0;
+    int trace_stack[8];              // open intervals (they nest)
+    int trace_depth = 0;
+    void *batch_plan = nullptr;      // captured batched step for the last set of shapes
 };
 
 struct gp_model {
@@ -135,6 +138,9 @@ int xkern_tc_prepare(gpbo_ctx *ctx, gp_model *m);
 bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
              float *mu);
+
+// batched.cu
+void batch_plan_free(void *plan);
 
 // screen.cu
 int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opts *o, double *score,

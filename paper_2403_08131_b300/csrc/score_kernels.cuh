@@ -1,0 +1,318 @@
+// Device bodies of the scoring kernels (candidates, cross-kernel, CUDA-core variance + EI,
+// argmax), shared by the single-problem kernels (score.cu) and the batched kernels
+// (batched.cu).  Each body takes its block coordinates as arguments.
+#pragma once
+
+#include "gpbo_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace gpbo {
+
+__device__ __forceinline__ void k_gen_candidates_body(uint64_t seed, int64_t first, int64_t M, int d, float *__restrict__ out, const int bx, const int by, const int gx)
+{
+    int64_t t = bx * (int64_t)blockDim.x + threadIdx.x;
+    int64_t total = M * d;
+    for (; t < total; t += (int64_t)gx * blockDim.x) {
+        int64_t c = t / d;
+        int k = (int)(t - c * d);
+        out[t] = uniform24f(seed, 2, (uint64_t)((first + c) * d + k));
+    }
+}
+
+template <typename A> __device__ __forceinline__ A matern_acc(A r2);
+template <> __device__ __forceinline__ double matern_acc<double>(double r2) { return matern52_r2(r2); }
+template <> __device__ __forceinline__ float matern_acc<float>(float r2) { return matern52_r2f(r2); }
+
+// Cross-kernel and mean for candidates [c0, c0 + C) of the pool.
+//   Acc  : arithmetic type (double for F64 scoring, float otherwise)
+//   Out  : K* element type (double / float / bf16 / half)
+//   Xc   : M x d FP32 candidates, or NULL to draw them from `seed`
+//   Xs   : d x n_pad observations divided by the lengthscales, zero padding
+//   Kst  : C x n_pad chunk buffer; mu: pool-indexed output
+// CTA = 256 threads: 32 candidates (4 per warp) x 128 observations per tile (4 per lane).
+template <typename Acc, typename Out>
+__device__ __forceinline__ void k_xkern_body(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
+                                               int d, const Acc *__restrict__ Xs, const Acc *__restrict__ alpha,
+                                               int n, int n_pad, Acc s2, Lengthscales_inv ls, Out *__restrict__ Kst,
+                                               Acc *__restrict__ mu, const int bx, const int by, const int gx)
+{
+    extern __shared__ unsigned char smraw[];
+    Acc *xc = reinterpret_cast<Acc *>(smraw);          // [32][d]
+    Acc *xo = xc + 32 * d;                              // [d][128]
+    Acc *al = xo + (int64_t)d * 128;                    // [128]
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    const int64_t cbase = bx * 32ll;
+    for (int e = tid; e < 32 * d; e += 256) {
+        int r = e / d, k = e % d;
+        int64_t c = c0 + cbase + r;
+        float x = Xc ? (cbase + r < C ? Xc[c * d + k] : 0.0f) : uniform24f(seed, 2, (uint64_t)(c * d + k));
+        xc[e] = (Acc)x * (Acc)ls.inv[k];
+    }
+    Acc mp[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+    for (int i0 = 0; i0 < n_pad; i0 += 128) {
+        __syncthreads();
+        for (int e = tid; e < d * 128; e += 256) {
+            int k = e / 128, q = e % 128;
+            xo[e] = i0 + q < n_pad ? Xs[(int64_t)k * n_pad + i0 + q] : Acc(0);
+        }
+        if (tid < 128) al[tid] = i0 + tid < n_pad ? alpha[i0 + tid] : Acc(0);
+        __syncthreads();
+        Acc r2[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) r2[a][b] = Acc(0);
+        for (int k = 0; k < d; ++k) {
+            Acc cv[4], ov[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) cv[a] = xc[(warp * 4 + a) * d + k];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ov[b] = xo[k * 128 + lane + 32 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    Acc t = cv[a] - ov[b];
+                    r2[a][b] = fma(t, t, r2[a][b]);
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t cl = cbase + warp * 4 + a;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = i0 + lane + 32 * b;
+                Acc kv = i < n ? s2 * matern_acc<Acc>(r2[a][b]) : Acc(0);
+                mp[a] = fma(kv, al[lane + 32 * b], mp[a]);
+                if (cl < C && i < n_pad) Kst[cl * n_pad + i] = (Out)kv;
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        Acc v = mp[a];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t cl = cbase + warp * 4 + a;
+        if (lane == 0 && cl < C) mu[c0 + cl] = v;
+    }
+}
+
+// FP32 cross-kernel and mean (F32, BF16 and F16 models): same results as k_xkern<float, Out>
+// up to the last bits of r = sqrt(r^2) and exp, with fewer instructions per K* element.
+// CTA = 256 threads = 8 warps x 8 candidates; each lane owns 4 consecutive observations of a
+// 128-observation chunk, read as one float4 per dimension straight from L1/L2; K* leaves as
+// one 8- or 16-byte store per candidate and chunk.
+template <typename Out> struct Pack4;
+template <> struct Pack4<float> {
+    using T = float4;
+    __device__ static T make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <> struct Pack4<__half> {
+    using T = uint2;
+    __device__ static T make(float a, float b, float c, float d)
+    {
+        __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
+        return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
+    }
+};
+template <> struct Pack4<__nv_bfloat16> {
+    using T = uint2;
+    __device__ static T make(float a, float b, float c, float d)
+    {
+        __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+        return make_uint2(*reinterpret_cast<uint32_t *>(&x), *reinterpret_cast<uint32_t *>(&y));
+    }
+};
+
+// s2 (1 + sqrt5 r + 5 r^2 / 3) exp(-sqrt5 r) with r = r2 rsqrt(r2) (r = 0 at coincidence).
+__device__ __forceinline__ float matern_fast(float r2, float s2)
+{
+    const float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
+    const float e = __expf(-2.2360680f * r);
+    return s2 * fmaf(1.6666666f, r2, fmaf(2.2360680f, r, 1.0f)) * e;
+}
+
+template <typename Out>
+__device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
+                                                 int d, const float *__restrict__ Xs, const float *__restrict__ alpha,
+                                                 int n, int n_pad, float s2, Lengthscales_inv ls, Out *__restrict__ Kst,
+                                                 float *__restrict__ mu, const int bx, const int by, const int gx)
+{
+    constexpr int CW = 8;                 // candidates per warp
+    extern __shared__ float cs[];         // [64][d]
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    const int64_t cbase = bx * 64ll;
+    for (int e = tid; e < 64 * d; e += 256) {
+        const int r = e / d, k = e - (e / d) * d;
+        const int64_t c = c0 + cbase + r;
+        const float x = Xc ? (cbase + r < C ? Xc[c * d + k] : 0.0f) : uniform24f(seed, 2, (uint64_t)(c * d + k));
+        cs[e] = x * (float)ls.inv[k];
+    }
+    __syncthreads();
+    const float *cw = cs + warp * CW * d;
+    float mp[CW];
+#pragma unroll
+    for (int a = 0; a < CW; ++a) mp[a] = 0.0f;
+    for (int i0 = 0; i0 < n_pad; i0 += 128) {
+        const int i = i0 + 4 * lane;
+        if (i >= n_pad) break;
+        float r2[CW][4];
+#pragma unroll
+        for (int a = 0; a < CW; ++a) r2[a][0] = r2[a][1] = r2[a][2] = r2[a][3] = 0.0f;
+        for (int k = 0; k < d; ++k) {
+            const float4 o = *reinterpret_cast<const float4 *>(Xs + (size_t)k * n_pad + i);
+#pragma unroll
+            for (int a = 0; a < CW; ++a) {
+                const float cv = cw[a * d + k];
+                const float t0 = cv - o.x, t1 = cv - o.y, t2 = cv - o.z, t3 = cv - o.w;
+                r2[a][0] = fmaf(t0, t0, r2[a][0]);
+                r2[a][1] = fmaf(t1, t1, r2[a][1]);
+                r2[a][2] = fmaf(t2, t2, r2[a][2]);
+                r2[a][3] = fmaf(t3, t3, r2[a][3]);
+            }
+        }
+        const float4 al = *reinterpret_cast<const float4 *>(alpha + i);
+        const bool v0 = i < n, v1 = i + 1 < n, v2 = i + 2 < n, v3 = i + 3 < n;
+#pragma unroll
+        for (int a = 0; a < CW; ++a) {
+            const float k0 = v0 ? matern_fast(r2[a][0], s2) : 0.0f;
+            const float k1 = v1 ? matern_fast(r2[a][1], s2) : 0.0f;
+            const float k2 = v2 ? matern_fast(r2[a][2], s2) : 0.0f;
+            const float k3 = v3 ? matern_fast(r2[a][3], s2) : 0.0f;
+            mp[a] = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mp[a]))));
+            const int64_t cl = cbase + warp * CW + a;
+            if (cl < C)
+                *reinterpret_cast<typename Pack4<Out>::T *>(Kst + cl * n_pad + i) = Pack4<Out>::make(k0, k1, k2, k3);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < CW; ++a) {
+        float v = mp[a];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int64_t cl = cbase + warp * CW + a;
+        if (lane == 0 && cl < C) mu[c0 + cl] = v;
+    }
+}
+
+// Variance, EI and per-CTA argmax on CUDA cores.  CTA = 64 candidates; it walks the
+// lower triangle of L^-1 in 64-row blocks (outputs) and 16-wide K steps.
+template <typename T>
+__device__ __forceinline__ void k_var_simt_body(const T *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
+                                                  const T *__restrict__ Linv, const T *__restrict__ mu, T s2,
+                                                  double y_best, const double *__restrict__ tau_dev, T xi,
+                                                  T *__restrict__ sigma_out, T *__restrict__ ei_out,
+                                                  T *__restrict__ part_ei, int64_t *__restrict__ part_idx,
+                                                  int part_base, const int bx, const int by, const int gx)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    __shared__ T red_v[BM];
+    __shared__ int64_t red_i[BM];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t cb = bx * (int64_t)BM;
+    T sig2[4] = {T(0), T(0), T(0), T(0)};
+    for (int i0 = 0; i0 < n_pad; i0 += BN) {
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        const int kend = i0 + BN;
+        for (int k0 = 0; k0 < kend; k0 += BK) {
+            {
+                const int r = tid / 4, c = (tid % 4) * 4;
+                const int64_t cr = cb + r;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    As[c + q][r] = cr < C ? Kst[cr * n_pad + k0 + c + q] : T(0);
+                    Bs[c + q][r] = Linv[(int64_t)(i0 + r) * n_pad + k0 + c + q];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int t = 0; t < BK; ++t) {
+                T x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { x[u] = As[t][ty + 16 * u]; y[u] = Bs[t][tx + 16 * u]; }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sig2[u] = fma(acc[u][v], acc[u][v], sig2[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        for (int o = 1; o < 16; o <<= 1) sig2[u] += __shfl_xor_sync(0xffffffffu, sig2[u], o);
+    const T tau = tau_dev ? (T)*tau_dev : (T)y_best;
+    if (tx == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = ty + 16 * u;
+            const int64_t cl = cb + r, c = c0 + cl;
+            T e = T(-1);
+            if (cl < C) {
+                T var = s2 - sig2[u];
+                T sg = var > T(0) ? sqrt(var) : T(0);
+                T m = mu[c];
+                if constexpr (sizeof(T) == 8) e = ei_min(m, sg, tau, xi);
+                else e = ei_minf(m, sg, tau, xi);
+                if (sigma_out) sigma_out[c] = sg;
+                if (ei_out) ei_out[c] = e;
+            }
+            red_v[r] = e;
+            red_i[r] = cl < C ? c : INT64_MAX;
+        }
+    }
+    __syncthreads();
+    for (int s = BM / 2; s; s >>= 1) {
+        if (tid < s) {
+            if (better(red_v[tid + s], red_i[tid + s], red_v[tid], red_i[tid])) {
+                red_v[tid] = red_v[tid + s];
+                red_i[tid] = red_i[tid + s];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        part_ei[part_base + bx] = red_v[0];
+        part_idx[part_base + bx] = red_i[0];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void k_argmax_final_body(const T *__restrict__ part_ei, const int64_t *__restrict__ part_idx,
+                                                       int np, double *__restrict__ out_ei, int64_t *__restrict__ out_idx, const int bx, const int by, const int gx)
+{
+    __shared__ T sv[1024];
+    __shared__ int64_t si[1024];
+    T bv = T(-2);
+    int64_t bi = INT64_MAX;
+    for (int p = threadIdx.x; p < np; p += blockDim.x)
+        if (better(part_ei[p], part_idx[p], bv, bi)) { bv = part_ei[p]; bi = part_idx[p]; }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s; s >>= 1) {
+        if (threadIdx.x < s && better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out_ei = (double)sv[0];
+        *out_idx = si[0];
+    }
+}
+
+
+}  // namespace gpbo

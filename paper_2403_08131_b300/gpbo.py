@@ -76,6 +76,9 @@ _model_info = _sig("gp_model_info", C.c_int, [_P, _I, _I, _I, _D])
 _model_read = _sig("gp_model_read", C.c_int, [_P, _P, _P])
 _posterior = _sig("gp_posterior_ei", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double, C.c_double, C.c_uint,
                                                _P, _P, _P, _L, _D])
+_step_batched = _sig("search_step_batched", C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), _I, _I,
+                                                     C.POINTER(GpHyper), _L, C.POINTER(C.c_uint64), C.c_double,
+                                                     C.c_int, C.c_uint, _D, _D, _L])
 _posterior_noalloc = _sig("gp_posterior_ei_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double,
                                                                C.c_double, _P, _P, _P, _L, _D])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
@@ -240,6 +243,42 @@ class Context:
         check(_step(self._h, _ptr(X), _ptr(y), n, d, C.byref(h), _ptr(Xc), int(M), int(seed), float(xi), PREC[prec],
                     flags, x_next.ctypes.data, C.byref(em), C.byref(am)), "search_step")
         return {"x_next": x_next, "ei_max": float(em.value), "argmax": int(am.value)}
+
+    def search_step_batched(self, problems, xi=0.0, prec="f32"):
+        """problems: list of dicts with X (n x d), y (n), lengthscale, signal_var, noise_var, M, seed.
+        X and y are all numpy arrays (host) or all torch CUDA tensors (device)."""
+        G = len(problems)
+        host = isinstance(problems[0]["X"], np.ndarray)
+        keep = []
+        Xp = (_P * G)()
+        yp = (_P * G)()
+        ns = np.zeros(G, dtype=np.int32)
+        ds = np.zeros(G, dtype=np.int32)
+        Ms = np.zeros(G, dtype=np.int64)
+        seeds = (C.c_uint64 * G)()
+        hyps = (GpHyper * G)()
+        for g, pb in enumerate(problems):
+            X, y = pb["X"], pb["y"]
+            if host:
+                X = np.ascontiguousarray(X, dtype=np.float64)
+                y = np.ascontiguousarray(y, dtype=np.float64)
+            keep += [X, y]
+            Xp[g] = _ptr(X)
+            yp[g] = _ptr(y)
+            ns[g], ds[g] = X.shape
+            Ms[g] = int(pb["M"])
+            seeds[g] = int(pb["seed"])
+            h, ls = _hyper(pb["lengthscale"], pb["signal_var"], pb["noise_var"])
+            keep.append(ls)
+            hyps[g] = h
+        x_next = np.zeros((G, 64))
+        ei_max = np.zeros(G)
+        am = np.zeros(G, dtype=np.int64)
+        check(_step_batched(self._h, G, Xp, yp, ns.ctypes.data_as(_I), ds.ctypes.data_as(_I), hyps,
+                            Ms.ctypes.data_as(_L), seeds, float(xi), PREC[prec], HOST_PTRS if host else 0,
+                            x_next.ctypes.data_as(_D), ei_max.ctypes.data_as(_D), am.ctypes.data_as(_L)),
+              "search_step_batched")
+        return {"x_next": [x_next[g, :ds[g]] for g in range(G)], "ei_max": ei_max, "argmax": am}
 
     # ------------------------------------------------------------ screen
     def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,

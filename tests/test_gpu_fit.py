@@ -64,3 +64,20 @@ def test_fit_rejects_bad_arguments(ctx):
     with pytest.raises(gpbo.GpboError) as e:
         ctx.fit(Xn, y, [0.3] * 3, 1.0, 1e-6)
     assert e.value.code == gpbo.GPBO_ENAN
+
+
+def test_trace_phases_nest(ctx):
+    """The Cholesky-update intervals nest inside the fit interval; both are recorded."""
+    import torch
+    w = W.config2()
+    ys = (w.y - w.y.mean()) / w.y.std()
+    ctx.trace(True)
+    m = ctx.fit(w.X, ys, w.lengthscale, 1.0, w.noise_var, prec="f16")
+    ctx.posterior_ei(m, None, M=4096, seed=1, y_best=float(ys.min()))
+    tr = ctx.trace_read()
+    ctx.trace(False)
+    assert tr["fit"]["intervals"] == 1 and tr["fit"]["ms"] > 0
+    assert tr["chol_update"]["intervals"] == 512 // 64 - 1
+    assert 0 < tr["chol_update"]["ms"] < tr["fit"]["ms"]
+    assert tr["variance"]["intervals"] >= 1 and tr["xkern"]["intervals"] >= 1
+    assert tr["chol_update"]["flops"] == sum(T * (T + 1) // 2 for T in range(1, 8)) * 2 * 64 ** 3

@@ -71,11 +71,11 @@ def lib():
 
 
 def _bind_mlp(L):
-    L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D]
-    L.orc_mlp_backward.argtypes = [_D, C.c_int, C.c_int, C.c_int, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
-                                   _D, _D, _D, _D, _D, _D, _D]
     L.orc_gelu.restype = C.c_double
     L.orc_gelu.argtypes = [C.c_double]
+    L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int] + [_D] * 10
+    L.orc_mlp_backward.restype = C.c_double
+    L.orc_mlp_backward.argtypes = [_D, C.c_int, C.c_int, C.c_int] + [_D] * 14
 
 
 def _d(a):
@@ -300,3 +300,49 @@ def partition_routine(S, owner, cutoff, max_dims):
 
 def block_owner(block_dim):
     return np.repeat(np.arange(len(block_dim)), block_dim).astype(np.int32)
+
+
+# ------------------------------------------------------------------ MLP (pre-screen network)
+def mlp_sizes(d, H):
+    """(name, shape) of each parameter block in the flat layout W1, b1, W2, b2, W3, b3."""
+    return [("W1", (d, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, 2)), ("b3", (2,))]
+
+
+def mlp_count(d, H):
+    return d * H + H + H * H + H + 2 * H + 2
+
+
+def mlp_split(theta, d, H):
+    out, o = [], 0
+    for _, shp in mlp_sizes(d, H):
+        k = int(np.prod(shp))
+        out.append(np.ascontiguousarray(theta[o:o + k], dtype=np.float64))
+        o += k
+    return out
+
+
+def gelu(z):
+    return float(lib().orc_gelu(float(z)))
+
+
+def mlp_forward(theta, X, d, H):
+    X, pX = _d(X)
+    B = X.shape[0]
+    parts = mlp_split(np.asarray(theta, dtype=np.float64), d, H)
+    o = np.empty((B, 2))
+    nul = C.cast(None, _D)
+    lib().orc_mlp_forward(pX, B, d, H, *[q.ctypes.data_as(_D) for q in parts], nul, nul, nul, o.ctypes.data_as(_D))
+    return o
+
+
+def mlp_grad(theta, X, T, d, H):
+    """(loss, flat gradient) of L = 1/(2B) sum (o - t)^2."""
+    X, pX = _d(X)
+    T, pT = _d(T)
+    B = X.shape[0]
+    parts = mlp_split(np.asarray(theta, dtype=np.float64), d, H)
+    grads = [np.empty_like(q) for q in parts]
+    loss = np.empty(1)
+    lib().orc_mlp_backward(pX, B, d, H, *[q.ctypes.data_as(_D) for q in parts], pT,
+                           *[g.ctypes.data_as(_D) for g in grads], loss.ctypes.data_as(_D))
+    return float(loss[0]), np.concatenate([g.ravel() for g in grads])

@@ -268,6 +268,44 @@ int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const doub
                         const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
                         gpbo_prec prec, unsigned flags, double *x_next, double *ei_max, int64_t *argmax);
 
+/* ------------------------------------------------------------------ learned pre-screen
+ * Not in the paper: a cheap surrogate of the GP posterior that pre-screens very large
+ * candidate pools so that the exact GP-EI (§III-A's acquisition) only scores the best k.
+ * An ensemble of E networks d -> H -> H -> 2 with the exact GELU g(z) = z Phi(z) predicts
+ * (mu, log sigma) in standardised units; members combine as mu_bar = mean mu_e and
+ * sigma_bar^2 = mean sigma_e^2 + var mu_e.  Per-network parameters (FP32, contiguous):
+ * W1 [d x H], b1 [H], W2 [H x H], b2 [H], W3 [H x 2], b3 [2] (weights input-major).
+ * Training loss per network: L = 1/(2B) sum (o - t)^2; Adam (lr, 0.9, 0.999, 1e-8). */
+typedef struct gpbo_mlp gpbo_mlp;
+/* E networks, Glorot-uniform weights from counter stream 5 of seed, zero biases. */
+int mlp_create(gpbo_ctx *ctx, int E, int d, int H, uint64_t seed, gpbo_mlp **out);
+/* Free the networks; like models, before the context they were created on. */
+int mlp_free(gpbo_mlp *net);
+/* Read (host_out) and/or write (host_in) all E x P parameters, host FP32.  Synchronises. */
+int mlp_params(gpbo_mlp *net, float *host_out, const float *host_in);
+/* Outputs of every network on B device rows X (B x d): out device E x B x 2.  Synchronises. */
+int mlp_forward(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int B, float *out);
+/* Loss and gradient of every network on one batch (device X: B x d, T: B x 2 targets);
+ * grads_host: E x P, loss_host: E (either may be NULL).  Synchronises. */
+int mlp_gradients(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *T, int B, float *grads_host,
+                  float *loss_host);
+/* Train on N device rows: inputs X (N x d) and the GP posterior mu, sigma (N each).  The
+ * targets are (mu, log sigma) standardised by their means and standard deviations over
+ * the N rows (kept in the net for scoring).  `steps` Adam steps on minibatches of `batch`
+ * rows drawn with replacement from counter stream 7 of seed.  final_loss: host, mean loss
+ * of the last step over the networks (may be NULL).  Synchronises. */
+int mlp_train(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *mu, const float *sigma, int64_t N, int steps,
+              int batch, float lr, uint64_t seed, float *final_loss);
+/* Target standardisation (mu mean, mu sd, log-sigma mean, log-sigma sd), host. */
+int mlp_norm(const gpbo_mlp *net, double *norm4);
+/* Draw M candidates from seed (stream 2), score them with the ensemble's EI below y_best,
+ * keep the k best (radix select; ties at the k-th value taken in any order), re-score those
+ * k with the exact GP-EI of `model` (FP32 or 16-bit scoring) and return the best pool index
+ * and its exact EI.  ei_pool: device M floats for the surrogate EI, or NULL (then the call
+ * allocates it); top_idx: host k pool indices of the selected set, or NULL.  Synchronises. */
+int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_t M, uint64_t seed, int k,
+                     double y_best, double xi, float *ei_pool, int64_t *top_idx, int64_t *argmax, double *ei_max);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,630 @@
+// Learned pre-screen: an ensemble of E small networks d -> H -> H -> 2 (exact GELU) trained
+// on (x, GP posterior) pairs to predict (mu, log sigma) in standardised units; it scores a
+// very large candidate pool cheaply, keeps the top k by the ensemble's expected improvement,
+// and the exact GP-EI re-scores those k (the exact score is both the fallback and the judge).
+//
+// Ensemble combine (mean of the members, total variance):
+//   mu_bar = mean_e mu_e,  sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e.
+// Training: L = 1/(2B) sum (o - t)^2 per network, Adam (lr, 0.9, 0.999, 1e-8), minibatches
+// drawn with replacement from the counter stream, all E networks in the same launches.
+//
+// Parameter layout per network (FP32, contiguous): W1 [d x H], b1 [H], W2 [H x H], b2 [H],
+// W3 [H x 2], b3 [2] -- weights stored input-major, the same layout as the FP64 oracle.
+#include "gpbo_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+struct gpbo_mlp {
+    gpbo_ctx *ctx = nullptr;
+    int E = 0, d = 0, H = 0;
+    int64_t P = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    int64_t step = 0;
+    double norm[4] = {0.0, 1.0, 0.0, 1.0};  // mu mean, mu sd, log-sigma mean, log-sigma sd
+    // training buffers (sized for `cap` rows)
+    int cap = 0;
+    float *bx = nullptr, *bt = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *o = nullptr;
+    float *d2 = nullptr, *d1 = nullptr, *dO = nullptr, *loss = nullptr;
+};
+
+namespace gpbo {
+
+namespace mlp {
+
+__device__ __forceinline__ float gelu(float z) { return z * 0.5f * erfcf(-z * 0.70710678f); }
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    return 0.5f * erfcf(-z * 0.70710678f) + z * 0.39894228f * expf(-0.5f * z * z);
+}
+
+struct Off {
+    int64_t W1, b1, W2, b2, W3, b3;
+};
+__host__ __device__ inline Off offsets(int d, int H)
+{
+    Off f;
+    f.W1 = 0;
+    f.b1 = f.W1 + (int64_t)d * H;
+    f.W2 = f.b1 + H;
+    f.b2 = f.W2 + (int64_t)H * H;
+    f.W3 = f.b2 + H;
+    f.b3 = f.W3 + 2 * (int64_t)H;
+    return f;
+}
+
+// Glorot-uniform weights from counter stream 5, zero biases.
+__global__ void k_init(float *theta, int E, int d, int H, int64_t P, uint64_t seed)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)E * P) return;
+    const int64_t i = t % P;
+    const Off f = offsets(d, H);
+    float fan_in = 0.f, fan_out = 0.f;
+    bool bias = false;
+    if (i < f.b1) { fan_in = d; fan_out = H; }
+    else if (i < f.W2) bias = true;
+    else if (i < f.b2) { fan_in = H; fan_out = H; }
+    else if (i < f.W3) bias = true;
+    else if (i < f.b3) { fan_in = H; fan_out = 2; }
+    else bias = true;
+    if (bias) { theta[t] = 0.0f; return; }
+    const float a = sqrtf(6.0f / (fan_in + fan_out));
+    theta[t] = (2.0f * uniform24f(seed, 5, (uint64_t)t) - 1.0f) * a;
+}
+
+// C[e] = epi( op(A[e]) op(B[e]) + bias[e] ), all row-major; op transposes when the flag is set.
+// epi: 0 store C; 1 store Z = C + bias and H = gelu(Z) (Z may be null); 2 store C * gelu'(Zref).
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm(const float *__restrict__ A, int64_t sA, int lda,
+                                              const float *__restrict__ B, int64_t sB, int ldb, float *__restrict__ C,
+                                              int64_t sC, int ldc, const float *__restrict__ bias, int64_t sbias,
+                                              float *__restrict__ H, const float *__restrict__ Zref, int M, int N, int K,
+                                              int epi)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ float As[BK][BM + 1];
+    __shared__ float Bs[BK][BN + 1];
+    const int e = blockIdx.z;
+    A += e * sA;
+    B += e * sB;
+    C += e * sC;
+    if (H) H += e * sC;
+    if (Zref) Zref += e * sC;
+    if (bias) bias += e * sbias;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int q = tid; q < BM * BK; q += 256) {
+            const int r = TA ? q % BM : q / BK, c = TA ? q / BM : q % BK;
+            const int gr = m0 + r, gc = k0 + c;
+            float v = 0.f;
+            if (gr < M && gc < K) v = TA ? A[(int64_t)gc * lda + gr] : A[(int64_t)gr * lda + gc];
+            As[c][r] = v;
+        }
+        for (int q = tid; q < BK * BN; q += 256) {
+            const int r = TB ? q % BK : q / BN, c = TB ? q / BK : q % BN;
+            const int gr = k0 + r, gc = n0 + c;
+            float v = 0.f;
+            if (gr < K && gc < N) v = TB ? B[(int64_t)gc * ldb + gr] : B[(int64_t)gr * ldb + gc];
+            Bs[r][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < BK; ++t) {
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { x[u] = As[t][ty + 16 * u]; y[u] = Bs[t][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(x[u], y[w], acc[u][w]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int gr = m0 + ty + 16 * u, gc = n0 + tx + 16 * w;
+            if (gr >= M || gc >= N) continue;
+            const int64_t at = (int64_t)gr * ldc + gc;
+            float v = acc[u][w] + (bias ? bias[gc] : 0.f);
+            if (epi == 1) {
+                if (C) C[at] = v;
+                H[at] = gelu(v);
+            } else if (epi == 2) {
+                C[at] = v * gelu_grad(Zref[at]);
+            } else {
+                C[at] = v;
+            }
+        }
+}
+
+// Output gradient dO = (o - t) / B and the loss per network.
+__global__ void k_out_grad(const float *o, const float *t, int B, float *dO, float *loss)
+{
+    const int e = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < 2 * B) {
+        const float r = o[(int64_t)e * 2 * B + i] - t[i];
+        dO[(int64_t)e * 2 * B + i] = r / B;
+        l = 0.5f * r * r / B;
+    }
+    for (int s = 16; s; s >>= 1) l += __shfl_xor_sync(0xffffffffu, l, s);
+    if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss + e, l);
+}
+
+// Column sums of a B x N row-major matrix (bias gradients): out[e][j] = sum_b X[e][b][j].
+__global__ void k_colsum(const float *X, int64_t sX, int B, int N, float *out, int64_t sOut)
+{
+    const int e = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += X[e * sX + (int64_t)b * N + j];
+    out[e * sOut + j] = s;
+}
+
+__global__ void k_adam(float *theta, const float *g, float *m, float *v, int64_t count, float lr, float c1, float c2)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// Minibatch: rows drawn with replacement (counter stream 7) from X (N x d) and the targets.
+__global__ void k_gather_batch(const float *X, const float *T, int64_t N, int d, int B, uint64_t seed, uint64_t step,
+                               float *bx, float *bt)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint64_t r = splitmix64(seed, 7, step * (uint64_t)B + b);
+    const int64_t i = (int64_t)((r >> 11) % (uint64_t)N);
+    for (int k = 0; k < d; ++k) bx[(int64_t)b * d + k] = X[i * d + k];
+    bt[2 * b] = T[2 * i];
+    bt[2 * b + 1] = T[2 * i + 1];
+}
+
+// Targets: t0 = (mu - mean) / sd, t1 = (log sigma - mean) / sd, statistics over all N rows.
+__global__ void __launch_bounds__(1024) k_target_stats(const float *mu, const float *sigma, int64_t N, double *stats)
+{
+    __shared__ double red[4][32];
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double a = mu[i], b = log(fmax((double)sigma[i], 1e-30));
+        s[0] += a; s[1] += a * a; s[2] += b; s[3] += b * b;
+    }
+    for (int q = 0; q < 4; ++q) {
+        double v = s[q];
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[4] = {0, 0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+            for (int q = 0; q < 4; ++q) t[q] += red[q][w];
+        const double m0 = t[0] / N, m1 = t[2] / N;
+        const double sd0 = sqrt(fmax(t[1] / N - m0 * m0, 1e-24)), sd1 = sqrt(fmax(t[3] / N - m1 * m1, 1e-24));
+        stats[0] = m0; stats[1] = sd0; stats[2] = m1; stats[3] = sd1;
+    }
+}
+
+__global__ void k_make_targets(const float *mu, const float *sigma, int64_t N, const double *stats, float *T)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    T[2 * i] = (float)((mu[i] - stats[0]) / stats[1]);
+    T[2 * i + 1] = (float)((log(fmax((double)sigma[i], 1e-30)) - stats[2]) / stats[3]);
+}
+
+// Ensemble EI per candidate from the networks' standardised outputs O [E][C][2].
+__global__ void k_ensemble_ei(const float *O, int E, int64_t C, int64_t c0, float n0, float n1, float n2, float n3,
+                              float tau, float xi, float *ei)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float sm = 0.f, sm2 = 0.f, sv = 0.f;
+    for (int e = 0; e < E; ++e) {
+        const float mu = O[((int64_t)e * C + c) * 2] * n1 + n0;
+        const float ls = O[((int64_t)e * C + c) * 2 + 1] * n3 + n2;
+        const float s = expf(ls);
+        sm += mu;
+        sm2 += mu * mu;
+        sv += s * s;
+    }
+    const float mbar = sm / E;
+    const float var = sv / E + fmaxf(sm2 / E - mbar * mbar, 0.f);
+    ei[c0 + c] = ei_minf(mbar, sqrtf(var), tau, xi);
+}
+
+__global__ void k_gen_rows(uint64_t seed, int64_t c0, int64_t C, int d, float *X)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= C * d) return;
+    const int64_t c = t / d;
+    const int k = (int)(t - c * d);
+    X[t] = uniform24f(seed, 2, (uint64_t)((c0 + c) * d + k));
+}
+
+// ------------------------------------------------------------------ top-k (radix select)
+// keys: EI >= 0 as float bits (order-preserving for non-negative floats); NaN counts as 0.
+__device__ __forceinline__ uint32_t key_of(float v) { return v > 0.f ? __float_as_uint(v) : 0u; }
+
+// pass p: histogram of digit p among keys whose higher digits equal the prefix chosen so far.
+// digits: bits [20,32) (4096 bins), [8,20) (4096), [0,8) (256).
+__global__ void k_radix_hist(const float *ei, int64_t M, int pass, const uint32_t *sel, uint32_t *hist)
+{
+    __shared__ uint32_t sh[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = sel[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = key_of(ei[i]);
+        uint32_t dig;
+        bool in;
+        if (pass == 0) { dig = k >> 20; in = true; }
+        else if (pass == 1) { dig = (k >> 8) & 0xFFFu; in = (k >> 20) == prefix; }
+        else { dig = k & 0xFFu; in = (k >> 8) == prefix; }
+        if (in) atomicAdd(&sh[dig], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Single thread: choose the digit where the running count from the top reaches `need`,
+// extend the prefix, and leave the remaining count for the next pass.  sel = {prefix, need}.
+__global__ void k_radix_pick(uint32_t *hist, int bins, int pass, uint32_t *sel)
+{
+    uint32_t need = sel[1];
+    uint32_t cum = 0;
+    int b = bins - 1;
+    for (; b > 0; --b) {
+        if (cum + hist[b] >= need) break;
+        cum += hist[b];
+    }
+    const uint32_t shift = pass == 2 ? 8u : 12u;
+    sel[0] = pass == 0 ? (uint32_t)b : (sel[0] << shift) | (uint32_t)b;
+    sel[1] = need - cum;
+    for (int i = 0; i < bins; ++i) hist[i] = 0;
+}
+
+// Keys above the threshold key T = sel[0] all go in; keys equal to T fill the remaining sel[1].
+__global__ void k_radix_gather(const float *ei, int64_t M, const uint32_t *sel, uint32_t *counters, int k,
+                               int64_t *out)
+{
+    const uint32_t T = sel[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = key_of(ei[i]);
+        if (key > T) {
+            const uint32_t p = atomicAdd(&counters[0], 1u);
+            if (p < (uint32_t)k) out[p] = i;
+        } else if (key == T) {
+            const uint32_t q = atomicAdd(&counters[1], 1u);
+            if (q < sel[1]) {
+                const uint32_t p = atomicAdd(&counters[0], 1u);
+                if (p < (uint32_t)k) out[p] = i;
+            }
+        }
+    }
+}
+
+__global__ void k_rows_from_index(const int64_t *idx, int k, uint64_t seed, int d, float *X)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= k * d) return;
+    const int r = t / d, c = t - r * d;
+    X[t] = uniform24f(seed, 2, (uint64_t)(idx[r] * d + c));
+}
+
+}  // namespace mlp
+
+using namespace mlp;
+
+static unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, cdiv64(n, t)); }
+
+static int ensure_batch(gpbo_mlp *net, int B)
+{
+    if (B <= net->cap) return GPBO_OK;
+    float **bufs[] = {&net->bx, &net->bt, &net->z1, &net->h1, &net->z2, &net->h2, &net->o, &net->d2, &net->d1, &net->dO};
+    for (float **b : bufs)
+        if (*b) { cudaFree(*b); *b = nullptr; }
+    const int64_t EBH = (int64_t)net->E * B * net->H;
+    GPBO_CUDA_TRY(cudaMalloc(&net->bx, sizeof(float) * (size_t)B * net->d));
+    GPBO_CUDA_TRY(cudaMalloc(&net->bt, sizeof(float) * (size_t)B * 2));
+    GPBO_CUDA_TRY(cudaMalloc(&net->z1, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->h1, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->z2, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->h2, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->o, sizeof(float) * (size_t)net->E * B * 2));
+    GPBO_CUDA_TRY(cudaMalloc(&net->d2, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->d1, sizeof(float) * EBH));
+    GPBO_CUDA_TRY(cudaMalloc(&net->dO, sizeof(float) * (size_t)net->E * B * 2));
+    net->cap = B;
+    return GPBO_OK;
+}
+
+// Forward of every network on B rows of X (shared by the networks).  keep: store Z for backward.
+static int forward(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int B, float *z1, float *h1, float *z2, float *h2,
+                   float *o, bool keep)
+{
+    const int E = net->E, d = net->d, H = net->H;
+    const Off f = offsets(d, H);
+    const int64_t P = net->P, BH = (int64_t)B * H;
+    cudaStream_t st = ctx->stream;
+    dim3 g1(nb(H, 64), nb(B, 64), E);
+    k_gemm<false, false><<<g1, 256, 0, st>>>(X, 0, d, net->theta + f.W1, P, H, keep ? z1 : nullptr, BH, H,
+                                             net->theta + f.b1, P, h1, nullptr, B, H, d, 1);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_gemm<false, false><<<g1, 256, 0, st>>>(h1, BH, H, net->theta + f.W2, P, H, keep ? z2 : nullptr, BH, H,
+                                             net->theta + f.b2, P, h2, nullptr, B, H, H, 1);
+    GPBO_LAUNCH_CHECK(ctx);
+    dim3 g3(1, nb(B, 64), E);
+    k_gemm<false, false><<<g3, 256, 0, st>>>(h2, BH, H, net->theta + f.W3, P, 2, o, (int64_t)B * 2, 2,
+                                             net->theta + f.b3, P, nullptr, nullptr, B, 2, H, 0);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+// Gradients of every network for the batch in net->bx / net->bt (B rows) into net->grad.
+static int backward(gpbo_ctx *ctx, gpbo_mlp *net, int B)
+{
+    const int E = net->E, d = net->d, H = net->H;
+    const Off f = offsets(d, H);
+    const int64_t P = net->P, BH = (int64_t)B * H;
+    cudaStream_t st = ctx->stream;
+    GPBO_TRY(forward(ctx, net, net->bx, B, net->z1, net->h1, net->z2, net->h2, net->o, true));
+    GPBO_CUDA_TRY(cudaMemsetAsync(net->loss, 0, sizeof(float) * E, st));
+    k_out_grad<<<dim3(nb(2 * B), E), 256, 0, st>>>(net->o, net->bt, B, net->dO, net->loss);
+    GPBO_LAUNCH_CHECK(ctx);
+    float *G = net->grad;
+    // dW3 = h2^T dO, db3 = sum dO
+    k_gemm<true, false><<<dim3(1, nb(H, 64), E), 256, 0, st>>>(net->h2, BH, H, net->dO, (int64_t)B * 2, 2, G + f.W3, P, 2,
+                                                               nullptr, 0, nullptr, nullptr, H, 2, B, 0);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_colsum<<<dim3(1, E), 32, 0, st>>>(net->dO, (int64_t)B * 2, B, 2, G + f.b3, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    // dZ2 = (dO W3^T) * gelu'(z2)
+    k_gemm<false, true><<<dim3(nb(H, 64), nb(B, 64), E), 256, 0, st>>>(net->dO, (int64_t)B * 2, 2, net->theta + f.W3, P, 2,
+                                                                       net->d2, BH, H, nullptr, 0, nullptr, net->z2, B,
+                                                                       H, 2, 2);
+    GPBO_LAUNCH_CHECK(ctx);
+    // dW2 = h1^T dZ2, db2 = sum dZ2
+    k_gemm<true, false><<<dim3(nb(H, 64), nb(H, 64), E), 256, 0, st>>>(net->h1, BH, H, net->d2, BH, H, G + f.W2, P, H,
+                                                                       nullptr, 0, nullptr, nullptr, H, H, B, 0);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_colsum<<<dim3(nb(H), E), 256, 0, st>>>(net->d2, BH, B, H, G + f.b2, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    // dZ1 = (dZ2 W2^T) * gelu'(z1)
+    k_gemm<false, true><<<dim3(nb(H, 64), nb(B, 64), E), 256, 0, st>>>(net->d2, BH, H, net->theta + f.W2, P, H, net->d1,
+                                                                       BH, H, nullptr, 0, nullptr, net->z1, B, H, H, 2);
+    GPBO_LAUNCH_CHECK(ctx);
+    // dW1 = x^T dZ1, db1 = sum dZ1
+    k_gemm<true, false><<<dim3(nb(H, 64), nb(d, 64), E), 256, 0, st>>>(net->bx, 0, d, net->d1, BH, H, G + f.W1, P, H,
+                                                                       nullptr, 0, nullptr, nullptr, d, H, B, 0);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_colsum<<<dim3(nb(H), E), 256, 0, st>>>(net->d1, BH, B, H, G + f.b1, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+}  // namespace gpbo
+
+using namespace gpbo;
+
+extern "C" {
+
+int mlp_create(gpbo_ctx *ctx, int E, int d, int H, uint64_t seed, gpbo_mlp **out)
+{
+    if (!ctx || !out || E < 1 || E > 64 || d < 1 || d > GPBO_MAX_D || H < 1 || H > 4096) return GPBO_EINVAL;
+    GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
+    gpbo_mlp *net = new gpbo_mlp();
+    net->ctx = ctx;
+    net->E = E;
+    net->d = d;
+    net->H = H;
+    net->P = (int64_t)d * H + H + (int64_t)H * H + H + 2 * (int64_t)H + 2;
+    const size_t bytes = sizeof(float) * (size_t)E * net->P;
+    if (cudaMalloc(&net->theta, bytes) != cudaSuccess || cudaMalloc(&net->grad, bytes) != cudaSuccess ||
+        cudaMalloc(&net->m, bytes) != cudaSuccess || cudaMalloc(&net->v, bytes) != cudaSuccess ||
+        cudaMalloc(&net->loss, sizeof(float) * E) != cudaSuccess) {
+        mlp_free(net);
+        return GPBO_ENOMEM;
+    }
+    cudaMemsetAsync(net->m, 0, bytes, ctx->stream);
+    cudaMemsetAsync(net->v, 0, bytes, ctx->stream);
+    k_init<<<nb((int64_t)E * net->P), 256, 0, ctx->stream>>>(net->theta, E, d, H, net->P, seed);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) {
+        mlp_free(net);
+        return GPBO_ECUDA;
+    }
+    *out = net;
+    return GPBO_OK;
+}
+
+int mlp_free(gpbo_mlp *net)
+{
+    if (!net) return GPBO_EINVAL;
+    cudaStreamSynchronize(net->ctx->stream);
+    float *bufs[] = {net->theta, net->grad, net->m,  net->v,  net->loss, net->bx, net->bt,
+                     net->z1,    net->h1,   net->z2, net->h2, net->o,    net->d2, net->d1, net->dO};
+    for (float *b : bufs)
+        if (b) cudaFree(b);
+    delete net;
+    return GPBO_OK;
+}
+
+int mlp_params(gpbo_mlp *net, float *host_out, const float *host_in)
+{
+    if (!net) return GPBO_EINVAL;
+    gpbo_ctx *ctx = net->ctx;
+    const size_t bytes = sizeof(float) * (size_t)net->E * net->P;
+    if (host_in) GPBO_CUDA_TRY(cudaMemcpyAsync(net->theta, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (host_out) GPBO_CUDA_TRY(cudaMemcpyAsync(host_out, net->theta, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GPBO_OK;
+}
+
+int mlp_forward(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int B, float *out)
+{
+    if (!ctx || !net || !X || !out || B < 1) return GPBO_EINVAL;
+    GPBO_TRY(ensure_batch(net, B));
+    GPBO_TRY(forward(ctx, net, X, B, nullptr, net->h1, nullptr, net->h2, out, false));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GPBO_OK;
+}
+
+int mlp_gradients(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *T, int B, float *grads_host,
+                  float *loss_host)
+{
+    if (!ctx || !net || !X || !T || B < 1) return GPBO_EINVAL;
+    GPBO_TRY(ensure_batch(net, B));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(net->bx, X, sizeof(float) * (size_t)B * net->d, cudaMemcpyDeviceToDevice, ctx->stream));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(net->bt, T, sizeof(float) * (size_t)B * 2, cudaMemcpyDeviceToDevice, ctx->stream));
+    GPBO_TRY(backward(ctx, net, B));
+    if (grads_host)
+        GPBO_CUDA_TRY(cudaMemcpyAsync(grads_host, net->grad, sizeof(float) * (size_t)net->E * net->P,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    if (loss_host)
+        GPBO_CUDA_TRY(cudaMemcpyAsync(loss_host, net->loss, sizeof(float) * net->E, cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GPBO_OK;
+}
+
+int mlp_train(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *mu, const float *sigma, int64_t N, int steps,
+              int batch, float lr, uint64_t seed, float *final_loss)
+{
+    if (!ctx || !net || !X || !mu || !sigma || N < 1 || steps < 1 || batch < 1 || !(lr > 0)) return GPBO_EINVAL;
+    GPBO_TRY(ensure_batch(net, batch));
+    float *T = nullptr;
+    double *stats = nullptr;
+    GPBO_CUDA_TRY(cudaMalloc(&T, sizeof(float) * 2 * (size_t)N));
+    GPBO_CUDA_TRY(cudaMalloc(&stats, sizeof(double) * 4));
+    cudaStream_t st = ctx->stream;
+    k_target_stats<<<1, 1024, 0, st>>>(mu, sigma, N, stats);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_make_targets<<<nb(N), 256, 0, st>>>(mu, sigma, N, stats, T);
+    GPBO_LAUNCH_CHECK(ctx);
+    int rc = GPBO_OK;
+    const int64_t count = (int64_t)net->E * net->P;
+    for (int s = 0; s < steps && rc == GPBO_OK; ++s) {
+        k_gather_batch<<<nb(batch), 256, 0, st>>>(X, T, N, net->d, batch, seed, (uint64_t)s, net->bx, net->bt);
+        ctx->launches++;
+        rc = backward(ctx, net, batch);
+        if (rc != GPBO_OK) break;
+        net->step++;
+        const float c1 = 1.0f - powf(0.9f, (float)net->step), c2 = 1.0f - powf(0.999f, (float)net->step);
+        k_adam<<<nb(count), 256, 0, st>>>(net->theta, net->grad, net->m, net->v, count, lr, c1, c2);
+        ctx->launches++;
+    }
+    if (rc == GPBO_OK && cudaGetLastError() != cudaSuccess) rc = GPBO_ECUDA;
+    double hs[4];
+    if (rc == GPBO_OK && cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = GPBO_ECUDA;
+    std::vector<float> l(net->E);
+    if (rc == GPBO_OK && cudaMemcpyAsync(l.data(), net->loss, sizeof(float) * net->E, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = GPBO_ECUDA;
+    cudaStreamSynchronize(st);
+    cudaFree(T);
+    cudaFree(stats);
+    if (rc != GPBO_OK) return rc;
+    for (int q = 0; q < 4; ++q) net->norm[q] = hs[q];
+    if (final_loss) {
+        double m = 0;
+        for (float x : l) m += x;
+        *final_loss = (float)(m / net->E);
+    }
+    return GPBO_OK;
+}
+
+int mlp_norm(const gpbo_mlp *net, double *norm4)
+{
+    if (!net || !norm4) return GPBO_EINVAL;
+    for (int q = 0; q < 4; ++q) norm4[q] = net->norm[q];
+    return GPBO_OK;
+}
+
+int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_t M, uint64_t seed, int k,
+                     double y_best, double xi, float *ei_pool, int64_t *top_idx, int64_t *argmax, double *ei_max)
+{
+    if (!ctx || !model || !net || !argmax || !ei_max || M < 1 || M > 0x7fffffffll || k < 1 || k > 1 << 20 ||
+        (int64_t)k > M || net->d != model->d)
+        return GPBO_EINVAL;
+    if (model->prec == GPBO_PREC_F64) return GPBO_ENOTSUP;
+    GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int d = net->d, H = net->H, E = net->E;
+    const int C = 32768;  // candidates per chunk
+    GPBO_TRY(ensure_batch(net, C));
+    float *ei = ei_pool;
+    float *own = nullptr;
+    if (!ei) {
+        GPBO_CUDA_TRY(cudaMalloc(&own, sizeof(float) * (size_t)M));
+        ei = own;
+    }
+    int64_t *idx = nullptr;
+    uint32_t *hist = nullptr;
+    float *Xk = nullptr;
+    GPBO_CUDA_TRY(cudaMalloc(&idx, sizeof(int64_t) * (size_t)k));
+    GPBO_CUDA_TRY(cudaMalloc(&hist, sizeof(uint32_t) * (4096 + 4)));
+    GPBO_CUDA_TRY(cudaMalloc(&Xk, sizeof(float) * (size_t)k * d));
+    uint32_t *sel = hist + 4096, *counters = hist + 4098;
+    int rc = GPBO_OK;
+    const double *nm = net->norm;
+    for (int64_t c0 = 0; c0 < M && rc == GPBO_OK; c0 += C) {
+        const int Cc = (int)std::min<int64_t>(C, M - c0);
+        k_gen_rows<<<nb((int64_t)Cc * d), 256, 0, st>>>(seed, c0, Cc, d, net->bx);
+        ctx->launches++;
+        rc = forward(ctx, net, net->bx, Cc, nullptr, net->h1, nullptr, net->h2, net->o, false);
+        if (rc != GPBO_OK) break;
+        k_ensemble_ei<<<nb(Cc), 256, 0, st>>>(net->o, E, Cc, c0, (float)nm[0], (float)nm[1], (float)nm[2], (float)nm[3],
+                                              (float)y_best, (float)xi, ei);
+        ctx->launches++;
+    }
+    // top k by the surrogate's EI
+    if (rc == GPBO_OK) {
+        uint32_t init[8] = {0, (uint32_t)k, 0, 0, 0, 0, 0, 0};
+        cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096, st);
+        cudaMemcpyAsync(sel, init, sizeof(uint32_t) * 4, cudaMemcpyHostToDevice, st);
+        for (int pass = 0; pass < 3; ++pass) {
+            k_radix_hist<<<std::min<unsigned>(nb(M), ctx->sm_count * 8), 256, 0, st>>>(ei, M, pass, sel, hist);
+            k_radix_pick<<<1, 1, 0, st>>>(hist, pass == 2 ? 256 : 4096, pass, sel);
+            ctx->launches += 2;
+        }
+        k_radix_gather<<<std::min<unsigned>(nb(M), ctx->sm_count * 8), 256, 0, st>>>(ei, M, sel, counters, k, idx);
+        k_rows_from_index<<<nb((int64_t)k * d), 256, 0, st>>>(idx, k, seed, d, Xk);
+        ctx->launches += 2;
+        if (cudaGetLastError() != cudaSuccess) rc = GPBO_ECUDA;
+    }
+    int64_t am = -1;
+    double em = 0.0;
+    if (rc == GPBO_OK) rc = score_model(ctx, model, Xk, k, 0, y_best, nullptr, xi, nullptr, nullptr, nullptr, &am, &em);
+    if (rc == GPBO_OK) {
+        int64_t pool = -1;
+        if (cudaMemcpyAsync(&pool, idx + am, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = GPBO_ECUDA;
+        if (top_idx && rc == GPBO_OK &&
+            cudaMemcpyAsync(top_idx, idx, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = GPBO_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = GPBO_ECUDA;
+        *argmax = pool;
+        *ei_max = em;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(idx);
+    cudaFree(hist);
+    cudaFree(Xk);
+    if (own) cudaFree(own);
+    return rc;
+}
+
+}  // extern "C"

@@ -81,6 +81,16 @@ _step_batched = _sig("search_step_batched", C.c_int, [_P, C.c_int, C.POINTER(_P)
                                                      C.c_int, C.c_uint, _D, _D, _L])
 _posterior_noalloc = _sig("gp_posterior_ei_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double,
                                                                C.c_double, _P, _P, _P, _L, _D])
+_mlp_create = _sig("mlp_create", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)])
+_mlp_free = _sig("mlp_free", C.c_int, [_P])
+_mlp_params = _sig("mlp_params", C.c_int, [_P, _P, _P])
+_mlp_forward = _sig("mlp_forward", C.c_int, [_P, _P, _P, C.c_int, _P])
+_mlp_grads = _sig("mlp_gradients", C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P])
+_mlp_train = _sig("mlp_train", C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_uint64,
+                                         C.POINTER(C.c_float)])
+_mlp_norm = _sig("mlp_norm", C.c_int, [_P, _D])
+_screen_sur = _sig("surrogate_screen", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_int, C.c_double, C.c_double,
+                                                 _P, _P, _L, _D])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
 _screen = _sig("interdep_screen", C.c_int, [_P, C.POINTER(GpboObjective), C.c_int, C.POINTER(ScreenOpts), _P, _P,
                                              _P, _I, _P])
@@ -322,6 +332,66 @@ class Context:
         check(_screen(self._h, C.byref(obj), d, C.byref(opts), score.ctypes.data, infl.ctypes.data,
                       group.ctypes.data, C.byref(ng), fixed.ctypes.data), "interdep_screen")
         return {"score": score, "influence": infl, "group_of": group, "n_groups": int(ng.value), "fixed": fixed}
+
+
+class Surrogate:
+    """Ensemble pre-screen network (learned form of candidate scoring)."""
+
+    def __init__(self, ctx, E=8, d=20, H=256, seed=5):
+        self.ctx = ctx
+        self.E, self.d, self.H = E, d, H
+        self.P = d * H + H + H * H + H + 2 * H + 2
+        self._h = _P()
+        check(_mlp_create(ctx._h, E, d, H, int(seed), C.byref(self._h)), "mlp_create")
+        ctx._models.add(self)   # freed before the context
+
+    def free(self):
+        if self._h:
+            _mlp_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def params(self, new=None):
+        out = np.empty((self.E, self.P), dtype=np.float32)
+        inp = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        check(_mlp_params(self._h, out.ctypes.data, None if inp is None else inp.ctypes.data), "mlp_params")
+        return out
+
+    def forward(self, X, out):
+        check(_mlp_forward(self.ctx._h, self._h, _ptr(X), int(X.shape[0]), _ptr(out)), "mlp_forward")
+        return out
+
+    def gradients(self, X, T):
+        g = np.empty((self.E, self.P), dtype=np.float32)
+        loss = np.empty(self.E, dtype=np.float32)
+        check(_mlp_grads(self.ctx._h, self._h, _ptr(X), _ptr(T), int(X.shape[0]), g.ctypes.data, loss.ctypes.data),
+              "mlp_gradients")
+        return loss, g
+
+    def train(self, X, mu, sigma, steps, batch=1024, lr=1e-3, seed=7):
+        fl = C.c_float(0.0)
+        check(_mlp_train(self.ctx._h, self._h, _ptr(X), _ptr(mu), _ptr(sigma), int(X.shape[0]), int(steps),
+                         int(batch), float(lr), int(seed), C.byref(fl)), "mlp_train")
+        return float(fl.value)
+
+    def norm(self):
+        v = np.empty(4)
+        check(_mlp_norm(self._h, v.ctypes.data_as(_D)), "mlp_norm")
+        return v
+
+    def screen(self, model, M, seed, k, y_best, xi=0.0, ei_pool=None, want_top=False):
+        am = C.c_int64(-1)
+        em = C.c_double(0.0)
+        top = np.empty(k, dtype=np.int64) if want_top else None
+        check(_screen_sur(self.ctx._h, model._h, self._h, int(M), int(seed), int(k), float(y_best), float(xi),
+                          _ptr(ei_pool), None if top is None else top.ctypes.data, C.byref(am), C.byref(em)),
+              "surrogate_screen")
+        return int(am.value), float(em.value), top
 
 
 class Model:

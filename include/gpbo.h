@@ -298,7 +298,18 @@ int mlp_train(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *mu, con
               int batch, float lr, uint64_t seed, float *final_loss);
 /* Target standardisation (mu mean, mu sd, log-sigma mean, log-sigma sd), host. */
 int mlp_norm(const gpbo_mlp *net, double *norm4);
-/* Draw M candidates from seed (stream 2), score them with the ensemble's EI below y_best,
+/* Ensemble scores of M candidates: rows of X (device, M x d FP32) or, with X = NULL,
+ * candidates 0 .. M-1 drawn from seed (stream 2, as gpbo_gen_candidates draws them).
+ * Writes device arrays of M floats: ei = EI(mu_bar, sigma_bar) below y_best (minimisation),
+ * mu = mu_bar and sigma = sigma_bar (mu and sigma may be NULL).
+ * prec GPBO_PREC_F32: FP32 forward on the CUDA cores (any d, H), exact GELU.
+ * prec GPBO_PREC_BF16: one tensor-core launch (tcgen05, BF16 weights and activations, FP32
+ * accumulate, tanh-form GELU), fused with the combine and the EI; needs H = 256 and
+ * d <= 31, else GPBO_ENOTSUP.  GPBO_ETIMEOUT if a bounded device wait gave up.  Synchronises. */
+int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t seed, double y_best, double xi,
+              int prec, float *ei, float *mu, float *sigma);
+/* Draw M candidates from seed (stream 2), score them with the ensemble's EI below y_best
+ * (the BF16 tensor-core path of mlp_score when H = 256 and d <= 31, else FP32),
  * keep the k best (radix select; ties at the k-th value taken in any order), re-score those
  * k with the exact GP-EI of `model` (FP32 or 16-bit scoring) and return the best pool index
  * and its exact EI.  ei_pool: device M floats for the surrogate EI, or NULL (then the call

@@ -12,8 +12,14 @@
  *     dO = (o - t) / B;  dW3 = h2^T dO;  db3 = sum_b dO;  dh2 = dO W3^T;  dz2 = dh2 g'(z2);
  *     dW2 = h1^T dz2;  db2 = sum_b dz2;  dh1 = dz2 W2^T;  dz1 = dh1 g'(z1);
  *     dW1 = x^T dz1;  db1 = sum_b dz1;   g'(z) = Phi(z) + z phi(z).
+ * Ensemble of E networks (the pre-screen's score of a candidate):
+ *     mu_e = o_e0 n1 + n0,  sigma_e = exp(o_e1 n3 + n2)   (n = target mean/sd of mu, log sigma)
+ *     mu_bar = (1/E) sum_e mu_e,  sigma_bar^2 = (1/E) sum_e sigma_e^2 + (1/E) sum_e (mu_e - mu_bar)^2
+ *     (the variance of the equal-weight mixture of the members), ei = EI(mu_bar, sigma_bar).
  * Pins: tests/test_oracle_mlp.py checks the forward against numpy matrix products, the
- * GELU against scipy's normal CDF, and every gradient against central finite differences.
+ * GELU against scipy's normal CDF, every gradient against central finite differences, and
+ * the ensemble against the one-member case, identical members, and the two-member closed
+ * form sigma_bar^2 = (s1^2 + s2^2)/2 + ((m1 - m2)/2)^2.
  */
 #include <math.h>
 #include <stdint.h>
@@ -115,4 +121,37 @@ double orc_mlp_backward(const double *x, int B, int d, int H, const double *W1, 
     free(Z1); free(Z2); free(H2); free(O); free(dz2); free(dz1);
     if (loss_out) *loss_out = L;
     return L;
+}
+
+double orc_ei(double mu, double sigma, double tau, double xi);
+
+/* theta: E x P (one network after another); X: B x d; norm4 = {n0, n1, n2, n3}.
+ * Outputs B values each (any may be NULL). */
+void orc_mlp_ensemble(const double *theta, int E, const double *X, int B, int d, int H, const double *norm4,
+                      double tau, double xi, double *mu_bar, double *sigma_bar, double *ei)
+{
+    const size_t P = (size_t)d * H + H + (size_t)H * H + H + 2 * (size_t)H + 2;
+    double *o = (double *)malloc(sizeof(double) * (size_t)E * B * 2);
+    for (int e = 0; e < E; ++e) {
+        const double *th = theta + (size_t)e * P;
+        const double *W1 = th, *b1 = W1 + (size_t)d * H, *W2 = b1 + H, *b2 = W2 + (size_t)H * H, *W3 = b2 + H,
+                     *b3 = W3 + 2 * (size_t)H;
+        orc_mlp_forward(X, B, d, H, W1, b1, W2, b2, W3, b3, NULL, NULL, NULL, o + (size_t)e * B * 2);
+    }
+    for (int b = 0; b < B; ++b) {
+        double m = 0.0, v = 0.0, s2 = 0.0;
+        for (int e = 0; e < E; ++e) m += o[((size_t)e * B + b) * 2] * norm4[1] + norm4[0];
+        m /= E;
+        for (int e = 0; e < E; ++e) {
+            const double mu = o[((size_t)e * B + b) * 2] * norm4[1] + norm4[0];
+            const double sg = exp(o[((size_t)e * B + b) * 2 + 1] * norm4[3] + norm4[2]);
+            v += (mu - m) * (mu - m);
+            s2 += sg * sg;
+        }
+        const double sb = sqrt(s2 / E + v / E);
+        if (mu_bar) mu_bar[b] = m;
+        if (sigma_bar) sigma_bar[b] = sb;
+        if (ei) ei[b] = orc_ei(m, sb, tau, xi);
+    }
+    free(o);
 }

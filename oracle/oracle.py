@@ -74,6 +74,8 @@ def _bind_mlp(L):
     L.orc_gelu.restype = C.c_double
     L.orc_gelu.argtypes = [C.c_double]
     L.orc_mlp_forward.argtypes = [_D, C.c_int, C.c_int, C.c_int] + [_D] * 10
+    L.orc_mlp_ensemble.argtypes = [_D, C.c_int, _D, C.c_int, C.c_int, C.c_int, _D, C.c_double, C.c_double, _D, _D,
+                                   _D]
     L.orc_mlp_backward.restype = C.c_double
     L.orc_mlp_backward.argtypes = [_D, C.c_int, C.c_int, C.c_int] + [_D] * 14
 
@@ -346,3 +348,16 @@ def mlp_grad(theta, X, T, d, H):
     lib().orc_mlp_backward(pX, B, d, H, *[q.ctypes.data_as(_D) for q in parts], pT,
                            *[g.ctypes.data_as(_D) for g in grads], loss.ctypes.data_as(_D))
     return float(loss[0]), np.concatenate([g.ravel() for g in grads])
+
+
+def mlp_ensemble(thetas, X, d, H, norm4=(0.0, 1.0, 0.0, 1.0), tau=0.0, xi=0.0):
+    """(mu_bar, sigma_bar, ei) of the ensemble `thetas` (E x P) on the rows of X."""
+    th, pth = _d(np.asarray(thetas, dtype=np.float64).reshape(-1))
+    E = th.shape[0] // mlp_count(d, H)
+    X, pX = _d(X)
+    B = X.shape[0]
+    nm, pn = _d(np.asarray(norm4, dtype=np.float64))
+    mu, sg, ei_ = np.empty(B), np.empty(B), np.empty(B)
+    lib().orc_mlp_ensemble(pth, E, pX, B, d, H, pn, float(tau), float(xi), mu.ctypes.data_as(_D),
+                           sg.ctypes.data_as(_D), ei_.ctypes.data_as(_D))
+    return mu, sg, ei_

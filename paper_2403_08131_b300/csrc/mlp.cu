@@ -27,6 +27,10 @@ struct gpbo_mlp {
     int cap = 0;
     float *bx = nullptr, *bt = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *o = nullptr;
     float *d2 = nullptr, *d1 = nullptr, *dO = nullptr, *loss = nullptr;
+    // tensor-core operands (BF16 K-major weights + FP32 aux), rebuilt when theta changes
+    void *wt16 = nullptr;
+    float *aux = nullptr;
+    int64_t version = 0, packed = -1;
 };
 
 namespace gpbo {
@@ -227,24 +231,30 @@ __global__ void k_make_targets(const float *mu, const float *sigma, int64_t N, c
     T[2 * i + 1] = (float)((log(fmax((double)sigma[i], 1e-30)) - stats[2]) / stats[3]);
 }
 
-// Ensemble EI per candidate from the networks' standardised outputs O [E][C][2].
+// Ensemble EI per candidate from the networks' standardised outputs O [E][C][2]; the sums
+// are taken about the first network's mean so that var_e mu_e does not cancel.
 __global__ void k_ensemble_ei(const float *O, int E, int64_t C, int64_t c0, float n0, float n1, float n2, float n3,
-                              float tau, float xi, float *ei)
+                              float tau, float xi, float *ei, float *mu_out, float *sigma_out)
 {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= C) return;
-    float sm = 0.f, sm2 = 0.f, sv = 0.f;
+    float shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;
     for (int e = 0; e < E; ++e) {
         const float mu = O[((int64_t)e * C + c) * 2] * n1 + n0;
         const float ls = O[((int64_t)e * C + c) * 2 + 1] * n3 + n2;
         const float s = expf(ls);
-        sm += mu;
-        sm2 += mu * mu;
-        sv += s * s;
+        if (e == 0) shift = mu;
+        const float dm = mu - shift;
+        sm += dm;
+        sm2 = fmaf(dm, dm, sm2);
+        sv = fmaf(s, s, sv);
     }
-    const float mbar = sm / E;
-    const float var = sv / E + fmaxf(sm2 / E - mbar * mbar, 0.f);
-    ei[c0 + c] = ei_minf(mbar, sqrtf(var), tau, xi);
+    const float invE = 1.0f / (float)E, mm = sm * invE;
+    const float mbar = shift + mm;
+    const float sbar = sqrtf(sv * invE + fmaxf(sm2 * invE - mm * mm, 0.f));
+    ei[c0 + c] = ei_minf(mbar, sbar, tau, xi);
+    if (mu_out) mu_out[c0 + c] = mbar;
+    if (sigma_out) sigma_out[c0 + c] = sbar;
 }
 
 __global__ void k_gen_rows(uint64_t seed, int64_t c0, int64_t C, int d, float *X)
@@ -418,6 +428,52 @@ static int backward(gpbo_ctx *ctx, gpbo_mlp *net, int B)
     return GPBO_OK;
 }
 
+static int ensure_packed(gpbo_ctx *ctx, gpbo_mlp *net)
+{
+    if (!mlp_tc_usable(net->d, net->H)) return GPBO_ENOTSUP;
+    if (!net->wt16) {
+        GPBO_CUDA_TRY(cudaMalloc(&net->wt16, mlp_tc_weight_bytes(net->E)));
+        GPBO_CUDA_TRY(cudaMalloc(&net->aux, sizeof(float) * mlp_tc_aux_floats(net->E)));
+    }
+    if (net->packed != net->version) {
+        const Off f = offsets(net->d, net->H);
+        const int64_t off[6] = {f.W1, f.b1, f.W2, f.b2, f.W3, f.b3};
+        GPBO_TRY(mlp_tc_pack(ctx, net->theta, net->E, net->d, net->P, off, net->wt16, net->aux));
+        net->packed = net->version;
+    }
+    return GPBO_OK;
+}
+
+// Ensemble (mu_bar, sigma_bar, EI) for M candidates: rows of X (device) or, when X is null,
+// pool candidates 0 .. M-1 drawn from seed.  BF16: one tensor-core launch; F32: CUDA-core
+// forward in chunks.  Outputs are pool-indexed device arrays (mu, sigma may be null).
+static int score_pool(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t seed, double tau, double xi,
+                      int prec, float *ei, float *mu, float *sigma)
+{
+    cudaStream_t st = ctx->stream;
+    const double *nm = net->norm;
+    if (prec == GPBO_PREC_BF16) {
+        GPBO_TRY(ensure_packed(ctx, net));
+        return mlp_tc_score(ctx, net->wt16, net->aux, net->E, net->d, nm, X, seed, 0, M, tau, xi, ei, mu, sigma);
+    }
+    if (prec != GPBO_PREC_F32) return GPBO_EINVAL;
+    const int C = 32768;  // candidates per chunk
+    GPBO_TRY(ensure_batch(net, C));
+    for (int64_t c0 = 0; c0 < M; c0 += C) {
+        const int Cc = (int)std::min<int64_t>(C, M - c0);
+        const float *xb = X ? X + c0 * net->d : net->bx;
+        if (!X) {
+            k_gen_rows<<<nb((int64_t)Cc * net->d), 256, 0, st>>>(seed, c0, Cc, net->d, net->bx);
+            GPBO_LAUNCH_CHECK(ctx);
+        }
+        GPBO_TRY(forward(ctx, net, xb, Cc, nullptr, net->h1, nullptr, net->h2, net->o, false));
+        k_ensemble_ei<<<nb(Cc), 256, 0, st>>>(net->o, net->E, Cc, c0, (float)nm[0], (float)nm[1], (float)nm[2],
+                                              (float)nm[3], (float)tau, (float)xi, ei, mu, sigma);
+        GPBO_LAUNCH_CHECK(ctx);
+    }
+    return GPBO_OK;
+}
+
 }  // namespace gpbo
 
 using namespace gpbo;
@@ -461,6 +517,8 @@ int mlp_free(gpbo_mlp *net)
                      net->z1,    net->h1,   net->z2, net->h2, net->o,    net->d2, net->d1, net->dO};
     for (float *b : bufs)
         if (b) cudaFree(b);
+    if (net->wt16) cudaFree(net->wt16);
+    if (net->aux) cudaFree(net->aux);
     delete net;
     return GPBO_OK;
 }
@@ -470,7 +528,10 @@ int mlp_params(gpbo_mlp *net, float *host_out, const float *host_in)
     if (!net) return GPBO_EINVAL;
     gpbo_ctx *ctx = net->ctx;
     const size_t bytes = sizeof(float) * (size_t)net->E * net->P;
-    if (host_in) GPBO_CUDA_TRY(cudaMemcpyAsync(net->theta, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (host_in) {
+        GPBO_CUDA_TRY(cudaMemcpyAsync(net->theta, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        net->version++;
+    }
     if (host_out) GPBO_CUDA_TRY(cudaMemcpyAsync(host_out, net->theta, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     return GPBO_OK;
@@ -528,6 +589,7 @@ int mlp_train(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *mu, con
         k_adam<<<nb(count), 256, 0, st>>>(net->theta, net->grad, net->m, net->v, count, lr, c1, c2);
         ctx->launches++;
     }
+    net->version++;
     if (rc == GPBO_OK && cudaGetLastError() != cudaSuccess) rc = GPBO_ECUDA;
     double hs[4];
     if (rc == GPBO_OK && cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = GPBO_ECUDA;
@@ -554,6 +616,20 @@ int mlp_norm(const gpbo_mlp *net, double *norm4)
     return GPBO_OK;
 }
 
+int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t seed, double y_best, double xi, int prec,
+              float *ei, float *mu, float *sigma)
+{
+    if (!ctx || !net || !ei || M < 1 || M > 0x7fffffffll) return GPBO_EINVAL;
+    if (prec != GPBO_PREC_BF16 && prec != GPBO_PREC_F32) return GPBO_EINVAL;
+    GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
+    GPBO_TRY(score_pool(ctx, net, X, M, seed, y_best, xi, prec, ei, mu, sigma));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    unsigned bits = 0;
+    GPBO_TRY(take_device_status(ctx, &bits));
+    if (bits & DEV_TIMEOUT) return GPBO_ETIMEOUT;
+    return GPBO_OK;
+}
+
 int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_t M, uint64_t seed, int k,
                      double y_best, double xi, float *ei_pool, int64_t *top_idx, int64_t *argmax, double *ei_max)
 {
@@ -563,9 +639,7 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
     if (model->prec == GPBO_PREC_F64) return GPBO_ENOTSUP;
     GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    const int d = net->d, H = net->H, E = net->E;
-    const int C = 32768;  // candidates per chunk
-    GPBO_TRY(ensure_batch(net, C));
+    const int d = net->d;
     float *ei = ei_pool;
     float *own = nullptr;
     if (!ei) {
@@ -579,18 +653,8 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
     GPBO_CUDA_TRY(cudaMalloc(&hist, sizeof(uint32_t) * (4096 + 4)));
     GPBO_CUDA_TRY(cudaMalloc(&Xk, sizeof(float) * (size_t)k * d));
     uint32_t *sel = hist + 4096, *counters = hist + 4098;
-    int rc = GPBO_OK;
-    const double *nm = net->norm;
-    for (int64_t c0 = 0; c0 < M && rc == GPBO_OK; c0 += C) {
-        const int Cc = (int)std::min<int64_t>(C, M - c0);
-        k_gen_rows<<<nb((int64_t)Cc * d), 256, 0, st>>>(seed, c0, Cc, d, net->bx);
-        ctx->launches++;
-        rc = forward(ctx, net, net->bx, Cc, nullptr, net->h1, nullptr, net->h2, net->o, false);
-        if (rc != GPBO_OK) break;
-        k_ensemble_ei<<<nb(Cc), 256, 0, st>>>(net->o, E, Cc, c0, (float)nm[0], (float)nm[1], (float)nm[2], (float)nm[3],
-                                              (float)y_best, (float)xi, ei);
-        ctx->launches++;
-    }
+    const int prec = mlp_tc_usable(d, net->H) ? GPBO_PREC_BF16 : GPBO_PREC_F32;
+    int rc = score_pool(ctx, net, nullptr, M, seed, y_best, xi, prec, ei, nullptr, nullptr);
     // top k by the surrogate's EI
     if (rc == GPBO_OK) {
         uint32_t init[8] = {0, (uint32_t)k, 0, 0, 0, 0, 0, 0};

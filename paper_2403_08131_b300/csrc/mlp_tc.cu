@@ -1,0 +1,467 @@
+// Ensemble pre-screen forward on the tensor cores (BF16 operands, FP32 accumulate), fused
+// with the ensemble combine and the expected improvement of every candidate.
+//
+// For a tile of 128 candidates and each network e of the ensemble (d -> 256 -> 256 -> 2):
+//   Z1 = [x | 1] [W1 ; b1]         tcgen05.mma, K = 32 (d <= 31 inputs, then the constant 1)
+//   H1 = bf16(gelu(Z1))            epilogue; written to shared memory as the next A operand
+//   Z2 = H1 W2                     tcgen05.mma, K = 256 in four 64-column K tiles
+//   o  = gelu(Z2 + b2) W3 + b3     epilogue, FP32 on the CUDA cores (two outputs)
+// then mu_e = o_0 sd_mu + mean_mu and sigma_e = exp(o_1 sd_ls + mean_ls); after the last
+// network mu_bar = mean_e mu_e, sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e and
+// EI(mu_bar, sigma_bar) for minimisation.
+// gelu is the tanh form of Hendrycks & Gimpel (2016), evaluated with the hardware
+// tanh.approx.f32; it differs from z Phi(z) by < 5e-4 absolute plus tanh.approx's relative
+// error (about 2^-11) times |z|/2, below the BF16 rounding of H1 for |z| >= 1/2.
+//
+// Roles (one CTA per SM, persistent over tiles; 576 threads):
+//   warp 0      TMA: per network, [W1 ; b1]^T (256 x 64, zero padded) then W2^T in four
+//               256 x 64 K chunks; 4 stages of 32 KiB.  The packed ensemble (8 networks,
+//               1.3 MB) is read from L2 for every tile.
+//   warp 1      TMEM (512 columns: Z1 in 0..255, Z2 in 256..511); one lane issues the MMAs
+//   warps 2-17  epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4;
+//               warps 2-5 (group 0) also build the x tile and own the ensemble state of
+//               their rows (one thread = one candidate)
+// H1 is written K tile by K tile (every warp does its 16 columns of tile q, then of q+1), and
+// the second layer's MMAs on K tile q start once tile q is complete, so layer 2 runs under
+// the first-layer epilogue; layer 1 of the next network runs under the second-layer one.
+// Every wait is bounded (about 2 s of SM clock); on timeout the kernel raises DEV_TIMEOUT,
+// every role leaves its loop, the producer waits (bounded) for its copies in flight, the MMA
+// issuer drains, and the allocating warp frees TMEM.
+#include "tc_common.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace gpbo {
+namespace mtc {
+
+using namespace tcx;
+
+constexpr int BM = 128;                  // candidates per tile
+constexpr int HID = 256;                 // hidden width (MMA N)
+constexpr int KT = 64;                   // K elements per 128-byte swizzled row
+constexpr int CHUNKS = 5;                // per network: [W1;b1]^T, then W2^T in 4 K chunks
+constexpr int STAGES = 4;
+constexpr int EPI_WARPS = 16;
+constexpr int GROUPS = EPI_WARPS / 4;    // column groups
+constexpr int THREADS = (2 + EPI_WARPS) * 32;
+constexpr int TMEM_COLS = 512;
+constexpr int TILE_BYTES = BM * 128;     // one 128 x 64 BF16 K tile
+constexpr int H1_BYTES = 4 * TILE_BYTES; // 128 x 256
+constexpr int X_BYTES = TILE_BYTES;
+constexpr int W_BYTES = HID * 128;       // one 256 x 64 BF16 chunk
+constexpr int AUX = 1024;                // per network FP32: b2 [256], W3 [256 x 2], b3 [2], pad
+constexpr int DMAX = 31;
+
+struct Shared {
+    uint64_t full[STAGES];
+    uint64_t empty[STAGES];
+    uint64_t z1_full, z2_full, z2_empty;
+    uint64_t h_full[4];
+    uint64_t x_full;
+    uint64_t part_ready[2], part_free[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    float2 part[2][GROUPS - 1][BM];      // layer-3 partial sums of column groups 1..3
+};
+
+inline size_t smem_bytes() { return (size_t)H1_BYTES + X_BYTES + (size_t)STAGES * W_BYTES + 1024 + sizeof(Shared); }
+
+struct Params {
+    int64_t C;          // candidates
+    int64_t c0;         // pool index of the first
+    int num_tiles;
+    int E, d, nk1;      // networks, inputs, layer-1 MMA K steps (16 each)
+    uint64_t seed;
+    const float *Xc;    // pool-indexed rows of d, or null: drawn from seed (stream 2)
+    const float *aux;   // E x AUX
+    float n0, n1, n2, n3;
+    float tau, xi;
+    float *ei, *mu, *sigma;  // pool-indexed; mu and sigma may be null
+    unsigned *status;
+    uint32_t idesc;
+};
+
+__device__ __forceinline__ float gelu_tanh(float z)
+{
+    const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);  // sqrt(2/pi) (z + 0.044715 z^3)
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+    const float hz = 0.5f * z;
+    return fmaf(hz, t, hz);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in BF16, 128-byte swizzled
+// (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
+__device__ __forceinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)
+{
+    const int64_t cl = t * BM + r;
+    const int64_t c = P.c0 + cl;
+    uint32_t w[16];
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+        float v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int kk = k + u;
+            float x = 0.0f;
+            if (kk < P.d) {
+                if (P.Xc) x = cl < P.C ? P.Xc[c * P.d + kk] : 0.5f;
+                else x = uniform24f(P.seed, 2, (uint64_t)(c * P.d + kk));
+            } else if (kk == P.d) {
+                x = 1.0f;
+            }
+            v[u] = x;
+        }
+        w[k / 2] = pack_bf16(v[0], v[1]);
+    }
+    unsigned char *row = xs + r * 128;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint4 val = j < 4 ? make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4 *>(row + ((j ^ (r & 7)) * 16)) = val;
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_constant__ CUtensorMap map_w, const Params P)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *h1 = base;                       // 4 K tiles
+    unsigned char *xs = base + H1_BYTES;            // 1 K tile
+    unsigned char *wst = xs + X_BYTES;              // STAGES x W_BYTES
+    Shared *sh = (Shared *)(wst + (size_t)STAGES * W_BYTES);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        mbar_init(&sh->z1_full, 1);
+        mbar_init(&sh->z2_full, 1);
+        mbar_init(&sh->z2_empty, EPI_WARPS);
+        for (int q = 0; q < 4; ++q) mbar_init(&sh->h_full[q], EPI_WARPS);
+        mbar_init(&sh->x_full, 4);
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(&sh->part_ready[p], 4 * (GROUPS - 1));
+            mbar_init(&sh->part_free[p], 4);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort_flag = &sh->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: the same chunk sequence for every tile
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_w) : "memory");
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];
+            uint32_t armed_par[STAGES];
+            for (int s = 0; s < STAGES; ++s) armed[s] = 0, armed_par[s] = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x)
+                for (int e = 0; ok && e < P.E; ++e)
+                    for (int c = 0; c < CHUNKS; ++c) {
+                        if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&sh->full[stage], W_BYTES);
+                        armed[stage] = 1;
+                        armed_par[stage] = phase;
+                        tma_load_2d(wst + (size_t)stage * W_BYTES, &map_w, 0, (e * CHUNKS + c) * HID, &sh->full[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s]) mbar_wait(&sh->full[s], armed_par[s], abort_flag, P.status, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t k = 0, ti = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x, ++ti) {
+                for (int e = 0; ok && e < P.E; ++e, ++k) {
+                    // layer 1 (Z1 is free: layer 2 of the previous network waited for all of H1)
+                    if (e == 0 && !mbar_wait(&sh->x_full, ti & 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                    tc_fence_after();
+                    {
+                        const unsigned char *w = wst + (size_t)stage * W_BYTES;
+                        for (int kk = 0; kk < P.nk1; ++kk)
+                            mma_f16(tmem, smem_desc(xs + kk * 32), smem_desc(w + kk * 32), P.idesc, kk ? 1u : 0u);
+                    }
+                    mma_commit(&sh->empty[stage]);
+                    mma_commit(&sh->z1_full);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    // layer 2, K tile by K tile as H1 fills
+                    if (!mbar_wait(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    for (int q = 0; q < 4; ++q) {
+                        if (!mbar_wait(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        tc_fence_after();
+                        const unsigned char *w = wst + (size_t)stage * W_BYTES;
+                        const unsigned char *a = h1 + q * TILE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16(tmem + HID, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc,
+                                    (q | kk) ? 1u : 0u);
+                        mma_commit(&sh->empty[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(&sh->z2_full);
+                }
+            }
+            mma_commit(&sh->drain);
+            mbar_wait(&sh->drain, 0, abort_flag, P.status, false);
+        }
+    } else {
+        // ---------------- epilogue
+        const int ew = warp - 2;
+        const int quad = warp & 3;
+        const int grp = ew >> 2;
+        const int row = quad * 32 + lane;
+        const bool builder = grp == 0;
+        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        const float invE = 1.0f / (float)P.E;
+        float mu_shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;  // ensemble state (group 0)
+        if (builder && (int)blockIdx.x < P.num_tiles) {
+            build_x(xs, row, blockIdx.x, P);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->x_full);
+        }
+        uint32_t k = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+            const int64_t cl = (int64_t)t * BM + row;
+            for (int e = 0; e < P.E; ++e, ++k) {
+                const float *aux = P.aux + (size_t)e * AUX;
+                // ---- layer-1 epilogue: H1 = bf16(gelu(Z1)), K tile by K tile
+                bool g = mbar_wait(&sh->z1_full, k & 1u, abort_flag, P.status);
+                if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
+                tc_fence_after();
+                if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
+                    // the last network's layer-1 MMAs are complete: the x tile is free
+                    build_x(xs, row, t + gridDim.x, P);
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->x_full);
+                }
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_addr + (uint32_t)(q * KT + grp * 16), v);
+                    uint32_t w[8];
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) w[j / 2] = pack_bf16(gelu_tanh(v[j]), gelu_tanh(v[j + 1]));
+                    unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
+                    const int j0 = 2 * grp, j1 = 2 * grp + 1;
+                    *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->h_full[q]);
+                }
+                // ---- layer-2 epilogue and layer 3
+                g = mbar_wait(&sh->z2_full, k & 1u, abort_flag, P.status);
+                if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
+                tc_fence_after();
+                float o0 = 0.f, o1 = 0.f;
+#pragma unroll 1
+                for (int cb = 0; cb < 2; ++cb) {
+                    float v[32];
+                    const int j0 = grp * 64 + cb * 32;
+                    tmem_ld32(tmem + lane_addr + (uint32_t)(HID + j0), v);
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 b = __ldg(reinterpret_cast<const float4 *>(aux + j0 + j));
+                        const float4 wa = __ldg(reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j)));
+                        const float4 wb = __ldg(reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4));
+                        const float h0 = gelu_tanh(v[j] + b.x), h1v = gelu_tanh(v[j + 1] + b.y);
+                        const float h2 = gelu_tanh(v[j + 2] + b.z), h3 = gelu_tanh(v[j + 3] + b.w);
+                        o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
+                        o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->z2_empty);
+                // ---- combine the column groups; group 0 updates the ensemble state
+                const int par = k & 1;
+                const uint32_t use = (k >> 1) & 1u;
+                if (!builder) {
+                    g = mbar_wait(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
+                    if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
+                    sh->part[par][grp - 1][row] = make_float2(o0, o1);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->part_ready[par]);
+                } else {
+                    g = mbar_wait(&sh->part_ready[par], use, abort_flag, P.status);
+                    if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
+#pragma unroll
+                    for (int gg = 0; gg < GROUPS - 1; ++gg) {
+                        const float2 p = sh->part[par][gg][row];
+                        o0 += p.x;
+                        o1 += p.y;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->part_free[par]);
+                    const float m = (o0 + aux[3 * HID]) * P.n1 + P.n0;
+                    const float s = expf((o1 + aux[3 * HID + 1]) * P.n3 + P.n2);
+                    if (e == 0) {
+                        mu_shift = m;
+                        sm = sm2 = sv = 0.f;
+                    }
+                    const float dm = m - mu_shift;
+                    sm += dm;
+                    sm2 = fmaf(dm, dm, sm2);
+                    sv = fmaf(s, s, sv);
+                    if (e == P.E - 1 && cl < P.C) {
+                        const float mm = sm * invE;
+                        const float mbar = mu_shift + mm;
+                        const float sbar = sqrtf(sv * invE + fmaxf(sm2 * invE - mm * mm, 0.f));
+                        const int64_t c = P.c0 + cl;
+                        P.ei[c] = ei_minf(mbar, sbar, P.tau, P.xi);
+                        if (P.mu) P.mu[c] = mbar;
+                        if (P.sigma) P.sigma[c] = sbar;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Pack one network's FP32 parameters (layout W1 [d x H], b1, W2 [H x H], b2, W3 [H x 2], b3)
+// into the kernel's operands: wt = E x 5 chunks of 256 x 64 BF16, K-major
+//   chunk 0: row j = [W1[0][j] .. W1[d-1][j], b1[j], 0 ...]
+//   chunk c = 1..4: row j = W2[64(c-1) .. 64c-1][j]
+// and aux = E x 1024 FP32: b2 [256], W3 [256 x 2] (row j = the two outputs), b3 [2], zeros.
+__global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P, int64_t oW1, int64_t ob1,
+                       int64_t oW2, int64_t ob2, int64_t oW3, int64_t ob3, __nv_bfloat16 *__restrict__ wt,
+                       float *__restrict__ aux)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)CHUNKS * HID * KT;
+    if (t < E * per) {
+        const int e = (int)(t / per);
+        const int64_t r = t - e * per;
+        const int c = (int)(r / (HID * KT));
+        const int j = (int)((r / KT) % HID);
+        const int kk = (int)(r % KT);
+        const float *th = theta + e * P;
+        float v;
+        if (c == 0) v = kk < d ? th[oW1 + (int64_t)kk * HID + j] : (kk == d ? th[ob1 + j] : 0.0f);
+        else v = th[oW2 + (int64_t)(64 * (c - 1) + kk) * HID + j];
+        wt[t] = __float2bfloat16_rn(v);
+    }
+    if (t < (int64_t)E * AUX) {
+        const int e = (int)(t / AUX);
+        const int i = (int)(t % AUX);
+        const float *th = theta + e * P;
+        float v = 0.0f;
+        if (i < HID) v = th[ob2 + i];
+        else if (i < 3 * HID) v = th[oW3 + (i - HID)];
+        else if (i < 3 * HID + 2) v = th[ob3 + (i - 3 * HID)];
+        aux[t] = v;
+    }
+}
+
+}  // namespace mtc
+
+bool mlp_tc_usable(int d, int H) { return H == mtc::HID && d >= 1 && d <= mtc::DMAX; }
+
+size_t mlp_tc_weight_bytes(int E) { return (size_t)E * mtc::CHUNKS * mtc::W_BYTES; }
+size_t mlp_tc_aux_floats(int E) { return (size_t)E * mtc::AUX; }
+
+int mlp_tc_pack(gpbo_ctx *ctx, const float *theta, int E, int d, int64_t P, const int64_t off[6], void *wt, float *aux)
+{
+    const int64_t total = std::max<int64_t>((int64_t)E * mtc::CHUNKS * mtc::HID * mtc::KT, (int64_t)E * mtc::AUX);
+    mtc::k_pack<<<(unsigned)cdiv64(total, 256), 256, 0, ctx->stream>>>(theta, E, d, P, off[0], off[1], off[2], off[3],
+                                                                       off[4], off[5], (__nv_bfloat16 *)wt, aux);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, const double norm[4], const float *Xc,
+                 uint64_t seed, int64_t c0, int64_t C, double tau, double xi, float *ei, float *mu, float *sigma)
+{
+    if (!mlp_tc_usable(d, mtc::HID) || E < 1 || C < 1 || !ei || ((uintptr_t)wt & 15) || ((uintptr_t)aux & 15))
+        return GPBO_EINVAL;
+    if (cdiv64(C, mtc::BM) > 0x7fffffffll) return GPBO_EINVAL;
+    CUtensorMap mw;
+    GPBO_TRY(encode_2d(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, wt, (uint64_t)E * mtc::CHUNKS * mtc::HID, mtc::KT,
+                       mtc::HID));
+    mtc::Params P;
+    P.C = C;
+    P.c0 = c0;
+    P.num_tiles = (int)cdiv64(C, mtc::BM);
+    P.E = E;
+    P.d = d;
+    P.nk1 = (d + 1 + 15) / 16;
+    P.seed = seed;
+    P.Xc = Xc;
+    P.aux = aux;
+    P.n0 = (float)norm[0];
+    P.n1 = (float)norm[1];
+    P.n2 = (float)norm[2];
+    P.n3 = (float)norm[3];
+    P.tau = (float)tau;
+    P.xi = (float)xi;
+    P.ei = ei;
+    P.mu = mu;
+    P.sigma = sigma;
+    P.status = ctx->dev_status;
+    P.idesc = tcx::idesc_f16(1u, mtc::HID, mtc::BM);
+    const size_t smem = mtc::smem_bytes();
+    GPBO_CUDA_TRY(cudaFuncSetAttribute(mtc::k_mlp_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::min(P.num_tiles, ctx->sm_count);
+    mtc::k_mlp_screen_tc<<<grid, mtc::THREADS, smem, ctx->stream>>>(mw, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+}  // namespace gpbo

@@ -89,6 +89,8 @@ _mlp_grads = _sig("mlp_gradients", C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P])
 _mlp_train = _sig("mlp_train", C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_uint64,
                                          C.POINTER(C.c_float)])
 _mlp_norm = _sig("mlp_norm", C.c_int, [_P, _D])
+_mlp_score = _sig("mlp_score", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double, C.c_double, C.c_int, _P,
+                                          _P, _P])
 _screen_sur = _sig("surrogate_screen", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_int, C.c_double, C.c_double,
                                                  _P, _P, _L, _D])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
@@ -383,6 +385,15 @@ class Surrogate:
         v = np.empty(4)
         check(_mlp_norm(self._h, v.ctypes.data_as(_D)), "mlp_norm")
         return v
+
+    def score(self, ei, X=None, M=None, seed=0, y_best=0.0, xi=0.0, prec="bf16", mu=None, sigma=None):
+        """Ensemble (EI, mu_bar, sigma_bar) of rows of X (device) or of M seeded candidates.
+        prec "bf16": tensor-core kernel; "f32": CUDA-core forward."""
+        if X is not None:
+            M = X.shape[0]
+        check(_mlp_score(self.ctx._h, self._h, _ptr(X), int(M), int(seed), float(y_best), float(xi), PREC[prec],
+                         _ptr(ei), _ptr(mu), _ptr(sigma)), "mlp_score")
+        return ei
 
     def screen(self, model, M, seed, k, y_best, xi=0.0, ei_pool=None, want_top=False):
         am = C.c_int64(-1)

@@ -113,3 +113,98 @@ def test_screen_gains_over_unscreened_subset(ctx, trained):
     assert em > best_rand
     # agreement with the exact argmax of the whole pool within the 16-bit bar (same scoring path)
     assert em >= gem * (1 - 2e-3)
+
+
+# ------------------------------------------------------------------ tensor-core (BF16) forward
+def _rand_biases(net, d, H, seed):
+    th = net.params()
+    rng = np.random.default_rng(seed)
+    o_b1, o_b2, o_b3 = d * H, d * H + H + H * H, d * H + H + H * H + H + 2 * H
+    for e in range(th.shape[0]):
+        th[e, o_b1:o_b1 + H] = rng.normal(0, 0.2, H)
+        th[e, o_b2:o_b2 + H] = rng.normal(0, 0.2, H)
+        th[e, o_b3:o_b3 + 2] = rng.normal(0, 0.2, 2)
+    net.params(th)
+    return th
+
+
+def _check_tc(orc, th, X, ei, mu, sg, nm, tau, d, H):
+    """Tensor-core (mu_bar, sigma_bar, EI) against the FP64 oracle within the BF16 tolerance;
+    returns the worst error / tolerance of each."""
+    from tests._util import bf16_ensemble_tol
+    th = np.asarray(th, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    rm, rs, re = orc.mlp_ensemble(th, X, d, H, nm, tau)
+    tm, ts, te = bf16_ensemble_tol(orc, th, X, d, H, nm, tau)
+    gm, gs, ge = (a.cpu().numpy().astype(np.float64) for a in (mu, sg, ei))
+    r = (np.max(np.abs(gm - rm) / tm), np.max(np.abs(gs - rs) / ts), np.max(np.abs(ge - re) / te))
+    assert max(r) <= 1.0, f"worst error / tolerance (mu_bar, sigma_bar, ei) = {r}"
+    return r
+
+
+@pytest.mark.parametrize("M", [1, 127, 129, 1000])
+def test_tc_forward_matches_oracle_within_bf16_tolerance(ctx, orc, M):
+    """Random-init ensemble (E = 3, random biases) on M explicit rows: the tensor-core
+    mu_bar, sigma_bar and EI against the FP64 oracle within the BF16 tolerance; the FP32
+    path within 1e-4 of it."""
+    import torch
+    d, H = 20, 256
+    net = _net(ctx, 3, d, H, seed=11)
+    th = _rand_biases(net, d, H, 12)
+    X = np.random.default_rng(M).random((M, d)).astype(np.float32)
+    outs = {p: [torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3)] for p in ("bf16", "f32")}
+    for p, (ei, mu, sg) in outs.items():
+        net.score(ei, X=to_dev(X), y_best=0.1, prec=p, mu=mu, sigma=sg)
+    rm, rs, _ = orc.mlp_ensemble(th.astype(np.float64), X.astype(np.float64), d, H, (0, 1, 0, 1), 0.1)
+    r = _check_tc(orc, th, X, *outs["bf16"], (0.0, 1.0, 0.0, 1.0), 0.1, d, H)
+    print(f"M={M}: worst error / tolerance (mu_bar, sigma_bar, ei) = {r[0]:.3f}, {r[1]:.3f}, {r[2]:.3f}")
+    fm, fs = outs["f32"][1].cpu().numpy(), outs["f32"][2].cpu().numpy()
+    assert np.max(np.abs(fm - rm) / (np.abs(rm) + 1)) <= 1e-4 and np.max(np.abs(fs - rs) / rs) <= 1e-4
+
+
+def test_tc_trained_ensemble_seeded_equals_explicit(ctx, orc, trained):
+    """Trained 8-member ensemble: seeded candidates equal the same rows passed explicitly
+    (bit for bit), and both agree with the oracle within the BF16 tolerance."""
+    import torch
+    w, ys, model, net, _, _ = trained
+    d, H, M, seed = 20, 256, 777, 31
+    X = torch.empty((M, d), dtype=torch.float32, device="cuda")
+    ctx.gen_candidates(X, seed=seed)
+    a = [torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3)]
+    b = [torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3)]
+    tau = float(ys.min())
+    net.score(a[0], X=X, y_best=tau, mu=a[1], sigma=a[2])
+    net.score(b[0], M=M, seed=seed, y_best=tau, mu=b[1], sigma=b[2])
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    nm = tuple(net.norm())
+    r = _check_tc(orc, net.params(), X.cpu().numpy(), *a, nm, tau, d, H)
+    print(f"trained: worst error / tolerance (mu_bar, sigma_bar, ei) = {r[0]:.3f}, {r[1]:.3f}, {r[2]:.3f}")
+
+
+def test_tc_full_size_sampled(ctx, orc, trained):
+    """2^22 seeded candidates in one launch: 64 sampled candidates against the oracle."""
+    import torch
+    w, ys, model, net, _, _ = trained
+    d, H, M, seed = 20, 256, 1 << 22, 4243
+    tau = float(ys.min())
+    ei, mu, sg = (torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3))
+    net.score(ei, M=M, seed=seed, y_best=tau, mu=mu, sigma=sg)
+    idx = np.sort(np.random.default_rng(3).choice(M, 64, replace=False))
+    idx[-1] = M - 1
+    X = np.concatenate([W.uniform_points(seed, W.STREAM_CAND, 1, d, first=int(i)) for i in idx])
+    sel = torch.from_numpy(idx).cuda()
+    r = _check_tc(orc, net.params(), X, ei[sel], mu[sel], sg[sel], tuple(net.norm()), tau, d, H)
+    print(f"2^22 sampled: worst error / tolerance = {r[0]:.3f}, {r[1]:.3f}, {r[2]:.3f}")
+    assert torch.isfinite(ei).all() and (ei >= 0).all()
+
+
+def test_tc_rejects_unsupported_shapes(ctx):
+    import torch
+    from paper_2403_08131_b300 import gpbo
+    net = _net(ctx, 2, 20, 128)
+    ei = torch.empty(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(gpbo.GpboError) as e:
+        net.score(ei, M=10, seed=1, prec="bf16")
+    assert e.value.code == gpbo.GPBO_ENOTSUP
+    net.score(ei, M=10, seed=1, prec="f32")

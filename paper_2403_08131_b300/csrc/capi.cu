@@ -28,6 +28,7 @@ int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
         if (ctx->ws) {
             // stream-ordered users of the old arena must finish before it is released
             GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+            if (ctx->side) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side));
             GPBO_CUDA_TRY(cudaFree(ctx->ws));
             ctx->ws = nullptr;
             ctx->ws_size = 0;
@@ -36,6 +37,18 @@ int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
         ctx->ws_size = bytes;
     }
     *out = ctx->ws;
+    return GPBO_OK;
+}
+
+int side_stream(gpbo_ctx *ctx, cudaStream_t *out)
+{
+    if (!ctx->side) {
+        int lo = 0, hi = 0;
+        GPBO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
+        for (cudaEvent_t &e : ctx->side_ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    *out = ctx->side;
     return GPBO_OK;
 }
 
@@ -247,6 +260,12 @@ int gpbo_destroy(gpbo_ctx *ctx)
     if (ctx->dev_status) cudaFree(ctx->dev_status);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    for (cudaEvent_t e : ctx->side_ev)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < ctx->trace_cap; ++i) {
         if (ctx->trace_recs[i].a) cudaEventDestroy(ctx->trace_recs[i].a);
         if (ctx->trace_recs[i].b) cudaEventDestroy(ctx->trace_recs[i].b);

@@ -46,9 +46,9 @@ __global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int 
     k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int n_pad, int kb, int nblk)
+__global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int n_pad, int kb, int nblk, int part)
 {
-    k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y);
+    k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y, part);
 }
 
 __global__ void k_zero_upper_blocks(double *__restrict__ A, int n_pad)
@@ -192,17 +192,18 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
 
 static unsigned blocks_for(int64_t count, int threads = 256) { return (unsigned)((count + threads - 1) / threads); }
 
-static int alpha_solve(gpbo_ctx *ctx, const gp_model *m, const double *rhs, double *work, double *out)
+static int alpha_solve(gpbo_ctx *ctx, cudaStream_t st, const gp_model *m, const double *rhs, double *work,
+                       double *out)
 {
     const int n_pad = m->n_pad, nblk = n_pad / NB;
-    GPBO_CUDA_TRY(cudaMemcpyAsync(work, rhs, sizeof(double) * n_pad, cudaMemcpyDeviceToDevice, ctx->stream));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(work, rhs, sizeof(double) * n_pad, cudaMemcpyDeviceToDevice, st));
     double *z = work + n_pad;
     for (int b = 0; b < nblk; ++b) {
-        k_fwd_step<<<std::max(1, nblk - b - 1), 256, 0, ctx->stream>>>(m->L, m->Dinv, n_pad, b, work, z);
+        k_fwd_step<<<std::max(1, nblk - b - 1), 256, 0, st>>>(m->L, m->Dinv, n_pad, b, work, z);
         GPBO_LAUNCH_CHECK(ctx);
     }
     for (int b = nblk - 1; b >= 0; --b) {
-        k_bwd_step<<<std::max(1, b), 256, 0, ctx->stream>>>(m->L, m->Dinv, n_pad, b, z, out);
+        k_bwd_step<<<std::max(1, b), 256, 0, st>>>(m->L, m->Dinv, n_pad, b, z, out);
         GPBO_LAUNCH_CHECK(ctx);
     }
     return GPBO_OK;
@@ -225,55 +226,88 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     }
     GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
     const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1);
-    for (int kb = 0; kb < nblk; ++kb) {
-        k_chol_diag<<<1, 256, smem2, st>>>(m->L, n_pad, kb, m->Dinv, ctx->dev_status);
+    // Right-looking blocked factorisation with a lookahead of one block column: the update
+    // of block column kb+1 by panel kb, the factorisation of its diagonal block and its panel
+    // run on the high-priority side stream while the rest of step kb's trailing update runs
+    // on the main stream.  The two touch disjoint tiles; column kb+2 is updated by the side
+    // stream only after the main stream's step-kb update (event ev_rest).
+    cudaStream_t side = nullptr;
+    GPBO_TRY(side_stream(ctx, &side));
+    cudaEvent_t ev_fork = ctx->side_ev[0], ev_panel = ctx->side_ev[1], ev_rest = ctx->side_ev[2],
+                ev_join = ctx->side_ev[3];
+    GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
+    k_chol_diag<<<1, 256, smem2, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
+    GPBO_LAUNCH_CHECK(ctx);
+    if (nblk > 1) {
+        k_chol_panel<<<(nblk - 1) * (NB / 16), 256, 0, side>>>(m->L, n_pad, 0, m->Dinv);
         GPBO_LAUNCH_CHECK(ctx);
+    }
+    GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
+    for (int kb = 0; kb + 1 < nblk; ++kb) {
         const int T = nblk - kb - 1;
-        if (T > 0) {
-            k_chol_panel<<<T * (NB / 16), 256, 0, st>>>(m->L, n_pad, kb, m->Dinv);
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));  // panel kb
+        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));  // step kb-1 done with column kb+1
+        k_chol_update<<<T, 256, smem2, side>>>(m->L, n_pad, kb, nblk, 1);
+        GPBO_LAUNCH_CHECK(ctx);
+        k_chol_diag<<<1, 256, smem2, side>>>(m->L, n_pad, kb + 1, m->Dinv, ctx->dev_status);
+        GPBO_LAUNCH_CHECK(ctx);
+        if (T > 1) {
+            k_chol_panel<<<(T - 1) * (NB / 16), 256, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
             GPBO_LAUNCH_CHECK(ctx);
-            const int64_t tiles = (int64_t)T * (T + 1) / 2;
+        }
+        GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
+        if (T > 1) {
+            const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk);
+            k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
             GPBO_LAUNCH_CHECK(ctx);
             GPBO_TRY(trace_end(ctx));
+            GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }
     }
+    GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     k_zero_upper_blocks<<<blocks_for((int64_t)n_pad * n_pad), 256, 0, st>>>(m->L, n_pad);
     GPBO_LAUNCH_CHECK(ctx);
     unsigned bits = 0;
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
 
-    // alpha = K^-1 y with one refinement step (FP64 throughout)
-    void *wsp = nullptr;
+    // One workspace reservation for both branches below (they run concurrently).
+    const int max_probs = 2 * nblk + 2;
+    const int64_t sq = (int64_t)n_pad * n_pad;
     const size_t vec = sizeof(double) * n_pad;
-    GPBO_TRY(ws_reserve(ctx, vec * 6, &wsp));
+    const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
+                             sizeof(GemmProb) * 2 * max_probs;
+    void *wsp = nullptr;
+    GPBO_TRY(ws_reserve(ctx, vec * 6 + inv_bytes, &wsp));
     double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *dlt = r + n_pad;
-    k_pad_copy<<<blocks_for(n_pad), 256, 0, st>>>(y_dev, n, n_pad, ypad);
+    void *w2 = (void *)((char *)wsp + vec * 6);
+
+    // alpha = K^-1 y with one refinement step (FP64 throughout), on the side stream: its
+    // substitution steps are latency-bound and overlap the L^-1 products on the main stream.
+    GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
+    k_pad_copy<<<blocks_for(n_pad), 256, 0, side>>>(y_dev, n, n_pad, ypad);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(alpha_solve(ctx, m, ypad, work, m->alpha64));
-    k_residual<<<(n_pad + 7) / 8, 256, 0, st>>>(m->K, m->alpha64, ypad, n_pad, r);
+    GPBO_TRY(alpha_solve(ctx, side, m, ypad, work, m->alpha64));
+    k_residual<<<(n_pad + 7) / 8, 256, 0, side>>>(m->K, m->alpha64, ypad, n_pad, r);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(alpha_solve(ctx, m, r, work, dlt));
-    k_axpy_cast<<<blocks_for(n_pad), 256, 0, st>>>(m->alpha64, dlt, n_pad, m->alpha32);
+    GPBO_TRY(alpha_solve(ctx, side, m, r, work, dlt));
+    k_axpy_cast<<<blocks_for(n_pad), 256, 0, side>>>(m->alpha64, dlt, n_pad, m->alpha32);
     GPBO_LAUNCH_CHECK(ctx);
+    GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
 
     // L^-1 for scoring
-    const int max_probs = 2 * nblk + 2;
     GemmProb *probs = nullptr;
-    const int64_t sq = (int64_t)n_pad * n_pad;
     if (m->prec == GPBO_PREC_F64) {
-        void *w2 = nullptr;
-        GPBO_TRY(ws_reserve(ctx, sizeof(double) * sq + sizeof(GemmProb) * 2 * max_probs, &w2));
         double *tmp = (double *)w2;
         probs = (GemmProb *)(tmp + sq);
         k_linv_init<double><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv64);
         GPBO_LAUNCH_CHECK(ctx);
         GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs));
     } else {
-        void *w2 = nullptr;
-        GPBO_TRY(ws_reserve(ctx, sizeof(float) * 2 * sq + sizeof(GemmProb) * 2 * max_probs, &w2));
         float *L32 = (float *)w2, *tmp = L32 + sq;
         probs = (GemmProb *)(tmp + sq);
         k_cast<double, float><<<blocks_for(sq), 256, 0, st>>>(m->L, sq, L32);
@@ -302,6 +336,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
             }
         }
     }
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
     return GPBO_OK;

@@ -153,16 +153,23 @@ __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_
 }
 
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.
-__device__ __forceinline__ void k_chol_update_body(double *__restrict__ A, int n_pad, int kb, int nblk, const int bx, const int by)
+// part 0: every tile of the trailing lower triangle (T(T+1)/2 CTAs, T = nblk - kb - 1);
+// part 1: block column kb+1 only (T CTAs); part 2: block columns kb+2 .. (T(T-1)/2 CTAs).
+__device__ __forceinline__ void k_chol_update_body(double *__restrict__ A, int n_pad, int kb, int nblk, const int bx, const int by,
+                                                   int part = 0)
 {
     extern __shared__ double sm[];
     double(*li)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
     double(*lj)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
-    const int64_t p = bx;
-    int ii = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= p) ++ii;
-    while ((int64_t)ii * (ii + 1) / 2 > p) --ii;
-    const int jj = (int)(p - (int64_t)ii * (ii + 1) / 2);
+    int ii = bx, jj = 0;
+    if (part != 1) {
+        const int64_t p = bx;
+        ii = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+        while ((int64_t)(ii + 1) * (ii + 2) / 2 <= p) ++ii;
+        while ((int64_t)ii * (ii + 1) / 2 > p) --ii;
+        jj = (int)(p - (int64_t)ii * (ii + 1) / 2);
+        if (part == 2) { ++ii; ++jj; }
+    }
     const int ib = kb + 1 + ii, jb = kb + 1 + jj;
     if (ib >= nblk || jb > ib) return;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;

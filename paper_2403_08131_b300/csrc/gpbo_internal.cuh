@@ -84,6 +84,8 @@ struct gpbo_ctx {
     int trace_stack[8];              // open intervals (they nest)
     int trace_depth = 0;
     void *batch_plan = nullptr;      // captured batched step for the last set of shapes
+    cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
+    cudaEvent_t side_ev[4] = {};     // fork / join events between the two streams
 };
 
 struct gp_model {
@@ -113,6 +115,9 @@ namespace gpbo {
 
 // capi.cu
 int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out);
+// The context's high-priority side stream (created on first use).  Every call that forks
+// work onto it joins back into ctx->stream before returning.
+int side_stream(gpbo_ctx *ctx, cudaStream_t *out);
 // Open / close a timed interval of `phase` on the context's stream (no-ops unless tracing).
 int trace_begin(gpbo_ctx *ctx, int phase, double flops);
 int trace_end(gpbo_ctx *ctx);

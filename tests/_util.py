@@ -52,46 +52,72 @@ def _gelu_slope(z):
     return 0.5 * scipy.special.erfc(-z / np.sqrt(2.0)) + z * np.exp(-0.5 * z * z) / np.sqrt(2 * np.pi)
 
 
-def _gelu_tanh_gap(z):
-    """|tanh-form GELU - z Phi(z)| plus tanh.approx's relative error (2^-11) times |z|/2."""
-    t = 0.5 * z * (1 + np.tanh(np.sqrt(2 / np.pi) * (z + 0.044715 * z ** 3)))
-    return np.abs(t - _gelu(z)) + np.abs(z) * 2.0 ** -12
+def _gelu_tanh(z):
+    return 0.5 * z * (1 + np.tanh(np.sqrt(2 / np.pi) * (z + 0.044715 * z ** 3)))
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    b = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
 
 
 def bf16_ensemble_tol(orc, thetas, X, d, H, nm, tau, lam=6.0):
     """Tolerances (mu_bar, sigma_bar, ei) of the BF16 tensor-core ensemble against the FP64
-    oracle, per candidate.  x, W1, b1, W2 and H1 are rounded to BF16 (unit roundoff u); b2,
-    W3, b3 and H2 stay FP32; GELU is the tanh form.  Rounding errors of an n-term sum grow
-    like sqrt(n) u with high probability (Higham & Mary, SIAM J. Sci. Comput. 2019), so each
-    layer's error is propagated as a root sum of squares through the next layer's weights;
-    lam is the number of standard deviations allowed."""
+    oracle, per candidate, derived from the kernel's arithmetic in two parts.
+    (1) Deterministic: x, W1, b1, W2 and H1 rounded to BF16 and the tanh-form GELU.  A
+        float64 emulation with exactly these roundings gives |emulation - oracle|.
+    (2) What the emulation cannot reproduce: tanh.approx's relative error (2^-11) on each
+        tanh, the FP32 accumulation, and the H1 roundings that this moves across a BF16
+        rounding boundary (one ulp, 2u|h1|, with probability about delta / (2u|h1|), so
+        expected square delta * 2u|h1|).  These are independent per element, so they are
+        propagated as a root sum of squares through the next layer's weights (the sqrt(n)
+        growth of Higham & Mary, SIAM J. Sci. Comput. 2019); lam is the number of standard
+        deviations allowed."""
     from scipy.stats import norm
     u = U_BF16
-    mus, dmus, ss, dss = [], [], [], []
+    X = np.asarray(X, dtype=np.float64)
+    Xq = bf16_round(X)
+    mus, emus, dmus, ss, ess, dss = [], [], [], [], [], []
     for th in np.asarray(thetas, dtype=np.float64):
         W1, b1, W2, b2, W3, b3 = [p.reshape(s) for p, (_, s) in zip(orc.mlp_split(th, d, H), orc.mlp_sizes(d, H))]
-        z1 = X @ W1 + b1
-        dz1 = u * np.sqrt(2 * (X ** 2) @ (W1 ** 2) + b1 ** 2) + 1e-7
-        h1 = _gelu(z1)
-        dh1 = np.sqrt((_gelu_slope(z1) * dz1) ** 2 + _gelu_tanh_gap(z1) ** 2 + (u * h1) ** 2)
-        z2 = h1 @ W2 + b2
-        dz2 = np.sqrt((dh1 ** 2 + (u * h1) ** 2) @ (W2 ** 2)) + 1e-7
-        h2 = _gelu(z2)
-        dh2 = np.sqrt((_gelu_slope(z2) * dz2) ** 2 + _gelu_tanh_gap(z2) ** 2)
-        o = h2 @ W3 + b3
-        do = np.sqrt((dh2 ** 2) @ (W3 ** 2)) + 1e-7
-        mu, s = o[:, 0] * nm[1] + nm[0], np.exp(o[:, 1] * nm[3] + nm[2])
-        mus.append(mu)
+        # reference (exact GELU, FP64) and emulation of the kernel's roundings
+        o = _gelu(_gelu(X @ W1 + b1) @ W2 + b2) @ W3 + b3
+        z1 = Xq @ bf16_round(W1) + bf16_round(b1)
+        h1 = bf16_round(_gelu_tanh(z1))
+        z2 = h1 @ bf16_round(W2) + b2
+        h2 = _gelu_tanh(z2)
+        oe = h2 @ W3 + b3
+        # residual, per element
+        t1 = np.abs(z1) * 2.0 ** -12 + 1e-7 * (np.abs(Xq) @ np.abs(W1) + 1)
+        dh1 = np.sqrt(t1 ** 2 + t1 * 2 * u * np.abs(h1))
+        dz2 = np.sqrt((dh1 ** 2) @ (W2 ** 2)) + 1e-7 * (np.abs(h1) @ np.abs(W2) + 1)
+        dh2 = np.sqrt((_gelu_slope(z2) * dz2) ** 2 + (np.abs(z2) * 2.0 ** -12) ** 2)
+        do = np.sqrt((dh2 ** 2) @ (W3 ** 2)) + 1e-7 * (np.abs(h2) @ np.abs(W3) + 1)
+        for out, oo in ((mus, o), (emus, oe)):
+            out.append(oo[:, 0] * nm[1] + nm[0])
+        ss.append(np.exp(o[:, 1] * nm[3] + nm[2]))
+        ess.append(np.exp(oe[:, 1] * nm[3] + nm[2]))
         dmus.append(nm[1] * do[:, 0])
-        ss.append(s)
-        dss.append(s * nm[3] * do[:, 1])
-    mus, dmus, ss, dss = map(np.array, (mus, dmus, ss, dss))
+        dss.append(ess[-1] * nm[3] * do[:, 1])
+    mus, emus, dmus, ss, ess, dss = map(np.array, (mus, emus, dmus, ss, ess, dss))
     E = mus.shape[0]
-    mbar = mus.mean(0)
-    sbar = np.sqrt((ss ** 2).mean(0) + ((mus - mbar) ** 2).mean(0))
+
+    def combine(m, s):
+        mb = m.mean(0)
+        return mb, np.sqrt((s ** 2).mean(0) + ((m - mb) ** 2).mean(0))
+
+    mbar, sbar = combine(mus, ss)
+    embar, esbar = combine(emus, ess)
     dm = np.sqrt((dmus ** 2).sum(0)) / E
-    dvar = np.sqrt(((2 * ss * dss) ** 2 + (2 * (mus - mbar) * dmus) ** 2).sum(0)) / E
-    ds = dvar / (2 * sbar)
+    dvar = np.sqrt(((2 * ess * dss) ** 2 + (2 * (emus - embar) * dmus) ** 2).sum(0)) / E
+    ds = dvar / (2 * esbar)
     z = (tau - mbar) / sbar
-    dei = np.sqrt((norm.cdf(z) * dm) ** 2 + (norm.pdf(z) * ds) ** 2)
-    return (lam * dm + 1e-6 * (np.abs(mbar) + 1), lam * ds + 1e-6 * sbar, lam * dei + 1e-6 * sbar)
+    ez = (tau - embar) / esbar
+    ei = (tau - mbar) * norm.cdf(z) + sbar * norm.pdf(z)
+    eei = (tau - embar) * norm.cdf(ez) + esbar * norm.pdf(ez)
+    dei = np.sqrt((norm.cdf(ez) * dm) ** 2 + (norm.pdf(ez) * ds) ** 2)
+    return (np.abs(embar - mbar) + lam * dm + 1e-6 * (np.abs(mbar) + 1),
+            np.abs(esbar - sbar) + lam * ds + 1e-6 * sbar,
+            np.abs(eei - ei) + lam * dei + 1e-6 * sbar)

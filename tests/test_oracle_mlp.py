@@ -123,3 +123,13 @@ def test_bf16_tolerance_detects_planted_mistakes(orc):
         mm, ms, _ = orc.mlp_ensemble(t, X, d, H, nm, tau)
         caught = (np.abs(mm - rm) > tm) | (np.abs(ms - rs) > ts)
         assert caught.mean() > 0.9, f"{name}: only {caught.mean():.2f} of candidates outside the tolerance"
+
+
+def test_bf16_round_matches_torch():
+    """The tolerance's BF16 emulation rounds like torch's CPU float32 -> bfloat16 cast."""
+    import torch
+    from tests._util import bf16_round
+    x = np.random.default_rng(10).normal(0, 3, 100000)
+    x[:4] = [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -0.0, 65504.0]
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(bf16_round(x), ref)

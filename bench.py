@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned pre-screen measurement")
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
                     help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
+    ap.add_argument("--profile-surrogate", type=int, default=0, metavar="M",
+                    help="profiling case: the BF16 ensemble forward (8 x 20-256-256-2) over M seeded candidates, "
+                         "run twice, no JSON")
     return ap.parse_args()
 
 
@@ -398,10 +401,30 @@ def profile_case(args):
     ctx.close()
 
 
+def profile_surrogate(args):
+    import torch
+
+    from paper_2403_08131_b300 import gpbo
+
+    ctx = gpbo.Context(0, torch.cuda.current_stream())
+    net = gpbo.Surrogate(ctx, E=8, d=20, H=256, seed=5)
+    M = args.profile_surrogate
+    ei = torch.empty(M, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        net.score(ei, M=M, seed=2408, y_best=-1.0, prec="bf16")
+    torch.cuda.synchronize()
+    print(f"profile surrogate: M={M} ei[0]={float(ei[0]):.6g} max={float(ei.max()):.6g}")
+    net.free()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.profile_case:
         profile_case(args)
+        return
+    if args.profile_surrogate:
+        profile_surrogate(args)
         return
     if args.impl == "reference":
         run_reference(args)

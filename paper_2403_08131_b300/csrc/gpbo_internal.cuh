@@ -144,8 +144,8 @@ bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
              float *mu);
 
-// mlp_tc.cu: the ensemble pre-screen forward on the tensor cores (hidden width 256, d <= 31).
-bool mlp_tc_usable(int d, int H);
+// mlp_tc.cu: the ensemble pre-screen forward on the tensor cores (hidden width 256, d <= 31, E <= 8).
+bool mlp_tc_usable(int d, int H, int E);
 size_t mlp_tc_weight_bytes(int E);
 size_t mlp_tc_aux_floats(int E);
 int mlp_tc_pack(gpbo_ctx *ctx, const float *theta, int E, int d, int64_t P, const int64_t off[6], void *wt, float *aux);

@@ -430,7 +430,7 @@ static int backward(gpbo_ctx *ctx, gpbo_mlp *net, int B)
 
 static int ensure_packed(gpbo_ctx *ctx, gpbo_mlp *net)
 {
-    if (!mlp_tc_usable(net->d, net->H)) return GPBO_ENOTSUP;
+    if (!mlp_tc_usable(net->d, net->H, net->E)) return GPBO_ENOTSUP;
     if (!net->wt16) {
         GPBO_CUDA_TRY(cudaMalloc(&net->wt16, mlp_tc_weight_bytes(net->E)));
         GPBO_CUDA_TRY(cudaMalloc(&net->aux, sizeof(float) * mlp_tc_aux_floats(net->E)));
@@ -653,7 +653,7 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
     GPBO_CUDA_TRY(cudaMalloc(&hist, sizeof(uint32_t) * (4096 + 4)));
     GPBO_CUDA_TRY(cudaMalloc(&Xk, sizeof(float) * (size_t)k * d));
     uint32_t *sel = hist + 4096, *counters = hist + 4098;
-    const int prec = mlp_tc_usable(d, net->H) ? GPBO_PREC_BF16 : GPBO_PREC_F32;
+    const int prec = mlp_tc_usable(d, net->H, net->E) ? GPBO_PREC_BF16 : GPBO_PREC_F32;
     int rc = score_pool(ctx, net, nullptr, M, seed, y_best, xi, prec, ei, nullptr, nullptr);
     // top k by the surrogate's EI
     if (rc == GPBO_OK) {

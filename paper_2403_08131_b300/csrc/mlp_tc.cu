@@ -15,8 +15,9 @@
 //
 // Roles (one CTA per SM, persistent over tiles; 576 threads):
 //   warp 0      TMA: per network, [W1 ; b1]^T (256 x 64, zero padded) then W2^T in four
-//               256 x 64 K chunks; 4 stages of 32 KiB.  The packed ensemble (8 networks,
-//               1.3 MB) is read from L2 for every tile.
+//               256 x 64 K chunks; 3 stages of 32 KiB.  The packed ensemble (8 networks,
+//               1.3 MB) is read from L2 for every tile; b2, W3 and b3 of every network
+//               (E <= 8) stay in shared memory.
 //   warp 1      TMEM (512 columns: Z1 in 0..255, Z2 in 256..511); one lane issues the MMAs
 //   warps 2-17  epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4;
 //               warps 2-5 (group 0) also build the x tile and own the ensemble state of
@@ -42,7 +43,7 @@ constexpr int BM = 128;                  // candidates per tile
 constexpr int HID = 256;                 // hidden width (MMA N)
 constexpr int KT = 64;                   // K elements per 128-byte swizzled row
 constexpr int CHUNKS = 5;                // per network: [W1;b1]^T, then W2^T in 4 K chunks
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 16;
 constexpr int GROUPS = EPI_WARPS / 4;    // column groups
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -51,10 +52,11 @@ constexpr int TILE_BYTES = BM * 128;     // one 128 x 64 BF16 K tile
 constexpr int H1_BYTES = 4 * TILE_BYTES; // 128 x 256
 constexpr int X_BYTES = TILE_BYTES;
 constexpr int W_BYTES = HID * 128;       // one 256 x 64 BF16 chunk
-constexpr int AUX = 1024;                // per network FP32: b2 [256], W3 [256 x 2], b3 [2], pad
+constexpr int AUX = 772;                 // per network FP32: b2 [256], W3 [256 x 2], b3 [2], pad 2
+constexpr int EMAX = 8;                  // networks whose AUX rows stay in shared memory
 constexpr int DMAX = 31;
 
-struct Shared {
+struct alignas(16) Shared {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
     uint64_t z1_full, z2_full, z2_empty;
@@ -67,7 +69,10 @@ struct Shared {
     float2 part[2][GROUPS - 1][BM];      // layer-3 partial sums of column groups 1..3
 };
 
-inline size_t smem_bytes() { return (size_t)H1_BYTES + X_BYTES + (size_t)STAGES * W_BYTES + 1024 + sizeof(Shared); }
+inline size_t smem_bytes()
+{
+    return (size_t)H1_BYTES + X_BYTES + (size_t)STAGES * W_BYTES + 1024 + sizeof(Shared) + sizeof(float) * EMAX * AUX;
+}
 
 struct Params {
     int64_t C;          // candidates
@@ -112,9 +117,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// TMEM loads without the wait, so that several can be in flight; tmem_wait() waits for all
+// of them, and pin() then ties the destination registers to that point: an empty volatile asm
+// that "modifies" them keeps the compiler from reading them before the wait.
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void pin16(uint32_t *r)
+{
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]));
+}
+
 // Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in BF16, 128-byte swizzled
 // (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
-__device__ __forceinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)
+__device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)
 {
     const int64_t cl = t * BM + r;
     const int64_t c = P.c0 + cl;
@@ -152,7 +177,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     unsigned char *xs = base + H1_BYTES;            // 1 K tile
     unsigned char *wst = xs + X_BYTES;              // STAGES x W_BYTES
     Shared *sh = (Shared *)(wst + (size_t)STAGES * W_BYTES);
+    float *aux_s = (float *)(sh + 1);               // E x AUX (16-byte aligned: Shared is)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int i = threadIdx.x; i < P.E * AUX; i += blockDim.x) aux_s[i] = P.aux[i];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -191,22 +218,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_w) : "memory");
             int stage = 0;
             uint32_t phase = 0;
-            int armed[STAGES];
-            uint32_t armed_par[STAGES];
-            for (int s = 0; s < STAGES; ++s) armed[s] = 0, armed_par[s] = 0;
+            uint32_t armed = 0, armed_par = 0;  // bit s: stage s has a copy issued, and its phase
             bool ok = true;
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x)
                 for (int e = 0; ok && e < P.E; ++e)
                     for (int c = 0; c < CHUNKS; ++c) {
-                        if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                         mbar_arrive_expect_tx(&sh->full[stage], W_BYTES);
-                        armed[stage] = 1;
-                        armed_par[stage] = phase;
+                        armed |= 1u << stage;
+                        armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
                         tma_load_2d(wst + (size_t)stage * W_BYTES, &map_w, 0, (e * CHUNKS + c) * HID, &sh->full[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
             for (int s = 0; s < STAGES; ++s)
-                if (armed[s]) mbar_wait(&sh->full[s], armed_par[s], abort_flag, P.status, false);
+                if ((armed >> s) & 1u) mbar_wait(&sh->full[s], (armed_par >> s) & 1u, abort_flag, P.status, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -218,8 +243,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x, ++ti) {
                 for (int e = 0; ok && e < P.E; ++e, ++k) {
                     // layer 1 (Z1 is free: layer 2 of the previous network waited for all of H1)
-                    if (e == 0 && !mbar_wait(&sh->x_full, ti & 1u, abort_flag, P.status)) { ok = false; break; }
-                    if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                    if (e == 0 && !mbar_wait_fast(&sh->x_full, ti & 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     {
                         const unsigned char *w = wst + (size_t)stage * W_BYTES;
@@ -230,10 +255,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     mma_commit(&sh->z1_full);
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     // layer 2, K tile by K tile as H1 fills
-                    if (!mbar_wait(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (!mbar_wait_fast(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     for (int q = 0; q < 4; ++q) {
-                        if (!mbar_wait(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
-                        if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned char *w = wst + (size_t)stage * W_BYTES;
                         const unsigned char *a = h1 + q * TILE_BYTES;
@@ -272,9 +297,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
             const int64_t cl = (int64_t)t * BM + row;
             for (int e = 0; e < P.E; ++e, ++k) {
-                const float *aux = P.aux + (size_t)e * AUX;
+                const float *aux = aux_s + e * AUX;
                 // ---- layer-1 epilogue: H1 = bf16(gelu(Z1)), K tile by K tile
-                bool g = mbar_wait(&sh->z1_full, k & 1u, abort_flag, P.status);
+                bool g = mbar_wait_fast(&sh->z1_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
                 if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
@@ -285,40 +310,56 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     if (lane == 0) mbar_arrive(&sh->x_full);
                 }
 #pragma unroll 1
-                for (int q = 0; q < 4; ++q) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_addr + (uint32_t)(q * KT + grp * 16), v);
-                    uint32_t w[8];
+                for (int qb = 0; qb < 4; qb += 2) {
+                    uint32_t v[2][16];
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) w[j / 2] = pack_bf16(gelu_tanh(v[j]), gelu_tanh(v[j + 1]));
-                    unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
-                    const int j0 = 2 * grp, j1 = 2 * grp + 1;
-                    *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-                    fence_async_smem();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->h_full[q]);
+                    for (int u = 0; u < 2; ++u) tmem_ld16_nw(tmem + lane_addr + (uint32_t)((qb + u) * KT + grp * 16), v[u]);
+                    tmem_wait();
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int q = qb + u;
+                        pin16(v[u]);
+                        uint32_t w[8];
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2)
+                            w[j / 2] = pack_bf16(gelu_tanh(__uint_as_float(v[u][j])), gelu_tanh(__uint_as_float(v[u][j + 1])));
+                        unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
+                        const int j0 = 2 * grp, j1 = 2 * grp + 1;
+                        *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+                        *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+                        fence_async_smem();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->h_full[q]);
+                    }
                 }
                 // ---- layer-2 epilogue and layer 3
-                g = mbar_wait(&sh->z2_full, k & 1u, abort_flag, P.status);
+                g = mbar_wait_fast(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
                 float o0 = 0.f, o1 = 0.f;
 #pragma unroll 1
-                for (int cb = 0; cb < 2; ++cb) {
-                    float v[32];
-                    const int j0 = grp * 64 + cb * 32;
-                    tmem_ld32(tmem + lane_addr + (uint32_t)(HID + j0), v);
+                for (int qb = 0; qb < 4; qb += 2) {
+                    uint32_t v[2][16];
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 b = __ldg(reinterpret_cast<const float4 *>(aux + j0 + j));
-                        const float4 wa = __ldg(reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j)));
-                        const float4 wb = __ldg(reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4));
-                        const float h0 = gelu_tanh(v[j] + b.x), h1v = gelu_tanh(v[j + 1] + b.y);
-                        const float h2 = gelu_tanh(v[j + 2] + b.z), h3 = gelu_tanh(v[j + 3] + b.w);
-                        o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
-                        o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
+                    for (int u = 0; u < 2; ++u) tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64 + (qb + u) * 16), v[u]);
+                    tmem_wait();
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        pin16(v[u]);
+                        const int j0 = grp * 64 + (qb + u) * 16;
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) {
+                            const float4 b = *reinterpret_cast<const float4 *>(aux + j0 + j);
+                            const float4 wa = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
+                            const float4 wb = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4);
+                            const float h0 = gelu_tanh(__uint_as_float(v[u][j]) + b.x);
+                            const float h1v = gelu_tanh(__uint_as_float(v[u][j + 1]) + b.y);
+                            const float h2 = gelu_tanh(__uint_as_float(v[u][j + 2]) + b.z);
+                            const float h3 = gelu_tanh(__uint_as_float(v[u][j + 3]) + b.w);
+                            o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
+                            o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
+                        }
                     }
                 }
                 tc_fence_before();
@@ -328,13 +369,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 const int par = k & 1;
                 const uint32_t use = (k >> 1) & 1u;
                 if (!builder) {
-                    g = mbar_wait(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
+                    g = mbar_wait_fast(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                     sh->part[par][grp - 1][row] = make_float2(o0, o1);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->part_ready[par]);
                 } else {
-                    g = mbar_wait(&sh->part_ready[par], use, abort_flag, P.status);
+                    g = mbar_wait_fast(&sh->part_ready[par], use, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
 #pragma unroll
                     for (int gg = 0; gg < GROUPS - 1; ++gg) {
@@ -412,7 +453,7 @@ __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P,
 
 }  // namespace mtc
 
-bool mlp_tc_usable(int d, int H) { return H == mtc::HID && d >= 1 && d <= mtc::DMAX; }
+bool mlp_tc_usable(int d, int H, int E) { return H == mtc::HID && d >= 1 && d <= mtc::DMAX && E >= 1 && E <= mtc::EMAX; }
 
 size_t mlp_tc_weight_bytes(int E) { return (size_t)E * mtc::CHUNKS * mtc::W_BYTES; }
 size_t mlp_tc_aux_floats(int E) { return (size_t)E * mtc::AUX; }
@@ -429,7 +470,7 @@ int mlp_tc_pack(gpbo_ctx *ctx, const float *theta, int E, int d, int64_t P, cons
 int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, const double norm[4], const float *Xc,
                  uint64_t seed, int64_t c0, int64_t C, double tau, double xi, float *ei, float *mu, float *sigma)
 {
-    if (!mlp_tc_usable(d, mtc::HID) || E < 1 || C < 1 || !ei || ((uintptr_t)wt & 15) || ((uintptr_t)aux & 15))
+    if (!mlp_tc_usable(d, mtc::HID, E) || C < 1 || !ei || ((uintptr_t)wt & 15) || ((uintptr_t)aux & 15))
         return GPBO_EINVAL;
     if (cdiv64(C, mtc::BM) > 0x7fffffffll) return GPBO_EINVAL;
     CUtensorMap mw;

@@ -60,6 +60,15 @@ static __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, vo
     }
 }
 
+// The same wait with its first attempt inline: the out-of-line slow path (and the register
+// saves around its call) only runs when the barrier is not ready at once.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *status,
+                                               bool honour_abort = true)
+{
+    if (mbar_try(bar, parity)) return true;
+    return mbar_wait(bar, parity, abort_flag, status, honour_abort);
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
     asm volatile(

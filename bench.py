@@ -141,7 +141,9 @@ def batched_form(ctx, W, dev, steps=3):
     torch.cuda.synchronize(dev)
     ts = time.perf_counter() - t0
     flops = sum(w.n * (w.n + 1) for w in subs) * 16384
+    tile, tune = ctx.batched_tuning()
     return {"workload": "64 GPs, d in U{2..12}, n in U{32..1024}, M=16384 each, FP32 scoring, one graph launch",
+            "variance_tile": tile, "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
             "value": round(64 * 16384 / tb, 1), "unit": "candidates/s", "ms_per_step": round(tb * 1e3, 3),
             "sequential_ms": round(ts * 1e3, 3), "speedup_vs_sequential": round(ts / tb, 2),
             "variance_tflops": round(flops / tb / 1e12, 3), "timing": "host wall clock around synchronised calls"}

@@ -50,7 +50,11 @@ struct BatchPlan {
     std::vector<int2> lvl_mm;
     int64_t sum_vec = 0;
     int max_npad = 0, max_nblk = 0, max_tiles64 = 0;
+    int64_t max_M = 0;
     int64_t max_sq = 0, max_dn = 0;
+    int tile_req = 0;    // requested variance tile (0: autotune)
+    int var_bm = 64;     // variance tile in use: candidates per CTA
+    float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 32, 64, 128
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -198,14 +202,15 @@ __global__ void __launch_bounds__(256) b_xkern(const BProb *P, const float *Xs32
                           (float)p.s2, ls_of(lsinv, blockIdx.y, p.d), Kst + p.off_kst, mu + p.off_mu, blockIdx.x, 0, 0);
 }
 
+template <int BM>
 __global__ void __launch_bounds__(256) b_var(const BProb *P, const float *Kst, const float *Linv, const float *mu,
                                              const double *tau, float xi, float *pei, int64_t *pidx)
 {
     const BProb &p = P[blockIdx.y];
-    if ((int64_t)blockIdx.x * 64 >= p.M) return;
-    k_var_simt_body<float>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
-                           tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0, blockIdx.x,
-                           0, 0);
+    if ((int64_t)blockIdx.x * BM >= p.M) return;
+    k_var_simt_body<float, BM>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
+                               tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0,
+                               blockIdx.x, 0, 0);
 }
 
 __global__ void __launch_bounds__(1024) b_argmax(const BProb *P, const float *pei, const int64_t *pidx, double *best_ei,
@@ -271,10 +276,11 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
         p.off_kst = skst; skst += p.M * p.n_pad;
         p.off_mu = smu;   smu += p.M;
         p.part_count = (int)cdiv64(p.M, 64);
-        p.off_part = spart; spart += p.part_count;
+        p.off_part = spart; spart += cdiv64(p.M, 32);  // room for the smallest variance tile
         pl->max_npad = std::max(pl->max_npad, p.n_pad);
         pl->max_nblk = std::max(pl->max_nblk, p.nblk);
         pl->max_tiles64 = std::max<int>(pl->max_tiles64, (int)cdiv64(p.M, 64));
+        pl->max_M = std::max<int64_t>(pl->max_M, p.M);
         pl->max_sq = std::max<int64_t>(pl->max_sq, (int64_t)p.n_pad * p.n_pad);
         pl->max_dn = std::max<int64_t>(pl->max_dn, (int64_t)p.d * p.n_pad);
     }
@@ -346,6 +352,65 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
 
 static unsigned gb(int64_t count, int threads = 256) { return (unsigned)std::max<int64_t>(1, cdiv64(count, threads)); }
 
+static int launch_var_bm(BatchPlan *pl, cudaStream_t st, float xi, int bm)
+{
+    const dim3 grid((unsigned)cdiv64(pl->max_M, bm), pl->G);
+    const BProb *P = pl->probs_dev;
+    if (bm == 32) b_var<32><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    else if (bm == 128) b_var<128><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    else b_var<64><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    GPBO_CUDA_TRY(cudaGetLastError());
+    return GPBO_OK;
+}
+
+static int launch_var(BatchPlan *pl, cudaStream_t st, float xi) { return launch_var_bm(pl, st, xi, pl->var_bm); }
+
+// Set the variance tile (candidates per CTA) and the per-problem partial-argmax counts.
+static void set_tile(BatchPlan *pl, int bm)
+{
+    pl->var_bm = bm;
+    for (BProb &p : pl->probs) p.part_count = (int)cdiv64(p.M, bm);
+}
+
+// Autotuner: time each variance tile on the plan's own (zeroed) buffers, three launches
+// after one warm-up, and keep the fastest.  The kernel's work and memory traffic do not
+// depend on the values, only on the shapes, which are the plan's.
+static int autotune(BatchPlan *pl)
+{
+    static const int tiles[3] = {32, 64, 128};
+    GPBO_CUDA_TRY(cudaMemsetAsync(pl->Kst, 0, sizeof(float) * (size_t)(pl->probs.back().off_kst +
+                                  pl->probs.back().M * (int64_t)pl->probs.back().n_pad), pl->cap));
+    GPBO_CUDA_TRY(cudaMemsetAsync(pl->Linv32, 0, sizeof(float) * (size_t)(pl->probs.back().off_sq +
+                                  (int64_t)pl->probs.back().n_pad * pl->probs.back().n_pad), pl->cap));
+    GPBO_CUDA_TRY(cudaMemsetAsync(pl->mu, 0, sizeof(float) * (size_t)(pl->probs.back().off_mu + pl->probs.back().M),
+                                  pl->cap));
+    GPBO_CUDA_TRY(cudaMemsetAsync(pl->tau, 0, sizeof(double) * pl->G, pl->cap));
+    cudaEvent_t a = nullptr, b = nullptr;
+    GPBO_CUDA_TRY(cudaEventCreate(&a));
+    GPBO_CUDA_TRY(cudaEventCreate(&b));
+    int best = 64;
+    float best_ms = 1e30f;
+    int rc = GPBO_OK;
+    for (int i = 0; i < 3 && rc == GPBO_OK; ++i) {
+        set_tile(pl, tiles[i]);
+        if (cudaMemcpyAsync(pl->probs_dev, pl->probs.data(), sizeof(BProb) * pl->G, cudaMemcpyHostToDevice, pl->cap) !=
+            cudaSuccess) { rc = GPBO_ECUDA; break; }
+        if ((rc = launch_var_bm(pl, pl->cap, 0.f, tiles[i])) != GPBO_OK) break;
+        cudaEventRecord(a, pl->cap);
+        for (int r = 0; r < 3 && rc == GPBO_OK; ++r) rc = launch_var_bm(pl, pl->cap, 0.f, tiles[i]);
+        cudaEventRecord(b, pl->cap);
+        if (cudaEventSynchronize(b) != cudaSuccess) { rc = GPBO_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        pl->tune_ms[i] = ms / 3;
+        if (ms / 3 < best_ms) { best_ms = ms / 3; best = tiles[i]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_tile(pl, best);
+    return rc;
+}
+
 // The batched step's kernels, in order, on stream st (captured into the plan's graph).
 static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
 {
@@ -390,7 +455,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     // scoring
     b_xkern<<<dim3(pl->max_tiles64, G), 256, sizeof(float) * 64 * GPBO_MAX_D, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,
                                                                                     pl->Kst, pl->mu);
-    b_var<<<dim3(pl->max_tiles64, G), 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    GPBO_TRY(launch_var(pl, st, xi));
     b_argmax<<<G, 1024, 0, st>>>(P, pl->pei, pl->pidx, pl->best_ei, pl->best_idx);
     b_gather<<<G, GPBO_MAX_D, 0, st>>>(P, pl->best_idx, pl->xnext);
     GPBO_CUDA_TRY(cudaGetLastError());
@@ -443,7 +508,7 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
     }
     GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
     BatchPlan *pl = g_last_plan_for_ctx(ctx);
-    if (!same_key(pl, G, n, d, M, hyp, xi)) {
+    if (!same_key(pl, G, n, d, M, hyp, xi) || pl->tile_req != ctx->batch_tile) {
         cudaStreamSynchronize(ctx->stream);
         free_plan(pl);
         ctx->batch_plan = nullptr;
@@ -458,7 +523,12 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
             pl->key_hyp.push_back(hyp[g].noise_var);
             for (int k = 0; k < d[g]; ++k) pl->key_hyp.push_back(hyp[g].lengthscale[k]);
         }
+        pl->tile_req = ctx->batch_tile;
         int st = build_plan(ctx, pl, hyp);
+        if (st == GPBO_OK) {
+            if (pl->tile_req) set_tile(pl, pl->tile_req);
+            else st = autotune(pl);
+        }
         if (st != GPBO_OK) {
             free_plan(pl);
             return st;
@@ -510,6 +580,24 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
         if (argmax) argmax[g] = bi[g];
         for (int k = 0; k < GPBO_MAX_D; ++k) x_next[(size_t)g * GPBO_MAX_D + k] = k < d[g] ? (double)xn[(size_t)g * GPBO_MAX_D + k] : 0.0;
     }
+    return GPBO_OK;
+}
+
+extern "C" int search_step_batched_tile(gpbo_ctx *ctx, int tile)
+{
+    if (!ctx || !(tile == 0 || tile == 32 || tile == 64 || tile == 128)) return GPBO_EINVAL;
+    ctx->batch_tile = tile;
+    return GPBO_OK;
+}
+
+extern "C" int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3)
+{
+    if (!ctx || !tile) return GPBO_EINVAL;
+    const BatchPlan *pl = (const BatchPlan *)ctx->batch_plan;
+    if (!pl) return GPBO_EINVAL;
+    *tile = pl->var_bm;
+    if (ms3)
+        for (int i = 0; i < 3; ++i) ms3[i] = pl->tune_ms[i];
     return GPBO_OK;
 }
 

@@ -84,6 +84,7 @@ struct gpbo_ctx {
     int trace_stack[8];              // open intervals (they nest)
     int trace_depth = 0;
     void *batch_plan = nullptr;      // captured batched step for the last set of shapes
+    int batch_tile = 0;              // batched variance tile (0: autotune)
     cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
     cudaEvent_t side_ev[4] = {};     // fork / join events between the two streams
 };

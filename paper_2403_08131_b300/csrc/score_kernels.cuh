@@ -196,9 +196,11 @@ __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uin
     }
 }
 
-// Variance, EI and per-CTA argmax on CUDA cores.  CTA = 64 candidates; it walks the
-// lower triangle of L^-1 in 64-row blocks (outputs) and 16-wide K steps.
-template <typename T>
+// Variance, EI and per-CTA argmax on CUDA cores.  CTA = BM candidates (32, 64 or 128; each
+// thread owns BM/16 of them); it walks the lower triangle of L^-1 in 64-row blocks (outputs)
+// and 16-wide K steps.  Every candidate's sums run in the same order for every BM, so the
+// results do not depend on the tile.
+template <typename T, int BM = 64>
 __device__ __forceinline__ void k_var_simt_body(const T *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
                                                   const T *__restrict__ Linv, const T *__restrict__ mu, T s2,
                                                   double y_best, const double *__restrict__ tau_dev, T xi,
@@ -206,56 +208,61 @@ __device__ __forceinline__ void k_var_simt_body(const T *__restrict__ Kst, int64
                                                   T *__restrict__ part_ei, int64_t *__restrict__ part_idx,
                                                   int part_base, const int bx, const int by, const int gx)
 {
-    constexpr int BM = 64, BN = 64, BK = 16;
+    static_assert(BM == 32 || BM == 64 || BM == 128, "tile");
+    constexpr int BN = 64, BK = 16, TM = BM / 16, EA = BM * BK / 256;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     __shared__ T red_v[BM];
     __shared__ int64_t red_i[BM];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int64_t cb = bx * (int64_t)BM;
-    T sig2[4] = {T(0), T(0), T(0), T(0)};
-    for (int i0 = 0; i0 < n_pad; i0 += BN) {
-        T acc[4][4];
+    T sig2[TM];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < TM; ++u) sig2[u] = T(0);
+    for (int i0 = 0; i0 < n_pad; i0 += BN) {
+        T acc[TM][4];
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
         const int kend = i0 + BN;
         for (int k0 = 0; k0 < kend; k0 += BK) {
             {
-                const int r = tid / 4, c = (tid % 4) * 4;
+                const int r = tid / (BK / EA), c = (tid % (BK / EA)) * EA;
                 const int64_t cr = cb + r;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    As[c + q][r] = cr < C ? Kst[cr * n_pad + k0 + c + q] : T(0);
-                    Bs[c + q][r] = Linv[(int64_t)(i0 + r) * n_pad + k0 + c + q];
-                }
+                for (int q = 0; q < EA; ++q) As[c + q][r] = cr < C ? Kst[cr * n_pad + k0 + c + q] : T(0);
+                const int rb = tid / 4, cbk = (tid % 4) * 4;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Bs[cbk + q][rb] = Linv[(int64_t)(i0 + rb) * n_pad + k0 + cbk + q];
             }
             __syncthreads();
 #pragma unroll
             for (int t = 0; t < BK; ++t) {
-                T x[4], y[4];
+                T x[TM], y[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) { x[u] = As[t][ty + 16 * u]; y[u] = Bs[t][tx + 16 * u]; }
+                for (int u = 0; u < TM; ++u) x[u] = As[t][ty + 16 * u];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int v = 0; v < 4; ++v) y[v] = Bs[t][tx + 16 * v];
+#pragma unroll
+                for (int u = 0; u < TM; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < TM; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) sig2[u] = fma(acc[u][v], acc[u][v], sig2[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < TM; ++u)
         for (int o = 1; o < 16; o <<= 1) sig2[u] += __shfl_xor_sync(0xffffffffu, sig2[u], o);
     const T tau = tau_dev ? (T)*tau_dev : (T)y_best;
     if (tx == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < TM; ++u) {
             const int r = ty + 16 * u;
             const int64_t cl = cb + r, c = c0 + cl;
             T e = T(-1);

@@ -79,6 +79,8 @@ _posterior = _sig("gp_posterior_ei", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64
 _step_batched = _sig("search_step_batched", C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(_P), _I, _I,
                                                      C.POINTER(GpHyper), _L, C.POINTER(C.c_uint64), C.c_double,
                                                      C.c_int, C.c_uint, _D, _D, _L])
+_batched_tile = _sig("search_step_batched_tile", C.c_int, [_P, C.c_int])
+_batched_tuning = _sig("search_step_batched_tuning", C.c_int, [_P, _I, C.POINTER(C.c_float)])
 _posterior_noalloc = _sig("gp_posterior_ei_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double,
                                                                C.c_double, _P, _P, _P, _L, _D])
 _mlp_create = _sig("mlp_create", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)])
@@ -291,6 +293,17 @@ class Context:
                             x_next.ctypes.data_as(_D), ei_max.ctypes.data_as(_D), am.ctypes.data_as(_L)),
               "search_step_batched")
         return {"x_next": [x_next[g, :ds[g]] for g in range(G)], "ei_max": ei_max, "argmax": am}
+
+    def batched_tile(self, tile=0):
+        """Variance tile of the batched step (32, 64, 128), or 0 for the autotuner."""
+        check(_batched_tile(self._h, int(tile)), "search_step_batched_tile")
+
+    def batched_tuning(self):
+        """(tile in use, {tile: autotuner ms per launch}) of the current batched plan."""
+        t = C.c_int(0)
+        ms = (C.c_float * 3)()
+        check(_batched_tuning(self._h, C.byref(t), ms), "search_step_batched_tuning")
+        return t.value, {k: float(v) for k, v in zip((32, 64, 128), ms) if v >= 0}
 
     # ------------------------------------------------------------ screen
     def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,

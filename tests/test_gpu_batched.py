@@ -44,3 +44,24 @@ def test_batched_shapes_are_uneven(ctx):
     assert len(ns) > 5 and len(ds) > 3
     assert min(w.d for w in subs) >= 2 and max(w.d for w in subs) <= 12
     assert min(w.n for w in subs) >= 32 and max(w.n for w in subs) <= 1024
+
+
+def test_autotuned_tile_is_the_fastest_measured_and_tiles_agree(ctx):
+    """The autotuner times the 32/64/128-candidate variance tiles on the plan and keeps the
+    fastest; every forced tile gives the same results bit for bit (each candidate's sums run
+    in the same order)."""
+    subs, probs = _problems(seed_shift=3)
+    ctx.batched_tile(0)
+    auto = ctx.search_step_batched(probs)
+    tile, ms = ctx.batched_tuning()
+    assert set(ms) == {32, 64, 128} and all(v > 0 for v in ms.values())
+    assert tile == min(ms, key=ms.get)
+    print(f"autotuner: {ms} -> {tile}")
+    for t in (32, 64, 128):
+        ctx.batched_tile(t)
+        out = ctx.search_step_batched(probs)
+        assert ctx.batched_tuning()[0] == t
+        assert np.array_equal(out["argmax"], auto["argmax"]) and np.array_equal(out["ei_max"], auto["ei_max"])
+    ctx.batched_tile(0)
+    with pytest.raises(Exception):
+        ctx.batched_tile(48)

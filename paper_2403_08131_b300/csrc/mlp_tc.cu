@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             for (int e = 0; e < P.E; ++e, ++k) {
                 const float *aux = aux_s + e * AUX;
                 // ---- layer-1 epilogue: H1 = bf16(gelu(Z1)), K tile by K tile
-                bool g = mbar_wait_fast(&sh->z1_full, k & 1u, abort_flag, P.status);
+                bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
                 if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     }
                 }
                 // ---- layer-2 epilogue and layer 3
-                g = mbar_wait_fast(&sh->z2_full, k & 1u, abort_flag, P.status);
+                g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
                 float o0 = 0.f, o1 = 0.f;
@@ -369,13 +369,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 const int par = k & 1;
                 const uint32_t use = (k >> 1) & 1u;
                 if (!builder) {
-                    g = mbar_wait_fast(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
+                    g = mbar_wait_inl(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                     sh->part[par][grp - 1][row] = make_float2(o0, o1);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->part_ready[par]);
                 } else {
-                    g = mbar_wait_fast(&sh->part_ready[par], use, abort_flag, P.status);
+                    g = mbar_wait_inl(&sh->part_ready[par], use, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
 #pragma unroll
                     for (int gg = 0; gg < GROUPS - 1; ++gg) {

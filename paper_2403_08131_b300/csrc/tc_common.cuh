@@ -60,6 +60,25 @@ static __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, vo
     }
 }
 
+// The same bounded loop, inlined: for hot loops whose waits often miss the first attempt,
+// where a call would save and restore live registers through local memory.
+__device__ __forceinline__ bool mbar_wait_inl(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *status)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > TIMEOUT_CYCLES) {
+                *abort_flag = 1;
+                atomicOr(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
 // The same wait with its first attempt inline: the out-of-line slow path (and the register
 // saves around its call) only runs when the barrier is not ready at once.
 __device__ __forceinline__ bool mbar_wait_fast(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *status,

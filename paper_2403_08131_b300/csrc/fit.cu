@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int
     k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y, part);
 }
 
+__global__ void __launch_bounds__(256) k_chol_update_slab(double *__restrict__ A, int n_pad, int kb, int part)
+{
+    k_chol_update_slab_body(A, n_pad, kb, blockIdx.x, part);
+}
+
 __global__ void k_zero_upper_blocks(double *__restrict__ A, int n_pad)
 {
     k_zero_upper_blocks_body(A, n_pad, blockIdx.x, blockIdx.y);
@@ -248,7 +253,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         const int T = nblk - kb - 1;
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));  // panel kb
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));  // step kb-1 done with column kb+1
-        k_chol_update<<<T, 256, smem2, side>>>(m->L, n_pad, kb, nblk, 1);
+        k_chol_update_slab<<<T * 4, 256, 0, side>>>(m->L, n_pad, kb, 1);
         GPBO_LAUNCH_CHECK(ctx);
         k_chol_diag<<<1, 256, smem2, side>>>(m->L, n_pad, kb + 1, m->Dinv, ctx->dev_status);
         GPBO_LAUNCH_CHECK(ctx);
@@ -260,7 +265,11 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
+            // whole tiles (3 CTAs of 66.5 KB per SM) while they fill two waves; 16-row slabs after
+            if (tiles >= 2 * 3 * (int64_t)ctx->sm_count)
+                k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
+            else
+                k_chol_update_slab<<<(unsigned)(tiles * 4), 256, 0, st>>>(m->L, n_pad, kb, 2);
             GPBO_LAUNCH_CHECK(ctx);
             GPBO_TRY(trace_end(ctx));
             GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));

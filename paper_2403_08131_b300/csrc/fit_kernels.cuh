@@ -65,66 +65,156 @@ __device__ __forceinline__ void k_kmat_body(const double *__restrict__ Xs, int n
 }
 
 // ------------------------------------------------------------------ Cholesky
-// Diagonal block k: unblocked right-looking factorisation in shared memory, then the
-// inverse of the factor (column j solves L x = e_j).  Writes L_kk (zeros above) and Dinv_k.
-// Pivots use one reciprocal square root: L_jj = p * rsqrt(p), 1/L_jj = rsqrt(p), so the
-// column scaling and the inverse multiply instead of divide.  The inverse gives each
-// column four threads (a lane quad) that split every dot product and combine by shuffles.
+// Diagonal block kb: factor the 64x64 block in place (right-looking, column by column) and
+// build its inverse X alongside (written to Dinv_kb; L_kk gets zeros above the diagonal).
+// Pass j applies the rank-1 updates with column j of L (already scaled by 1 / L_jj) to the
+// trailing lower triangle of the block and to the rows of X below j:
+//     a_ic -= l_ij l_cj  (j < c <= i),        x_kc -= l_kj x_jc  (k > j, c <= j),
+// enumerated as one index range (the triangle from a column-major table, the rectangle
+// row-major by multiply-shift division) so that every lane of warps 1.. has an element.
+// Warp 0 meanwhile finishes a_{j+1,j+1} and takes the next pivot, L_{j+1,j+1} = p rsqrt(p)
+// with 1/L_{j+1,j+1} = rsqrt(p), and publishes it through a shared flag.  The elements of
+// column j+1 and of row j+1 of X come last in the range: their owners wait (bounded) for the
+// flag and store them scaled, so one barrier per column suffices.  The factor's arithmetic per
+// element is that of a plain right-looking loop.
 __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status, const int bx, const int by)
 {
     extern __shared__ double sm[];
     double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    double(*inv)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
+    double(*x)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
+    constexpr int TRI = NB * (NB + 1) / 2;
     __shared__ double rdiag[NB];
+    __shared__ uint16_t tab[TRI];  // lower triangle, column-major: row | col << 8
+    __shared__ int ready;          // highest column whose pivot is published
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
-    for (int e = tid; e < NB * NB; e += blockDim.x) a[e / NB][e % NB] = A[base + (int64_t)(e / NB) * n_pad + e % NB];
-    for (int j = 0; j < NB; ++j) {
-        __syncthreads();
+    auto coff = [](int c) { return c * NB - c * (c - 1) / 2; };  // first entry of column c
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        a[r][c] = A[base + (int64_t)r * n_pad + c];
+        x[r][c] = r == c ? 1.0 : 0.0;
+    }
+    for (int e = tid; e < TRI; e += blockDim.x) {
+        // column c: the largest with coff(c) <= e (closed form, then exact integer fix-up)
+        int c = (int)((129.0f - sqrtf(16641.0f - 8.0f * (float)e)) * 0.5f);
+        c = max(0, min(NB - 1, c));
+        while (c > 0 && coff(c) > e) --c;
+        while (c < NB - 1 && coff(c + 1) <= e) ++c;
+        tab[e] = (uint16_t)((c + (e - coff(c))) | (c << 8));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double p = a[0][0];
+        if (!(p > 0.0)) {
+            atomicOr(status, DEV_NOTSPD);
+            p = 1.0;
+        }
+        const double r = rsqrt(p);
+        a[0][0] = p * r;
+        rdiag[0] = r;
+        x[0][0] = r;
+        ready = 0;
+    }
+    __syncthreads();
+    if (tid > 0 && tid < NB) a[tid][0] *= rdiag[0];
+    __syncthreads();
+    volatile int *vready = &ready;
+    volatile double *vrdiag = rdiag;
+    for (int j = 0; j + 1 < NB; ++j) {
+        const int m = NB - 1 - j;                      // rows below j
+        const int nF = TRI - coff(j + 2);              // triangle, columns >= j+2
+        const int nX = (m - 1) * (j + 1);              // X rows >= j+2, columns <= j
+        const int nT = nF + nX + (m - 1) + (j + 1);    // + column j+1 below its diagonal + X row j+1
+        const uint32_t w = (uint32_t)(j + 1);
+        const uint64_t magic = ((1ull << 32) + w - 1) / w;
         if (tid == 0) {
-            double p = a[j][j];
+            double p = fma(-a[j + 1][j], a[j + 1][j], a[j + 1][j + 1]);
             if (!(p > 0.0)) {
                 atomicOr(status, DEV_NOTSPD);
                 p = 1.0;
             }
-            const double r = rsqrt(p);
-            a[j][j] = p * r;
-            rdiag[j] = r;
+            const double rr = rsqrt(p);
+            a[j + 1][j + 1] = p * rr;
+            x[j + 1][j + 1] = rr;
+            vrdiag[j + 1] = rr;
+            __threadfence_block();
+            *vready = j + 1;
+        }
+        for (int e = tid - 32; e < nT; e += (int)blockDim.x - 32) {
+            if (tid < 32) break;
+            if (e < nF) {
+                const int t = tab[coff(j + 2) + e], i = t & 255, c = t >> 8;
+                a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+            } else if (e < nF + nX) {
+                const uint32_t q = (uint32_t)(e - nF);
+                const int k = j + 2 + (int)(((uint64_t)q * magic) >> 32);
+                const int c = (int)(q - (uint32_t)(k - j - 2) * w);
+                x[k][c] = fma(-a[k][j], x[j][c], x[k][c]);
+            } else {
+                // last: elements that pass j makes final; store them scaled by 1 / L_{j+1,j+1}
+                const int q = e - nF - nX;
+                double v;
+                if (q < m - 1) v = fma(-a[j + 2 + q][j], a[j + 1][j], a[j + 2 + q][j + 1]);
+                else v = fma(-a[j + 1][j], x[j][q - (m - 1)], x[j + 1][q - (m - 1)]);
+                for (int it = 0; *vready < j + 1; ++it) {
+                    if (it == (1 << 24)) {  // cannot happen: warp 0 publishes unconditionally
+                        atomicOr(status, DEV_TIMEOUT);
+                        break;
+                    }
+                }
+                __threadfence_block();
+                const double rr = vrdiag[j + 1];
+                if (q < m - 1) a[j + 2 + q][j + 1] = v * rr;
+                else x[j + 1][q - (m - 1)] = v * rr;
+            }
         }
         __syncthreads();
-        const double r = rdiag[j];
-        for (int i = j + 1 + tid; i < NB; i += blockDim.x) a[i][j] *= r;
-        __syncthreads();
-        const int cnt = NB - 1 - j;
-        for (int e = tid; e < cnt * cnt; e += blockDim.x) {
-            int i = j + 1 + e / cnt, c = j + 1 + e % cnt;
-            if (c <= i) a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-        }
     }
-    __syncthreads();
-    {
-        const int j = tid >> 2, sub = tid & 3;
-        const unsigned mask = 0xFu << (threadIdx.x & 28);
-        for (int i = sub; i < j; i += 4) inv[i][j] = 0.0;
-        if (sub == 0) inv[j][j] = rdiag[j];
-        __syncwarp(mask);
-        for (int i = j + 1; i < NB; ++i) {
-            double s = 0.0;
-            for (int t = j + sub; t < i; t += 4) s = fma(a[i][t], inv[t][j], s);
-            s += __shfl_xor_sync(mask, s, 1);
-            s += __shfl_xor_sync(mask, s, 2);
-            if (sub == 0) inv[i][j] = -s * rdiag[i];
-            __syncwarp(mask);
-        }
-    }
-    __syncthreads();
     double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         int i = e / NB, c = e % NB;
         A[base + (int64_t)i * n_pad + c] = c <= i ? a[i][c] : 0.0;
-        D[e] = inv[i][c];
+        D[e] = x[i][c];
     }
+}
+
+// Trailing update in 16-row slabs (4 CTAs per 64x64 tile), for launches too small to fill the
+// GPU with whole tiles.  part 1: block column kb+1 (T tiles: CTA bx updates rows
+// 16 (bx % 4) .. +15 of block row kb+1+bx/4); part 2: block columns kb+2 .. (the tiles of
+// k_chol_update part 2, in the same order, 4 slabs each).  Same per-element arithmetic as
+// the full-tile update.
+__device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, int n_pad, int kb, const int bx,
+                                                          int part = 1)
+{
+    __shared__ double li[16][NB + 1];
+    __shared__ double lj[NB][NB + 1];
+    int ii = bx / 4, jj = 0;
+    if (part == 2) {
+        const int64_t p = bx / 4;
+        ii = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+        while ((int64_t)(ii + 1) * (ii + 2) / 2 <= p) ++ii;
+        while ((int64_t)ii * (ii + 1) / 2 > p) --ii;
+        jj = (int)(p - (int64_t)ii * (ii + 1) / 2);
+        ++ii;
+        ++jj;
+    }
+    const int ib = kb + 1 + ii, jb = kb + 1 + jj;
+    const int64_t r0 = (int64_t)ib * NB + (bx % 4) * 16;
+    const int tid = threadIdx.x, tx = tid % 64, ty = tid / 64;
+    for (int e = tid; e < 16 * NB; e += blockDim.x)
+        li[e / NB][e % NB] = A[(r0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
+    for (int e = tid; e < NB * NB; e += blockDim.x)
+        lj[e / NB][e % NB] = A[((int64_t)jb * NB + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
+    __syncthreads();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = 0; t < NB; ++t) {
+        const double y = lj[tx][t];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(li[ty + 4 * u][t], y, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) A[(r0 + ty + 4 * u) * n_pad + (int64_t)jb * NB + tx] -= acc[u];
 }
 
 // Panel: L_ik = A_ik L_kk^-T for the block rows i > k, one CTA per 16-row slab so that

@@ -5,10 +5,11 @@
 //
 // The cross term z_c . z_i is a dense (candidates x d) by (d x observations) contraction.
 // Each coordinate is split into FP16 hi = fp16(z) and lo = fp16(z - hi); with
-// A' = [hi | hi | lo] and B' = [hi | lo | hi] (32 columns each, zero padded to 128) one
-// kind::f16 MMA chain of K = 128 accumulates hi.hi + hi.lo + lo.hi in FP32 -- about 22
-// significant bits, the accuracy of an FP32 dot product.  Centring the coordinates at 1/2
-// keeps |z|^2 small, so the subtraction |z_c|^2 + |z_i|^2 - 2 z_c . z_i cancels little.
+// A' = -2 [hi | hi | lo | 1 1 0 ..] and B' = [hi | lo | hi | s_hi s_lo 0 ..] (32 columns each,
+// K = 128), where s = |z_i|^2 split the same way and the -2 is exact, one kind::f16 MMA
+// chain accumulates |z_i|^2 - 2 (hi.hi + hi.lo + lo.hi) in FP32 -- about 22 significant bits,
+// the accuracy of an FP32 dot product -- so the epilogue only adds |z_c|^2.  Centring the
+// coordinates at 1/2 keeps |z|^2 small, so r^2 = |z_c|^2 + |z_i|^2 - 2 z_c . z_i cancels little.
 // The Matern evaluation, the mean and the 16-bit rounding of K* run in the epilogue, where
 // each thread owns one candidate (one TMEM lane) and a quarter of a 256-observation chunk.
 //
@@ -132,18 +133,23 @@ __device__ __forceinline__ float build_row(unsigned char *a, int r, int64_t t, c
     for (int k = 0; k < DMAX; k += 2) {
         const __half h0 = __float2half_rn(z[k]), h1 = __float2half_rn(z[k + 1]);
         const __half l0 = __float2half_rn(z[k] - __half2float(h0)), l1 = __float2half_rn(z[k + 1] - __half2float(h1));
-        __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+        // -2 x (exact in FP16)
+        __half2 hh = __hmul2(__halves2half2(h0, h1), __float2half2_rn(-2.0f));
+        __half2 ll = __hmul2(__halves2half2(l0, l1), __float2half2_rn(-2.0f));
         hi[k / 2] = *reinterpret_cast<uint32_t *>(&hh);
         lo[k / 2] = *reinterpret_cast<uint32_t *>(&ll);
     }
+    __half2 one2 = __float2half2_rn(1.0f);
+    const uint32_t ones = *reinterpret_cast<uint32_t *>(&one2);
     // chunk j (16 bytes = 8 halves) of row r sits at r * 128 + ((j ^ (r & 7)) * 16)
     unsigned char *row0 = a + r * 128, *row1 = a + A_TILE + r * 128;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int sj = (j ^ (r & 7)) * 16;
         const int src = (j & 3) * 4;  // 4 uint32 = 8 halves
-        uint4 v0 = make_uint4(hi[src], hi[src + 1], hi[src + 2], hi[src + 3]);                  // [hi | hi]
-        uint4 v1 = j < 4 ? make_uint4(lo[src], lo[src + 1], lo[src + 2], lo[src + 3]) : make_uint4(0, 0, 0, 0);  // [lo | 0]
+        uint4 v0 = make_uint4(hi[src], hi[src + 1], hi[src + 2], hi[src + 3]);  // [hi | hi]
+        uint4 v1 = j < 4 ? make_uint4(lo[src], lo[src + 1], lo[src + 2], lo[src + 3])
+                         : (j == 4 ? make_uint4(ones, 0, 0, 0) : make_uint4(0, 0, 0, 0));  // [lo | 1 1 0 ..]
         *reinterpret_cast<uint4 *>(row0 + sj) = v0;
         *reinterpret_cast<uint4 *>(row1 + sj) = v1;
     }
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             const int tn = t + gridDim.x;
             if (builder && tn < P.num_tiles) {
                 const int ns = (k + 1) & 1;
-                const bool g = mbar_wait(&sh->a_empty[ns], ((uint32_t)((k + 1) >> 1) & 1u) ^ 1u, abort_flag, P.status);
+                const bool g = mbar_wait_inl(&sh->a_empty[ns], ((uint32_t)((k + 1) >> 1) & 1u) ^ 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 sh->na[ns][row] = build_row(aslot + (size_t)ns * A_SLOT, row, tn, P);
                 fence_async_smem();
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                 if (lane == 0) mbar_arrive(&sh->a_full[ns]);
             }
             // this tile's |z_c|^2
-            const bool ga = mbar_wait(&sh->a_full[slot], (uint32_t)(k >> 1) & 1u, abort_flag, P.status);
+            const bool ga = mbar_wait_inl(&sh->a_full[slot], (uint32_t)(k >> 1) & 1u, abort_flag, P.status);
             if (!__all_sync(0xffffffffu, ga)) { ok = false; break; }
             const float na = sh->na[slot][row];
             __syncwarp();
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             const int64_t cl = (int64_t)t * BM + row;
             float mu = 0.0f;
             for (int q = 0; q < nq; ++q) {
-                const bool g = mbar_wait(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
+                const bool g = mbar_wait_inl(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
@@ -307,14 +313,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
-                        const float4 nb = *reinterpret_cast<const float4 *>(P.nb + i0 + j);
                         const float4 al = *reinterpret_cast<const float4 *>(P.alpha + i0 + j);
                         // padded observations: alpha = 0 and the 16-bit L^-1 rows are zero there,
                         // so their (finite) K* values never reach mu or sigma
-                        const float k0 = matern_folded(fmaxf(fmaf(-2.0f, v[j], na + nb.x), 0.0f), s2, c1, c2);
-                        const float k1 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 1], na + nb.y), 0.0f), s2, c1, c2);
-                        const float k2 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 2], na + nb.z), 0.0f), s2, c1, c2);
-                        const float k3 = matern_folded(fmaxf(fmaf(-2.0f, v[j + 3], na + nb.w), 0.0f), s2, c1, c2);
+                        const float k0 = matern_folded(fmaxf(v[j] + na, 0.0f), s2, c1, c2);
+                        const float k1 = matern_folded(fmaxf(v[j + 1] + na, 0.0f), s2, c1, c2);
+                        const float k2 = matern_folded(fmaxf(v[j + 2] + na, 0.0f), s2, c1, c2);
+                        const float k3 = matern_folded(fmaxf(v[j + 3] + na, 0.0f), s2, c1, c2);
                         mu = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mu))));
                         pk[j / 2] = Pack8<Out>::two(k0, k1);
                         pk[j / 2 + 1] = Pack8<Out>::two(k2, k3);
@@ -335,13 +340,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             // combine the column groups' partial means (group 0 writes the result)
             const uint32_t use = (uint32_t)(k >> 1) & 1u;
             if (!builder) {
-                const bool g = mbar_wait(&sh->mu_free[slot], use ^ 1u, abort_flag, P.status);
+                const bool g = mbar_wait_inl(&sh->mu_free[slot], use ^ 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 sh->mu_part[slot][grp - 1][row] = mu;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->mu_ready[slot]);
             } else {
-                const bool g = mbar_wait(&sh->mu_ready[slot], use, abort_flag, P.status);
+                const bool g = mbar_wait_inl(&sh->mu_ready[slot], use, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 float m = mu;
 #pragma unroll
@@ -360,7 +365,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
     }
 }
 
-// Observation split B' = [hi | lo | hi | 0] (n_pad x 128 FP16) and |z_i|^2, from FP64 X.
+// Observation split B' = [hi | lo | hi | s_hi s_lo 0 ..] (n_pad x 128 FP16) with s = |z_i|^2,
+// and s in FP32, from FP64 X.
 __global__ void k_obs_split(const double *__restrict__ X, int n, int d, int n_pad, Lengthscales_inv ls,
                             __half *__restrict__ B, float *__restrict__ nb)
 {
@@ -379,6 +385,9 @@ __global__ void k_obs_split(const double *__restrict__ X, int n, int d, int n_pa
         row[96 + k] = __float2half_rn(0.0f);
     }
     nb[i] = (float)s;
+    const __half sh = __float2half_rn((float)s);
+    row[96] = sh;
+    row[97] = __float2half_rn((float)(s - (double)__half2float(sh)));
 }
 
 }  // namespace xtc

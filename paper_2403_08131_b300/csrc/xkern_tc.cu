@@ -48,7 +48,7 @@ constexpr int A_SLOT = 2 * A_TILE;         // A' = 2 K tiles
 constexpr int B_TILE = BN * 128;
 constexpr int B_STAGE = 2 * B_TILE;
 
-struct Shared {
+struct alignas(16) Shared {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
     uint64_t acc_full[2];
@@ -64,7 +64,12 @@ struct Shared {
     float mu_part[2][GROUPS - 1][BM]; // column groups 1..3: partial means per slot
 };
 
-inline size_t smem_bytes() { return (size_t)2 * A_SLOT + (size_t)STAGES * B_STAGE + 1024 + sizeof(Shared); }
+constexpr int ALPHA_SMEM_MAX = 4096;  // models up to this n_pad keep alpha in shared memory
+inline size_t smem_bytes(bool alpha_smem)
+{
+    return (size_t)2 * A_SLOT + (size_t)STAGES * B_STAGE + 1024 + sizeof(Shared) +
+           (alpha_smem ? sizeof(float) * ALPHA_SMEM_MAX : 0);
+}
 
 struct Params {
     int64_t C;            // candidates in this chunk
@@ -156,7 +161,7 @@ __device__ __forceinline__ float build_row(unsigned char *a, int r, int64_t t, c
     return na;
 }
 
-template <typename Out>
+template <typename Out, bool ALPHA_SMEM>
 __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__ CUtensorMap map_b, const Params P)
 {
     extern __shared__ unsigned char smraw[];
@@ -164,6 +169,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
     unsigned char *aslot = base;                       // 2 x A_SLOT
     unsigned char *bst = base + 2 * A_SLOT;            // STAGES x B_STAGE
     Shared *sh = (Shared *)(bst + (size_t)STAGES * B_STAGE);
+    float *alpha_s = (float *)(sh + 1);  // n_pad floats when ALPHA_SMEM
+    if (ALPHA_SMEM)
+        for (int i = threadIdx.x; i < P.n_pad; i += blockDim.x) alpha_s[i] = P.alpha[i];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nq = P.n_pad / BN;
 
@@ -313,7 +321,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
-                        const float4 al = *reinterpret_cast<const float4 *>(P.alpha + i0 + j);
+                        const float4 al = ALPHA_SMEM ? *reinterpret_cast<const float4 *>(alpha_s + i0 + j)
+                                                     : *reinterpret_cast<const float4 *>(P.alpha + i0 + j);
                         // padded observations: alpha = 0 and the 16-bit L^-1 rows are zero there,
                         // so their (finite) K* values never reach mu or sigma
                         const float k0 = matern_folded(fmaxf(v[j] + na, 0.0f), s2, c1, c2);
@@ -429,15 +438,17 @@ int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, i
     P.status = ctx->dev_status;
     P.idesc = tcx::idesc_f16(0u, xtc::BN, xtc::BM);
     const int grid = std::min(P.num_tiles, ctx->sm_count);
-    const size_t smem = xtc::smem_bytes();
+    const bool as = m->n_pad <= xtc::ALPHA_SMEM_MAX;
+    const size_t smem = xtc::smem_bytes(as);
+    auto launch = [&](auto kern) -> int {
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, P);
+        return GPBO_OK;
+    };
     if (m->prec == GPBO_PREC_BF16) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(xtc::k_xkern_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        xtc::k_xkern_tc<__nv_bfloat16><<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, P);
+        GPBO_TRY(as ? launch(xtc::k_xkern_tc<__nv_bfloat16, true>) : launch(xtc::k_xkern_tc<__nv_bfloat16, false>));
     } else {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(xtc::k_xkern_tc<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        xtc::k_xkern_tc<__half><<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, P);
+        GPBO_TRY(as ? launch(xtc::k_xkern_tc<__half, true>) : launch(xtc::k_xkern_tc<__half, false>));
     }
     GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;

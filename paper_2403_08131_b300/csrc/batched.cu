@@ -193,6 +193,12 @@ __global__ void __launch_bounds__(256) b_gemm(const float *A, const float *B, fl
     k_gemm_batched_body<float>(A, B, Cc, 0, 0, 0, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y);
 }
 
+__global__ void __launch_bounds__(256) b_gemm128(const float *A, const float *B, float *Cc, const GemmProb *probs,
+                                                 float alpha, int tri_a, int tri_b)
+{
+    k_gemm128_body(A, B, Cc, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 __global__ void __launch_bounds__(256) b_xkern(const BProb *P, const float *Xs32, const float *alpha32, const double *lsinv,
                                                float *Kst, float *mu)
 {
@@ -447,6 +453,13 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     b_cast_L<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L, pl->L32);
     b_linv_init<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->Dinv, pl->Linv32);
     for (size_t l = 0; l < pl->lvl_first.size(); ++l) {
+        if (pl->lvl_mm[l].y >= 128) {  // the single-problem path's rule: 128 x 128 tiles on large levels
+            dim3 g((pl->lvl_mm[l].y + 127) / 128, (pl->lvl_mm[l].x + 127) / 128, pl->lvl_count[l]);
+            b_gemm128<<<g, 256, 0, st>>>(pl->L32, pl->Linv32, pl->tmp, pl->gemm_dev + pl->lvl_first[l], 1.0f, 0, 1);
+            b_gemm128<<<g, 256, 0, st>>>(pl->Linv32, pl->tmp, pl->Linv32,
+                                         pl->gemm_dev + pl->lvl_first[l] + pl->lvl_count[l], -1.0f, 1, 0);
+            continue;
+        }
         dim3 grid((pl->lvl_mm[l].y + 63) / 64, (pl->lvl_mm[l].x + 63) / 64, pl->lvl_count[l]);
         b_gemm<<<grid, 256, 0, st>>>(pl->L32, pl->Linv32, pl->tmp, pl->gemm_dev + pl->lvl_first[l], 1.0f, 0, 1);
         b_gemm<<<grid, 256, 0, st>>>(pl->Linv32, pl->tmp, pl->Linv32, pl->gemm_dev + pl->lvl_first[l] + pl->lvl_count[l],

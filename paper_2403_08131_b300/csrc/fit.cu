@@ -4,9 +4,10 @@
 // FP32 from the FP64 factor.
 //
 //   K      = s2 m(r) + sn2 I            k_kmat            (Matern-5/2 ARD)
-//   K      = L L^T                      k_chol_*          (blocked, right-looking, NB = 64)
-//   alpha  = L^-T L^-1 y, refined once  k_fwd_step/k_bwd_step/k_residual
-//   L^-1                                k_gemm_batched    (level-by-level block recursion)
+//   K      = L L^T                      k_chol_*          (blocked, right-looking, NB = 64,
+//                                                          lookahead of one block column)
+//   alpha  = L^-T L^-1 y, refined once  k_fwd_wave/k_bwd_wave/k_residual (one launch per substitution)
+//   L^-1                                k_gemm_batched, k_gemm128 (level-by-level block recursion)
 //
 // Padding: n is padded to n_pad (a multiple of 64, or of 256 for tensor-core models).
 // Padded rows/columns of K are the identity, so L and L^-1 are the identity there, the
@@ -17,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 namespace gpbo {
@@ -61,18 +63,6 @@ __global__ void k_zero_upper_blocks(double *__restrict__ A, int n_pad)
     k_zero_upper_blocks_body(A, n_pad, blockIdx.x, blockIdx.y);
 }
 
-__global__ void __launch_bounds__(256) k_fwd_step(const double *__restrict__ L, const double *__restrict__ Dinv,
-                                                  int n_pad, int b, double *__restrict__ w, double *__restrict__ z)
-{
-    k_fwd_step_body(L, Dinv, n_pad, b, w, z, blockIdx.x, blockIdx.y);
-}
-
-__global__ void __launch_bounds__(256) k_bwd_step(const double *__restrict__ L, const double *__restrict__ Dinv,
-                                                  int n_pad, int b, double *__restrict__ w, double *__restrict__ x)
-{
-    k_bwd_step_body(L, Dinv, n_pad, b, w, x, blockIdx.x, blockIdx.y);
-}
-
 __global__ void k_residual(const double *__restrict__ K, const double *__restrict__ alpha,
                            const double *__restrict__ y, int n_pad, double *__restrict__ r)
 {
@@ -96,6 +86,27 @@ __global__ void __launch_bounds__(256) k_gemm_batched(const T *__restrict__ Abas
                                                       int tri_b)
 {
     k_gemm_batched_body<T>(Abase, Bbase, Cbase, lda, ldb, ldc, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) k_fwd_wave(const double *__restrict__ L, const double *__restrict__ Dinv,
+                                                  int n_pad, const double *__restrict__ w, double *z, int *flags,
+                                                  int *ticket, unsigned *status)
+{
+    k_fwd_wave_body(L, Dinv, n_pad, w, z, flags, ticket, status);
+}
+
+__global__ void __launch_bounds__(256) k_bwd_wave(const double *__restrict__ L, const double *__restrict__ Dinv,
+                                                  int n_pad, const double *__restrict__ w, double *x, int *flags,
+                                                  int *ticket, unsigned *status)
+{
+    k_bwd_wave_body(L, Dinv, n_pad, w, x, flags, ticket, status);
+}
+
+__global__ void __launch_bounds__(256) k_gemm128(const float *__restrict__ A, const float *__restrict__ B,
+                                                 float *__restrict__ C, const GemmProb *__restrict__ probs, float alpha,
+                                                 int tri_a, int tri_b)
+{
+    k_gemm128_body(A, B, C, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -184,6 +195,17 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
     GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, probs.data(), sizeof(GemmProb) * probs.size(), cudaMemcpyHostToDevice,
                                   ctx->stream));
     for (size_t l = 0; l < first.size(); ++l) {
+        if (std::is_same<T, float>::value && mm[l].y >= 128) {
+            // large FP32 levels: 128 x 128 tiles (the batched step uses the same rule per level)
+            dim3 grid((mm[l].y + 127) / 128, (mm[l].x + 127) / 128, count[l]);
+            k_gemm128<<<grid, 256, 0, ctx->stream>>>((const float *)Ls, (const float *)Linv, (float *)tmp,
+                                                     probs_dev + first[l], 1.0f, 0, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_gemm128<<<grid, 256, 0, ctx->stream>>>((const float *)Linv, (const float *)tmp, (float *)Linv,
+                                                     probs_dev + first[l] + count[l], -1.0f, 1, 0);
+            GPBO_LAUNCH_CHECK(ctx);
+            continue;
+        }
         dim3 grid((mm[l].y + 63) / 64, (mm[l].x + 63) / 64, count[l]);
         k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Ls, Linv, tmp, n_pad, n_pad, n_pad, probs_dev + first[l],
                                                          T(1), 0, 1);
@@ -197,20 +219,19 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
 
 static unsigned blocks_for(int64_t count, int threads = 256) { return (unsigned)((count + threads - 1) / threads); }
 
+// Solve K x = rhs with the factor: L z = rhs, then L^T x = z, each as one wavefront launch.
+// sync: 2 nblk + 2 ints of scratch (flags and tickets of the two launches).
 static int alpha_solve(gpbo_ctx *ctx, cudaStream_t st, const gp_model *m, const double *rhs, double *work,
-                       double *out)
+                       double *out, int *sync)
 {
     const int n_pad = m->n_pad, nblk = n_pad / NB;
-    GPBO_CUDA_TRY(cudaMemcpyAsync(work, rhs, sizeof(double) * n_pad, cudaMemcpyDeviceToDevice, st));
     double *z = work + n_pad;
-    for (int b = 0; b < nblk; ++b) {
-        k_fwd_step<<<std::max(1, nblk - b - 1), 256, 0, st>>>(m->L, m->Dinv, n_pad, b, work, z);
-        GPBO_LAUNCH_CHECK(ctx);
-    }
-    for (int b = nblk - 1; b >= 0; --b) {
-        k_bwd_step<<<std::max(1, b), 256, 0, st>>>(m->L, m->Dinv, n_pad, b, z, out);
-        GPBO_LAUNCH_CHECK(ctx);
-    }
+    GPBO_CUDA_TRY(cudaMemsetAsync(sync, 0, sizeof(int) * (2 * nblk + 2), st));
+    k_fwd_wave<<<nblk, 256, 0, st>>>(m->L, m->Dinv, n_pad, rhs, z, sync, sync + 2 * nblk, ctx->dev_status);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_bwd_wave<<<nblk, 256, 0, st>>>(m->L, m->Dinv, n_pad, z, out, sync + nblk, sync + 2 * nblk + 1,
+                                     ctx->dev_status);
+    GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;
 }
 
@@ -289,10 +310,12 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     const size_t vec = sizeof(double) * n_pad;
     const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
                              sizeof(GemmProb) * 2 * max_probs;
+    const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
     void *wsp = nullptr;
-    GPBO_TRY(ws_reserve(ctx, vec * 6 + inv_bytes, &wsp));
+    GPBO_TRY(ws_reserve(ctx, vec * 6 + sync_bytes + inv_bytes, &wsp));
     double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *dlt = r + n_pad;
-    void *w2 = (void *)((char *)wsp + vec * 6);
+    int *sync = (int *)((char *)wsp + vec * 6);
+    void *w2 = (void *)((char *)wsp + vec * 6 + sync_bytes);
 
     // alpha = K^-1 y with one refinement step (FP64 throughout), on the side stream: its
     // substitution steps are latency-bound and overlap the L^-1 products on the main stream.
@@ -300,10 +323,10 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_pad_copy<<<blocks_for(n_pad), 256, 0, side>>>(y_dev, n, n_pad, ypad);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(alpha_solve(ctx, side, m, ypad, work, m->alpha64));
+    GPBO_TRY(alpha_solve(ctx, side, m, ypad, work, m->alpha64, sync));
     k_residual<<<(n_pad + 7) / 8, 256, 0, side>>>(m->K, m->alpha64, ypad, n_pad, r);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(alpha_solve(ctx, side, m, r, work, dlt));
+    GPBO_TRY(alpha_solve(ctx, side, m, r, work, dlt, sync));
     k_axpy_cast<<<blocks_for(n_pad), 256, 0, side>>>(m->alpha64, dlt, n_pad, m->alpha32);
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
@@ -348,6 +371,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
+    if (bits & DEV_TIMEOUT) return GPBO_ETIMEOUT;
     return GPBO_OK;
 }
 

@@ -369,6 +369,118 @@ __device__ __forceinline__ void k_bwd_step_body(const double *__restrict__ L, co
     if (tid < NB) w[cb * NB + tid] -= red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
 }
 
+// Wavefront forms of the two substitutions: one launch each, one CTA per 64-row block, with
+// the same arithmetic per element as the step kernels above (so the results are identical).
+// A CTA takes its block from an atomic ticket in the order CTAs start, and only waits for
+// blocks with smaller tickets, which have all started: no wait can depend on a CTA that is not
+// running.  A finished block publishes its solution and then sets flags[block] = 1 (release:
+// the solution's stores are fenced before the flag); a waiter spins on the flag (bounded),
+// fences, and reads the solution past L1.  flags (nblk) and ticket must be zero at launch.
+__device__ __forceinline__ bool wave_wait(const int *flag, unsigned *status)
+{
+    for (long it = 0; *(volatile const int *)flag == 0; ++it)
+        if (it == (1l << 26)) {  // ~seconds: set the error and give up rather than hang
+            atomicOr(status, DEV_TIMEOUT);
+            return false;
+        }
+    __threadfence();
+    return true;
+}
+
+// Forward: L z = w.  Ticket q handles block b = q; w is read once, z written.
+__device__ __forceinline__ void k_fwd_wave_body(const double *__restrict__ L, const double *__restrict__ Dinv,
+                                                int n_pad, const double *__restrict__ w, double *z, int *flags,
+                                                int *ticket, unsigned *status)
+{
+    __shared__ double zp[NB], wb[NB];
+    __shared__ double D[NB][NB + 1];
+    __shared__ int sb;
+    const int tid = threadIdx.x;
+    if (tid == 0) sb = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int b = sb;
+    const double *Db = Dinv + (int64_t)b * NB * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Db[e];
+    const int r = tid >> 2, part = tid & 3;
+    const int64_t row = (int64_t)b * NB + r;
+    double acc = w[row];
+    for (int p = 0; p < b; ++p) {
+        double lv[16];
+        const double *Lr = L + row * n_pad + (int64_t)p * NB + part * 16;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) lv[t] = Lr[t];
+        if (tid == 0) wave_wait(flags + p, status);
+        __syncthreads();
+        if (tid < NB) zp[tid] = __ldcg(z + (int64_t)p * NB + tid);
+        __syncthreads();
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) s = fma(lv[t], zp[part * 16 + t], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        acc -= s;
+    }
+    if (part == 0) wb[r] = acc;
+    __syncthreads();
+    double s = 0.0;
+    for (int t = part; t <= r; t += 4) s = fma(D[r][t], wb[t], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0) {
+        z[row] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) *(volatile int *)(flags + b) = 1;
+}
+
+// Backward: L^T x = w.  Ticket q handles block c = nblk - 1 - q.
+__device__ __forceinline__ void k_bwd_wave_body(const double *__restrict__ L, const double *__restrict__ Dinv,
+                                                int n_pad, const double *__restrict__ w, double *x, int *flags,
+                                                int *ticket, unsigned *status)
+{
+    __shared__ double xp[NB], wb[NB], red[4][NB];
+    __shared__ double D[NB][NB + 1];
+    __shared__ int sb;
+    const int tid = threadIdx.x, nblk = n_pad / NB;
+    if (tid == 0) sb = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int c = nblk - 1 - sb;
+    const double *Dc = Dinv + (int64_t)c * NB * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) D[e / NB][e % NB] = Dc[e];
+    const int col = tid & 63, part = tid >> 6;
+    double acc = tid < NB ? w[(int64_t)c * NB + tid] : 0.0;
+    for (int b = nblk - 1; b > c; --b) {
+        double lv[16];
+        const double *Lb = L + (int64_t)(b * NB + part * 16) * n_pad + (int64_t)c * NB + col;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) lv[t] = Lb[(int64_t)t * n_pad];
+        if (tid == 0) wave_wait(flags + b, status);
+        __syncthreads();
+        if (tid < NB) xp[tid] = __ldcg(x + (int64_t)b * NB + tid);
+        __syncthreads();
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) s = fma(lv[t], xp[part * 16 + t], s);
+        red[part][col] = s;
+        __syncthreads();
+        if (tid < NB) acc -= red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
+    }
+    if (tid < NB) wb[tid] = acc;
+    __syncthreads();
+    const int rr = tid >> 2, sub = tid & 3;
+    double s = 0.0;
+    for (int t = rr + sub; t < NB; t += 4) s = fma(D[t][rr], wb[t], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (sub == 0) {
+        x[(int64_t)c * NB + rr] = s;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) *(volatile int *)(flags + c) = 1;
+}
+
 // r = y - K alpha (one warp per row).
 __device__ __forceinline__ void k_residual_body(const double *__restrict__ K, const double *__restrict__ alpha,
                            const double *__restrict__ y, int n_pad, double *__restrict__ r, const int bx, const int by)
@@ -457,6 +569,92 @@ __device__ __forceinline__ void k_gemm_batched_body(const T *__restrict__ Abase,
             int gr = m0 + ty + 16 * u, gc = n0 + tx + 16 * v;
             if (gr < pr.m && gc < pr.n) C[(int64_t)gr * pr.ld + gc] = alpha * acc[u][v];
         }
+}
+
+// FP32 form of the same product for the large levels of the recursion (m, n >= 128): CTA tile
+// 128 x 128, K steps of 8, 256 threads with an 8 x 8 register tile each (rows ty*4 + {0..3}
+// and 64 + ty*4 + {0..3}, the same for columns), 128-bit shared-memory reads, and the next K
+// step's global loads held in registers while the current one is multiplied (two smem
+// buffers, one barrier per step).  m, n, k and the offsets are multiples of 64, so the only
+// ragged edge is a half tile in m or n, which is zero-filled.
+__device__ __forceinline__ void k_gemm128_body(const float *__restrict__ Abase, const float *__restrict__ Bbase,
+                                               float *__restrict__ Cbase, const GemmProb *__restrict__ probs,
+                                               float alpha, int tri_a, int tri_b, const int bx, const int by,
+                                               const int bz)
+{
+    constexpr int BM = 128, BN = 128, BK = 8;
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    const GemmProb pr = probs[bz];
+    const int m0 = by * BM, n0 = bx * BN;
+    if (m0 >= pr.m || n0 >= pr.n) return;
+    const float *A = Abase + pr.a_off;
+    const float *B = Bbase + pr.b_off;
+    float *C = Cbase + pr.c_off;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    int kbeg = 0, kend = pr.k;
+    if (tri_a) kend = min(kend, m0 + BM);
+    if (tri_b) kbeg = n0;
+    // loader roles: A rows ra (2 threads per row, 4 k each), B row rb (32 threads per row, 4 cols each)
+    const int ra = tid / 2, ca = (tid % 2) * 4;
+    const int rb = tid / 32, cb = (tid % 32) * 4;
+    const bool a_ok = m0 + ra < pr.m, b_ok = n0 + cb < pr.n;
+    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+    auto fetch = [&](int k0) {
+        pa = a_ok ? *reinterpret_cast<const float4 *>(A + (int64_t)(m0 + ra) * pr.ld + k0 + ca) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pb = b_ok ? *reinterpret_cast<const float4 *>(B + (int64_t)(k0 + rb) * pr.ld + n0 + cb) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto stash = [&](int buf) {
+        As[buf][ca + 0][ra] = pa.x;
+        As[buf][ca + 1][ra] = pa.y;
+        As[buf][ca + 2][ra] = pa.z;
+        As[buf][ca + 3][ra] = pa.w;
+        *reinterpret_cast<float4 *>(&Bs[buf][rb][cb]) = pb;
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    int buf = 0;
+    if (kbeg < kend) {
+        fetch(kbeg);
+        stash(0);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        const bool more = k0 + BK < kend;
+        if (more) fetch(k0 + BK);
+#pragma unroll
+        for (int t = 0; t < BK; ++t) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][t][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][t][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][t][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][t][64 + tx * 4]);
+            const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        }
+        if (more) stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int gr = m0 + (u < 4 ? ty * 4 + u : 64 + ty * 4 + (u - 4));
+        if (gr >= pr.m) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int gc = n0 + h * 64 + tx * 4;
+            if (gc >= pr.n) continue;
+            float4 o = make_float4(alpha * acc[u][h * 4], alpha * acc[u][h * 4 + 1], alpha * acc[u][h * 4 + 2],
+                                   alpha * acc[u][h * 4 + 3]);
+            *reinterpret_cast<float4 *>(C + (int64_t)gr * pr.ld + gc) = o;
+        }
+    }
 }
 
 // Linv's diagonal blocks from Dinv (rounded to T); everything else zero.

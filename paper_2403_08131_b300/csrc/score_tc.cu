@@ -278,14 +278,19 @@ static int get_encoder()
 int encode_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t rows, uint64_t cols,
                      uint32_t box_rows)
 {
+    return encode_2d_box(map, dt, base, rows, cols, box_rows, 64, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+int encode_2d_box(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t rows, uint64_t cols,
+                  uint32_t box_rows, uint32_t box_cols, CUtensorMapSwizzle swizzle)
+{
     GPBO_TRY(get_encoder());
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)tc::BK, box_rows};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = g_encode(map, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         fprintf(stderr, "gpbo: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
         return GPBO_ECUDA;

@@ -165,5 +165,8 @@ __device__ __forceinline__ void named_sync(int id, int count)
 // 2-D row-major 16-bit matrix (rows x cols, cols contiguous), box = box_rows x 64 cols, 128B swizzle.
 int encode_2d(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t rows, uint64_t cols,
               uint32_t box_rows);
+// The same with box = box_rows x box_cols and the given swizzle (box_cols x 2 bytes = the swizzle span).
+int encode_2d_box(CUtensorMap *map, CUtensorMapDataType dt, const void *base, uint64_t rows, uint64_t cols,
+                  uint32_t box_rows, uint32_t box_cols, CUtensorMapSwizzle swizzle);
 
 }  // namespace gpbo

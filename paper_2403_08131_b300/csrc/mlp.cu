@@ -6,7 +6,8 @@
 // Ensemble combine (mean of the members, total variance):
 //   mu_bar = mean_e mu_e,  sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e.
 // Training: L = 1/(2B) sum (o - t)^2 per network, Adam (lr, 0.9, 0.999, 1e-8), minibatches
-// drawn with replacement from the counter stream, all E networks in the same launches.
+// drawn with replacement from the counter stream, all E networks in the same launches; the
+// step is captured once per call into a CUDA graph and replayed.
 //
 // Parameter layout per network (FP32, contiguous): W1 [d x H], b1 [H], W2 [H x H], b2 [H],
 // W3 [H x 2], b3 [2] -- weights stored input-major, the same layout as the FP64 oracle.
@@ -27,6 +28,8 @@ struct gpbo_mlp {
     int cap = 0;
     float *bx = nullptr, *bt = nullptr, *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *o = nullptr;
     float *d2 = nullptr, *d1 = nullptr, *dO = nullptr, *loss = nullptr;
+    int64_t *dctr = nullptr;         // device step counters: [0] within this train call, [1] Adam steps
+    cudaStream_t cap_stream = nullptr;  // private stream for capturing the training step
     // tensor-core operands (BF16 K-major weights + FP32 aux), rebuilt when theta changes
     void *wt16 = nullptr;
     float *aux = nullptr;
@@ -173,10 +176,14 @@ __global__ void k_colsum(const float *X, int64_t sX, int B, int N, float *out, i
     out[e * sOut + j] = s;
 }
 
-__global__ void k_adam(float *theta, const float *g, float *m, float *v, int64_t count, float lr, float c1, float c2)
+// Adam step t = adam_steps + 1 (bias corrections 1 - 0.9^t, 1 - 0.999^t).
+__global__ void k_adam(float *theta, const float *g, float *m, float *v, int64_t count, float lr,
+                       const int64_t *adam_steps)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= count) return;
+    const float t = (float)(*adam_steps + 1);
+    const float c1 = 1.0f - powf(0.9f, t), c2 = 1.0f - powf(0.999f, t);
     const float gi = g[i];
     const float mi = 0.9f * m[i] + 0.1f * gi;
     const float vi = 0.999f * v[i] + 0.001f * gi * gi;
@@ -186,11 +193,19 @@ __global__ void k_adam(float *theta, const float *g, float *m, float *v, int64_t
 }
 
 // Minibatch: rows drawn with replacement (counter stream 7) from X (N x d) and the targets.
-__global__ void k_gather_batch(const float *X, const float *T, int64_t N, int d, int B, uint64_t seed, uint64_t step,
-                               float *bx, float *bt)
+// Advance the step counters (after every kernel of the step has read them).
+__global__ void k_step_inc(int64_t *ctr)
+{
+    ctr[0] += 1;
+    ctr[1] += 1;
+}
+
+__global__ void k_gather_batch(const float *X, const float *T, int64_t N, int d, int B, uint64_t seed,
+                               const int64_t *step_dev, float *bx, float *bt)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    const uint64_t step = (uint64_t)*step_dev;
     const uint64_t r = splitmix64(seed, 7, step * (uint64_t)B + b);
     const int64_t i = (int64_t)((r >> 11) % (uint64_t)N);
     for (int k = 0; k < d; ++k) bx[(int64_t)b * d + k] = X[i * d + k];
@@ -366,12 +381,12 @@ static int ensure_batch(gpbo_mlp *net, int B)
 
 // Forward of every network on B rows of X (shared by the networks).  keep: store Z for backward.
 static int forward(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int B, float *z1, float *h1, float *z2, float *h2,
-                   float *o, bool keep)
+                   float *o, bool keep, cudaStream_t stream = nullptr)
 {
     const int E = net->E, d = net->d, H = net->H;
     const Off f = offsets(d, H);
     const int64_t P = net->P, BH = (int64_t)B * H;
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = stream ? stream : ctx->stream;
     dim3 g1(nb(H, 64), nb(B, 64), E);
     k_gemm<false, false><<<g1, 256, 0, st>>>(X, 0, d, net->theta + f.W1, P, H, keep ? z1 : nullptr, BH, H,
                                              net->theta + f.b1, P, h1, nullptr, B, H, d, 1);
@@ -387,13 +402,13 @@ static int forward(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int B, float *z
 }
 
 // Gradients of every network for the batch in net->bx / net->bt (B rows) into net->grad.
-static int backward(gpbo_ctx *ctx, gpbo_mlp *net, int B)
+static int backward(gpbo_ctx *ctx, gpbo_mlp *net, int B, cudaStream_t stream = nullptr)
 {
     const int E = net->E, d = net->d, H = net->H;
     const Off f = offsets(d, H);
     const int64_t P = net->P, BH = (int64_t)B * H;
-    cudaStream_t st = ctx->stream;
-    GPBO_TRY(forward(ctx, net, net->bx, B, net->z1, net->h1, net->z2, net->h2, net->o, true));
+    cudaStream_t st = stream ? stream : ctx->stream;
+    GPBO_TRY(forward(ctx, net, net->bx, B, net->z1, net->h1, net->z2, net->h2, net->o, true, st));
     GPBO_CUDA_TRY(cudaMemsetAsync(net->loss, 0, sizeof(float) * E, st));
     k_out_grad<<<dim3(nb(2 * B), E), 256, 0, st>>>(net->o, net->bt, B, net->dO, net->loss);
     GPBO_LAUNCH_CHECK(ctx);
@@ -493,7 +508,8 @@ int mlp_create(gpbo_ctx *ctx, int E, int d, int H, uint64_t seed, gpbo_mlp **out
     const size_t bytes = sizeof(float) * (size_t)E * net->P;
     if (cudaMalloc(&net->theta, bytes) != cudaSuccess || cudaMalloc(&net->grad, bytes) != cudaSuccess ||
         cudaMalloc(&net->m, bytes) != cudaSuccess || cudaMalloc(&net->v, bytes) != cudaSuccess ||
-        cudaMalloc(&net->loss, sizeof(float) * E) != cudaSuccess) {
+        cudaMalloc(&net->loss, sizeof(float) * E) != cudaSuccess ||
+        cudaMalloc(&net->dctr, sizeof(int64_t) * 2) != cudaSuccess) {
         mlp_free(net);
         return GPBO_ENOMEM;
     }
@@ -519,6 +535,8 @@ int mlp_free(gpbo_mlp *net)
         if (b) cudaFree(b);
     if (net->wt16) cudaFree(net->wt16);
     if (net->aux) cudaFree(net->aux);
+    if (net->dctr) cudaFree(net->dctr);
+    if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
     delete net;
     return GPBO_OK;
 }
@@ -579,16 +597,35 @@ int mlp_train(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, const float *mu, con
     GPBO_LAUNCH_CHECK(ctx);
     int rc = GPBO_OK;
     const int64_t count = (int64_t)net->E * net->P;
-    for (int s = 0; s < steps && rc == GPBO_OK; ++s) {
-        k_gather_batch<<<nb(batch), 256, 0, st>>>(X, T, N, net->d, batch, seed, (uint64_t)s, net->bx, net->bt);
+    // One training step (minibatch draw, forward, backward, Adam, counter advance) is captured
+    // once into a CUDA graph on a private stream and replayed `steps` times on the context's
+    // stream; the step counters live on the device so every replay draws its own batch.
+    const int64_t ctr0[2] = {0, net->step};
+    GPBO_CUDA_TRY(cudaMemcpyAsync(net->dctr, ctr0, sizeof(ctr0), cudaMemcpyHostToDevice, st));
+    if (!net->cap_stream) GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+    const int64_t launches0 = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GPBO_CUDA_TRY(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
+    {
+        cudaStream_t cs = net->cap_stream;
+        k_gather_batch<<<nb(batch), 256, 0, cs>>>(X, T, N, net->d, batch, seed, net->dctr, net->bx, net->bt);
         ctx->launches++;
-        rc = backward(ctx, net, batch);
-        if (rc != GPBO_OK) break;
-        net->step++;
-        const float c1 = 1.0f - powf(0.9f, (float)net->step), c2 = 1.0f - powf(0.999f, (float)net->step);
-        k_adam<<<nb(count), 256, 0, st>>>(net->theta, net->grad, net->m, net->v, count, lr, c1, c2);
-        ctx->launches++;
+        rc = backward(ctx, net, batch, cs);
+        k_adam<<<nb(count), 256, 0, cs>>>(net->theta, net->grad, net->m, net->v, count, lr, net->dctr + 1);
+        k_step_inc<<<1, 1, 0, cs>>>(net->dctr);
+        ctx->launches += 2;
     }
+    cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &graph);
+    if (rc == GPBO_OK && ce != cudaSuccess) rc = GPBO_ECUDA;
+    if (rc == GPBO_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = GPBO_ECUDA;
+    const int64_t per_step = ctx->launches - launches0;
+    for (int s = 0; s < steps && rc == GPBO_OK; ++s)
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = GPBO_ECUDA;
+    if (rc == GPBO_OK) ctx->launches += per_step * (steps - 1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc == GPBO_OK) net->step += steps;
     net->version++;
     if (rc == GPBO_OK && cudaGetLastError() != cudaSuccess) rc = GPBO_ECUDA;
     double hs[4];

@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
                     help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
     ap.add_argument("--profile-surrogate", type=int, default=0, metavar="M",
-                    help="profiling case: the BF16 ensemble forward (8 x 20-256-256-2) over M seeded candidates, "
+                    help="profiling case: the FP16 ensemble forward (8 x 20-256-256-2) over M seeded candidates, "
                          "run twice, no JSON")
     return ap.parse_args()
 
@@ -185,7 +185,7 @@ def surrogate_form(ctx, gpbo, W, dev, plain_value=None):
     gam, gem = ctx.posterior_ei(model, None, M=M, seed=seed, y_best=tau)
     t_exact = time.perf_counter() - t0
     out = {"workload": "8 x MLP 20-256-256-2 on 200k posterior samples of the n=4096 d=20 GP; 2^24 candidates "
-                       "scored by the BF16 tensor-core ensemble, top-4096 re-scored exactly (FP16 tiles)",
+                       "scored by the FP16 tensor-core ensemble, top-4096 re-scored exactly (FP16 tiles)",
            "value": round(M / t_screen, 1), "unit": "candidates/s", "screen_ms": round(t_screen * 1e3, 2),
            "train_s": round(t_train, 2), "train_loss": round(loss, 4),
            "exact_all_ms": round(t_exact * 1e3, 2), "speedup_vs_exact_f16": round(t_exact / t_screen, 2),
@@ -417,7 +417,7 @@ def profile_surrogate(args):
     M = args.profile_surrogate
     ei = torch.empty(M, dtype=torch.float32, device="cuda")
     for _ in range(2):
-        net.score(ei, M=M, seed=2408, y_best=-1.0, prec="bf16")
+        net.score(ei, M=M, seed=2408, y_best=-1.0, prec="f16")
     torch.cuda.synchronize()
     print(f"profile surrogate: M={M} ei[0]={float(ei[0]):.6g} max={float(ei.max()):.6g}")
     net.free()

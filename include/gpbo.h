@@ -313,13 +313,15 @@ int mlp_norm(const gpbo_mlp *net, double *norm4);
  * Writes device arrays of M floats: ei = EI(mu_bar, sigma_bar) below y_best (minimisation),
  * mu = mu_bar and sigma = sigma_bar (mu and sigma may be NULL).
  * prec GPBO_PREC_F32: FP32 forward on the CUDA cores (any d, H), exact GELU.
- * prec GPBO_PREC_BF16: one tensor-core launch (tcgen05, BF16 weights and activations, FP32
- * accumulate, tanh-form GELU), fused with the combine and the EI; needs H = 256 and
- * d <= 31, else GPBO_ENOTSUP.  GPBO_ETIMEOUT if a bounded device wait gave up.  Synchronises. */
+ * prec GPBO_PREC_F16: one tensor-core launch (tcgen05): FP16 inputs, first-layer weights,
+ * first-layer activations and second-layer weights; FP32 accumulation, FP32 GELU in the
+ * tanh form and FP32 from the second layer's output on; fused with the combine and the
+ * EI.  Needs H = 256, d <= 31 and E <= 8, else GPBO_ENOTSUP.  GPBO_PREC_BF16: GPBO_ENOTSUP.
+ * GPBO_ETIMEOUT if a bounded device wait gave up.  Synchronises. */
 int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t seed, double y_best, double xi,
               int prec, float *ei, float *mu, float *sigma);
 /* Draw M candidates from seed (stream 2), score them with the ensemble's EI below y_best
- * (the BF16 tensor-core path of mlp_score when H = 256 and d <= 31, else FP32),
+ * (the FP16 tensor-core path of mlp_score when H = 256, d <= 31 and E <= 8, else FP32),
  * keep the k best (radix select; ties at the k-th value taken in any order), re-score those
  * k with the exact GP-EI of `model` (FP32 or 16-bit scoring) and return the best pool index
  * and its exact EI.  ei_pool: device M floats for the surrogate EI, or NULL (then the call

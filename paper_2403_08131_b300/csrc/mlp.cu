@@ -460,14 +460,14 @@ static int ensure_packed(gpbo_ctx *ctx, gpbo_mlp *net)
 }
 
 // Ensemble (mu_bar, sigma_bar, EI) for M candidates: rows of X (device) or, when X is null,
-// pool candidates 0 .. M-1 drawn from seed.  BF16: one tensor-core launch; F32: CUDA-core
+// pool candidates 0 .. M-1 drawn from seed.  F16: one tensor-core launch; F32: CUDA-core
 // forward in chunks.  Outputs are pool-indexed device arrays (mu, sigma may be null).
 static int score_pool(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t seed, double tau, double xi,
                       int prec, float *ei, float *mu, float *sigma)
 {
     cudaStream_t st = ctx->stream;
     const double *nm = net->norm;
-    if (prec == GPBO_PREC_BF16) {
+    if (prec == GPBO_PREC_F16) {
         GPBO_TRY(ensure_packed(ctx, net));
         return mlp_tc_score(ctx, net->wt16, net->aux, net->E, net->d, nm, X, seed, 0, M, tau, xi, ei, mu, sigma);
     }
@@ -657,7 +657,8 @@ int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t 
               float *ei, float *mu, float *sigma)
 {
     if (!ctx || !net || !ei || M < 1 || M > 0x7fffffffll) return GPBO_EINVAL;
-    if (prec != GPBO_PREC_BF16 && prec != GPBO_PREC_F32) return GPBO_EINVAL;
+    if (prec == GPBO_PREC_BF16) return GPBO_ENOTSUP;  // the tensor-core forward uses FP16 operands
+    if (prec != GPBO_PREC_F16 && prec != GPBO_PREC_F32) return GPBO_EINVAL;
     GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
     GPBO_TRY(score_pool(ctx, net, X, M, seed, y_best, xi, prec, ei, mu, sigma));
     GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -690,7 +691,7 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
     GPBO_CUDA_TRY(cudaMalloc(&hist, sizeof(uint32_t) * (4096 + 4)));
     GPBO_CUDA_TRY(cudaMalloc(&Xk, sizeof(float) * (size_t)k * d));
     uint32_t *sel = hist + 4096, *counters = hist + 4098;
-    const int prec = mlp_tc_usable(d, net->H, net->E) ? GPBO_PREC_BF16 : GPBO_PREC_F32;
+    const int prec = mlp_tc_usable(d, net->H, net->E) ? GPBO_PREC_F16 : GPBO_PREC_F32;
     int rc = score_pool(ctx, net, nullptr, M, seed, y_best, xi, prec, ei, nullptr, nullptr);
     // top k by the surrogate's EI
     if (rc == GPBO_OK) {

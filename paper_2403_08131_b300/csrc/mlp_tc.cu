@@ -1,17 +1,18 @@
-// Ensemble pre-screen forward on the tensor cores (BF16 operands, FP32 accumulate), fused
+// Ensemble pre-screen forward on the tensor cores (FP16 operands, FP32 accumulate), fused
 // with the ensemble combine and the expected improvement of every candidate.
 //
 // For a tile of 128 candidates and each network e of the ensemble (d -> 256 -> 256 -> 2):
 //   Z1 = [x | 1] [W1 ; b1]         tcgen05.mma, K = 32 (d <= 31 inputs, then the constant 1)
-//   H1 = bf16(gelu(Z1))            epilogue; written to shared memory as the next A operand
+//   H1 = fp16(gelu(Z1))            epilogue; written to shared memory as the next A operand
 //   Z2 = H1 W2                     tcgen05.mma, K = 256 in four 64-column K tiles
 //   o  = gelu(Z2 + b2) W3 + b3     epilogue, FP32 on the CUDA cores (two outputs)
 // then mu_e = o_0 sd_mu + mean_mu and sigma_e = exp(o_1 sd_ls + mean_ls); after the last
 // network mu_bar = mean_e mu_e, sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e and
 // EI(mu_bar, sigma_bar) for minimisation.
-// gelu is the tanh form of Hendrycks & Gimpel (2016), evaluated with the hardware
-// tanh.approx.f32; it differs from z Phi(z) by < 5e-4 absolute plus tanh.approx's relative
-// error (about 2^-11) times |z|/2, below the BF16 rounding of H1 for |z| >= 1/2.
+// gelu is the tanh form of Hendrycks & Gimpel (2016) with the hardware tanh.approx.f32; it
+// differs from z Phi(z) by < 5e-4 absolute.  Its factor 1/2 is folded into W2 and W3 (exact: a power of two), so the epilogues
+// compute h' = z (1 + t) = 2 gelu(z) with one FMA.  FP16 rather than BF16 operands: the same
+// tensor rate, 11 significant bits instead of 8.
 //
 // Roles (one CTA per SM, persistent over tiles; 576 threads):
 //   warp 0      TMA: per network, [W1 ; b1]^T (256 x 64, zero padded) then W2^T in four
@@ -30,7 +31,7 @@
 // issuer drains, and the allocating warp frees TMEM.
 #include "tc_common.cuh"
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -89,18 +90,18 @@ struct Params {
     uint32_t idesc;
 };
 
-__device__ __forceinline__ float gelu_tanh(float z)
+// 2 gelu(z) in the tanh form: z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+__device__ __forceinline__ float gelu2_tanh(float z)
 {
-    const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);  // sqrt(2/pi) (z + 0.044715 z^3)
+    const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    const float hz = 0.5f * z;
-    return fmaf(hz, t, hz);
+    return fmaf(z, t, z);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+__device__ __forceinline__ uint32_t pack_f16(float a, float b)
 {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
@@ -137,7 +138,7 @@ __device__ __forceinline__ void pin16(uint32_t *r)
                    "+r"(r[15]));
 }
 
-// Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in BF16, 128-byte swizzled
+// Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in FP16, 128-byte swizzled
 // (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
 __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)
 {
@@ -159,7 +160,7 @@ __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const 
             }
             v[u] = x;
         }
-        w[k / 2] = pack_bf16(v[0], v[1]);
+        w[k / 2] = pack_f16(v[0], v[1]);
     }
     unsigned char *row = xs + r * 128;
 #pragma unroll
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             const int64_t cl = (int64_t)t * BM + row;
             for (int e = 0; e < P.E; ++e, ++k) {
                 const float *aux = aux_s + e * AUX;
-                // ---- layer-1 epilogue: H1 = bf16(gelu(Z1)), K tile by K tile
+                // ---- layer-1 epilogue: H1 = fp16(2 gelu(Z1)), K tile by K tile
                 bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                         uint32_t w[8];
 #pragma unroll
                         for (int j = 0; j < 16; j += 2)
-                            w[j / 2] = pack_bf16(gelu_tanh(__uint_as_float(v[u][j])), gelu_tanh(__uint_as_float(v[u][j + 1])));
+                            w[j / 2] = pack_f16(gelu2_tanh(__uint_as_float(v[u][j])), gelu2_tanh(__uint_as_float(v[u][j + 1])));
                         unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
                         const int j0 = 2 * grp, j1 = 2 * grp + 1;
                         *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -353,10 +354,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                             const float4 b = *reinterpret_cast<const float4 *>(aux + j0 + j);
                             const float4 wa = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
                             const float4 wb = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4);
-                            const float h0 = gelu_tanh(__uint_as_float(v[u][j]) + b.x);
-                            const float h1v = gelu_tanh(__uint_as_float(v[u][j + 1]) + b.y);
-                            const float h2 = gelu_tanh(__uint_as_float(v[u][j + 2]) + b.z);
-                            const float h3 = gelu_tanh(__uint_as_float(v[u][j + 3]) + b.w);
+                            const float h0 = gelu2_tanh(__uint_as_float(v[u][j]) + b.x);
+                            const float h1v = gelu2_tanh(__uint_as_float(v[u][j + 1]) + b.y);
+                            const float h2 = gelu2_tanh(__uint_as_float(v[u][j + 2]) + b.z);
+                            const float h3 = gelu2_tanh(__uint_as_float(v[u][j + 3]) + b.w);
                             o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
                             o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
                         }
@@ -417,12 +418,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
 }
 
 // Pack one network's FP32 parameters (layout W1 [d x H], b1, W2 [H x H], b2, W3 [H x 2], b3)
-// into the kernel's operands: wt = E x 5 chunks of 256 x 64 BF16, K-major
+// into the kernel's operands: wt = E x 5 chunks of 256 x 64 FP16, K-major
 //   chunk 0: row j = [W1[0][j] .. W1[d-1][j], b1[j], 0 ...]
-//   chunk c = 1..4: row j = W2[64(c-1) .. 64c-1][j]
-// and aux = E x 1024 FP32: b2 [256], W3 [256 x 2] (row j = the two outputs), b3 [2], zeros.
+//   chunk c = 1..4: row j = W2[64(c-1) .. 64c-1][j] / 2
+// and aux = E x AUX FP32: b2 [256], W3 [256 x 2] / 2 (row j = the two outputs), b3 [2], zeros.
+// The halves absorb gelu's factor 1/2 (the epilogues produce 2 gelu).
 __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P, int64_t oW1, int64_t ob1,
-                       int64_t oW2, int64_t ob2, int64_t oW3, int64_t ob3, __nv_bfloat16 *__restrict__ wt,
+                       int64_t oW2, int64_t ob2, int64_t oW3, int64_t ob3, __half *__restrict__ wt,
                        float *__restrict__ aux)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -436,8 +438,8 @@ __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P,
         const float *th = theta + e * P;
         float v;
         if (c == 0) v = kk < d ? th[oW1 + (int64_t)kk * HID + j] : (kk == d ? th[ob1 + j] : 0.0f);
-        else v = th[oW2 + (int64_t)(64 * (c - 1) + kk) * HID + j];
-        wt[t] = __float2bfloat16_rn(v);
+        else v = 0.5f * th[oW2 + (int64_t)(64 * (c - 1) + kk) * HID + j];
+        wt[t] = __float2half_rn(v);
     }
     if (t < (int64_t)E * AUX) {
         const int e = (int)(t / AUX);
@@ -445,7 +447,7 @@ __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P,
         const float *th = theta + e * P;
         float v = 0.0f;
         if (i < HID) v = th[ob2 + i];
-        else if (i < 3 * HID) v = th[oW3 + (i - HID)];
+        else if (i < 3 * HID) v = 0.5f * th[oW3 + (i - HID)];
         else if (i < 3 * HID + 2) v = th[ob3 + (i - 3 * HID)];
         aux[t] = v;
     }
@@ -462,7 +464,7 @@ int mlp_tc_pack(gpbo_ctx *ctx, const float *theta, int E, int d, int64_t P, cons
 {
     const int64_t total = std::max<int64_t>((int64_t)E * mtc::CHUNKS * mtc::HID * mtc::KT, (int64_t)E * mtc::AUX);
     mtc::k_pack<<<(unsigned)cdiv64(total, 256), 256, 0, ctx->stream>>>(theta, E, d, P, off[0], off[1], off[2], off[3],
-                                                                       off[4], off[5], (__nv_bfloat16 *)wt, aux);
+                                                                       off[4], off[5], (__half *)wt, aux);
     GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;
 }
@@ -474,7 +476,7 @@ int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, 
         return GPBO_EINVAL;
     if (cdiv64(C, mtc::BM) > 0x7fffffffll) return GPBO_EINVAL;
     CUtensorMap mw;
-    GPBO_TRY(encode_2d(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, wt, (uint64_t)E * mtc::CHUNKS * mtc::HID, mtc::KT,
+    GPBO_TRY(encode_2d(&mw, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, wt, (uint64_t)E * mtc::CHUNKS * mtc::HID, mtc::KT,
                        mtc::HID));
     mtc::Params P;
     P.C = C;
@@ -496,7 +498,7 @@ int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, 
     P.mu = mu;
     P.sigma = sigma;
     P.status = ctx->dev_status;
-    P.idesc = tcx::idesc_f16(1u, mtc::HID, mtc::BM);
+    P.idesc = tcx::idesc_f16(0u, mtc::HID, mtc::BM);  // FP16 A and B
     const size_t smem = mtc::smem_bytes();
     GPBO_CUDA_TRY(cudaFuncSetAttribute(mtc::k_mlp_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::min(P.num_tiles, ctx->sm_count);

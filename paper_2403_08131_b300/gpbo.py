@@ -399,9 +399,9 @@ class Surrogate:
         check(_mlp_norm(self._h, v.ctypes.data_as(_D)), "mlp_norm")
         return v
 
-    def score(self, ei, X=None, M=None, seed=0, y_best=0.0, xi=0.0, prec="bf16", mu=None, sigma=None):
+    def score(self, ei, X=None, M=None, seed=0, y_best=0.0, xi=0.0, prec="f16", mu=None, sigma=None):
         """Ensemble (EI, mu_bar, sigma_bar) of rows of X (device) or of M seeded candidates.
-        prec "bf16": tensor-core kernel; "f32": CUDA-core forward."""
+        prec "f16": tensor-core kernel (FP16 operands); "f32": CUDA-core forward."""
         if X is not None:
             M = X.shape[0]
         check(_mlp_score(self.ctx._h, self._h, _ptr(X), int(M), int(seed), float(y_best), float(xi), PREC[prec],

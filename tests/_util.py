@@ -38,8 +38,8 @@ def to_dev(a, dtype=None):
     return t.cuda()
 
 
-# ---------------------------------------------------------------- BF16 ensemble forward tolerance
-U_BF16 = 2.0 ** -8  # unit roundoff of BF16 (8-bit significand)
+# ---------------------------------------------------------------- FP16 ensemble forward tolerance
+U_F16 = 2.0 ** -11  # unit roundoff of FP16 (11-bit significand)
 
 
 def _gelu(z):
@@ -56,40 +56,41 @@ def _gelu_tanh(z):
     return 0.5 * z * (1 + np.tanh(np.sqrt(2 / np.pi) * (z + 0.044715 * z ** 3)))
 
 
-def bf16_round(a):
-    """Round to the nearest BF16 value (ties to even), returned as float64."""
-    b = np.ascontiguousarray(np.asarray(a, dtype=np.float32)).view(np.uint32).astype(np.uint64)
-    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
-    return b.view(np.float32).astype(np.float64)
+def f16_round(a):
+    """Round to FP32, then to the nearest FP16 value (ties to even), as the kernel's FP32 ->
+    FP16 conversions do; returned as float64."""
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float16).astype(np.float64)
 
 
-def bf16_ensemble_tol(orc, thetas, X, d, H, nm, tau, lam=6.0):
-    """Tolerances (mu_bar, sigma_bar, ei) of the BF16 tensor-core ensemble against the FP64
+def f16_ensemble_tol(orc, thetas, X, d, H, nm, tau, lam=6.0):
+    """Tolerances (mu_bar, sigma_bar, ei) of the FP16 tensor-core ensemble against the FP64
     oracle, per candidate, derived from the kernel's arithmetic in two parts.
-    (1) Deterministic: x, W1, b1, W2 and H1 rounded to BF16 and the tanh-form GELU.  A
-        float64 emulation with exactly these roundings gives |emulation - oracle|.
-    (2) What the emulation cannot reproduce: tanh.approx's relative error (2^-11) on each
-        tanh, the FP32 accumulation, and the H1 roundings that this moves across a BF16
-        rounding boundary (one ulp, 2u|h1|, with probability about delta / (2u|h1|), so
-        expected square delta * 2u|h1|).  These are independent per element, so they are
-        propagated as a root sum of squares through the next layer's weights (the sqrt(n)
-        growth of Higham & Mary, SIAM J. Sci. Comput. 2019); lam is the number of standard
-        deviations allowed."""
+    (1) Deterministic: x, W1, b1, W2 (halved, exactly) and H1 rounded to FP16, GELU in the
+        tanh form.  A float64 emulation with exactly these roundings gives
+        |emulation - oracle|.
+    (2) What the emulation cannot reproduce: tanh.approx.f32's relative error (2^-11) on
+        each tanh, the FP32 accumulation, and the H1 roundings that this moves across an
+        FP16 rounding boundary (one ulp, 2u|h1|, with probability about delta / (2u|h1|), so
+        expected square delta * 2u|h1|).  These vary in sign from element to
+        element, so they are propagated as a root sum of squares through the next layer's
+        weights (the sqrt(n) growth of Higham & Mary, SIAM J. Sci. Comput. 2019); lam is the
+        number of standard deviations allowed."""
     from scipy.stats import norm
-    u = U_BF16
+    u = U_F16
     X = np.asarray(X, dtype=np.float64)
-    Xq = bf16_round(X)
+    Xq = f16_round(X)
     mus, emus, dmus, ss, ess, dss = [], [], [], [], [], []
     for th in np.asarray(thetas, dtype=np.float64):
         W1, b1, W2, b2, W3, b3 = [p.reshape(s) for p, (_, s) in zip(orc.mlp_split(th, d, H), orc.mlp_sizes(d, H))]
         # reference (exact GELU, FP64) and emulation of the kernel's roundings
         o = _gelu(_gelu(X @ W1 + b1) @ W2 + b2) @ W3 + b3
-        z1 = Xq @ bf16_round(W1) + bf16_round(b1)
-        h1 = bf16_round(_gelu_tanh(z1))
-        z2 = h1 @ bf16_round(W2) + b2
+        z1 = Xq @ f16_round(W1) + f16_round(b1)
+        h1 = f16_round(_gelu_tanh(z1))           # the kernel stores fp16(2 gelu) = 2 fp16(gelu)
+        z2 = h1 @ (2.0 * f16_round(0.5 * W2)) + b2
         h2 = _gelu_tanh(z2)
         oe = h2 @ W3 + b3
-        # residual, per element
+        # residual, per element: tanh.approx.f32 (2^-11 relative, times |z|/2) and the FP32
+        # accumulation of z1
         t1 = np.abs(z1) * 2.0 ** -12 + 1e-7 * (np.abs(Xq) @ np.abs(W1) + 1)
         dh1 = np.sqrt(t1 ** 2 + t1 * 2 * u * np.abs(h1))
         dz2 = np.sqrt((dh1 ** 2) @ (W2 ** 2)) + 1e-7 * (np.abs(h1) @ np.abs(W2) + 1)

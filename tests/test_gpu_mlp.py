@@ -129,13 +129,13 @@ def _rand_biases(net, d, H, seed):
 
 
 def _check_tc(orc, th, X, ei, mu, sg, nm, tau, d, H):
-    """Tensor-core (mu_bar, sigma_bar, EI) against the FP64 oracle within the BF16 tolerance;
+    """Tensor-core (mu_bar, sigma_bar, EI) against the FP64 oracle within the FP16 tolerance;
     returns the worst error / tolerance of each."""
-    from tests._util import bf16_ensemble_tol
+    from tests._util import f16_ensemble_tol
     th = np.asarray(th, dtype=np.float64)
     X = np.asarray(X, dtype=np.float64)
     rm, rs, re = orc.mlp_ensemble(th, X, d, H, nm, tau)
-    tm, ts, te = bf16_ensemble_tol(orc, th, X, d, H, nm, tau)
+    tm, ts, te = f16_ensemble_tol(orc, th, X, d, H, nm, tau)
     gm, gs, ge = (a.cpu().numpy().astype(np.float64) for a in (mu, sg, ei))
     r = (np.max(np.abs(gm - rm) / tm), np.max(np.abs(gs - rs) / ts), np.max(np.abs(ge - re) / te))
     assert max(r) <= 1.0, f"worst error / tolerance (mu_bar, sigma_bar, ei) = {r}"
@@ -143,20 +143,20 @@ def _check_tc(orc, th, X, ei, mu, sg, nm, tau, d, H):
 
 
 @pytest.mark.parametrize("M", [1, 127, 129, 1000])
-def test_tc_forward_matches_oracle_within_bf16_tolerance(ctx, orc, M):
+def test_tc_forward_matches_oracle_within_f16_tolerance(ctx, orc, M):
     """Random-init ensemble (E = 3, random biases) on M explicit rows: the tensor-core
-    mu_bar, sigma_bar and EI against the FP64 oracle within the BF16 tolerance; the FP32
+    mu_bar, sigma_bar and EI against the FP64 oracle within the FP16 tolerance; the FP32
     path within 1e-4 of it."""
     import torch
     d, H = 20, 256
     net = _net(ctx, 3, d, H, seed=11)
     th = _rand_biases(net, d, H, 12)
     X = np.random.default_rng(M).random((M, d)).astype(np.float32)
-    outs = {p: [torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3)] for p in ("bf16", "f32")}
+    outs = {p: [torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3)] for p in ("f16", "f32")}
     for p, (ei, mu, sg) in outs.items():
         net.score(ei, X=to_dev(X), y_best=0.1, prec=p, mu=mu, sigma=sg)
     rm, rs, _ = orc.mlp_ensemble(th.astype(np.float64), X.astype(np.float64), d, H, (0, 1, 0, 1), 0.1)
-    r = _check_tc(orc, th, X, *outs["bf16"], (0.0, 1.0, 0.0, 1.0), 0.1, d, H)
+    r = _check_tc(orc, th, X, *outs["f16"], (0.0, 1.0, 0.0, 1.0), 0.1, d, H)
     print(f"M={M}: worst error / tolerance (mu_bar, sigma_bar, ei) = {r[0]:.3f}, {r[1]:.3f}, {r[2]:.3f}")
     fm, fs = outs["f32"][1].cpu().numpy(), outs["f32"][2].cpu().numpy()
     assert np.max(np.abs(fm - rm) / (np.abs(rm) + 1)) <= 1e-4 and np.max(np.abs(fs - rs) / rs) <= 1e-4
@@ -164,7 +164,7 @@ def test_tc_forward_matches_oracle_within_bf16_tolerance(ctx, orc, M):
 
 def test_tc_trained_ensemble_seeded_equals_explicit(ctx, orc, trained):
     """Trained 8-member ensemble: seeded candidates equal the same rows passed explicitly
-    (bit for bit), and both agree with the oracle within the BF16 tolerance."""
+    (bit for bit), and both agree with the oracle within the FP16 tolerance."""
     import torch
     w, ys, model, net, _, _ = trained
     d, H, M, seed = 20, 256, 777, 31
@@ -205,6 +205,10 @@ def test_tc_rejects_unsupported_shapes(ctx):
     net = _net(ctx, 2, 20, 128)
     ei = torch.empty(10, dtype=torch.float32, device="cuda")
     with pytest.raises(gpbo.GpboError) as e:
-        net.score(ei, M=10, seed=1, prec="bf16")
+        net.score(ei, M=10, seed=1, prec="f16")
     assert e.value.code == gpbo.GPBO_ENOTSUP
     net.score(ei, M=10, seed=1, prec="f32")
+    net2 = _net(ctx, 2, 20, 256)
+    with pytest.raises(gpbo.GpboError) as e:   # the tensor-core forward has FP16 operands only
+        net2.score(ei, M=10, seed=1, prec="bf16")
+    assert e.value.code == gpbo.GPBO_ENOTSUP

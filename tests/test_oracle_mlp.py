@@ -81,12 +81,12 @@ def test_ensemble_two_members_mixture_variance(orc):
     assert np.allclose(sg ** 2, (sa ** 2 + sb ** 2) / 2 + ((ma - mb) / 2) ** 2, rtol=1e-12)
 
 
-def test_bf16_tolerance_detects_planted_mistakes(orc):
-    """The tolerance the GPU parity tests use for the BF16 ensemble is tight enough to fail
+def test_f16_tolerance_detects_planted_mistakes(orc):
+    """The tolerance the GPU parity tests use for the FP16 ensemble is tight enough to fail
     plausible kernel mistakes: each is planted in the oracle's parameters (W2 used
     transposed, b1 dropped, the two output columns of W3 swapped, one member left out) and
     must move mu_bar or sigma_bar beyond the tolerance for most candidates."""
-    from tests._util import bf16_ensemble_tol
+    from tests._util import f16_ensemble_tol
     d, H, E, B = 20, 256, 3, 200
     rng = np.random.default_rng(9)
     th = []
@@ -99,7 +99,7 @@ def test_bf16_tolerance_detects_planted_mistakes(orc):
     X = rng.random((B, d))
     nm, tau = (0.1, 1.3, -0.5, 0.7), 0.0
     rm, rs, _ = orc.mlp_ensemble(th, X, d, H, nm, tau)
-    tm, ts, _ = bf16_ensemble_tol(orc, th, X, d, H, nm, tau)
+    tm, ts, _ = f16_ensemble_tol(orc, th, X, d, H, nm, tau)
     oW2, ob1, oW3 = d * H + H, d * H, d * H + H + H * H + H
 
     def mutate(f):
@@ -125,11 +125,11 @@ def test_bf16_tolerance_detects_planted_mistakes(orc):
         assert caught.mean() > 0.9, f"{name}: only {caught.mean():.2f} of candidates outside the tolerance"
 
 
-def test_bf16_round_matches_torch():
-    """The tolerance's BF16 emulation rounds like torch's CPU float32 -> bfloat16 cast."""
+def test_f16_round_matches_torch():
+    """The tolerance's FP16 emulation rounds FP32 values like torch's CPU float32 -> float16 cast."""
     import torch
-    from tests._util import bf16_round
-    x = np.random.default_rng(10).normal(0, 3, 100000)
-    x[:4] = [1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -0.0, 65504.0]
-    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
-    assert np.array_equal(bf16_round(x), ref)
+    from tests._util import f16_round
+    x = np.random.default_rng(10).normal(0, 3, 100000).astype(np.float32)
+    x[:5] = [1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, -0.0, 65504.0, 2 ** -20]
+    ref = torch.from_numpy(x).to(torch.float16).to(torch.float64).numpy()
+    assert np.array_equal(f16_round(x), ref)

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // the compensated form runs the K loop twice: hi operand, then lo
                     for (int ks2 = 0; ks2 < ksteps * (1 + P.split); ++ks2) {
                         const int ks = ks2 < ksteps ? ks2 : ks2 - ksteps;
-                        if (!mbar_wait(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                         unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                         unsigned char *b = a + A_BYTES;
                         mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
@@ -166,12 +166,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
                 for (int q = 0; ok && q < nq; ++q) {
-                    if (!mbar_wait(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (!mbar_wait_fast(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
                     const int ksteps = (q + 1) * (BN / BK) * (1 + P.split);
                     for (int ks = 0; ks < ksteps; ++ks) {
-                        if (!mbar_wait(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                         const unsigned char *b = a + A_BYTES;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             float ss = 0.0f;
             for (int q = 0; q < nq; ++q) {
                 // every lane waits; the warp leaves together so tcgen05.ld stays warp-uniform
-                const bool got = mbar_wait(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
+                const bool got = mbar_wait_inl(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1

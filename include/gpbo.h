@@ -268,14 +268,14 @@ int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const doub
                         const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
                         gpbo_prec prec, unsigned flags, double *x_next, double *ei_max, int64_t *argmax);
 
-/* Variance tile of the batched step (candidates per CTA of its FP32 variance kernel: 32,
- * 64 or 128), or 0 (the default) for the autotuner: when a call meets a new set of shapes it
+/* Variance tile of the batched step (candidates per CTA of its FP32 variance kernel: 64,
+ * 128 or 256), or 0 (the default) for the autotuner: when a call meets a new set of shapes it
  * times each tile on the plan's own buffers (one warm-up and three launches each) and
  * captures the fastest into the graph.  The tile changes no result: every candidate's sums
  * run in the same order.  Takes effect at the next search_step_batched call. */
 int search_step_batched_tile(gpbo_ctx *ctx, int tile);
-/* The current plan's tile and the autotuner's mean time per launch (ms) of the 32, 64 and
- * 128 tiles (negative when not measured).  GPBO_EINVAL before the first batched call. */
+/* The current plan's tile and the autotuner's mean time per launch (ms) of the 64, 128 and
+ * 256 tiles (negative when not measured).  GPBO_EINVAL before the first batched call. */
 int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3);
 
 /* ------------------------------------------------------------------ learned pre-screen

@@ -53,8 +53,8 @@ struct BatchPlan {
     int64_t max_M = 0;
     int64_t max_sq = 0, max_dn = 0;
     int tile_req = 0;    // requested variance tile (0: autotune)
-    int var_bm = 64;     // variance tile in use: candidates per CTA
-    float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 32, 64, 128
+    int var_bm = 128;    // variance tile in use: candidates per CTA
+    float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 64, 128, 256
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -214,9 +214,8 @@ __global__ void __launch_bounds__(256) b_var(const BProb *P, const float *Kst, c
 {
     const BProb &p = P[blockIdx.y];
     if ((int64_t)blockIdx.x * BM >= p.M) return;
-    k_var_simt_body<float, BM>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
-                               tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0,
-                               blockIdx.x, 0, 0);
+    k_var_f32_body<BM>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
+                       tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(1024) b_argmax(const BProb *P, const float *pei, const int64_t *pidx, double *best_ei,
@@ -282,7 +281,7 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
         p.off_kst = skst; skst += p.M * p.n_pad;
         p.off_mu = smu;   smu += p.M;
         p.part_count = (int)cdiv64(p.M, 64);
-        p.off_part = spart; spart += cdiv64(p.M, 32);  // room for the smallest variance tile
+        p.off_part = spart; spart += cdiv64(p.M, 64);  // room for the smallest variance tile
         pl->max_npad = std::max(pl->max_npad, p.n_pad);
         pl->max_nblk = std::max(pl->max_nblk, p.nblk);
         pl->max_tiles64 = std::max<int>(pl->max_tiles64, (int)cdiv64(p.M, 64));
@@ -362,9 +361,9 @@ static int launch_var_bm(BatchPlan *pl, cudaStream_t st, float xi, int bm)
 {
     const dim3 grid((unsigned)cdiv64(pl->max_M, bm), pl->G);
     const BProb *P = pl->probs_dev;
-    if (bm == 32) b_var<32><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
-    else if (bm == 128) b_var<128><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
-    else b_var<64><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    if (bm == 64) b_var<64><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    else if (bm == 256) b_var<256><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
+    else b_var<128><<<grid, 256, 0, st>>>(P, pl->Kst, pl->Linv32, pl->mu, pl->tau, xi, pl->pei, pl->pidx);
     GPBO_CUDA_TRY(cudaGetLastError());
     return GPBO_OK;
 }
@@ -383,7 +382,7 @@ static void set_tile(BatchPlan *pl, int bm)
 // depend on the values, only on the shapes, which are the plan's.
 static int autotune(BatchPlan *pl)
 {
-    static const int tiles[3] = {32, 64, 128};
+    static const int tiles[3] = {64, 128, 256};
     GPBO_CUDA_TRY(cudaMemsetAsync(pl->Kst, 0, sizeof(float) * (size_t)(pl->probs.back().off_kst +
                                   pl->probs.back().M * (int64_t)pl->probs.back().n_pad), pl->cap));
     GPBO_CUDA_TRY(cudaMemsetAsync(pl->Linv32, 0, sizeof(float) * (size_t)(pl->probs.back().off_sq +
@@ -394,7 +393,7 @@ static int autotune(BatchPlan *pl)
     cudaEvent_t a = nullptr, b = nullptr;
     GPBO_CUDA_TRY(cudaEventCreate(&a));
     GPBO_CUDA_TRY(cudaEventCreate(&b));
-    int best = 64;
+    int best = 128;
     float best_ms = 1e30f;
     int rc = GPBO_OK;
     for (int i = 0; i < 3 && rc == GPBO_OK; ++i) {
@@ -598,7 +597,7 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
 
 extern "C" int search_step_batched_tile(gpbo_ctx *ctx, int tile)
 {
-    if (!ctx || !(tile == 0 || tile == 32 || tile == 64 || tile == 128)) return GPBO_EINVAL;
+    if (!ctx || !(tile == 0 || tile == 64 || tile == 128 || tile == 256)) return GPBO_EINVAL;
     ctx->batch_tile = tile;
     return GPBO_OK;
 }

@@ -56,6 +56,11 @@ __global__ void __launch_bounds__(256) k_xkern32(const float *__restrict__ Xc, u
     k_xkern32_body<Out>(Xc, seed, c0, C, d, Xs, alpha, n, n_pad, s2, ls, Kst, mu, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
+// Candidates per CTA of the variance kernel: FP32 uses the 128-candidate tile of
+// k_var_f32_body, FP64 the 64-candidate k_var_simt_body.
+constexpr int VAR_BM32 = 128;
+template <typename T> constexpr int var_bm() { return sizeof(T) == 4 ? VAR_BM32 : 64; }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_var_simt(const T *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
                                                   const T *__restrict__ Linv, const T *__restrict__ mu, T s2,
@@ -64,7 +69,12 @@ __global__ void __launch_bounds__(256) k_var_simt(const T *__restrict__ Kst, int
                                                   T *__restrict__ part_ei, int64_t *__restrict__ part_idx,
                                                   int part_base)
 {
-    k_var_simt_body<T>(Kst, C, c0, n_pad, Linv, mu, s2, y_best, tau_dev, xi, sigma_out, ei_out, part_ei, part_idx, part_base, blockIdx.x, blockIdx.y, gridDim.x);
+    if constexpr (sizeof(T) == 4)
+        k_var_f32_body<VAR_BM32>(Kst, C, c0, n_pad, Linv, mu, s2, y_best, tau_dev, xi, sigma_out, ei_out, part_ei,
+                                 part_idx, part_base, blockIdx.x);
+    else
+        k_var_simt_body<T>(Kst, C, c0, n_pad, Linv, mu, s2, y_best, tau_dev, xi, sigma_out, ei_out, part_ei, part_idx,
+                           part_base, blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 template <typename T>
@@ -135,7 +145,7 @@ static int score_simt(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t
         GPBO_TRY(trace_begin(ctx, PH_XKERN, (double)Cc * (3.0 * nn * m->d + 2.0 * nn)));
         GPBO_TRY((launch_xkern<T, T>(ctx, m, Xc, seed, c0, Cc, Xs, alpha, Kst, mu)));
         GPBO_TRY(trace_end(ctx));
-        const unsigned g = (unsigned)cdiv64(Cc, 64);
+        const unsigned g = (unsigned)cdiv64(Cc, var_bm<T>());
         GPBO_TRY(trace_begin(ctx, PH_VAR, (double)Cc * nn * (nn + 1.0)));
         k_var_simt<T><<<g, 256, 0, ctx->stream>>>(Kst, Cc, c0, n_pad, Linv, mu, (T)m->s2, y_best, tau_dev, (T)xi,
                                                   sigma_out, ei_out, pei, pidx, part);
@@ -326,7 +336,7 @@ static int score_noalloc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int6
         // the kernels index mu by pool position; the chunk buffer stands in for [c0, c0 + Cc)
         T *mu = mu_out ? mu_out : mu_chunk - c0;
         GPBO_TRY((launch_xkern<T, T>(ctx, m, Xc, seed, c0, Cc, Xs, alpha, Kst, mu)));
-        const unsigned g = (unsigned)cdiv64(Cc, 64);
+        const unsigned g = (unsigned)cdiv64(Cc, var_bm<T>());
         k_var_simt<T><<<g, 256, 0, ctx->stream>>>(Kst, Cc, c0, n_pad, Linv, mu, (T)m->s2, y_best, nullptr, (T)xi,
                                                   sigma_out, ei_out, pei, pidx, 0);
         GPBO_LAUNCH_CHECK(ctx);

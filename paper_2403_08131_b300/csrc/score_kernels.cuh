@@ -295,6 +295,136 @@ __device__ __forceinline__ void k_var_simt_body(const T *__restrict__ Kst, int64
     }
 }
 
+// FP32 variance, EI and per-CTA argmax on CUDA cores, BM = 64, 128 or 256 candidates per CTA.
+// Thread (ty, tx) of 16 x 16 owns candidates ty*TM .. ty*TM+TM-1 (TM = BM/16) and, in each
+// 64-row output chunk of L^-1, rows tx*4 .. tx*4+3, so its shared-memory reads are 128-bit;
+// K steps of 16 through transposed shared tiles, with the next step's global loads held in
+// registers while the current one is multiplied.  Every candidate's sums run in the same order
+// for every BM, so the tile changes no result.
+template <int BM>
+__device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
+                                               const float *__restrict__ Linv, const float *__restrict__ mu, float s2,
+                                               double y_best, const double *__restrict__ tau_dev, float xi,
+                                               float *__restrict__ sigma_out, float *__restrict__ ei_out,
+                                               float *__restrict__ part_ei, int64_t *__restrict__ part_idx,
+                                               int part_base, const int bx)
+{
+    static_assert(BM == 64 || BM == 128 || BM == 256, "tile");
+    constexpr int BN = 64, BK = 16, TM = BM / 16, PAD = 4;
+    constexpr int AE = BM * BK / 256;  // K* elements each thread loads per K step
+    constexpr int AQ = AE / 4;         // ... as float4s
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
+    __shared__ float red_v[BM];
+    __shared__ int64_t red_i[BM];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int64_t cb = bx * (int64_t)BM;
+    const int ra = tid / (BK / AE), ka = (tid % (BK / AE)) * AE;  // K* loader: candidate, first k
+    const int rb = tid / 4, kb = (tid % 4) * 4;                    // L^-1 loader: row, first k
+    const bool a_ok = cb + ra < C;
+    const float *arow = Kst + (cb + ra) * n_pad + ka;
+    float4 pa[AQ], pb;
+    auto fetch = [&](int k0, int i0) {
+#pragma unroll
+        for (int q = 0; q < AQ; ++q)
+            pa[q] = a_ok ? *reinterpret_cast<const float4 *>(arow + k0 + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        pb = *reinterpret_cast<const float4 *>(Linv + (int64_t)(i0 + rb) * n_pad + k0 + kb);
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < AQ; ++q) {
+            As[buf][ka + 4 * q + 0][ra] = pa[q].x;
+            As[buf][ka + 4 * q + 1][ra] = pa[q].y;
+            As[buf][ka + 4 * q + 2][ra] = pa[q].z;
+            As[buf][ka + 4 * q + 3][ra] = pa[q].w;
+        }
+        Bs[buf][kb + 0][rb] = pb.x;
+        Bs[buf][kb + 1][rb] = pb.y;
+        Bs[buf][kb + 2][rb] = pb.z;
+        Bs[buf][kb + 3][rb] = pb.w;
+    };
+    float sig2[TM];
+#pragma unroll
+    for (int u = 0; u < TM; ++u) sig2[u] = 0.f;
+    int buf = 0;
+    for (int i0 = 0; i0 < n_pad; i0 += BN) {
+        float acc[TM][4];
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        const int kend = i0 + BN;
+        fetch(0, i0);
+        stash(buf);
+        __syncthreads();
+        for (int k0 = 0; k0 < kend; k0 += BK) {
+            const bool more = k0 + BK < kend;
+            if (more) fetch(k0 + BK, i0);
+#pragma unroll
+            for (int t = 0; t < BK; ++t) {
+                float a[TM];
+#pragma unroll
+                for (int q = 0; q < TM / 4; ++q) {
+                    const float4 f = *reinterpret_cast<const float4 *>(&As[buf][t][ty * TM + 4 * q]);
+                    a[4 * q] = f.x;
+                    a[4 * q + 1] = f.y;
+                    a[4 * q + 2] = f.z;
+                    a[4 * q + 3] = f.w;
+                }
+                const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][t][tx * 4]);
+#pragma unroll
+                for (int u = 0; u < TM; ++u) {
+                    acc[u][0] = fmaf(a[u], b.x, acc[u][0]);
+                    acc[u][1] = fmaf(a[u], b.y, acc[u][1]);
+                    acc[u][2] = fmaf(a[u], b.z, acc[u][2]);
+                    acc[u][3] = fmaf(a[u], b.w, acc[u][3]);
+                }
+            }
+            if (more) stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sig2[u] = fmaf(acc[u][v], acc[u][v], sig2[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+        for (int o = 1; o < 16; o <<= 1) sig2[u] += __shfl_xor_sync(0xffffffffu, sig2[u], o);
+    const float tau = tau_dev ? (float)*tau_dev : (float)y_best;
+    if (tx == 0) {
+#pragma unroll
+        for (int u = 0; u < TM; ++u) {
+            const int r = ty * TM + u;
+            const int64_t cl = cb + r, c = c0 + cl;
+            float e = -1.0f;
+            if (cl < C) {
+                const float var = s2 - sig2[u];
+                const float sg = var > 0.0f ? sqrtf(var) : 0.0f;
+                e = ei_minf(mu[c], sg, tau, xi);
+                if (sigma_out) sigma_out[c] = sg;
+                if (ei_out) ei_out[c] = e;
+            }
+            red_v[r] = e;
+            red_i[r] = cl < C ? c : INT64_MAX;
+        }
+    }
+    __syncthreads();
+    for (int s = BM / 2; s; s >>= 1) {
+        for (int i = tid; i < s; i += blockDim.x)
+            if (better(red_v[i + s], red_i[i + s], red_v[i], red_i[i])) {
+                red_v[i] = red_v[i + s];
+                red_i[i] = red_i[i + s];
+            }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        part_ei[part_base + bx] = red_v[0];
+        part_idx[part_base + bx] = red_i[0];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void k_argmax_final_body(const T *__restrict__ part_ei, const int64_t *__restrict__ part_idx,
                                                        int np, double *__restrict__ out_ei, int64_t *__restrict__ out_idx, const int bx, const int by, const int gx)

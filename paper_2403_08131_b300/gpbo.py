@@ -295,7 +295,7 @@ class Context:
         return {"x_next": [x_next[g, :ds[g]] for g in range(G)], "ei_max": ei_max, "argmax": am}
 
     def batched_tile(self, tile=0):
-        """Variance tile of the batched step (32, 64, 128), or 0 for the autotuner."""
+        """Variance tile of the batched step (64, 128, 256), or 0 for the autotuner."""
         check(_batched_tile(self._h, int(tile)), "search_step_batched_tile")
 
     def batched_tuning(self):
@@ -303,7 +303,7 @@ class Context:
         t = C.c_int(0)
         ms = (C.c_float * 3)()
         check(_batched_tuning(self._h, C.byref(t), ms), "search_step_batched_tuning")
-        return t.value, {k: float(v) for k, v in zip((32, 64, 128), ms) if v >= 0}
+        return t.value, {k: float(v) for k, v in zip((64, 128, 256), ms) if v >= 0}
 
     # ------------------------------------------------------------ screen
     def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,

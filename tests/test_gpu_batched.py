@@ -47,17 +47,17 @@ def test_batched_shapes_are_uneven(ctx):
 
 
 def test_autotuned_tile_is_the_fastest_measured_and_tiles_agree(ctx):
-    """The autotuner times the 32/64/128-candidate variance tiles on the plan and keeps the
+    """The autotuner times the 64/128/256-candidate variance tiles on the plan and keeps the
     fastest; every forced tile gives the same results bit for bit (each candidate's sums run
     in the same order)."""
     subs, probs = _problems(seed_shift=3)
     ctx.batched_tile(0)
     auto = ctx.search_step_batched(probs)
     tile, ms = ctx.batched_tuning()
-    assert set(ms) == {32, 64, 128} and all(v > 0 for v in ms.values())
+    assert set(ms) == {64, 128, 256} and all(v > 0 for v in ms.values())
     assert tile == min(ms, key=ms.get)
     print(f"autotuner: {ms} -> {tile}")
-    for t in (32, 64, 128):
+    for t in (64, 128, 256):
         ctx.batched_tile(t)
         out = ctx.search_step_batched(probs)
         assert ctx.batched_tuning()[0] == t

@@ -83,6 +83,11 @@ __global__ void k_init(float *theta, int E, int d, int H, int64_t P, uint64_t se
 
 // C[e] = epi( op(A[e]) op(B[e]) + bias[e] ), all row-major; op transposes when the flag is set.
 // epi: 0 store C; 1 store Z = C + bias and H = gelu(Z) (Z may be null); 2 store C * gelu'(Zref).
+// 64 x 64 CTA tile, K steps of 16; thread (ty, tx) owns the contiguous 4 x 4 block at rows
+// 4 ty, columns 4 tx, read from transposed shared tiles 128 bits at a time; the next K step's
+// global loads (128-bit where the operand is contiguous along the loaded dimension and in
+// range) are held in registers while the current one is multiplied.  Each output sums over k
+// in order, for any M, N, K.
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(const float *__restrict__ A, int64_t sA, int lda,
                                               const float *__restrict__ B, int64_t sB, int ldb, float *__restrict__ C,
@@ -90,9 +95,9 @@ __global__ void __launch_bounds__(256) k_gemm(const float *__restrict__ A, int64
                                               float *__restrict__ H, const float *__restrict__ Zref, int M, int N, int K,
                                               int epi)
 {
-    constexpr int BM = 64, BN = 64, BK = 16;
-    __shared__ float As[BK][BM + 1];
-    __shared__ float Bs[BK][BN + 1];
+    constexpr int BM = 64, BN = 64, BK = 16, PAD = 4;
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     const int e = blockIdx.z;
     A += e * sA;
     B += e * sB;
@@ -102,40 +107,101 @@ __global__ void __launch_bounds__(256) k_gemm(const float *__restrict__ A, int64
     if (bias) bias += e * sbias;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const bool va = ((uintptr_t)A % 16 == 0) && (lda % 4 == 0);
+    const bool vb = ((uintptr_t)B % 16 == 0) && (ldb % 4 == 0);
+    // loader roles: a quad of 4 consecutive elements along the operand's contiguous dimension
+    //   A (M x K):  !TA -> row m = tid/4, k = 4 (tid%4);  TA -> k = tid/16, m = 4 (tid%16)
+    //   B (K x N):  !TB -> k = tid/16, n = 4 (tid%16);    TB -> n = tid/4, k = 4 (tid%4)
+    const int am = TA ? 4 * (tid % 16) : tid / 4, ak = TA ? tid / 16 : 4 * (tid % 4);
+    const int bk = TB ? 4 * (tid % 4) : tid / 16, bn = TB ? tid / 4 : 4 * (tid % 16);
+    float pa[4], pb[4];
+    auto fetch = [&](int k0) {
+        if (!TA) {
+            const int gr = m0 + am, gc = k0 + ak;
+            const float *src = A + (int64_t)gr * lda + gc;
+            if (va && gr < M && gc + 3 < K) {
+                const float4 f = *reinterpret_cast<const float4 *>(src);
+                pa[0] = f.x; pa[1] = f.y; pa[2] = f.z; pa[3] = f.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pa[q] = (gr < M && gc + q < K) ? src[q] : 0.f;
+            }
+        } else {
+            const int gk = k0 + ak, gm = m0 + am;
+            const float *src = A + (int64_t)gk * lda + gm;
+            if (va && gk < K && gm + 3 < M) {
+                const float4 f = *reinterpret_cast<const float4 *>(src);
+                pa[0] = f.x; pa[1] = f.y; pa[2] = f.z; pa[3] = f.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pa[q] = (gk < K && gm + q < M) ? src[q] : 0.f;
+            }
+        }
+        if (!TB) {
+            const int gk = k0 + bk, gn = n0 + bn;
+            const float *src = B + (int64_t)gk * ldb + gn;
+            if (vb && gk < K && gn + 3 < N) {
+                const float4 f = *reinterpret_cast<const float4 *>(src);
+                pb[0] = f.x; pb[1] = f.y; pb[2] = f.z; pb[3] = f.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pb[q] = (gk < K && gn + q < N) ? src[q] : 0.f;
+            }
+        } else {
+            const int gn = n0 + bn, gk = k0 + bk;
+            const float *src = B + (int64_t)gn * ldb + gk;
+            if (vb && gn < N && gk + 3 < K) {
+                const float4 f = *reinterpret_cast<const float4 *>(src);
+                pb[0] = f.x; pb[1] = f.y; pb[2] = f.z; pb[3] = f.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pb[q] = (gn < N && gk + q < K) ? src[q] : 0.f;
+            }
+        }
+    };
+    auto stash = [&](int buf) {
+        if (!TA) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) As[buf][ak + q][am] = pa[q];
+        } else {
+            *reinterpret_cast<float4 *>(&As[buf][ak][am]) = make_float4(pa[0], pa[1], pa[2], pa[3]);
+        }
+        if (!TB) {
+            *reinterpret_cast<float4 *>(&Bs[buf][bk][bn]) = make_float4(pb[0], pb[1], pb[2], pb[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Bs[buf][bk + q][bn] = pb[q];
+        }
+    };
     float acc[4][4] = {};
+    int buf = 0;
+    if (K > 0) {
+        fetch(0);
+        stash(0);
+    }
+    __syncthreads();
     for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int q = tid; q < BM * BK; q += 256) {
-            const int r = TA ? q % BM : q / BK, c = TA ? q / BM : q % BK;
-            const int gr = m0 + r, gc = k0 + c;
-            float v = 0.f;
-            if (gr < M && gc < K) v = TA ? A[(int64_t)gc * lda + gr] : A[(int64_t)gr * lda + gc];
-            As[c][r] = v;
-        }
-        for (int q = tid; q < BK * BN; q += 256) {
-            const int r = TB ? q % BK : q / BN, c = TB ? q / BK : q % BN;
-            const int gr = k0 + r, gc = n0 + c;
-            float v = 0.f;
-            if (gr < K && gc < N) v = TB ? B[(int64_t)gc * ldb + gr] : B[(int64_t)gr * ldb + gc];
-            Bs[r][c] = v;
-        }
-        __syncthreads();
+        const bool more = k0 + BK < K;
+        if (more) fetch(k0 + BK);
 #pragma unroll
         for (int t = 0; t < BK; ++t) {
-            float x[4], y[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { x[u] = As[t][ty + 16 * u]; y[u] = Bs[t][tx + 16 * u]; }
+            const float4 x = *reinterpret_cast<const float4 *>(&As[buf][t][ty * 4]);
+            const float4 y = *reinterpret_cast<const float4 *>(&Bs[buf][t][tx * 4]);
+            const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(x[u], y[w], acc[u][w]);
+                for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(xa[u], ya[w], acc[u][w]);
         }
+        if (more) stash(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const int gr = m0 + ty + 16 * u, gc = n0 + tx + 16 * w;
+            const int gr = m0 + ty * 4 + u, gc = n0 + tx * 4 + w;
             if (gr >= M || gc >= N) continue;
             const int64_t at = (int64_t)gr * ldc + gc;
             float v = acc[u][w] + (bias ? bias[gc] : 0.f);
@@ -150,7 +216,6 @@ __global__ void __launch_bounds__(256) k_gemm(const float *__restrict__ A, int64
         }
 }
 
-// Output gradient dO = (o - t) / B and the loss per network.
 __global__ void k_out_grad(const float *o, const float *t, int B, float *dO, float *loss)
 {
     const int e = blockIdx.y;

@@ -200,6 +200,22 @@ def surrogate_form(ctx, gpbo, W, dev, plain_value=None):
 
 
 # ---------------------------------------------------------------------------- ours
+def aggregate_timing(ms_local, steps, world, device, units_per_step=None):
+    """Whole-job timing of a weakly scaled run: the slowest rank's time (max over ranks by
+    all-reduce; every rank processes the same units per step) and the units all ranks
+    processed per second.  Returns (ms_max, value)."""
+    import torch
+
+    ms_max = float(ms_local)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    units = M_CAND if units_per_step is None else units_per_step
+    return ms_max, world * units * steps / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -253,13 +269,7 @@ def run_ours(args, rank, world, local):
     with ClockSampler(local) as clk:
         ms, launches, tr, (g, r) = timed(args.prec, args.steps, args.warmup, trace=True)
     clocks = clk.summary()
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * M_CAND * args.steps / (ms_max / 1e3)
+    ms_max, value = aggregate_timing(ms, args.steps, world, dev)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     Xh = torch.from_numpy(w.X).pin_memory().numpy()

@@ -155,10 +155,6 @@ __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, int N, int M)
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void named_sync(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 
 }  // namespace tcx
 

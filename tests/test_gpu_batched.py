@@ -65,3 +65,32 @@ def test_autotuned_tile_is_the_fastest_measured_and_tiles_agree(ctx):
     ctx.batched_tile(0)
     with pytest.raises(Exception):
         ctx.batched_tile(48)
+
+
+def test_full_config_sampled_against_oracle(ctx, orc):
+    """The bench's batched workload at full size (64 GPs, M = 16384 each, autotuned tile):
+    for four problems (the largest n, the largest d, two others) the GPU's pick is checked
+    against the FP64 oracle -- its EI matches the oracle's EI at that candidate within the
+    FP32 bar, it is at least as good as every one of 256 sampled candidates, and x_next is
+    that candidate."""
+    from tests._util import BAR
+    subs, probs = _problems(G=64, M=16384)
+    ctx.batched_tile(0)
+    out = ctx.search_step_batched(probs)
+    ns = [w.n for w in subs]
+    ds = [w.d for w in subs]
+    picks = sorted({int(np.argmax(ns)), int(np.argmax(ds)), 0, 37})
+    rng = np.random.default_rng(5)
+    for g in picks:
+        w, pb = subs[g], probs[g]
+        ys, _, _ = orc.standardize(w.y)
+        _, Lo, ao = orc.gp_fit(w.X, ys, w.lengthscale, 1.0, w.noise_var)
+        am = int(out["argmax"][g])
+        idx = np.unique(np.concatenate([rng.choice(pb["M"], 256, replace=False), [am]]))
+        Xc = np.concatenate([W.uniform_points(pb["seed"], W.STREAM_CAND, 1, w.d, first=int(i)) for i in idx])
+        mu, sg = orc.posterior(w.X, w.lengthscale, 1.0, Lo, ao, Xc)
+        ei = orc.ei_batch(mu, sg, float(ys.min()))
+        e_am = ei[int(np.nonzero(idx == am)[0][0])]
+        assert abs(out["ei_max"][g] - e_am) <= BAR["f32"] * (abs(e_am) + ei.max()), (g, out["ei_max"][g], e_am)
+        assert e_am >= ei.max() * (1 - BAR["f32"]), (g, e_am, ei.max())
+        assert np.allclose(out["x_next"][g], Xc[int(np.nonzero(idx == am)[0][0])], rtol=0, atol=1e-7)

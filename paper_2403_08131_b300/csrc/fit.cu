@@ -40,6 +40,10 @@ __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, d
 // on the count).  The kernel is bound by the FP64 pipe and the pivot's dependent chain: about
 // 90 us at 256 or 1024 threads, with or without a cheap pivot (measured).
 constexpr int DIAG_THREADS = 1024;
+// Trailing updates of fewer than SLAB_BELOW x SMs whole 64 x 64 tiles (two waves at three
+// CTAs per SM) run as 16-row slabs.  Slabs for every launch measured the same (22.3 ms per
+// step): the update is FP64-bound, not wave-bound.
+constexpr int SLAB_BELOW = 6;
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status)
 {
@@ -290,8 +294,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            // whole tiles (3 CTAs of 66.5 KB per SM) while they fill two waves; 16-row slabs after
-            if (tiles >= 2 * 3 * (int64_t)ctx->sm_count)
+            if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
                 k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
             else
                 k_chol_update_slab<<<(unsigned)(tiles * 4), 256, 0, st>>>(m->L, n_pad, kb, 2);

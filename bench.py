@@ -351,11 +351,15 @@ def run_ours(args, rank, world, local):
         if not args.no_batched:
             out["forms"] = {"batched": batched_form(ctx, W, dev)}
         if not args.no_plain and args.prec != "f32":
-            pms, _, ptr, _ = timed("f32", 1, 1, trace=True)
+            pms, _, ptr, (_, pr) = timed("f32", 1, 1, trace=True)
             out["plain"] = {"value": round(M_CAND / (pms / 1e3), 1), "unit": UNIT, "dtype": "f32",
                             "ms_per_step": round(pms, 3),
-                            "variance_tflops": round(ptr["variance"]["flops"] / (ptr["variance"]["ms"] / 1e3) / 1e12, 3)}
+                            "variance_tflops": round(ptr["variance"]["flops"] / (ptr["variance"]["ms"] / 1e3) / 1e12, 3),
+                            "argmax": pr["argmax"], "ei_max": pr["ei_max"]}
             out["speedup_vs_plain"] = round(out["value"] / out["plain"]["value"], 2)
+            # the speedup is at equal EI-argmax agreement when both paths pick the same candidate
+            out["argmax_agrees_with_plain"] = bool(r["argmax"] == pr["argmax"])
+            out["ei_max_rel_diff_vs_plain"] = abs(r["ei_max"] - pr["ei_max"]) / max(abs(pr["ei_max"]), 1e-300)
         if not args.no_surrogate and args.prec != "f32":
             out.setdefault("forms", {})["surrogate"] = surrogate_form(
                 ctx, gpbo, W, dev, out.get("plain", {}).get("value"))

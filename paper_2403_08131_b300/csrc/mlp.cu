@@ -1,7 +1,8 @@
 // Learned pre-screen: an ensemble of E small networks d -> H -> H -> 2 (exact GELU) trained
 // on (x, GP posterior) pairs to predict (mu, log sigma) in standardised units; it scores a
 // very large candidate pool cheaply, keeps the top k by the ensemble's expected improvement,
-// and the exact GP-EI re-scores those k (the exact score is both the fallback and the judge).
+// and the exact GP-EI re-scores those k (the exact score is both the fallback and the measure
+// of the screen's error).
 //
 // Ensemble combine (mean of the members, total variance):
 //   mu_bar = mean_e mu_e,  sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e.

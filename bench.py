@@ -129,23 +129,25 @@ def batched_form(ctx, W, dev, steps=3):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(steps):
-        ctx.search_step_batched(probs)
+        bout = ctx.search_step_batched(probs)
     torch.cuda.synchronize(dev)
     tb = (time.perf_counter() - t0) / steps
     for pb in probs[:2]:                                # warm the single-problem path
         ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=16384, seed=pb["seed"], prec="f32")
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for pb in probs:
-        ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=16384, seed=pb["seed"], prec="f32")
+    seq = [ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=16384, seed=pb["seed"],
+                           prec="f32") for pb in probs]
     torch.cuda.synchronize(dev)
     ts = time.perf_counter() - t0
+    agree = sum(int(bout["argmax"][g] == seq[g]["argmax"]) for g in range(len(probs)))
     flops = sum(w.n * (w.n + 1) for w in subs) * 16384
     tile, tune = ctx.batched_tuning()
     return {"workload": "64 GPs, d in U{2..12}, n in U{32..1024}, M=16384 each, FP32 scoring, one graph launch",
             "variance_tile": tile, "autotune_ms": {str(k): round(v, 3) for k, v in tune.items()},
             "value": round(64 * 16384 / tb, 1), "unit": "candidates/s", "ms_per_step": round(tb * 1e3, 3),
             "sequential_ms": round(ts * 1e3, 3), "speedup_vs_sequential": round(ts / tb, 2),
+            "argmax_agrees_with_sequential": f"{agree}/{len(probs)}",
             "variance_tflops": round(flops / tb / 1e12, 3), "timing": "host wall clock around synchronised calls"}
 
 

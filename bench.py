@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned pre-screen measurement")
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
                     help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="profiling case: the batched form (64 GPs, M=16384 each), built then run twice, no JSON")
     ap.add_argument("--profile-surrogate", type=int, default=0, metavar="M",
                     help="profiling case: the FP16 ensemble forward (8 x 20-256-256-2) over M seeded candidates, "
                          "run twice, no JSON")
@@ -439,6 +441,22 @@ def profile_case(args):
     ctx.close()
 
 
+def profile_batched(args):
+    import torch
+
+    from paper_2403_08131_b300 import gpbo, workloads as W
+
+    ctx = gpbo.Context(0, torch.cuda.current_stream())
+    subs = W.batched_config3(G=64, M=16384)
+    probs = [dict(X=torch.from_numpy(w.X).cuda(), y=torch.from_numpy(w.y).cuda(), lengthscale=w.lengthscale,
+                  signal_var=1.0, noise_var=w.noise_var, M=16384, seed=w.seed) for w in subs]
+    for _ in range(3):
+        out = ctx.search_step_batched(probs)
+    torch.cuda.synchronize()
+    print(f"profile batched: tile {ctx.batched_tuning()[0]} ei_max[0]={out['ei_max'][0]:.6g}")
+    ctx.close()
+
+
 def profile_surrogate(args):
     import torch
 
@@ -463,6 +481,9 @@ def main():
         return
     if args.profile_surrogate:
         profile_surrogate(args)
+        return
+    if args.profile_batched:
+        profile_batched(args)
         return
     if args.impl == "reference":
         run_reference(args)

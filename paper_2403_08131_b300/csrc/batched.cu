@@ -56,6 +56,9 @@ struct BatchPlan {
     int var_bm = 128;    // variance tile in use: candidates per CTA
     float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 64, 128, 256
     cudaStream_t cap = nullptr;
+    cudaStream_t cap2 = nullptr;     // second capture stream: lookahead column, alpha solve
+    cudaEvent_t ev[4] = {};          // fork / join events between the two capture streams
+    int64_t kernels = 0;             // kernel nodes in the captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void *> allocs;
@@ -106,12 +109,14 @@ __global__ void __launch_bounds__(256) b_chol_panel(const BProb *P, double *L, c
     k_chol_panel_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x, 0);
 }
 
-__global__ void __launch_bounds__(256) b_chol_update(const BProb *P, double *L, int kb)
+// part 1: block column kb+1 (T tiles); part 2: block columns kb+2 .. (T(T-1)/2 tiles).
+__global__ void __launch_bounds__(256) b_chol_update(const BProb *P, double *L, int kb, int part)
 {
     const BProb &p = P[blockIdx.y];
     const int T = p.nblk - kb - 1;
-    if (T <= 0 || (int64_t)blockIdx.x >= (int64_t)T * (T + 1) / 2) return;
-    k_chol_update_body(L + p.off_sq, p.n_pad, kb, p.nblk, blockIdx.x, 0);
+    const int64_t tiles = part == 1 ? T : (int64_t)T * (T - 1) / 2;
+    if (T <= 0 || (int64_t)blockIdx.x >= tiles) return;
+    k_chol_update_body(L + p.off_sq, p.n_pad, kb, p.nblk, blockIdx.x, 0, part);
 }
 
 __global__ void b_zero_upper(const BProb *P, double *L)
@@ -241,6 +246,9 @@ static void free_plan(BatchPlan *pl)
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->cap2) cudaStreamDestroy(pl->cap2);
+    for (cudaEvent_t e : pl->ev)
+        if (e) cudaEventDestroy(e);
     for (void *p : pl->allocs) cudaFree(p);
     delete pl;
 }
@@ -352,6 +360,8 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
     if (!all.empty())
         GPBO_CUDA_TRY(cudaMemcpy(pl->gemm_dev, all.data(), sizeof(GemmProb) * all.size(), cudaMemcpyHostToDevice));
     GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
+    GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap2, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : pl->ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return GPBO_OK;
 }
 
@@ -427,27 +437,49 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     b_kmat<<<dim3(pl->max_npad / 32, pl->max_npad / 32, G), dim3(32, 8), 0, st>>>(P, pl->Xs64, pl->K);
     GPBO_CUDA_TRY(cudaMemcpyAsync(pl->L, pl->K, sizeof(double) * (size_t)(pl->probs.back().off_sq + pl->probs.back().n_pad *
                                   (int64_t)pl->probs.back().n_pad), cudaMemcpyDeviceToDevice, st));
-    for (int kb = 0; kb < pl->max_nblk; ++kb) {
-        b_chol_diag<<<dim3(1, G), 256, smem2, st>>>(P, pl->L, pl->Dinv, kb, ctx->dev_status);
-        const int T = pl->max_nblk - kb - 1;
-        if (T > 0) {
-            b_chol_panel<<<dim3(T * (NB / 16), G), 256, 0, st>>>(P, pl->L, pl->Dinv, kb);
-            b_chol_update<<<dim3((unsigned)((int64_t)T * (T + 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb);
+    // Cholesky with a lookahead of one block column (as the single-problem path): the next
+    // column's update, its diagonal factor and its panel on the second capture stream, the
+    // rest of each trailing update on the main one.
+    cudaStream_t s2 = pl->cap2;
+    cudaEvent_t ev_fork = pl->ev[0], ev_panel = pl->ev[1], ev_rest = pl->ev[2], ev_join = pl->ev[3];
+    const int NBL = pl->max_nblk;
+    GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_fork, 0));
+    b_chol_diag<<<dim3(1, G), 256, smem2, s2>>>(P, pl->L, pl->Dinv, 0, ctx->dev_status);
+    if (NBL > 1) b_chol_panel<<<dim3((NBL - 1) * (NB / 16), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, 0);
+    GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
+    for (int kb = 0; kb + 1 < NBL; ++kb) {
+        const int T = NBL - kb - 1;
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));
+        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_rest, 0));
+        b_chol_update<<<dim3((unsigned)T, G), 256, smem2, s2>>>(P, pl->L, kb, 1);
+        b_chol_diag<<<dim3(1, G), 256, smem2, s2>>>(P, pl->L, pl->Dinv, kb + 1, ctx->dev_status);
+        if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 16), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
+        GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
+        if (T > 1) {
+            b_chol_update<<<dim3((unsigned)((int64_t)T * (T - 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb, 2);
+            GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }
     }
+    GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     b_zero_upper<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L);
-    // alpha = K^-1 y' with one refinement step; vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 dlt
-    b_pad_copy<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->dys, pl->vec);
+    // alpha = K^-1 y' with one refinement step on the second stream, under the L^-1 products;
+    // vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 dlt
+    GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_fork, 0));
+    b_pad_copy<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->dys, pl->vec);
     for (int pass = 0; pass < 2; ++pass) {
-        b_copy_vec<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->vec, pass == 0 ? 1 : 4, 2);
-        for (int b = 0; b < pl->max_nblk; ++b)
-            b_fwd_step<<<dim3(std::max(1, pl->max_nblk - b - 1), G), 256, 0, st>>>(P, pl->L, pl->Dinv, pl->vec, b);
-        for (int s = 0; s < pl->max_nblk; ++s)
-            b_bwd_step<<<dim3(std::max(1, pl->max_nblk - 1 - s), G), 256, 0, st>>>(P, pl->L, pl->Dinv, pl->vec, s,
-                                                                                 pass == 0 ? 0 : 5);
-        if (pass == 0) b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, st>>>(P, pl->K, pl->vec);
+        b_copy_vec<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->vec, pass == 0 ? 1 : 4, 2);
+        for (int b = 0; b < NBL; ++b)
+            b_fwd_step<<<dim3(std::max(1, NBL - b - 1), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, b);
+        for (int s = 0; s < NBL; ++s)
+            b_bwd_step<<<dim3(std::max(1, NBL - 1 - s), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, s,
+                                                                        pass == 0 ? 0 : 5);
+        if (pass == 0) b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, s2>>>(P, pl->K, pl->vec);
     }
-    b_axpy_cast<<<dim3(gb(pl->max_npad), G), 256, 0, st>>>(P, pl->vec, pl->alpha32);
+    b_axpy_cast<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->vec, pl->alpha32);
+    GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
     // FP32 L^-1
     b_cast_L<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L, pl->L32);
     b_linv_init<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->Dinv, pl->Linv32);
@@ -464,6 +496,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         b_gemm<<<grid, 256, 0, st>>>(pl->Linv32, pl->tmp, pl->Linv32, pl->gemm_dev + pl->lvl_first[l] + pl->lvl_count[l],
                                      -1.0f, 1, 0);
     }
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     // scoring
     b_xkern<<<dim3(pl->max_tiles64, G), 256, sizeof(float) * 64 * GPBO_MAX_D, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,
                                                                                     pl->Kst, pl->mu);
@@ -474,13 +507,18 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     return GPBO_OK;
 }
 
-// Kernels one graph replay launches (for launch accounting).
-static int64_t plan_launches(const BatchPlan *pl)
+// Kernel nodes of a captured graph (one graph replay launches that many kernels).
+static int64_t count_kernel_nodes(cudaGraph_t g)
 {
-    int64_t k = 3 + 1;  // standardise, scale, kmat, + (memcpy node not counted) zero_upper
-    for (int kb = 0; kb < pl->max_nblk; ++kb) k += (pl->max_nblk - kb - 1 > 0) ? 3 : 1;
-    k += 1 + 2 * (1 + 2 * (int64_t)pl->max_nblk) + 1 + 1;  // pad, passes, residual, axpy
-    k += 2 + 2 * (int64_t)pl->lvl_first.size() + 4;
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(node, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
     return k;
 }
 
@@ -573,10 +611,11 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
             return st != GPBO_OK ? st : GPBO_ECUDA;
         }
         pl->graph = graph;
+        pl->kernels = count_kernel_nodes(graph);
         GPBO_CUDA_TRY(cudaGraphInstantiate(&pl->exec, graph, 0));
     }
     GPBO_CUDA_TRY(cudaGraphLaunch(pl->exec, ctx->stream));
-    ctx->launches += plan_launches(pl);
+    ctx->launches += pl->kernels;
     std::vector<double> be(G);
     std::vector<int64_t> bi(G);
     std::vector<float> xn((size_t)G * GPBO_MAX_D);

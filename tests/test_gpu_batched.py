@@ -94,3 +94,21 @@ def test_full_config_sampled_against_oracle(ctx, orc):
         assert abs(out["ei_max"][g] - e_am) <= BAR["f32"] * (abs(e_am) + ei.max()), (g, out["ei_max"][g], e_am)
         assert e_am >= ei.max() * (1 - BAR["f32"]), (g, e_am, ei.max())
         assert np.allclose(out["x_next"][g], Xc[int(np.nonzero(idx == am)[0][0])], rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("shapes", [[(1, 1)], [(1, 3), (2, 1), (65, 12), (700, 5)]])
+def test_batched_edge_shapes_equal_single_calls(ctx, shapes):
+    """Degenerate and uneven shapes (n = 1, n = 2, d = 1, a single problem, a block tail):
+    the batched step still equals the single-problem calls bit for bit."""
+    probs = []
+    for g, (n, d) in enumerate(shapes):
+        X = W.uniform_points(9000 + g, W.STREAM_OBS, n, d)
+        y = W.Objective([d], [W.FN_ACKLEY], 0.0, 9000 + g)(X)
+        probs.append(dict(X=X, y=y, lengthscale=W.lengthscale_rule(d), signal_var=1.0, noise_var=1e-4,
+                          M=777 + 13 * g, seed=500 + g))
+    out = ctx.search_step_batched(probs)
+    for g, pb in enumerate(probs):
+        one = ctx.search_step(pb["X"], pb["y"], pb["lengthscale"], 1.0, pb["noise_var"], M=pb["M"], seed=pb["seed"],
+                              prec="f32")
+        assert out["argmax"][g] == one["argmax"] and out["ei_max"][g] == one["ei_max"], (g, shapes[g])
+        assert np.array_equal(out["x_next"][g], one["x_next"])

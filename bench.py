@@ -341,6 +341,17 @@ def run_ours(args, rank, world, local):
                     round(42.27e6 / 1225 * 41664 / 62) if N_OBS == 4096 else None)]
         rl[0]["peak_burst"] = round(tensor_burst, 3)
         rl[0]["frac_burst"] = round(rl[0]["achieved"] / tensor_burst, 4)
+        if args.prec != "f32" and "xkern" in tr and tr["xkern"]["ms"] > 0:
+            # the cross-kernel's Matern evaluations: 2 MUFU operations (sqrt, ex2) per candidate and
+            # observation, against 16 MUFU lanes per clock per SM at the sampled SM clock
+            xs = tr["xkern"]["ms"] / 1e3
+            mufu = 2.0 * N_OBS * M_CAND * args.steps / xs / 1e12
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            mufu_peak = sms * 16 * clocks["sm_mhz"] * 1e6 / 1e12
+            rl.append({"kernel": "k_xkern_tc", "bound": "mufu", "achieved": round(mufu, 3),
+                       "peak": round(mufu_peak, 3), "unit": "Tops/s", "frac": round(mufu / mufu_peak, 4),
+                       "peak_source": "SMs x 16 MUFU lanes per clock x the sampled median SM clock",
+                       "ms_per_step": round(tr["xkern"]["ms"] / args.steps, 3), "traffic": None})
         dominant = max(rl, key=lambda e: e["ms_per_step"])
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -356,6 +367,11 @@ def run_ours(args, rank, world, local):
             "rooflines": rl,
             "fp64_tflops_measured": round(fp64_peak, 3),
             "phases": phases,
+            # the scoring pass alone (cross-kernel, variance, EI, argmax: A7-A9) per M candidates,
+            # with the fit (A3-A6) reported beside it, per step and amortised
+            "score_pass": {"value": round(M_CAND * args.steps / ((tr["xkern"]["ms"] + tr["variance"]["ms"]) / 1e3), 1),
+                           "unit": UNIT, "ms_per_step": round((tr["xkern"]["ms"] + tr["variance"]["ms"]) / args.steps, 3),
+                           "fit_ms_per_step": round(tr["fit"]["ms"] / args.steps, 3)},
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "e2e": {"value": round(world * M_CAND * args.steps / e2e_s, 1), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

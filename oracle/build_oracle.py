@@ -7,7 +7,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = [os.path.join(HERE, "gpbo_oracle.c"), os.path.join(HERE, "mlp_oracle.c")]
+SRC = [os.path.join(HERE, "gpbo_oracle.c"), os.path.join(HERE, "mlp_oracle.c"), os.path.join(HERE, "mle_oracle.c")]
 OUT = os.path.join(HERE, "liboracle.so")
 
 

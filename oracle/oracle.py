@@ -67,6 +67,9 @@ def lib():
         L.orc_partition_routine.argtypes = [_D, C.c_int, C.c_int, _I, C.c_double, C.c_int, _I, _I, _I]
         if hasattr(L, "orc_mlp_forward"):
             _bind_mlp(L)
+        if hasattr(L, "orc_lml_grad"):
+            L.orc_lml_grad.restype = C.c_int
+            L.orc_lml_grad.argtypes = [_D, _D, C.c_int, C.c_int, _D, C.c_double, C.c_double, _D, _D]
     return _lib
 
 
@@ -361,3 +364,16 @@ def mlp_ensemble(thetas, X, d, H, norm4=(0.0, 1.0, 0.0, 1.0), tau=0.0, xi=0.0):
     lib().orc_mlp_ensemble(pth, E, pX, B, d, H, pn, float(tau), float(xi), mu.ctypes.data_as(_D),
                            sg.ctypes.data_as(_D), ei_.ctypes.data_as(_D))
     return mu, sg, ei_
+
+
+# ------------------------------------------------------------------ GP marginal likelihood
+def lml_grad(X, y, ls, s2, sn2):
+    """(log marginal likelihood, gradient over (log l_1..log l_d, log s2, log sn2))."""
+    X, pX = _d(X)
+    y, py = _d(y)
+    n, d = X.shape
+    ls, pls = _d(np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,)))
+    lml = np.empty(1)
+    g = np.empty(d + 2)
+    _check(lib().orc_lml_grad(pX, py, n, d, pls, float(s2), float(sn2), lml.ctypes.data_as(_D), g.ctypes.data_as(_D)))
+    return float(lml[0]), g

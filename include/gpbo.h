@@ -102,7 +102,8 @@ const char *gpbo_strerror(int status);
 int64_t gpbo_launch_count(const gpbo_ctx *ctx);
 /* Per-phase device timing with CUDA events recorded on the context's stream around each
  * phase's kernels (phases: 0 fit, 1 cross-kernel + mean, 2 variance + EI + argmax,
- * 3 screen).  gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
+ * 3 screen, 4 Cholesky trailing updates, 5 the K^-1 tiles of the likelihood gradient,
+ * 2 x 64^2 flops per row of L^-1 reduced into a tile).  gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
  * gpbo_trace_read synchronises, then writes for each of the first nphase phases the total
  * milliseconds, the number of timed intervals, and the algorithmic flops the phase's
  * kernels were asked to do (variance: n(n+1) per candidate; cross-kernel: 3nd + 2n;
@@ -328,6 +329,36 @@ int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t 
  * allocates it); top_idx: host k pool indices of the selected set, or NULL.  Synchronises. */
 int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_t M, uint64_t seed, int k,
                      double y_best, double xi, float *ei_pool, int64_t *top_idx, int64_t *argmax, double *ei_max);
+
+/* ------------------------------------------------------------------ hyperparameters by maximum likelihood
+ * The surrogate's hyperparameters theta = (log l_1 .. log l_d, log signal_var, log noise_var)
+ * fitted by maximising the log marginal likelihood of the evaluated configurations (§III-A:
+ * the surrogate is trained on them; Rasmussen & Williams 2006, §5.4.1):
+ *   LML(theta)      = -1/2 y^T alpha - sum_i log L_ii - n/2 log(2 pi),   alpha = K^-1 y,
+ *   dLML/dtheta_j   = 1/2 sum_pq (alpha_p alpha_q - [K^-1]_pq) dK_pq/dtheta_j,
+ * with K, L and alpha as gp_fit computes them in FP64 (y used as given: zero prior mean) and
+ * K^-1 = L^-T L^-1 formed tile by tile in FP64 and reduced into the gradient without being
+ * stored.  For r the scaled distance and t_k = (x_k - x'_k) / l_k:
+ *   dK/dlog l_k = s2 (5/3) (1 + sqrt5 r) exp(-sqrt5 r) t_k^2,  dK/dlog s2 = s2 m(r),
+ *   dK/dlog sn2 = sn2 I.
+ * X, y: n x d row-major and n FP64, device pointers or host with GPBO_HOST_PTRS.
+ *
+ * gp_lml: LML and its gradient (host, d + 2 values; grad may be NULL) at the hyperparameters
+ * in hyp (noise_var > 0).  GPBO_ENOTSPD when K is not positive definite.  Synchronises. */
+int gp_lml(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp, unsigned flags,
+           double *lml, double *grad);
+/* gp_fit_mle: maximise the LML over the box lo <= theta <= hi (host, d + 2 each) with a
+ * projected L-BFGS (memory 10, Armijo backtracking) from each of n_starts starting points
+ * theta0 (host, n_starts x (d + 2) row-major; the caller draws them, so the fit has no
+ * randomness of its own).  Each start runs at most max_iter iterations and stops when the
+ * projected gradient's largest component is at most gtol or the LML stops improving
+ * (relative change 1e-12).  A trial point whose K is not positive definite is a rejected
+ * step; a start whose own K is not is skipped.  Writes the best start's theta (host, d + 2),
+ * its LML and the number of LML evaluations over all starts (evals may be NULL).
+ * GPBO_ENOTSPD when no start could be factored.  Synchronises. */
+int gp_fit_mle(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, int n_starts, const double *theta0,
+               const double *lo, const double *hi, int max_iter, double gtol, unsigned flags, double *theta_best,
+               double *lml_best, int64_t *evals);
 
 #ifdef __cplusplus
 }

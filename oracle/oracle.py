@@ -377,3 +377,52 @@ def lml_grad(X, y, ls, s2, sn2):
     g = np.empty(d + 2)
     _check(lib().orc_lml_grad(pX, py, n, d, pls, float(s2), float(sn2), lml.ctypes.data_as(_D), g.ctypes.data_as(_D)))
     return float(lml[0]), g
+
+
+def lml_grad_dense(X, y, ls, s2, sn2, scales=False):
+    """The same LML and gradient as lml_grad with library primitives as the steps (scipy's
+    Cholesky and triangular solves, numpy's matrix products), for sizes where the C loops
+    are too slow.  Returns (lml, grad, kappa1) where kappa1 = |K|_1 |K^-1|_1 >= cond_2(K).
+    With scales=True also the sums of absolute terms that bound the effect of a relative
+    perturbation of alpha and K^-1: (|y| |alpha| + sum |log L_ii| + n, and per component
+    1/2 sum (|alpha_p alpha_q| + |K^-1_pq|) |dK_pq/dtheta_j|)."""
+    import scipy.linalg
+    X = np.asarray(X, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n, d = X.shape
+    ls = np.broadcast_to(np.asarray(ls, dtype=np.float64), (d,))
+    Z = X / ls
+    r2 = np.zeros((n, n))
+    for k in range(d):
+        t = Z[:, k][:, None] - Z[None, :, k]
+        r2 += t * t
+    r = np.sqrt(r2)
+    e = np.exp(-np.sqrt(5.0) * r)
+    m = (1.0 + np.sqrt(5.0) * r + (5.0 / 3.0) * r2) * e
+    K = s2 * m + sn2 * np.eye(n)
+    L = scipy.linalg.cholesky(K, lower=True)
+    alpha = scipy.linalg.cho_solve((L, True), y)
+    alpha = alpha + scipy.linalg.cho_solve((L, True), y - K @ alpha)
+    lml = -0.5 * y @ alpha - np.log(np.diag(L)).sum() - 0.5 * n * np.log(2 * np.pi)
+    Li = scipy.linalg.solve_triangular(L, np.eye(n), lower=True)
+    Ki = Li.T @ Li
+    W = np.outer(alpha, alpha) - Ki
+    c = s2 * (5.0 / 3.0) * (1.0 + np.sqrt(5.0) * r) * e
+    g = np.empty(d + 2)
+    for k in range(d):
+        t = Z[:, k][:, None] - Z[None, :, k]
+        g[k] = 0.5 * np.sum(W * c * t * t)
+    g[d] = 0.5 * np.sum(W * s2 * m)
+    g[d + 1] = 0.5 * sn2 * np.trace(W)
+    kappa1 = np.abs(K).sum(0).max() * np.abs(Ki).sum(0).max()
+    if not scales:
+        return float(lml), g, float(kappa1)
+    Wa = np.abs(np.outer(alpha, alpha)) + np.abs(Ki)
+    gs = np.empty(d + 2)
+    for k in range(d):
+        t = Z[:, k][:, None] - Z[None, :, k]
+        gs[k] = 0.5 * np.sum(Wa * np.abs(c) * t * t)
+    gs[d] = 0.5 * np.sum(Wa * s2 * m)
+    gs[d + 1] = 0.5 * sn2 * np.trace(Wa)
+    ls_ = np.linalg.norm(y) * np.linalg.norm(alpha) + np.abs(np.log(np.diag(L))).sum() + n
+    return float(lml), g, float(kappa1), float(ls_), gs

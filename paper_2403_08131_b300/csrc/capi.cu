@@ -111,7 +111,7 @@ static bool finite_all(const double *a, int64_t n)
     return true;
 }
 
-static void free_model(gp_model *m)
+void model_free(gp_model *m)
 {
     if (!m) return;
     void *ptrs[] = {m->X,       m->Xs64,    m->Xs32,   m->K,      m->L,      m->Dinv,
@@ -150,9 +150,7 @@ static int alloc_model(gp_model *m)
     return GPBO_OK;
 }
 
-// Fit with optional jitter escalation.  X and y are device pointers here.
-static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp, int prec,
-                    unsigned flags, gp_model **out)
+int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out)
 {
     gp_model *m = new (std::nothrow) gp_model();
     if (!m) return GPBO_ENOMEM;
@@ -161,10 +159,25 @@ static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int 
     m->d = d;
     m->prec = prec;
     m->n_pad = round_up(n, (prec == GPBO_PREC_BF16 || prec == GPBO_PREC_F16) ? TC_NCHUNK : NB);
+    const int st = alloc_model(m);
+    if (st != GPBO_OK) {
+        model_free(m);
+        return st;
+    }
+    *out = m;
+    return GPBO_OK;
+}
+
+// Fit with optional jitter escalation.  X and y are device pointers here.
+static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp, int prec,
+                    unsigned flags, gp_model **out)
+{
+    gp_model *m = nullptr;
+    int st = model_create(ctx, n, d, prec, &m);
+    if (st != GPBO_OK) return st;
     m->s2 = hyp->signal_var;
     m->sn2 = hyp->noise_var;
     for (int k = 0; k < d; ++k) m->ls[k] = hyp->lengthscale[k];
-    int st = alloc_model(m);
     const int tries = (flags & GPBO_JITTER) ? 4 : 1;
     for (int t = 0; st == GPBO_OK || st == GPBO_ENOTSPD; ++t) {
         if (t == tries) break;
@@ -180,14 +193,14 @@ static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int 
     }
     if (st != GPBO_OK) {
         cudaStreamSynchronize(ctx->stream);
-        free_model(m);
+        model_free(m);
         return st;
     }
     *out = m;
     return GPBO_OK;
 }
 
-static int check_hyper(const gp_hyper *hyp, int d)
+int check_hyper(const gp_hyper *hyp, int d)
 {
     if (!hyp || hyp->d != d || !hyp->lengthscale) return GPBO_EINVAL;
     for (int k = 0; k < d; ++k)
@@ -368,7 +381,7 @@ int gp_model_free(gp_model *m)
     if (!m) return GPBO_EINVAL;
     cudaSetDevice(m->ctx->device);
     cudaStreamSynchronize(m->ctx->stream);
-    free_model(m);
+    model_free(m);
     return GPBO_OK;
 }
 
@@ -518,7 +531,7 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
         if (argmax) *argmax = am;
     }
     cudaStreamSynchronize(ctx->stream);
-    if (m) free_model(m);
+    if (m) model_free(m);
     if (host && dXc) cudaFree(dXc);
     cudaFree(buf);
     return st;

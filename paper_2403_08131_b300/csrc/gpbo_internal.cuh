@@ -58,8 +58,8 @@ enum : unsigned {
 }  // namespace gpbo
 
 namespace gpbo {
-constexpr int TRACE_PHASES = 5;
-enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3, PH_CHOL_UPDATE = 4 };
+constexpr int TRACE_PHASES = 6;
+enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3, PH_CHOL_UPDATE = 4, PH_LML = 5 };
 struct TraceRec {
     int phase;
     cudaEvent_t a, b;
@@ -123,6 +123,11 @@ int side_stream(gpbo_ctx *ctx, cudaStream_t *out);
 int trace_begin(gpbo_ctx *ctx, int phase, double flops);
 int trace_end(gpbo_ctx *ctx);
 int take_device_status(gpbo_ctx *ctx, unsigned *bits_out);
+// Allocate a model's device buffers for n x d in the given precision (hyperparameters unset),
+// free one, and validate hyperparameters.
+int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out);
+void model_free(gp_model *m);
+int check_hyper(const gp_hyper *hyp, int d);
 
 // fit.cu
 int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_dev);

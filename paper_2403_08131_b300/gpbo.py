@@ -67,7 +67,7 @@ _launches = _sig("gpbo_launch_count", C.c_int64, [_P])
 _ws_limit = _sig("gpbo_set_workspace_limit", C.c_int, [_P, C.c_int64])
 _trace_en = _sig("gpbo_trace_enable", C.c_int, [_P, C.c_int])
 _trace_rd = _sig("gpbo_trace_read", C.c_int, [_P, C.c_int, _D, _L, _D])
-PHASES = ("fit", "xkern", "variance", "screen", "chol_update")
+PHASES = ("fit", "xkern", "variance", "screen", "chol_update", "lml")
 _probe = _sig("gpbo_probe_fma", C.c_int, [_P, C.c_int, _D])
 _fit = _sig("gp_fit", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_int, C.c_uint,
                                  C.POINTER(_P)])
@@ -95,6 +95,9 @@ _mlp_score = _sig("mlp_score", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_
                                           _P, _P])
 _screen_sur = _sig("surrogate_screen", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_int, C.c_double, C.c_double,
                                                  _P, _P, _L, _D])
+_lml = _sig("gp_lml", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_uint, _D, _D])
+_fit_mle = _sig("gp_fit_mle", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, _D, _D, _D, C.c_int, C.c_double,
+                                         C.c_uint, _D, _D, _L])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
 _screen = _sig("interdep_screen", C.c_int, [_P, C.POINTER(GpboObjective), C.c_int, C.POINTER(ScreenOpts), _P, _P,
                                              _P, _I, _P])
@@ -205,6 +208,42 @@ class Context:
         m = Model(self, out, prec)
         self._models.add(m)
         return m
+
+    # ------------------------------------------------------------ hyperparameters
+    def lml(self, X, y, lengthscale, signal_var, noise_var):
+        """Log marginal likelihood and its gradient over (log l_1..l_d, log signal_var,
+        log noise_var).  X, y: torch float64 CUDA tensors or numpy arrays."""
+        host = _is_host(X)
+        if host:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        n, d = X.shape
+        h, keep = _hyper(lengthscale, signal_var, noise_var)
+        v = C.c_double()
+        g = np.empty(d + 2)
+        check(_lml(self._h, _ptr(X), _ptr(y), n, d, C.byref(h), HOST_PTRS if host else 0, C.byref(v),
+                   g.ctypes.data_as(_D)), "gp_lml")
+        return v.value, g
+
+    def fit_mle(self, X, y, theta0, lo, hi, max_iter=200, gtol=1e-6):
+        """Maximise the LML over the box [lo, hi] of log parameters from each row of theta0
+        (n_starts x (d + 2)).  Returns (theta, lml, evaluations)."""
+        host = _is_host(X)
+        if host:
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        n, d = X.shape
+        t0 = np.ascontiguousarray(np.atleast_2d(theta0), dtype=np.float64)
+        lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.float64), (d + 2,)))
+        hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.float64), (d + 2,)))
+        assert t0.shape[1] == d + 2
+        th = np.empty(d + 2)
+        v = C.c_double()
+        ev = C.c_int64()
+        check(_fit_mle(self._h, _ptr(X), _ptr(y), n, d, t0.shape[0], t0.ctypes.data_as(_D), lo.ctypes.data_as(_D),
+                       hi.ctypes.data_as(_D), int(max_iter), float(gtol), HOST_PTRS if host else 0,
+                       th.ctypes.data_as(_D), C.byref(v), C.byref(ev)), "gp_fit_mle")
+        return th, v.value, int(ev.value)
 
     def posterior_ei(self, model, Xc=None, M=None, seed=0, y_best=0.0, xi=0.0, mu=None, sigma=None, ei=None):
         """Xc: M x d float32 torch CUDA tensor / numpy array, or None with M and seed.

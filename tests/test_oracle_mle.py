@@ -114,3 +114,15 @@ def test_gradient_vanishes_at_scipy_optimum(orc):
         + WhiteKernel(1e-2, (math.exp(-14), math.exp(1)))
     gp = GaussianProcessRegressor(k, alpha=0.0, n_restarts_optimizer=0).fit(X, y)
     assert -r.fun == pytest.approx(gp.log_marginal_likelihood_value_, rel=1e-5, abs=1e-5)
+
+
+@pytest.mark.parametrize("n,d,seed", [(1, 2, 7), (45, 3, 8), (130, 5, 9)])
+def test_dense_form_equals_c_oracle(orc, n, d, seed):
+    """The library-primitive form used at large sizes agrees with the C loops."""
+    X, y = _data(n, d, seed) if n > 1 else (np.array([[0.2, 0.9]]), np.array([0.7]))
+    ls = np.linspace(0.3, 0.8, d)
+    l1, g1 = orc.lml_grad(X, y, ls, 0.8, 4e-3)
+    l2, g2, kap = orc.lml_grad_dense(X, y, ls, 0.8, 4e-3)
+    assert l2 == pytest.approx(l1, rel=1e-11, abs=1e-11)
+    assert np.allclose(g2, g1, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(g1).max()))
+    assert kap >= 1.0 - 1e-12

@@ -22,6 +22,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -43,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned pre-screen measurement")
+    ap.add_argument("--no-mle", action="store_true", help="skip the hyperparameter-fit measurement")
+    ap.add_argument("--profile-mle", type=int, default=0, metavar="N",
+                    help="run two LML evaluations at N observations, d=20, for an ncu capture")
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
                     help="profiling case: one n=4096 fit and one scoring pass over M seeded candidates, no JSON")
     ap.add_argument("--profile-batched", action="store_true",
@@ -210,6 +215,51 @@ def surrogate_form(ctx, gpbo, W, dev, plain_value=None):
     net.free()
     model.free()
     return out
+
+
+# ---------------------------------------------------------------------------- hyperparameter fit
+def mle_form(ctx, W, dev, fp64_peak, starts=2, max_iter=15, evals=5):
+    """The LML and its gradient at n=4096, d=20 (the five-block workload's observations,
+    standardised), timed per evaluation with the K^-1 tile kernel's FP64 roofline, and a short
+    multi-start L-BFGS fit."""
+    import torch
+
+    w = W.config4()
+    ys = (w.y - w.y.mean()) / w.y.std()
+    X = torch.from_numpy(w.X).to(dev)
+    y = torch.from_numpy(ys).to(dev)
+    ctx.lml(X, y, w.lengthscale, 1.0, 1e-3)                     # warm
+    ctx.trace(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        lml, g = ctx.lml(X, y, w.lengthscale, 1.0, 1e-3)
+    te = (time.perf_counter() - t0) / evals
+    tr = ctx.trace_read()
+    ctx.trace(False)
+    lt = tr["lml"]
+    ach = lt["flops"] / (lt["ms"] / 1e3) / 1e12
+    lo, hi = W.mle_box(w.d)
+    t0s = W.mle_starts(2409, starts, w.d)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    th, best, ne = ctx.fit_mle(X, y, t0s, lo, hi, max_iter=max_iter, gtol=1e-5)
+    tf = time.perf_counter() - t0
+    return {"workload": f"LML + gradient over {w.d + 2} log hyperparameters, n={w.n}, d={w.d} (five-block "
+                        "observations, standardised); FP64 fit + K^-1 tiles fused into the gradient",
+            "value": round(1.0 / te, 2), "unit": "LML+gradient evaluations/s", "ms_per_eval": round(te * 1e3, 2),
+            "fit_ms_per_eval": round(tr["fit"]["ms"] / evals, 2),
+            "roofline": {"kernel": "k_lml_pairs", "bound": "fp64", "achieved": round(ach, 3),
+                         "peak": round(fp64_peak, 3), "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
+                         "peak_source": "FP64 DFMA throughput measured on this GPU by gpbo_probe_fma",
+                         "ms_per_launch": round(lt["ms"] / max(lt["intervals"], 1), 3)},
+            "lml_at_rule": lml,
+            "fit": {"starts": starts, "max_iter": max_iter, "evaluations": ne, "seconds": round(tf, 2),
+                    "lml_best": best, "lml_gain": best - lml,
+                    "lengthscale_range": [round(float(np.exp(th[:w.d]).min()), 4),
+                                          round(float(np.exp(th[:w.d]).max()), 4)],
+                    "signal_var": round(float(np.exp(th[w.d])), 4), "noise_var": float(np.exp(th[w.d + 1]))},
+            "timing": "host wall clock around synchronised calls; kernel time from events on the context stream"}
 
 
 # ---------------------------------------------------------------------------- ours
@@ -389,6 +439,8 @@ def run_ours(args, rank, world, local):
             # the speedup is at equal EI-argmax agreement when both paths pick the same candidate
             out["argmax_agrees_with_plain"] = bool(r["argmax"] == pr["argmax"])
             out["ei_max_rel_diff_vs_plain"] = abs(r["ei_max"] - pr["ei_max"]) / max(abs(pr["ei_max"]), 1e-300)
+        if not args.no_mle:
+            out.setdefault("forms", {})["mle"] = mle_form(ctx, W, dev, fp64_peak)
         if not args.no_surrogate and args.prec != "f32":
             out.setdefault("forms", {})["surrogate"] = surrogate_form(
                 ctx, gpbo, W, dev, out.get("plain", {}).get("value"))
@@ -490,6 +542,23 @@ def profile_surrogate(args):
     ctx.close()
 
 
+def profile_mle(args):
+    import torch
+
+    from paper_2403_08131_b300 import gpbo
+    from paper_2403_08131_b300 import workloads as W
+
+    ctx = gpbo.Context(0, torch.cuda.current_stream())
+    w = W.config4(n=args.profile_mle)
+    ys = (w.y - w.y.mean()) / w.y.std()
+    X = torch.from_numpy(w.X).cuda()
+    y = torch.from_numpy(ys).cuda()
+    for _ in range(2):
+        lml, g = ctx.lml(X, y, w.lengthscale, 1.0, 1e-3)
+    print(f"profile mle: n={w.n} lml={lml:.10g} |g|={float(np.abs(g).max()):.6g}")
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.profile_case:
@@ -500,6 +569,9 @@ def main():
         return
     if args.profile_batched:
         profile_batched(args)
+        return
+    if args.profile_mle:
+        profile_mle(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -102,8 +102,9 @@ const char *gpbo_strerror(int status);
 int64_t gpbo_launch_count(const gpbo_ctx *ctx);
 /* Per-phase device timing with CUDA events recorded on the context's stream around each
  * phase's kernels (phases: 0 fit, 1 cross-kernel + mean, 2 variance + EI + argmax,
- * 3 screen, 4 Cholesky trailing updates, 5 the K^-1 tiles of the likelihood gradient,
- * 2 x 64^2 flops per row of L^-1 reduced into a tile).  gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
+ * 3 screen, 4 Cholesky trailing updates, 5 the K^-1 tiles of the likelihood gradient:
+ * 2 (p + 1)(n - p) flops for row p of the lower triangle of L^-T L^-1).
+ * gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
  * gpbo_trace_read synchronises, then writes for each of the first nphase phases the total
  * milliseconds, the number of timed intervals, and the algorithmic flops the phase's
  * kernels were asked to do (variance: n(n+1) per candidate; cross-kernel: 3nd + 2n;

@@ -269,8 +269,9 @@ static int mle_eval(MleState &s, const double *theta, double *lml, double *grad)
     GPBO_TRY(fit_model(ctx, m, s.X, s.y));
     GPBO_TRY(trace_end(ctx));
     const int kend = (int)round_up(n, LBK);
+    // algorithmic flops: [K^-1]_pq for q <= p needs the n - p products of rows k >= p
     double flops = 0.0;
-    for (int I = 0; I < n_pad / LT; ++I) flops += (double)(I + 1) * 2.0 * LT * LT * (double)(kend - I * LT);
+    for (int p = 0; p < n; ++p) flops += 2.0 * (double)(p + 1) * (double)(n - p);
     GPBO_TRY(trace_begin(ctx, PH_LML, flops));
     k_lml_pairs<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, m->alpha64, n, d, n_pad, kend, m->s2, m->sn2,
                                                    s.ntiles, s.part);

@@ -34,6 +34,7 @@ STREAM_NOISE = 4
 STREAM_INIT = 5
 STREAM_SHAPES = 6
 STREAM_TRAIN = 7
+STREAM_MLE_STARTS = 8
 
 # Objective block codes (same numbering as the C ABI's gpbo_fn).
 FN_ACKLEY = 0
@@ -220,3 +221,25 @@ def batched_config3(seed: int = 2406, G: int = 64, M: int = 16384):
         obj = Objective([int(ds[g])], [fns[g % 3]], 0.01, seed * 1000 + g)
         out.append(make_gp_workload(f"sub{g}", seed * 1000 + g, int(ns[g]), obj, M, "f32"))
     return out
+
+
+def mle_box(d: int):
+    """Bounds on theta = (log l_1..l_d, log signal_var, log noise_var) for standardised y in
+    the unit cube: lengthscales 0.01..100, signal variance e^-3..e^3, noise variance
+    e^-14..1."""
+    lo = np.concatenate([np.full(d, math.log(0.01)), [-3.0, -14.0]])
+    hi = np.concatenate([np.full(d, math.log(100.0)), [3.0, 0.0]])
+    return lo, hi
+
+
+def mle_starts(seed: int, count: int, d: int) -> np.ndarray:
+    """Starting points of the multi-start hyperparameter fit: the rule's point
+    (lengthscale_rule, signal 1, noise 1e-3) first, then draws uniform in the log box
+    narrowed to lengthscales 0.05..5, signal e^-1..e^1, noise e^-10..e^-2 (stream 8)."""
+    base = np.concatenate([np.log(lengthscale_rule(d)), [0.0, math.log(1e-3)]])
+    if count <= 1:
+        return np.repeat(base[None, :], count, axis=0)
+    u = uniform_points(seed, STREAM_MLE_STARTS, count - 1, d + 2)
+    lo = np.concatenate([np.full(d, math.log(0.05)), [-1.0, -10.0]])
+    hi = np.concatenate([np.full(d, math.log(5.0)), [1.0, -2.0]])
+    return np.vstack([base, lo + u * (hi - lo)])

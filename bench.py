@@ -382,13 +382,21 @@ def run_ours(args, rank, world, local):
         var_traffic = round(2.2205e9 / 65536 * 131072) if args.prec == "f16" else None
         rl = [entry("variance", var_kernel, "tensor" if args.prec != "f32" else "fma",
                     tensor_peak, f"bf16_tflops_sustained ({src}): timed inside a long step under the power cap; "
-                    "FP16 kind::f16 runs at the BF16 rate", var_traffic),
-              # DRAM bytes of k_chol_update from the ncu capture of a 1225-tile launch at n=4096
-              # (42.27 MB, 34.5 KB per tile), times the mean tiles per launch of this step
-              # (41664 tiles in 62 launches after the lookahead column)
-              entry("chol_update", "k_chol_update", "fp64", fp64_peak,
-                    "FP64 DFMA throughput measured on this GPU by gpbo_probe_fma",
-                    round(42.27e6 / 1225 * 41664 / 62) if N_OBS == 4096 else None)]
+                    "FP16 kind::f16 runs at the BF16 rate", var_traffic)]
+        # the trailing updates of the n=4096 fit run on the tensor cores (FP64 accuracy by exact
+        # 8-bit slice products, 34 BF16 slice-pair products per FP64 product): the tensor roofline
+        # counts those BF16 flops against the sustained peak, with the FP64-equivalent rate
+        # against the FP64 pipe beside it
+        cu = tr["chol_update"]
+        if cu["ms"] > 0:
+            f64 = cu["flops"] / (cu["ms"] / 1e3) / 1e12
+            rl.append({"kernel": "k_chol_update_tc", "bound": "tensor", "achieved": round(34 * f64, 3),
+                       "peak": round(tensor_peak, 3), "unit": "TFLOP/s", "frac": round(34 * f64 / tensor_peak, 4),
+                       "peak_source": f"bf16_tflops_sustained ({src})",
+                       "fp64_equivalent_tflops": round(f64, 3), "fp64_pipe_peak": round(fp64_peak, 3),
+                       "fp64_equivalent_frac": round(f64 / fp64_peak, 3),
+                       "note": "includes the last few updates, which stay on the FP64 pipe (k_chol_update_slab)",
+                       "ms_per_step": round(cu["ms"] / args.steps, 3), "traffic": None})
         rl[0]["peak_burst"] = round(tensor_burst, 3)
         rl[0]["frac_burst"] = round(rl[0]["achieved"] / tensor_burst, 4)
         if args.prec != "f32" and "xkern" in tr and tr["xkern"]["ms"] > 0:

@@ -1,0 +1,318 @@
+// Trailing update of the FP64 Cholesky factorisation on the tensor cores (tcgen05), at FP64
+// accuracy, by exact products of 8-bit integer slices (the error-free splitting of Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59, 2012).
+//
+// Step kb of the right-looking factorisation subtracts P P^T from the trailing lower tiles,
+// P = L[rows below, block column kb] (64 columns).  Each row r of P is written as
+//     P_r = 2^(e_r - 7) (a_1 + 2^-8 a_2 + ... + 2^-48 a_7) + rest,    |a_s| <= 128 integers,
+// with e_r the exponent that puts the row's largest |entry| just below 2^e_r, a_1 = rint(2^7 x),
+// and each later slice the rounded remainder of the one before scaled by 2^8 (|rest| <=
+// 2^(e_r - 56)).  A slice is exact in BF16, a product of two is an integer below 2^14, and up to
+// 7 x 64 of them sum below 2^23: every partial sum of a tensor-core MMA with FP32 accumulation
+// is an exact integer, whatever the order or rounding mode.  Products of slices s and t carry
+// the weight 2^(e_r + e_c - 14 - 8 (s + t - 2)); the kernel keeps the 34 pairs with
+// s + t <= 9, summing each level s + t in its own FP32 accumulator (8 levels x 64 columns = 512
+// TMEM columns), and combines the levels exactly in int64 before two FP64 FMAs per element.  The terms left out weigh
+// below 2^-56 |P_r| |P_c| per product, and the result is within a small multiple of FP64
+// rounding of the exact P P^T (measured on Cholesky panels of the Matern kernel matrices: at
+// or below the error of an FP64 dot product, relative to |P_r| |P_c|).
+//
+//   k_chol_split      one warp per row of P: e_r and the seven BF16 slices, stored slice-major
+//                     (slice s, row r: 64 contiguous values, 128 bytes)
+//   k_chol_update_tc  one CTA per 128 x 64 output tile (two block rows, one block column) of
+//                     block columns kb+2 .. (the next column is updated on the side stream):
+//                     TMA of the 7 + 7 slice tiles (168 KiB), one thread issues 34 x 4 MMAs
+//                     (M = 128, N = 64, K = 16, BF16, FP32 accumulate), then 8 warps read the
+//                     8 accumulators back, combine them and subtract from A.
+// Every mbarrier wait is bounded; on timeout DEV_TIMEOUT is raised, the copies and MMAs the
+// CTA issued are waited for (bounded) and TMEM is freed before the CTA exits.
+#include "tc_common.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace gpbo {
+
+namespace ctc {
+
+constexpr int SLICES = 7;
+constexpr int LEVEL_MAX = 9;         // keep slice pairs s + t <= 9
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;  // one slice of the row strip
+constexpr int B_BYTES = BN * BK * 2;  // one slice of the column block
+constexpr int THREADS = 256;
+constexpr int TMEM_COLS = 512;
+constexpr size_t SMEM_BYTES = (size_t)SLICES * (A_BYTES + B_BYTES) + 1024 + 1024;
+
+struct Shared {
+    uint64_t full;
+    uint64_t done;
+    uint32_t tmem_base;
+    int abort;
+    int er[BM];
+    int ec[BN];
+};
+
+using namespace tcx;
+
+__global__ void __launch_bounds__(256) k_chol_split(const double *__restrict__ A, int n_pad, int kb, int r0,
+                                                    __nv_bfloat16 *__restrict__ slices, int *__restrict__ exps)
+{
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int r = r0 + warp;
+    if (r >= n_pad) return;
+    const double *row = A + (int64_t)r * n_pad + (int64_t)kb * NB;
+    const double2 v = *reinterpret_cast<const double2 *>(row + 2 * lane);
+    double mx = fmax(fabs(v.x), fabs(v.y));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+    double t0 = scalbn(v.x, 7 - e), t1 = scalbn(v.y, 7 - e);  // |x| < 1, times 2^7
+    for (int s = 0; s < SLICES; ++s) {
+        const double a0 = rint(t0), a1 = rint(t1);
+        __nv_bfloat162 p;
+        p.x = __double2bfloat16(a0);
+        p.y = __double2bfloat16(a1);
+        *reinterpret_cast<__nv_bfloat162 *>(slices + ((int64_t)s * n_pad + r) * BK + 2 * lane) = p;
+        t0 = (t0 - a0) * 256.0;
+        t1 = (t1 - a1) * 256.0;
+    }
+    if (lane == 0) exps[r] = e;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// x 2^k as a double, built on the integer pipe: normalise |x| by its leading zeros, write the
+// exponent with k folded in and the top 52 bits after the leading one (truncated: relative
+// error below 2^-52).  Values outside the normal range take scalbn.
+__device__ __forceinline__ double scaled_to_double(long long x, int k)
+{
+    if (x == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)x & 0x8000000000000000ull;
+    const unsigned long long ux = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const int lz = __clzll((long long)ux);
+    const int ex = 1023 + 63 - lz + k;
+    if (ex <= 0 || ex >= 2047) return scalbn((double)x, k);
+    const unsigned long long m = (ux << lz) >> 11;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
+struct Params {
+    double *A;
+    const int *exps;
+    unsigned *status;
+    int n_pad, nblk, b0;  // b0 = kb + 2: first block row / column of the update
+    uint32_t idesc;
+};
+
+// Tile t -> (strip i2, block column jb): strip i2 covers block rows b0 + 2 i2 and b0 + 2 i2 + 1
+// and meets block columns b0 .. min(b0 + 2 i2 + 1, nblk - 1).
+__device__ __forceinline__ void tile_coords(int t, int b0, int nblk, int &i2, int &jb)
+{
+    const int T2 = nblk - b0;
+    i2 = 0;
+    for (;; ++i2) {
+        const int c = min(2 * i2 + 2, T2);
+        if (t < c) break;
+        t -= c;
+    }
+    jb = b0 + t;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_chol_update_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, Params P)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char *tiles = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sa = tiles;                                 // SLICES x A_BYTES
+    unsigned char *sb = tiles + (size_t)SLICES * A_BYTES;      // SLICES x B_BYTES
+    Shared *sh = (Shared *)(sb + (size_t)SLICES * B_BYTES);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    int i2, jb;
+    tile_coords(blockIdx.x, P.b0, P.nblk, i2, jb);
+    const int row0 = (P.b0 + 2 * i2) * NB;  // first row of the strip
+    const int col0 = jb * NB;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&sh->full, 1);
+        mbar_init(&sh->done, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < BM; i += THREADS) sh->er[i] = row0 + i < P.n_pad ? P.exps[row0 + i] : 0;
+    for (int i = threadIdx.x; i < BN; i += THREADS) sh->ec[i] = P.exps[col0 + i];
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort_flag = &sh->abort;
+
+    bool issued = false;
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_a) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_b) : "memory");
+        mbar_arrive_expect_tx(&sh->full, SLICES * (A_BYTES + B_BYTES));
+        for (int s = 0; s < SLICES; ++s) {
+            tma_load_2d(sa + (size_t)s * A_BYTES, &map_a, 0, s * P.n_pad + row0, &sh->full);
+            tma_load_2d(sb + (size_t)s * B_BYTES, &map_b, 0, s * P.n_pad + col0, &sh->full);
+        }
+        if (mbar_wait(&sh->full, 0, abort_flag, P.status)) {
+            tc_fence_after();
+            for (int l = 2; l <= LEVEL_MAX; ++l) {
+                const uint32_t d = tmem + (uint32_t)((l - 2) * BN);
+                bool first = true;
+                for (int s = 1; s <= SLICES; ++s) {
+                    const int t = l - s;
+                    if (t < 1 || t > SLICES) continue;
+                    const unsigned char *a = sa + (size_t)(s - 1) * A_BYTES;
+                    const unsigned char *b = sb + (size_t)(t - 1) * B_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_f16(d, smem_desc(a + kk * 32), smem_desc(b + kk * 32), P.idesc, (first && kk == 0) ? 0u : 1u);
+                    first = false;
+                }
+            }
+            mma_commit(&sh->done);
+            issued = true;
+        } else {
+            *abort_flag = 1;
+            mbar_wait(&sh->full, 0, abort_flag, P.status, false);  // no copy left in flight
+        }
+    }
+
+    // ---------------- epilogue: all 8 warps; TMEM lane quadrant = warp % 4, column half = warp / 4.
+    // The accumulators hold exact integers below 2^23; they are read back as integers and folded
+    // by Horner in int64, levels 2..5 into hi and 6..9 into lo (each below 2^47, so exact).  Then
+    // C = hi 2^16 + floor(lo / 2^16) < 2^63 is the level sum times 2^40 to within one unit
+    // (2^-54 |P_r|max |P_c|max in A's units, below the terms already left out), and
+    // A -= C 2^(E - 40), E = e_r + e_c - 14, with the double built on the integer pipe: one FP64
+    // operation per element, since the FP64 pipe is the scarce one.
+    {
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const int r = row0 + row;
+        const int ib = r / NB;
+        const bool live = r < P.n_pad && ib >= jb;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16);
+        const bool got = mbar_wait_inl(&sh->done, 0, abort_flag, P.status);
+        if (__all_sync(0xffffffffu, got)) {
+            tc_fence_after();
+            const int er = sh->er[row];
+#pragma unroll 1
+            for (int g = 0; g < 2; ++g) {
+                const int c0 = half * 32 + g * 16;
+                long long hi[16], lo[16];
+                uint32_t v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hi[j] = __float2int_rn(__uint_as_float(v[j]));
+#pragma unroll 1
+                for (int l = 3; l <= 5; ++l) {
+                    tmem_ld16(taddr + (uint32_t)((l - 2) * BN + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) hi[j] = hi[j] * 256 + __float2int_rn(__uint_as_float(v[j]));
+                }
+                tmem_ld16(taddr + (uint32_t)(4 * BN + c0), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) lo[j] = __float2int_rn(__uint_as_float(v[j]));
+#pragma unroll 1
+                for (int l = 7; l <= LEVEL_MAX; ++l) {
+                    tmem_ld16(taddr + (uint32_t)((l - 2) * BN + c0), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) lo[j] = lo[j] * 256 + __float2int_rn(__uint_as_float(v[j]));
+                }
+                if (live) {
+                    double *dst = P.A + (int64_t)r * P.n_pad + col0 + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        double2 a = *reinterpret_cast<double2 *>(dst + j);
+                        const long long C0 = hi[j] * 65536 + (lo[j] >> 16), C1 = hi[j + 1] * 65536 + (lo[j + 1] >> 16);
+                        a.x -= scaled_to_double(C0, er + sh->ec[c0 + j] - 54);
+                        a.y -= scaled_to_double(C1, er + sh->ec[c0 + j + 1] - 54);
+                        *reinterpret_cast<double2 *>(dst + j) = a;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && issued) mbar_wait(&sh->done, 0, abort_flag, P.status, false);  // MMAs drained
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+}  // namespace ctc
+
+bool chol_tc_enabled(const gp_model *m) { return m->cslices != nullptr; }
+
+size_t chol_tc_slice_bytes(int n_pad) { return (size_t)ctc::SLICES * n_pad * ctc::BK * 2; }
+
+int chol_tc_maps(const gp_model *m, void *map_a, void *map_b)
+{
+    const uint64_t rows = (uint64_t)ctc::SLICES * m->n_pad;
+    GPBO_TRY(encode_2d_box((CUtensorMap *)map_a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->cslices, rows, ctc::BK, ctc::BM,
+                           ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
+    GPBO_TRY(encode_2d_box((CUtensorMap *)map_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->cslices, rows, ctc::BK, ctc::BN,
+                           ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
+    return GPBO_OK;
+}
+
+int64_t chol_tc_tiles(int nblk, int kb)
+{
+    const int T2 = nblk - (kb + 2);
+    int64_t t = 0;
+    for (int i2 = 0; 2 * i2 < T2; ++i2) t += std::min(2 * i2 + 2, T2);
+    return t;
+}
+
+// Split panel kb (rows of block rows kb+2 ..) and update block columns kb+2 .. on stream st.
+int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b)
+{
+    const int n_pad = m->n_pad, nblk = n_pad / NB;
+    if (kb + 2 >= nblk) return GPBO_OK;
+    static bool attr = false;
+    if (!attr) {
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(ctc::k_chol_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ctc::SMEM_BYTES));
+        attr = true;
+    }
+    const int r0 = (kb + 2) * NB, rows = n_pad - r0;
+    ctc::k_chol_split<<<(unsigned)cdiv64((int64_t)rows * 32, 256), 256, 0, st>>>(
+        m->L, n_pad, kb, r0, (__nv_bfloat16 *)m->cslices, m->cexps);
+    GPBO_LAUNCH_CHECK(ctx);
+    ctc::Params P;
+    P.A = m->L;
+    P.exps = m->cexps;
+    P.status = ctx->dev_status;
+    P.n_pad = n_pad;
+    P.nblk = nblk;
+    P.b0 = kb + 2;
+    P.idesc = tcx::idesc_f16(1u, ctc::BN, ctc::BM);
+    const int64_t tiles = chol_tc_tiles(nblk, kb);
+    ctc::k_chol_update_tc<<<(unsigned)tiles, ctc::THREADS, ctc::SMEM_BYTES, st>>>(
+        *(const CUtensorMap *)map_a, *(const CUtensorMap *)map_b, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+}  // namespace gpbo

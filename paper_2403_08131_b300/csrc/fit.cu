@@ -44,6 +44,9 @@ constexpr int DIAG_THREADS = 1024;
 // CTAs per SM) run as 16-row slabs.  Slabs for every launch measured the same (22.3 ms per
 // step): the update is FP64-bound, not wave-bound.
 constexpr int SLAB_BELOW = 6;
+// Models with the tensor-core update use it while at least CHOL_TC_MIN_T block columns remain
+// after the lookahead column; the last few small updates stay on the FP64 pipe.
+constexpr int CHOL_TC_MIN_T = 4;
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status)
 {
@@ -278,6 +281,10 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
+    // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
+    alignas(64) unsigned char tc_maps[2][128];
+    const bool tc = chol_tc_enabled(m);
+    if (tc) GPBO_TRY(chol_tc_maps(m, tc_maps[0], tc_maps[1]));
     for (int kb = 0; kb + 1 < nblk; ++kb) {
         const int T = nblk - kb - 1;
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));  // panel kb
@@ -294,11 +301,15 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
-                k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
-            else
-                k_chol_update_slab<<<(unsigned)(tiles * 4), 256, 0, st>>>(m->L, n_pad, kb, 2);
-            GPBO_LAUNCH_CHECK(ctx);
+            if (tc && T - 1 >= CHOL_TC_MIN_T) {
+                GPBO_TRY(chol_tc_update(ctx, m, kb, st, tc_maps[0], tc_maps[1]));
+            } else {
+                if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
+                    k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
+                else
+                    k_chol_update_slab<<<(unsigned)(tiles * 4), 256, 0, st>>>(m->L, n_pad, kb, 2);
+                GPBO_LAUNCH_CHECK(ctx);
+            }
             GPBO_TRY(trace_end(ctx));
             GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }

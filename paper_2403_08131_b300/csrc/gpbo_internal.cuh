@@ -110,6 +110,8 @@ struct gp_model {
     void *Linv16 = nullptr;     // F16: L^-1 rounded; BF16: hi = bf16(L^-1) then lo = bf16(L^-1 - hi)
     void *Zsplit = nullptr;     // 16-bit models, d <= 32: n_pad x 128 FP16 [hi | lo | hi | 0] of (x - 1/2) / l
     float *nb32 = nullptr;      // 16-bit models: |(x_i - 1/2) / l|^2
+    void *cslices = nullptr;    // n_pad >= CHOL_TC_MIN_NPAD: 7 BF16 slices of a Cholesky panel, slice-major
+    int *cexps = nullptr;       // their per-row exponents
 };
 
 namespace gpbo {
@@ -146,6 +148,15 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
 
 // xkern_tc.cu: the cross-kernel on tensor cores for 16-bit models with d <= 32.
 int xkern_tc_prepare(gpbo_ctx *ctx, gp_model *m);
+
+// chol_tc.cu: trailing updates of the Cholesky factorisation on the tensor cores at FP64
+// accuracy (exact 8-bit slice products), for models with n_pad >= CHOL_TC_MIN_NPAD.
+constexpr int CHOL_TC_MIN_NPAD = 1536;
+bool chol_tc_enabled(const gp_model *m);
+size_t chol_tc_slice_bytes(int n_pad);
+int chol_tc_maps(const gp_model *m, void *map_a, void *map_b);  // two 128-byte CUtensorMap
+int64_t chol_tc_tiles(int nblk, int kb);
+int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b);
 bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
              float *mu);

@@ -29,6 +29,22 @@ def test_fit_factor_and_alpha_match_oracle(ctx, orc, n, d, prec):
     m.free()
 
 
+@pytest.mark.parametrize("n,d,prec", [(1536, 20, "f64"), (2000, 8, "f16"), (2113, 20, "f32")])
+def test_fit_tensor_core_update_matches_oracle(ctx, orc, n, d, prec):
+    """n_pad >= 1536: the trailing updates run on the tensor cores (exact 8-bit slice
+    products); L and alpha keep the FP64 bars."""
+    from tests._util import to_dev
+    X, y = _obs(n, d, 1100 + n)
+    ls = W.lengthscale_rule(d)
+    m = ctx.fit(to_dev(X), to_dev(y), ls, 1.0, 1e-4, prec=prec)
+    Lg, ag = m.read()
+    _, Lo, ao = orc.gp_fit(X, y, ls, 1.0, 1e-4)
+    assert np.abs(Lg - Lo).max() <= 1e-11 * np.abs(Lo).max()
+    assert np.abs(ag - ao).max() <= 1e-9 * (np.abs(ao).max() + 1)
+    assert np.all(np.triu(Lg, 1) == 0)
+    m.free()
+
+
 def test_fit_host_pointers_equal_device(ctx):
     from tests._util import to_dev
     X, y = _obs(200, 5, 7)

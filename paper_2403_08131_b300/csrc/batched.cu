@@ -101,11 +101,18 @@ __global__ void __launch_bounds__(256) b_chol_diag(const BProb *P, double *L, do
     k_chol_diag_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, status, 0, 0);
 }
 
+__global__ void __launch_bounds__(128) b_chol_inv(const BProb *P, const double *L, double *Dinv, int kb)
+{
+    const BProb &p = P[blockIdx.y];
+    if (kb >= p.nblk) return;
+    k_chol_inv_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x);
+}
+
 __global__ void __launch_bounds__(256) b_chol_panel(const BProb *P, double *L, const double *Dinv, int kb)
 {
     const BProb &p = P[blockIdx.y];
     const int T = p.nblk - kb - 1;
-    if (T <= 0 || (int)blockIdx.x >= T * (NB / 16)) return;
+    if (T <= 0 || (int)blockIdx.x >= T * (NB / 4)) return;
     k_chol_panel_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x, 0);
 }
 
@@ -431,7 +438,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
 {
     const int G = pl->G;
     const BProb *P = pl->probs_dev;
-    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1);
+    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
     b_standardize<<<G, 1024, 0, st>>>(P, pl->dy, pl->dys, pl->tau);
     b_scale_x<<<dim3(gb(pl->max_dn), G), 256, 0, st>>>(P, pl->dX, pl->lsinv, pl->Xs64, pl->Xs32);
     b_kmat<<<dim3(pl->max_npad / 32, pl->max_npad / 32, G), dim3(32, 8), 0, st>>>(P, pl->Xs64, pl->K);
@@ -445,16 +452,18 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     const int NBL = pl->max_nblk;
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_fork, 0));
-    b_chol_diag<<<dim3(1, G), 256, smem2, s2>>>(P, pl->L, pl->Dinv, 0, ctx->dev_status);
-    if (NBL > 1) b_chol_panel<<<dim3((NBL - 1) * (NB / 16), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, 0);
+    b_chol_diag<<<dim3(1, G), 256, smem1, s2>>>(P, pl->L, pl->Dinv, 0, ctx->dev_status);
+    b_chol_inv<<<dim3(NB / 4, G), 128, 0, s2>>>(P, pl->L, pl->Dinv, 0);
+    if (NBL > 1) b_chol_panel<<<dim3((NBL - 1) * (NB / 4), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, 0);
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
     for (int kb = 0; kb + 1 < NBL; ++kb) {
         const int T = NBL - kb - 1;
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_rest, 0));
         b_chol_update<<<dim3((unsigned)T, G), 256, smem2, s2>>>(P, pl->L, kb, 1);
-        b_chol_diag<<<dim3(1, G), 256, smem2, s2>>>(P, pl->L, pl->Dinv, kb + 1, ctx->dev_status);
-        if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 16), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
+        b_chol_diag<<<dim3(1, G), 256, smem1, s2>>>(P, pl->L, pl->Dinv, kb + 1, ctx->dev_status);
+        b_chol_inv<<<dim3(NB / 4, G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
+        if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
         if (T > 1) {
             b_chol_update<<<dim3((unsigned)((int64_t)T * (T - 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb, 2);

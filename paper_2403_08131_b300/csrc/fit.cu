@@ -36,14 +36,14 @@ __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, d
     k_kmat_body(Xs, n, d, n_pad, s2, sn2, K, blockIdx.x, blockIdx.y);
 }
 
-// 1024 threads (31 warps share each column's pass; the arithmetic per element does not depend
-// on the count).  The kernel is bound by the FP64 pipe and the pivot's dependent chain: about
-// 90 us at 256 or 1024 threads, with or without a cheap pivot (measured).
+// Blocked diagonal factor: warp 0 factors each 16 x 16 sub-block; the other threads share the
+// panel solve and the trailing update (the arithmetic per element does not depend on the count).
 constexpr int DIAG_THREADS = 1024;
 // Trailing updates of fewer than SLAB_BELOW x SMs whole 64 x 64 tiles (two waves at three
 // CTAs per SM) run as 16-row slabs.  Slabs for every launch measured the same (22.3 ms per
 // step): the update is FP64-bound, not wave-bound.
 constexpr int SLAB_BELOW = 6;
+constexpr int SLAB_ROWS = 4;
 // Models with the tensor-core update use it while at least CHOL_TC_MIN_T block columns remain
 // after the lookahead column; the last few small updates stay on the FP64 pipe.
 constexpr int CHOL_TC_MIN_T = 4;
@@ -51,6 +51,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double *__restrict__
                                                    double *__restrict__ Dinv, unsigned *status)
 {
     k_chol_diag_body(A, n_pad, kb, Dinv, status, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(128) k_chol_inv(const double *__restrict__ A, int n_pad, int kb,
+                                                  double *__restrict__ Dinv)
+{
+    k_chol_inv_body(A, n_pad, kb, Dinv, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
@@ -64,9 +70,10 @@ __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int
     k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y, part);
 }
 
-__global__ void __launch_bounds__(256) k_chol_update_slab(double *__restrict__ A, int n_pad, int kb, int part)
+__global__ void __launch_bounds__(256) k_chol_update_slab(double *__restrict__ A, int n_pad, int kb, int part,
+                                                          int t0)
 {
-    k_chol_update_slab_body(A, n_pad, kb, blockIdx.x, part);
+    k_chol_update_slab_body<SLAB_ROWS>(A, n_pad, kb, blockIdx.x, part, t0);
 }
 
 __global__ void k_zero_upper_blocks(double *__restrict__ A, int n_pad)
@@ -262,22 +269,25 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
     }
     GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
-    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1);
+    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
     // Right-looking blocked factorisation with a lookahead of one block column: the update
-    // of block column kb+1 by panel kb, the factorisation of its diagonal block and its panel
-    // run on the high-priority side stream while the rest of step kb's trailing update runs
-    // on the main stream.  The two touch disjoint tiles; column kb+2 is updated by the side
-    // stream only after the main stream's step-kb update (event ev_rest).
+    // of block column kb+1 by panel kb, the factorisation of its diagonal block, its inverse
+    // and its panel run on the high-priority side stream (the chain every step waits on)
+    // while the rest of step kb's trailing update runs on the main stream.  The two touch
+    // disjoint tiles; column kb+2 is updated by the side stream only after the main stream's
+    // step-kb update (event ev_rest).
     cudaStream_t side = nullptr;
     GPBO_TRY(side_stream(ctx, &side));
     cudaEvent_t ev_fork = ctx->side_ev[0], ev_panel = ctx->side_ev[1], ev_rest = ctx->side_ev[2],
                 ev_join = ctx->side_ev[3];
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
-    k_chol_diag<<<1, DIAG_THREADS, smem2, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
+    k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
+    GPBO_LAUNCH_CHECK(ctx);
+    k_chol_inv<<<NB / 4, 128, 0, side>>>(m->L, n_pad, 0, m->Dinv);
     GPBO_LAUNCH_CHECK(ctx);
     if (nblk > 1) {
-        k_chol_panel<<<(nblk - 1) * (NB / 16), 256, 0, side>>>(m->L, n_pad, 0, m->Dinv);
+        k_chol_panel<<<(nblk - 1) * (NB / 4), 256, 0, side>>>(m->L, n_pad, 0, m->Dinv);
         GPBO_LAUNCH_CHECK(ctx);
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
@@ -289,12 +299,14 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         const int T = nblk - kb - 1;
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));  // panel kb
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));  // step kb-1 done with column kb+1
-        k_chol_update_slab<<<T * 4, 256, 0, side>>>(m->L, n_pad, kb, 1);
+        k_chol_update_slab<<<T * (NB / SLAB_ROWS), 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
         GPBO_LAUNCH_CHECK(ctx);
-        k_chol_diag<<<1, DIAG_THREADS, smem2, side>>>(m->L, n_pad, kb + 1, m->Dinv, ctx->dev_status);
+        k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, kb + 1, m->Dinv, ctx->dev_status);
+        GPBO_LAUNCH_CHECK(ctx);
+        k_chol_inv<<<NB / 4, 128, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
         GPBO_LAUNCH_CHECK(ctx);
         if (T > 1) {
-            k_chol_panel<<<(T - 1) * (NB / 16), 256, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
+            k_chol_panel<<<(T - 1) * (NB / 4), 256, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
             GPBO_LAUNCH_CHECK(ctx);
         }
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
@@ -307,7 +319,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
                 if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
                     k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
                 else
-                    k_chol_update_slab<<<(unsigned)(tiles * 4), 256, 0, st>>>(m->L, n_pad, kb, 2);
+                    k_chol_update_slab<<<(unsigned)(tiles * (NB / SLAB_ROWS)), 256, 0, st>>>(m->L, n_pad, kb, 2, 0);
                 GPBO_LAUNCH_CHECK(ctx);
             }
             GPBO_TRY(trace_end(ctx));

@@ -65,133 +65,144 @@ __device__ __forceinline__ void k_kmat_body(const double *__restrict__ Xs, int n
 }
 
 // ------------------------------------------------------------------ Cholesky
-// Diagonal block kb: factor the 64x64 block in place (right-looking, column by column) and
-// build its inverse X alongside (written to Dinv_kb; L_kk gets zeros above the diagonal).
-// Pass j applies the rank-1 updates with column j of L (already scaled by 1 / L_jj) to the
-// trailing lower triangle of the block and to the rows of X below j:
-//     a_ic -= l_ij l_cj  (j < c <= i),        x_kc -= l_kj x_jc  (k > j, c <= j),
-// enumerated as one index range (the triangle from a column-major table, the rectangle
-// row-major by multiply-shift division) so that every lane of warps 1.. has an element.
-// Warp 0 meanwhile finishes a_{j+1,j+1} and takes the next pivot, L_{j+1,j+1} = p rsqrt(p)
-// with 1/L_{j+1,j+1} = rsqrt(p), and publishes it through a shared flag.  The elements of
-// column j+1 and of row j+1 of X come last in the range: their owners wait (bounded) for the
-// flag and store them scaled, so one barrier per column suffices.  The factor's arithmetic per
-// element is that of a plain right-looking loop.
+// Diagonal block kb: factor the 64x64 block in place, blocked by 16 columns, with every element
+// taking the FMAs of a right-looking column-by-column factorisation in the same order (so the
+// factor is the same bit for bit):  a_ic -= l_it l_ct for t = 0, 1, .. (t < c <= i), and
+// l_ij = a_ij / L_jj with the pivot L_jj = p rsqrt(p), 1 / L_jj = rsqrt(p), p = a_jj.
+// For each 16-column panel: warp 0 factors the 16 x 16 diagonal sub-block column by column
+// (warp-synchronous); one thread per row below solves its 16 panel entries in order; then
+// all threads apply the panel's 16 columns to the trailing lower triangle, one element at a
+// time in t order.  Four barriers per panel instead of one per column.  The reciprocal pivots
+// go to the diagonal of Dinv_kb; k_chol_inv builds the rest of the inverse for the panel.
 __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status, const int bx, const int by)
 {
     extern __shared__ double sm[];
     double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    double(*x)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm + NB * (NB + 1));
-    constexpr int TRI = NB * (NB + 1) / 2;
-    __shared__ double rdiag[NB];
-    __shared__ uint16_t tab[TRI];  // lower triangle, column-major: row | col << 8
-    __shared__ int ready;          // highest column whose pivot is published
-    const int tid = threadIdx.x;
+    __shared__ double rd[NB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
-    auto coff = [](int c) { return c * NB - c * (c - 1) / 2; };  // first entry of column c
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         a[r][c] = A[base + (int64_t)r * n_pad + c];
-        x[r][c] = r == c ? 1.0 : 0.0;
-    }
-    for (int e = tid; e < TRI; e += blockDim.x) {
-        // column c: the largest with coff(c) <= e (closed form, then exact integer fix-up)
-        int c = (int)((129.0f - sqrtf(16641.0f - 8.0f * (float)e)) * 0.5f);
-        c = max(0, min(NB - 1, c));
-        while (c > 0 && coff(c) > e) --c;
-        while (c < NB - 1 && coff(c + 1) <= e) ++c;
-        tab[e] = (uint16_t)((c + (e - coff(c))) | (c << 8));
     }
     __syncthreads();
-    if (tid == 0) {
-        double p = a[0][0];
-        if (!(p > 0.0)) {
-            atomicOr(status, DEV_NOTSPD);
-            p = 1.0;
-        }
-        const double r = rsqrt(p);
-        a[0][0] = p * r;
-        rdiag[0] = r;
-        x[0][0] = r;
-        ready = 0;
-    }
-    __syncthreads();
-    if (tid > 0 && tid < NB) a[tid][0] *= rdiag[0];
-    __syncthreads();
-    volatile int *vready = &ready;
-    volatile double *vrdiag = rdiag;
-    for (int j = 0; j + 1 < NB; ++j) {
-        const int m = NB - 1 - j;                      // rows below j
-        const int nF = TRI - coff(j + 2);              // triangle, columns >= j+2
-        const int nX = (m - 1) * (j + 1);              // X rows >= j+2, columns <= j
-        const int nT = nF + nX + (m - 1) + (j + 1);    // + column j+1 below its diagonal + X row j+1
-        const uint32_t w = (uint32_t)(j + 1);
-        const uint64_t magic = ((1ull << 32) + w - 1) / w;
-        if (tid == 0) {
-            double p = fma(-a[j + 1][j], a[j + 1][j], a[j + 1][j + 1]);
-            if (!(p > 0.0)) {
-                atomicOr(status, DEV_NOTSPD);
-                p = 1.0;
-            }
-            const double rr = rsqrt(p);
-            a[j + 1][j + 1] = p * rr;
-            x[j + 1][j + 1] = rr;
-            vrdiag[j + 1] = rr;
-            __threadfence_block();
-            *vready = j + 1;
-        }
-        for (int e = tid - 32; e < nT; e += (int)blockDim.x - 32) {
-            if (tid < 32) break;
-            if (e < nF) {
-                const int t = tab[coff(j + 2) + e], i = t & 255, c = t >> 8;
-                a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-            } else if (e < nF + nX) {
-                const uint32_t q = (uint32_t)(e - nF);
-                const int k = j + 2 + (int)(((uint64_t)q * magic) >> 32);
-                const int c = (int)(q - (uint32_t)(k - j - 2) * w);
-                x[k][c] = fma(-a[k][j], x[j][c], x[k][c]);
-            } else {
-                // last: elements that pass j makes final; store them scaled by 1 / L_{j+1,j+1}
-                const int q = e - nF - nX;
-                double v;
-                if (q < m - 1) v = fma(-a[j + 2 + q][j], a[j + 1][j], a[j + 2 + q][j + 1]);
-                else v = fma(-a[j + 1][j], x[j][q - (m - 1)], x[j + 1][q - (m - 1)]);
-                for (int it = 0; *vready < j + 1; ++it) {
-                    if (it == (1 << 24)) {  // cannot happen: warp 0 publishes unconditionally
-                        atomicOr(status, DEV_TIMEOUT);
-                        break;
+    constexpr int PW = 16;
+    for (int c0 = 0; c0 < NB; c0 += PW) {
+        if (warp == 0) {
+            for (int j = c0; j < c0 + PW; ++j) {
+                if (lane == 0) {
+                    double p = a[j][j];
+                    if (!(p > 0.0)) {
+                        atomicOr(status, DEV_NOTSPD);
+                        p = 1.0;
                     }
+                    const double r = rsqrt(p);
+                    a[j][j] = p * r;
+                    rd[j] = r;
                 }
-                __threadfence_block();
-                const double rr = vrdiag[j + 1];
-                if (q < m - 1) a[j + 2 + q][j + 1] = v * rr;
-                else x[j + 1][q - (m - 1)] = v * rr;
+                __syncwarp();
+                const int i = j + 1 + lane;
+                if (i < c0 + PW) a[i][j] *= rd[j];
+                __syncwarp();
+                // the sub-block's trailing triangle j < c <= i < c0 + PW, row-major
+                const int m = c0 + PW - 1 - j;
+                for (int e = lane; e < m * (m + 1) / 2; e += 32) {
+                    int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                    while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+                    while (ii * (ii + 1) / 2 > e) --ii;
+                    const int cc = e - ii * (ii + 1) / 2;
+                    const int r = j + 1 + ii, c = j + 1 + cc;
+                    a[r][c] = fma(-a[r][j], a[c][j], a[r][c]);
+                }
+                __syncwarp();
             }
+        }
+        __syncthreads();
+        const int nr = NB - c0 - PW;
+        if (nr == 0) break;
+        if (tid < nr) {
+            const int r = c0 + PW + tid;
+            double y[PW];
+#pragma unroll
+            for (int jj = 0; jj < PW; ++jj) {
+                double s = a[r][c0 + jj];
+#pragma unroll
+                for (int t = 0; t < jj; ++t) s = fma(-y[t], a[c0 + jj][c0 + t], s);
+                y[jj] = s * rd[c0 + jj];
+                a[r][c0 + jj] = y[jj];
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * (nr + 1) / 2; e += blockDim.x) {
+            int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+            while (ii * (ii + 1) / 2 > e) --ii;
+            const int r = c0 + PW + ii, c = c0 + PW + (e - ii * (ii + 1) / 2);
+            double v = a[r][c];
+#pragma unroll
+            for (int t = 0; t < PW; ++t) v = fma(-a[r][c0 + t], a[c][c0 + t], v);
+            a[r][c] = v;
         }
         __syncthreads();
     }
     double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, c = e % NB;
+        const int i = e / NB, c = e % NB;
         A[base + (int64_t)i * n_pad + c] = c <= i ? a[i][c] : 0.0;
-        D[e] = x[i][c];
     }
+    if (tid < NB) D[tid * NB + tid] = rd[tid];
 }
 
-// Trailing update in 16-row slabs (4 CTAs per 64x64 tile), for launches too small to fill the
-// GPU with whole tiles.  part 1: block column kb+1 (T tiles: CTA bx updates rows
-// 16 (bx % 4) .. +15 of block row kb+1+bx/4); part 2: block columns kb+2 .. (the tiles of
-// k_chol_update part 2, in the same order, 4 slabs each).  Same per-element arithmetic as
-// the full-tile update.
-__device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, int n_pad, int kb, const int bx,
-                                                          int part = 1)
+// Inverse X = L_kk^-1 of diagonal block kb (after k_chol_diag_body), by forward substitution of
+// the unit columns, one warp per column (CTA bx: columns 4 bx .. 4 bx + 3), lanes owning rows
+// lane and lane + 32.  With rd_t = 1 / L_tt (the pivot's rsqrt, from Dinv's diagonal) and the
+// scaled columns l'_it = l_it rd_t, the unscaled solution x~ takes x~_ic -= l'_it x~_tc for
+// t = c .. i - 1, and X_ic = rd_i x~_ic: one shuffle and one or two FP64 FMAs per step (on this
+// part every FP64 warp instruction holds its SMSP's FP64 unit for 64 cycles, so the step count
+// of this chain is what the factorisation waits on).  Launch: 16 CTAs of 128 threads.
+__device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, int n_pad, int kb,
+                                                  double *__restrict__ Dinv, const int bx)
 {
-    __shared__ double li[16][NB + 1];
+    __shared__ double l[NB][NB + 1];
+    __shared__ double rd[NB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
+    double *D = Dinv + (int64_t)kb * NB * NB;
+    if (tid < NB) rd[tid] = D[tid * NB + tid];
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, t = e % NB;
+        l[i][t] = t < i ? A[base + (int64_t)i * n_pad + t] * rd[t] : 0.0;
+    }
+    __syncthreads();
+    const int c = bx * 4 + warp;
+    double x0 = lane == c ? 1.0 : 0.0, x1 = lane + 32 == c ? 1.0 : 0.0;
+    for (int t = c; t < NB; ++t) {
+        const double v = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
+        if (t < 31 && lane > t) x0 = fma(-l[lane][t], v, x0);
+        if (lane + 32 > t) x1 = fma(-l[lane + 32][t], v, x1);
+    }
+    D[lane * NB + c] = x0 * rd[lane];   // zero above the diagonal (rows < c never change)
+    D[(lane + 32) * NB + c] = x1 * rd[lane + 32];
+}
+
+// Trailing update in slabs of SR rows (64 / SR CTAs per 64x64 tile), for launches too small to
+// fill the GPU with whole tiles: on this part a CTA's FP64 work sets its latency, so short
+// slabs keep the late, small updates short.  part 1: block column kb+1 from tile t0 on (CTA bx
+// updates rows SR (bx % (64 / SR)) .. of block row kb+1+t0+bx/(64/SR)); part 2: block columns
+// kb+2 .. (the tiles of k_chol_update part 2, in the same order).  Same per-element arithmetic
+// as the full-tile update.
+template <int SR>
+__device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, int n_pad, int kb, const int bx,
+                                                          int part = 1, int t0 = 0)
+{
+    constexpr int PER = NB / SR;
+    __shared__ double li[SR][NB + 1];
     __shared__ double lj[NB][NB + 1];
-    int ii = bx / 4, jj = 0;
+    int ii = t0 + bx / PER, jj = 0;
     if (part == 2) {
-        const int64_t p = bx / 4;
+        const int64_t p = bx / PER;
         ii = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
         while ((int64_t)(ii + 1) * (ii + 2) / 2 <= p) ++ii;
         while ((int64_t)ii * (ii + 1) / 2 > p) --ii;
@@ -200,46 +211,41 @@ __device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, 
         ++jj;
     }
     const int ib = kb + 1 + ii, jb = kb + 1 + jj;
-    const int64_t r0 = (int64_t)ib * NB + (bx % 4) * 16;
+    const int64_t r0 = (int64_t)ib * NB + (bx % PER) * SR;
     const int tid = threadIdx.x, tx = tid % 64, ty = tid / 64;
-    for (int e = tid; e < 16 * NB; e += blockDim.x)
+    for (int e = tid; e < SR * NB; e += blockDim.x)
         li[e / NB][e % NB] = A[(r0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
     for (int e = tid; e < NB * NB; e += blockDim.x)
         lj[e / NB][e % NB] = A[((int64_t)jb * NB + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
     __syncthreads();
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[SR / 4];
+#pragma unroll
+    for (int u = 0; u < SR / 4; ++u) acc[u] = 0.0;
     for (int t = 0; t < NB; ++t) {
         const double y = lj[tx][t];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(li[ty + 4 * u][t], y, acc[u]);
+        for (int u = 0; u < SR / 4; ++u) acc[u] = fma(li[ty + 4 * u][t], y, acc[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) A[(r0 + ty + 4 * u) * n_pad + (int64_t)jb * NB + tx] -= acc[u];
+    for (int u = 0; u < SR / 4; ++u) A[(r0 + ty + 4 * u) * n_pad + (int64_t)jb * NB + tx] -= acc[u];
 }
 
-// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, one CTA per 16-row slab so that
-// the short panels at the end of the factorisation still spread over many SMs.
+// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, four rows per CTA (thread = row ty,
+// column tx; L_kk^-T is lower, so t <= tx), so that short panels still spread over many SMs.
 __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv, const int bx, const int by)
 {
-    __shared__ double a[16][NB + 1];
+    __shared__ double a[4][NB + 1];
     __shared__ double dv[NB][NB + 1];
-    const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)bx * 16;
-    const int tid = threadIdx.x, tx = tid % 64, ty = tid / 64;
+    const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)bx * 4;
+    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
     const double *D = Dinv + (int64_t)kb * NB * NB;
-    for (int e = tid; e < 16 * NB; e += blockDim.x)
-        a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
+    for (int e = tid; e < 4 * NB; e += blockDim.x) a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
     for (int e = tid; e < NB * NB; e += blockDim.x) dv[e / NB][e % NB] = D[e];
     __syncthreads();
-    // thread (ty, tx): rows ty, ty+4, ty+8, ty+12; column tx; L_kk^-T is lower, so t <= tx
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = 0; t <= tx; ++t) {
-        const double y = dv[tx][t];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fma(a[ty + 4 * u][t], y, acc[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) A[(row0 + ty + 4 * u) * n_pad + (int64_t)kb * NB + tx] = acc[u];
+    double acc = 0.0;
+    for (int t = 0; t <= tx; ++t) acc = fma(a[ty][t], dv[tx][t], acc);
+    A[(row0 + ty) * n_pad + (int64_t)kb * NB + tx] = acc;
 }
 
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.

@@ -247,7 +247,9 @@ int interdep_screen(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const scree
  * z-score y (population std, 1 when zero), fit on (X, y'), score the M candidates (Xc, or
  * drawn from seed when Xc is NULL) with EI below tau = min y', and return the EI argmax:
  * x_next (host, d doubles), ei_max (host, standardised units), argmax (host, may be NULL).
- * flags: GPBO_HOST_PTRS applies to X, y and Xc.  Synchronises. */
+ * flags: GPBO_HOST_PTRS applies to X, y and Xc.  The context keeps the step's model and
+ * staging buffers for its next search_step of the same n, d and precision (a BO loop calls
+ * it repeatedly), and frees them on a shape change or in gpbo_destroy.  Synchronises. */
 int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp,
                 const float *Xc, int64_t M, uint64_t seed, double xi, gpbo_prec prec, unsigned flags,
                 double *x_next, double *ei_max, int64_t *argmax);

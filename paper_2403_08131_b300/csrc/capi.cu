@@ -173,13 +173,12 @@ int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out)
     return GPBO_OK;
 }
 
-// Fit with optional jitter escalation.  X and y are device pointers here.
-static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp, int prec,
-                    unsigned flags, gp_model **out)
+// Fit model m (allocated for this n, d, prec) with optional jitter escalation.  X and y are
+// device pointers here.
+static int fit_run(gpbo_ctx *ctx, gp_model *m, const double *X, const double *y, const gp_hyper *hyp, unsigned flags)
 {
-    gp_model *m = nullptr;
-    int st = model_create(ctx, n, d, prec, &m);
-    if (st != GPBO_OK) return st;
+    const int n = m->n, d = m->d;
+    int st = GPBO_OK;
     m->s2 = hyp->signal_var;
     m->sn2 = hyp->noise_var;
     for (int k = 0; k < d; ++k) m->ls[k] = hyp->lengthscale[k];
@@ -196,8 +195,19 @@ static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int 
         if (s2 != GPBO_OK) { st = s2; break; }
         if (st == GPBO_OK) break;
     }
+    if (st != GPBO_OK) cudaStreamSynchronize(ctx->stream);
+    return st;
+}
+
+// Allocate and fit a new model.
+static int fit_impl(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp, int prec,
+                    unsigned flags, gp_model **out)
+{
+    gp_model *m = nullptr;
+    int st = model_create(ctx, n, d, prec, &m);
+    if (st != GPBO_OK) return st;
+    st = fit_run(ctx, m, X, y, hyp, flags);
     if (st != GPBO_OK) {
-        cudaStreamSynchronize(ctx->stream);
         model_free(m);
         return st;
     }
@@ -274,6 +284,8 @@ int gpbo_destroy(gpbo_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->batch_plan) batch_plan_free(ctx->batch_plan);
+    if (ctx->step_model) model_free(ctx->step_model);
+    if (ctx->step_buf) cudaFree(ctx->step_buf);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dev_status) cudaFree(ctx->dev_status);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -498,10 +510,19 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
     // private device staging: X, y, standardised y, tau, and (host) candidates
     const bool host = flags & GPBO_HOST_PTRS;
     if (host && (!finite_all(X, (int64_t)n * d) || !finite_all(y, n))) return GPBO_ENAN;
-    double *buf = nullptr;
+    // the staging buffer and the model stay with the context for the next call of this shape
     float *dXc = nullptr;
     const size_t nd = (size_t)n * d;
-    GPBO_CUDA_TRY(cudaMalloc(&buf, sizeof(double) * (nd + 2 * (size_t)n + 2 + GPBO_MAX_D)));
+    const size_t buf_bytes = sizeof(double) * (nd + 2 * (size_t)n + 2 + GPBO_MAX_D);
+    if (ctx->step_buf_bytes < buf_bytes) {
+        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (ctx->step_buf) GPBO_CUDA_TRY(cudaFree(ctx->step_buf));
+        ctx->step_buf = nullptr;
+        ctx->step_buf_bytes = 0;
+        GPBO_CUDA_TRY(cudaMalloc(&ctx->step_buf, buf_bytes));
+        ctx->step_buf_bytes = buf_bytes;
+    }
+    double *buf = (double *)ctx->step_buf;
     double *dX = buf, *dy = buf + nd, *ys = dy + n, *tau = ys + n;
     float *xsel = (float *)(tau + 2);
     int st = GPBO_OK;
@@ -519,7 +540,15 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
         dXc = const_cast<float *>(Xc);
     }
     if (st == GPBO_OK) st = standardize_dev(ctx, dy, n, ys, tau);
-    if (st == GPBO_OK) st = fit_impl(ctx, dX, ys, n, d, hyp, prec, flags & ~GPBO_HOST_PTRS, &m);
+    m = ctx->step_model;
+    if (st == GPBO_OK && (!m || m->n != n || m->d != d || m->prec != prec)) {
+        cudaStreamSynchronize(ctx->stream);
+        if (m) model_free(m);
+        m = ctx->step_model = nullptr;
+        st = model_create(ctx, n, d, prec, &m);
+        if (st == GPBO_OK) ctx->step_model = m;
+    }
+    if (st == GPBO_OK) st = fit_run(ctx, m, dX, ys, hyp, flags & ~GPBO_HOST_PTRS);
     int64_t am = -1;
     double em = 0.0;
     if (st == GPBO_OK) st = score_model(ctx, m, dXc, M, seed, 0.0, tau, xi, nullptr, nullptr, nullptr, &am, &em);
@@ -536,9 +565,7 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
         if (argmax) *argmax = am;
     }
     cudaStreamSynchronize(ctx->stream);
-    if (m) model_free(m);
     if (host && dXc) cudaFree(dXc);
-    cudaFree(buf);
     return st;
 }
 

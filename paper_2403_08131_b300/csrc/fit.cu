@@ -14,6 +14,8 @@
 // padded right-hand side is zero, and alpha is zero there.  No kernel needs a ragged tail.
 #include "fit_kernels.cuh"
 
+#include <utility>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -47,21 +49,54 @@ constexpr int SLAB_ROWS = 4;
 // Models with the tensor-core update use it while at least CHOL_TC_MIN_T block columns remain
 // after the lookahead column; the last few small updates stay on the FP64 pipe.
 constexpr int CHOL_TC_MIN_T = 4;
+// Programmatic dependent launch along the factorisation's chain (next-column update -> diagonal
+// factor -> inverse -> panel, one stream): each kernel lets the next one be scheduled as soon as
+// all of its own CTAs are running, and each waits (griddepcontrol.wait: the previous kernel has
+// completed and its writes are visible) before it reads anything, so the launch latency of a
+// dependent kernel overlaps the kernel before it.  Without the launch attribute both
+// instructions do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static int launch_pdl(gpbo_ctx *ctx, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GPBO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...));
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
 __global__ void __launch_bounds__(DIAG_THREADS) k_chol_diag(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status)
 {
+    pdl_wait();
+    pdl_trigger();
     k_chol_diag_body(A, n_pad, kb, Dinv, status, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(128) k_chol_inv(const double *__restrict__ A, int n_pad, int kb,
                                                   double *__restrict__ Dinv)
 {
+    pdl_wait();
+    pdl_trigger();
     k_chol_inv_body(A, n_pad, kb, Dinv, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv)
 {
+    pdl_wait();
     k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y);
 }
 
@@ -73,6 +108,7 @@ __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int
 __global__ void __launch_bounds__(256) k_chol_update_slab(double *__restrict__ A, int n_pad, int kb, int part,
                                                           int t0)
 {
+    pdl_trigger();
     k_chol_update_slab_body<SLAB_ROWS>(A, n_pad, kb, blockIdx.x, part, t0);
 }
 
@@ -284,12 +320,10 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
     GPBO_LAUNCH_CHECK(ctx);
-    k_chol_inv<<<NB / 4, 128, 0, side>>>(m->L, n_pad, 0, m->Dinv);
-    GPBO_LAUNCH_CHECK(ctx);
-    if (nblk > 1) {
-        k_chol_panel<<<(nblk - 1) * (NB / 4), 256, 0, side>>>(m->L, n_pad, 0, m->Dinv);
-        GPBO_LAUNCH_CHECK(ctx);
-    }
+    GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, 0, m->Dinv));
+    if (nblk > 1)
+        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((nblk - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, 0,
+                            m->Dinv));
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
     // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
     alignas(64) unsigned char tc_maps[2][128];
@@ -301,14 +335,12 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));  // step kb-1 done with column kb+1
         k_chol_update_slab<<<T * (NB / SLAB_ROWS), 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
         GPBO_LAUNCH_CHECK(ctx);
-        k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, kb + 1, m->Dinv, ctx->dev_status);
-        GPBO_LAUNCH_CHECK(ctx);
-        k_chol_inv<<<NB / 4, 128, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
-        GPBO_LAUNCH_CHECK(ctx);
-        if (T > 1) {
-            k_chol_panel<<<(T - 1) * (NB / 4), 256, 0, side>>>(m->L, n_pad, kb + 1, m->Dinv);
-            GPBO_LAUNCH_CHECK(ctx);
-        }
+        GPBO_TRY(launch_pdl(ctx, k_chol_diag, dim3(1), dim3(DIAG_THREADS), smem1, side, m->L, n_pad, kb + 1, m->Dinv,
+                            ctx->dev_status));
+        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb + 1, m->Dinv));
+        if (T > 1)
+            GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((T - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, kb + 1,
+                                m->Dinv));
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;

@@ -87,6 +87,9 @@ struct gpbo_ctx {
     int batch_tile = 0;              // batched variance tile (0: autotune)
     cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
     cudaEvent_t side_ev[4] = {};     // fork / join events between the two streams
+    gp_model *step_model = nullptr;  // search_step's model, kept for the next call of the same shape
+    void *step_buf = nullptr;        // search_step's device staging
+    size_t step_buf_bytes = 0;
 };
 
 struct gp_model {

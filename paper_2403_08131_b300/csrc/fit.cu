@@ -38,8 +38,8 @@ __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, d
     k_kmat_body(Xs, n, d, n_pad, s2, sn2, K, blockIdx.x, blockIdx.y);
 }
 
-// Blocked diagonal factor: warp 0 factors each 16 x 16 sub-block; the other threads share the
-// panel solve and the trailing update (the arithmetic per element does not depend on the count).
+// Diagonal factor: warp 0 takes the pivots, 31 warps share each column's updates (the
+// arithmetic per element does not depend on the count).
 constexpr int DIAG_THREADS = 1024;
 // Trailing updates of fewer than SLAB_BELOW x SMs whole 64 x 64 tiles (two waves at three
 // CTAs per SM) run as 16-row slabs.  Slabs for every launch measured the same (22.3 ms per

@@ -65,84 +65,92 @@ __device__ __forceinline__ void k_kmat_body(const double *__restrict__ Xs, int n
 }
 
 // ------------------------------------------------------------------ Cholesky
-// Diagonal block kb: factor the 64x64 block in place, blocked by 16 columns, with every element
-// taking the FMAs of a right-looking column-by-column factorisation in the same order (so the
-// factor is the same bit for bit):  a_ic -= l_it l_ct for t = 0, 1, .. (t < c <= i), and
-// l_ij = a_ij / L_jj with the pivot L_jj = p rsqrt(p), 1 / L_jj = rsqrt(p), p = a_jj.
-// For each 16-column panel: warp 0 factors the 16 x 16 diagonal sub-block column by column
-// (warp-synchronous); one thread per row below solves its 16 panel entries in order; then
-// all threads apply the panel's 16 columns to the trailing lower triangle, one element at a
-// time in t order.  Four barriers per panel instead of one per column.  The reciprocal pivots
-// go to the diagonal of Dinv_kb; k_chol_inv builds the rest of the inverse for the panel.
+// Diagonal block kb: factor the 64x64 block in place, right-looking, column by column.
+// Pass j applies the rank-1 update with column j of L (already scaled by 1 / L_jj) to the
+// trailing lower triangle of the block, a_ic -= l_ij l_cj (j < c <= i), enumerated from a
+// column-major table so that every lane of warps 1.. has an element.  Warp 0 meanwhile
+// finishes a_{j+1,j+1} and takes the next pivot, L_{j+1,j+1} = p rsqrt(p) with
+// 1 / L_{j+1,j+1} = rsqrt(p), and publishes it through a shared flag: the pivot chain (on this
+// part an FP64 rsqrt alone takes about 440 cycles) runs beside the updates instead of after
+// them.  The elements of column j+1 come last in the range: their owners wait (bounded) for
+// the flag and store them scaled, so one barrier per column suffices.  The factor's arithmetic
+// per element is that of a plain right-looking loop.  The reciprocal pivots go to the diagonal
+// of Dinv_kb; k_chol_inv builds the rest of the inverse for the panel.
 __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_pad, int kb,
                                                    double *__restrict__ Dinv, unsigned *status, const int bx, const int by)
 {
     extern __shared__ double sm[];
     double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    __shared__ double rd[NB];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int TRI = NB * (NB + 1) / 2;
+    __shared__ double rdiag[NB];
+    __shared__ uint16_t tab[TRI];  // lower triangle, column-major: row | col << 8
+    __shared__ int ready;          // highest column whose pivot is published
+    const int tid = threadIdx.x;
     const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
+    auto coff = [](int c) { return c * NB - c * (c - 1) / 2; };  // first entry of column c
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int r = e / NB, c = e % NB;
         a[r][c] = A[base + (int64_t)r * n_pad + c];
     }
+    for (int e = tid; e < TRI; e += blockDim.x) {
+        // column c: the largest with coff(c) <= e (closed form, then exact integer fix-up)
+        int c = (int)((129.0f - sqrtf(16641.0f - 8.0f * (float)e)) * 0.5f);
+        c = max(0, min(NB - 1, c));
+        while (c > 0 && coff(c) > e) --c;
+        while (c < NB - 1 && coff(c + 1) <= e) ++c;
+        tab[e] = (uint16_t)((c + (e - coff(c))) | (c << 8));
+    }
     __syncthreads();
-    constexpr int PW = 16;
-    for (int c0 = 0; c0 < NB; c0 += PW) {
-        if (warp == 0) {
-            for (int j = c0; j < c0 + PW; ++j) {
-                if (lane == 0) {
-                    double p = a[j][j];
-                    if (!(p > 0.0)) {
-                        atomicOr(status, DEV_NOTSPD);
-                        p = 1.0;
+    if (tid == 0) {
+        double p = a[0][0];
+        if (!(p > 0.0)) {
+            atomicOr(status, DEV_NOTSPD);
+            p = 1.0;
+        }
+        const double r = rsqrt(p);
+        a[0][0] = p * r;
+        rdiag[0] = r;
+        ready = 0;
+    }
+    __syncthreads();
+    if (tid > 0 && tid < NB) a[tid][0] *= rdiag[0];
+    __syncthreads();
+    volatile int *vready = &ready;
+    volatile double *vrdiag = rdiag;
+    for (int j = 0; j + 1 < NB; ++j) {
+        const int m = NB - 1 - j;           // rows below j
+        const int nF = TRI - coff(j + 2);   // triangle, columns >= j+2
+        const int nT = nF + (m - 1);        // + column j+1 below its diagonal
+        if (tid == 0) {
+            double p = fma(-a[j + 1][j], a[j + 1][j], a[j + 1][j + 1]);
+            if (!(p > 0.0)) {
+                atomicOr(status, DEV_NOTSPD);
+                p = 1.0;
+            }
+            const double rr = rsqrt(p);
+            a[j + 1][j + 1] = p * rr;
+            vrdiag[j + 1] = rr;
+            __threadfence_block();
+            *vready = j + 1;
+        }
+        for (int e = tid - 32; e < nT; e += (int)blockDim.x - 32) {
+            if (tid < 32) break;
+            if (e < nF) {
+                const int t = tab[coff(j + 2) + e], i = t & 255, c = t >> 8;
+                a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
+            } else {
+                // last: column j+1 below its diagonal, final after this pass; stored scaled
+                const int q = e - nF;
+                const double v = fma(-a[j + 2 + q][j], a[j + 1][j], a[j + 2 + q][j + 1]);
+                for (int it = 0; *vready < j + 1; ++it) {
+                    if (it == (1 << 24)) {  // cannot happen: warp 0 publishes unconditionally
+                        atomicOr(status, DEV_TIMEOUT);
+                        break;
                     }
-                    const double r = rsqrt(p);
-                    a[j][j] = p * r;
-                    rd[j] = r;
                 }
-                __syncwarp();
-                const int i = j + 1 + lane;
-                if (i < c0 + PW) a[i][j] *= rd[j];
-                __syncwarp();
-                // the sub-block's trailing triangle j < c <= i < c0 + PW, row-major
-                const int m = c0 + PW - 1 - j;
-                for (int e = lane; e < m * (m + 1) / 2; e += 32) {
-                    int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-                    while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-                    while (ii * (ii + 1) / 2 > e) --ii;
-                    const int cc = e - ii * (ii + 1) / 2;
-                    const int r = j + 1 + ii, c = j + 1 + cc;
-                    a[r][c] = fma(-a[r][j], a[c][j], a[r][c]);
-                }
-                __syncwarp();
+                __threadfence_block();
+                a[j + 2 + q][j + 1] = v * vrdiag[j + 1];
             }
-        }
-        __syncthreads();
-        const int nr = NB - c0 - PW;
-        if (nr == 0) break;
-        if (tid < nr) {
-            const int r = c0 + PW + tid;
-            double y[PW];
-#pragma unroll
-            for (int jj = 0; jj < PW; ++jj) {
-                double s = a[r][c0 + jj];
-#pragma unroll
-                for (int t = 0; t < jj; ++t) s = fma(-y[t], a[c0 + jj][c0 + t], s);
-                y[jj] = s * rd[c0 + jj];
-                a[r][c0 + jj] = y[jj];
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < nr * (nr + 1) / 2; e += blockDim.x) {
-            int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
-            while (ii * (ii + 1) / 2 > e) --ii;
-            const int r = c0 + PW + ii, c = c0 + PW + (e - ii * (ii + 1) / 2);
-            double v = a[r][c];
-#pragma unroll
-            for (int t = 0; t < PW; ++t) v = fma(-a[r][c0 + t], a[c][c0 + t], v);
-            a[r][c] = v;
         }
         __syncthreads();
     }
@@ -151,7 +159,7 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
         const int i = e / NB, c = e % NB;
         A[base + (int64_t)i * n_pad + c] = c <= i ? a[i][c] : 0.0;
     }
-    if (tid < NB) D[tid * NB + tid] = rd[tid];
+    if (tid < NB) D[tid * NB + tid] = rdiag[tid];
 }
 
 // Inverse X = L_kk^-1 of diagonal block kb (after k_chol_diag_body), by forward substitution of

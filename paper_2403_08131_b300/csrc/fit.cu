@@ -362,9 +362,8 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     k_zero_upper_blocks<<<blocks_for((int64_t)n_pad * n_pad), 256, 0, st>>>(m->L, n_pad);
     GPBO_LAUNCH_CHECK(ctx);
-    unsigned bits = 0;
-    GPBO_TRY(take_device_status(ctx, &bits));
-    if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
+    // A pivot that was not positive is reported by the status check at the end (the factor
+    // carries on with 1 in its place, so what follows stays finite): no host round trip here.
 
     // One workspace reservation for both branches below (they run concurrently).
     const int max_probs = 2 * nblk + 2;
@@ -431,6 +430,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         }
     }
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
+    unsigned bits = 0;
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
     if (bits & DEV_TIMEOUT) return GPBO_ETIMEOUT;

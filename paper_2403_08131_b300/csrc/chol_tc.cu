@@ -210,11 +210,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int ib = r / NB;
         const bool live = r < P.n_pad && ib >= jb;
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16);
+        // this thread's 32 values of A, loaded while the copies and MMAs are in flight
+        double2 pre[2][8];
+        {
+            const double *src = P.A + (int64_t)r * P.n_pad + col0 + half * 32;
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    pre[g][q] = live ? *reinterpret_cast<const double2 *>(src + g * 16 + 2 * q) : make_double2(0.0, 0.0);
+        }
         const bool got = mbar_wait_inl(&sh->done, 0, abort_flag, P.status);
         if (__all_sync(0xffffffffu, got)) {
             tc_fence_after();
             const int er = sh->er[row];
-#pragma unroll 1
+#pragma unroll
             for (int g = 0; g < 2; ++g) {
                 const int c0 = half * 32 + g * 16;
                 long long hi[16], lo[16];
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     double *dst = P.A + (int64_t)r * P.n_pad + col0 + c0;
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
-                        double2 a = *reinterpret_cast<double2 *>(dst + j);
+                        double2 a = pre[g][j / 2];
                         const long long C0 = hi[j] * 65536 + (lo[j] >> 16), C1 = hi[j + 1] * 65536 + (lo[j + 1] >> 16);
                         a.x -= scaled_to_double(C0, er + sh->ec[c0 + j] - 54);
                         a.y -= scaled_to_double(C1, er + sh->ec[c0 + j + 1] - 54);

@@ -105,26 +105,6 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// TMEM loads without the wait, so that several can be in flight; tmem_wait() waits for all
-// of them, and pin() then ties the destination registers to that point: an empty volatile asm
-// that "modifies" them keeps the compiler from reading them before the wait.
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t *r)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void pin16(uint32_t *r)
-{
-    asm volatile(""
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]));
-}
-
 // Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in FP16, 128-byte swizzled
 // (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
 __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)

@@ -68,7 +68,7 @@ __device__ __forceinline__ void k_kmat_body(const double *__restrict__ Xs, int n
 // Diagonal block kb: factor the 64x64 block in place, right-looking, column by column.
 // Pass j applies the rank-1 update with column j of L (already scaled by 1 / L_jj) to the
 // trailing lower triangle of the block, a_ic -= l_ij l_cj (j < c <= i), enumerated from a
-// column-major table so that every lane of warps 1.. has an element.  Warp 0 meanwhile
+// column-major table so that every lane of the worker warps has an element.  Warp 0 meanwhile
 // finishes a_{j+1,j+1} and takes the next pivot, L_{j+1,j+1} = p rsqrt(p) with
 // 1 / L_{j+1,j+1} = rsqrt(p), and publishes it through a shared flag: the pivot chain (on this
 // part an FP64 rsqrt alone takes about 440 cycles) runs beside the updates instead of after
@@ -133,8 +133,12 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
             __threadfence_block();
             *vready = j + 1;
         }
-        for (int e = tid - 32; e < nT; e += (int)blockDim.x - 32) {
-            if (tid < 32) break;
+        // workers: the warps on schedulers 1-3, so that the pivot's FP64 instructions have
+        // scheduler 0's FP64 unit to themselves (each FP64 warp instruction holds it 64 cycles)
+        const int warp = tid >> 5, nw = (int)(blockDim.x >> 5), workers = nw - (nw + 3) / 4;
+        const int wid = warp - warp / 4 - 1;
+        for (int e = wid * 32 + (tid & 31); e < nT; e += workers * 32) {
+            if ((warp & 3) == 0) break;
             if (e < nF) {
                 const int t = tab[coff(j + 2) + e], i = t & 255, c = t >> 8;
                 a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);

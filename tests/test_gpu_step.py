@@ -42,3 +42,22 @@ def test_step_rejects_nan_and_bad_sizes(ctx):
     with pytest.raises(gpbo.GpboError) as e:
         ctx.search_step(w.X, w.y, w.lengthscale, 1.0, w.noise_var, M=0, seed=1)
     assert e.value.code == gpbo.GPBO_EINVAL
+
+
+def test_step_reuses_model_across_calls_and_shapes(ctx):
+    """The context keeps search_step's model for the next call of the same shape: repeated
+    calls give identical results, and calls of other shapes and precisions in between (which
+    replace the kept model) change nothing."""
+    w = W.config2()
+    M = 8192
+    args = (w.X, w.y, w.lengthscale, 1.0, w.noise_var)
+    a = ctx.search_step(*args, M=M, seed=w.seed, prec="f16")
+    b = ctx.search_step(*args, M=M, seed=w.seed, prec="f16")
+    small = W.config1()
+    ctx.search_step(small.X, small.y, small.lengthscale, 1.0, small.noise_var, M=1024, seed=3, prec="f64")
+    ctx.search_step(w.X[:300], w.y[:300], w.lengthscale, 1.0, w.noise_var, M=M, seed=w.seed, prec="f16")
+    ctx.search_step(*args, M=M, seed=w.seed, prec="f32")
+    c = ctx.search_step(*args, M=M, seed=w.seed, prec="f16")
+    for r in (b, c):
+        assert r["argmax"] == a["argmax"] and r["ei_max"] == a["ei_max"]
+        assert np.array_equal(r["x_next"], a["x_next"])

@@ -248,8 +248,9 @@ int interdep_screen(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const scree
  * drawn from seed when Xc is NULL) with EI below tau = min y', and return the EI argmax:
  * x_next (host, d doubles), ei_max (host, standardised units), argmax (host, may be NULL).
  * flags: GPBO_HOST_PTRS applies to X, y and Xc.  The context keeps the step's model and
- * staging buffers for its next search_step of the same n, d and precision (a BO loop calls
- * it repeatedly), and frees them on a shape change or in gpbo_destroy.  Synchronises. */
+ * staging buffers for its next search_step of the same d and precision whose n pads to the
+ * same size (a BO loop calls it with n growing by one), and frees them on any other shape
+ * or in gpbo_destroy.  Synchronises. */
 int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, const gp_hyper *hyp,
                 const float *Xc, int64_t M, uint64_t seed, double xi, gpbo_prec prec, unsigned flags,
                 double *x_next, double *ei_max, int64_t *argmax);
@@ -332,6 +333,36 @@ int mlp_score(gpbo_ctx *ctx, gpbo_mlp *net, const float *X, int64_t M, uint64_t 
  * allocates it); top_idx: host k pool indices of the selected set, or NULL.  Synchronises. */
 int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_t M, uint64_t seed, int k,
                      double y_best, double xi, float *ei_pool, int64_t *top_idx, int64_t *argmax, double *ei_max);
+
+/* ------------------------------------------------------------------ a BO search (§III-A, §IV-D)
+ * One Bayesian-optimisation search over k variables scaled into the unit cube: n_init initial
+ * configurations (given: the caller draws them, 5 random ones in the paper), then one
+ * search_step per evaluation until `budget` evaluations (the paper: 10 x k): standardise y,
+ * fit, score M candidates drawn on the device from seed + t (gpbo_gen_candidates, t the
+ * evaluation index), evaluate the EI argmax.  With refit = 1 each step first refits the
+ * hyperparameters by gp_fit_mle on the standardised observations (box: lengthscales
+ * 0.01..100, signal variance e^-3..e^3, noise variance e^-14..1; starts: the previous
+ * step's fit, then hyp), at most mle_iters L-BFGS iterations (30 when 0); with refit = 0 the
+ * hyperparameters are hyp throughout.  Fits use GPBO_JITTER.
+ * fn: the objective, called on the host with one configuration u (k values in [0,1]); it
+ * writes f and returns 0, nonzero for a failed evaluation (bo_search then returns
+ * GPBO_EINVAL).  X (host, budget x k) and y (host, budget) receive every evaluated
+ * configuration and value in order; best (host, may be NULL) the index of the smallest y. */
+typedef int (*gpbo_eval_fn)(const double *u, int k, double *f, void *user);
+typedef struct bo_opts {
+    int budget;
+    int n_init;
+    const double *x_init; /* host, n_init x k, in [0,1] */
+    int64_t M;
+    uint64_t seed;
+    int prec;             /* gpbo_prec of the scoring */
+    int refit;
+    gp_hyper hyp;
+    double xi;
+    int mle_iters;
+} bo_opts;
+int bo_search(gpbo_ctx *ctx, int k, gpbo_eval_fn fn, void *user, const bo_opts *opts, double *X, double *y,
+              int *best);
 
 /* ------------------------------------------------------------------ hyperparameters by maximum likelihood
  * The surrogate's hyperparameters theta = (log l_1 .. log l_d, log signal_var, log noise_var)

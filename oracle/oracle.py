@@ -426,3 +426,18 @@ def lml_grad_dense(X, y, ls, s2, sn2, scales=False):
     gs[d + 1] = 0.5 * sn2 * np.trace(Wa)
     ls_ = np.linalg.norm(y) * np.linalg.norm(alpha) + np.abs(np.log(np.diag(L))).sum() + n
     return float(lml), g, float(kappa1), float(ls_), gs
+
+
+# ------------------------------------------------------------------ a BO search
+def bo_search(fn, x_init, budget, M, seed, ls, s2, sn2, xi=0.0):
+    """One BO search with fixed hyperparameters (§III-A): evaluate the initial design, then at
+    evaluation t take the EI argmax of search_step over the M candidates drawn from seed + t
+    and evaluate it.  Returns (X, y, index of the smallest y)."""
+    X = [np.asarray(u, dtype=np.float64) for u in np.atleast_2d(x_init)]
+    y = [float(fn(u)) for u in X]
+    for t in range(len(X), budget):
+        r = search_step(np.array(X), np.array(y), ls, s2, sn2, M=M, seed=seed + t, xi=xi)
+        X.append(r["x_next"])
+        y.append(float(fn(r["x_next"])))
+    y = np.array(y)
+    return np.array(X), y, int(np.argmin(y))

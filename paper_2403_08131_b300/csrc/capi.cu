@@ -132,7 +132,7 @@ static int dalloc(T **p, size_t count)
 static int alloc_model(gp_model *m)
 {
     const size_t sq = (size_t)m->n_pad * m->n_pad;
-    GPBO_TRY(dalloc(&m->X, (size_t)m->n * m->d));
+    GPBO_TRY(dalloc(&m->X, (size_t)m->n_pad * m->d));  // room for any n with this n_pad
     GPBO_TRY(dalloc(&m->Xs64, (size_t)m->d * m->n_pad));
     GPBO_TRY(dalloc(&m->Xs32, (size_t)m->d * m->n_pad));
     GPBO_TRY(dalloc(&m->K, sq));
@@ -155,6 +155,11 @@ static int alloc_model(gp_model *m)
     return GPBO_OK;
 }
 
+int model_n_pad(int n, int prec)
+{
+    return round_up(n, (prec == GPBO_PREC_BF16 || prec == GPBO_PREC_F16) ? TC_NCHUNK : NB);
+}
+
 int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out)
 {
     gp_model *m = new (std::nothrow) gp_model();
@@ -163,7 +168,7 @@ int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out)
     m->n = n;
     m->d = d;
     m->prec = prec;
-    m->n_pad = round_up(n, (prec == GPBO_PREC_BF16 || prec == GPBO_PREC_F16) ? TC_NCHUNK : NB);
+    m->n_pad = model_n_pad(n, prec);
     const int st = alloc_model(m);
     if (st != GPBO_OK) {
         model_free(m);
@@ -541,7 +546,9 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
     }
     if (st == GPBO_OK) st = standardize_dev(ctx, dy, n, ys, tau);
     m = ctx->step_model;
-    if (st == GPBO_OK && (!m || m->n != n || m->d != d || m->prec != prec)) {
+    if (st == GPBO_OK && m && m->d == d && m->prec == prec && m->n_pad == model_n_pad(n, prec)) {
+        m->n = n;  // same buffers: every n-dependent part of the fit is recomputed
+    } else if (st == GPBO_OK) {
         cudaStreamSynchronize(ctx->stream);
         if (m) model_free(m);
         m = ctx->step_model = nullptr;

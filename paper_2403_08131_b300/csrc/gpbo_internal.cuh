@@ -131,6 +131,7 @@ int take_device_status(gpbo_ctx *ctx, unsigned *bits_out);
 // Allocate a model's device buffers for n x d in the given precision (hyperparameters unset),
 // free one, and validate hyperparameters.
 int model_create(gpbo_ctx *ctx, int n, int d, int prec, gp_model **out);
+int model_n_pad(int n, int prec);
 void model_free(gp_model *m);
 int check_hyper(const gp_hyper *hyp, int d);
 

@@ -39,6 +39,12 @@ class GpHyper(C.Structure):
 
 
 HOST_FN = C.CFUNCTYPE(C.c_int, _D, C.c_int, _D, _D, C.c_void_p)
+EVAL_FN = C.CFUNCTYPE(C.c_int, _D, C.c_int, _D, C.c_void_p)
+
+
+class BoOpts(C.Structure):
+    _fields_ = [("budget", C.c_int), ("n_init", C.c_int), ("x_init", _D), ("M", C.c_int64), ("seed", C.c_uint64),
+                ("prec", C.c_int), ("refit", C.c_int), ("hyp", GpHyper), ("xi", C.c_double), ("mle_iters", C.c_int)]
 
 
 class GpboObjective(C.Structure):
@@ -98,6 +104,7 @@ _screen_sur = _sig("surrogate_screen", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint
 _lml = _sig("gp_lml", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_uint, _D, _D])
 _fit_mle = _sig("gp_fit_mle", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, _D, _D, _D, C.c_int, C.c_double,
                                          C.c_uint, _D, _D, _L])
+_bo = _sig("bo_search", C.c_int, [_P, C.c_int, EVAL_FN, C.c_void_p, C.POINTER(BoOpts), _D, _D, _I])
 _gen = _sig("gpbo_gen_candidates", C.c_int, [_P, C.c_uint64, C.c_int64, C.c_int64, C.c_int, _P])
 _screen = _sig("interdep_screen", C.c_int, [_P, C.POINTER(GpboObjective), C.c_int, C.POINTER(ScreenOpts), _P, _P,
                                              _P, _I, _P])
@@ -208,6 +215,36 @@ class Context:
         m = Model(self, out, prec)
         self._models.add(m)
         return m
+
+    # ------------------------------------------------------------ a BO search
+    def bo_search(self, fn, x_init, budget, M, seed, lengthscale, signal_var, noise_var, prec="f64", refit=False,
+                  xi=0.0, mle_iters=0):
+        """fn(u) -> float for u (k,) in the unit cube (called on the host); x_init (n_init x k).
+        Returns (X (budget x k), y (budget,), index of the best y)."""
+        x_init = np.ascontiguousarray(np.atleast_2d(x_init), dtype=np.float64)
+        n_init, k = x_init.shape
+        err = []
+
+        def tramp(up, kk, fp, user):
+            try:
+                fp[0] = float(fn(np.ctypeslib.as_array(up, shape=(kk,)).copy()))
+                return 0
+            except Exception as e:  # reported after the call returns
+                err.append(e)
+                return 1
+
+        cb = EVAL_FN(tramp)
+        ls = np.ascontiguousarray(np.broadcast_to(np.asarray(lengthscale, dtype=np.float64), (k,)))
+        o = BoOpts(int(budget), n_init, x_init.ctypes.data_as(_D), int(M), int(seed), PREC[prec], int(bool(refit)),
+                   GpHyper(k, ls.ctypes.data_as(_D), float(signal_var), float(noise_var)), float(xi), int(mle_iters))
+        X = np.empty((budget, k))
+        y = np.empty(budget)
+        best = C.c_int(-1)
+        code = _bo(self._h, k, cb, None, C.byref(o), X.ctypes.data_as(_D), y.ctypes.data_as(_D), C.byref(best))
+        if err:
+            raise err[0]
+        check(code, "bo_search")
+        return X, y, int(best.value)
 
     # ------------------------------------------------------------ hyperparameters
     def lml(self, X, y, lengthscale, signal_var, noise_var):

@@ -35,6 +35,7 @@ STREAM_INIT = 5
 STREAM_SHAPES = 6
 STREAM_TRAIN = 7
 STREAM_MLE_STARTS = 8
+STREAM_BO_INIT = 9
 
 # Objective block codes (same numbering as the C ABI's gpbo_fn).
 FN_ACKLEY = 0
@@ -126,6 +127,69 @@ class Objective:
             cnt = np.arange(f.shape[0], dtype=np.uint64) + np.uint64(noise_counter0)
             f = f + self.noise_sd * normal(self.seed, STREAM_NOISE, cnt)
         return f
+
+
+class PaperSynthetic:
+    """The 20-dimensional synthetic function of the paper's evaluation (§III, Fig. `equation`
+    and Table `group3_defs`), a black box: four groups (routines) of five variables each,
+    x = -50 + 100 u for u in the unit cube, and each group's value entering the total as
+    log|G_g|.  With A_i = 10 cos(2 pi (x_i - 1)) + eps:
+      G1 = sum_{i=0..3} (x_i - x_{i+1})^2 + sum_{i=0..4} A_i
+      G2 = sum_{k=5..8} (x_k - x_{k+1})^4 + sum_{k=5..9} A_k
+      G3 = Case 1: sum x_u + sum cos(2 pi x_v) + eps     Case 2: sum x_u^2 + sum x_v + eps
+           Case 3: sum x_u^2 + sum x_v^2 + eps           Case 4: sum (x_u x_{u+5}^4)^2 + eps
+           Case 5: sum (x_u x_{u+5}^8)^2 + eps           (u = 10..14, v = 15..19)
+      G4 = sum_{v=15..19} 1 / x_v + eps
+    Readings of the garbled or unstated points: G2's A_j runs over G2's own indices; Cases 4-5
+    pair u with v = u + 5; |x_v| below 1e-3 is moved out to 1e-3 (keeping its sign) in 1/x_v;
+    log|G| is floored at log(1e-12); every eps is its own N(0, noise_sd^2) draw, twelve per
+    evaluation, from counters 12 e .. 12 e + 11 of the noise stream (e the evaluation index)."""
+
+    d = 20
+    n_routines = 4
+    GROUPS = ((0, 5), (5, 10), (10, 15), (15, 20))
+
+    def __init__(self, case: int, noise_sd: float = 0.0, seed: int = 0):
+        assert case in (1, 2, 3, 4, 5)
+        self.case, self.noise_sd, self.seed = case, float(noise_sd), int(seed)
+
+    def group_values(self, U: np.ndarray, noise_counter0: int = 0) -> np.ndarray:
+        """(..., 4) raw group values G1..G4 (before the logarithm)."""
+        U = np.asarray(U, dtype=np.float64)
+        x = -50.0 + 100.0 * U
+        lead = x.shape[:-1]
+        if self.noise_sd > 0:
+            n = int(np.prod(lead)) if lead else 1
+            cnt = (np.arange(n, dtype=np.uint64)[:, None] + np.uint64(noise_counter0)) * np.uint64(12) \
+                + np.arange(12, dtype=np.uint64)[None, :]
+            eps = (self.noise_sd * normal(self.seed, STREAM_NOISE, cnt)).reshape(lead + (12,))
+        else:
+            eps = np.zeros(lead + (12,))
+        A = 10.0 * np.cos(2.0 * math.pi * (x[..., 0:10] - 1.0)) + eps[..., 0:10]
+        g1 = np.sum((x[..., 0:4] - x[..., 1:5]) ** 2, axis=-1) + np.sum(A[..., 0:5], axis=-1)
+        g2 = np.sum((x[..., 5:9] - x[..., 6:10]) ** 4, axis=-1) + np.sum(A[..., 5:10], axis=-1)
+        xu, xv = x[..., 10:15], x[..., 15:20]
+        if self.case == 1:
+            g3 = np.sum(xu, axis=-1) + np.sum(np.cos(2.0 * math.pi * xv), axis=-1)
+        elif self.case == 2:
+            g3 = np.sum(xu ** 2, axis=-1) + np.sum(xv, axis=-1)
+        elif self.case == 3:
+            g3 = np.sum(xu ** 2, axis=-1) + np.sum(xv ** 2, axis=-1)
+        elif self.case == 4:
+            g3 = np.sum((xu * xv ** 4) ** 2, axis=-1)
+        else:
+            g3 = np.sum((xu * xv ** 8) ** 2, axis=-1)
+        g3 = g3 + eps[..., 10]
+        xs = np.where(np.abs(xv) < 1e-3, np.where(xv < 0, -1e-3, 1e-3), xv)
+        g4 = np.sum(1.0 / xs, axis=-1) + eps[..., 11]
+        return np.stack([g1, g2, g3, g4], axis=-1)
+
+    def routines(self, U: np.ndarray, noise_counter0: int = 0) -> np.ndarray:
+        """(..., 4) routine outputs log|G_g|."""
+        return np.log(np.maximum(np.abs(self.group_values(U, noise_counter0)), 1e-12))
+
+    def __call__(self, U: np.ndarray, noise_counter0: int = 0) -> np.ndarray:
+        return self.routines(U, noise_counter0).sum(axis=-1)
 
 
 def five_block_objective(seed: int, noise_sd: float = 0.01) -> Objective:

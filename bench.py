@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned pre-screen measurement")
     ap.add_argument("--no-mle", action="store_true", help="skip the hyperparameter-fit measurement")
+    ap.add_argument("--no-bo", action="store_true", help="skip the BO-search strategies on the paper's cases")
     ap.add_argument("--profile-mle", type=int, default=0, metavar="N",
                     help="run two LML evaluations at N observations, d=20, for an ncu capture")
     ap.add_argument("--profile-case", type=int, default=0, metavar="M",
@@ -262,6 +263,39 @@ def mle_form(ctx, W, dev, fp64_peak, starts=2, max_iter=15, evals=5):
             "timing": "host wall clock around synchronised calls; kernel time from events on the context stream"}
 
 
+# ---------------------------------------------------------------------------- BO searches
+def bo_form(ctx, W):
+    """The paper's synthetic Cases 1-5 (20-D, noise 0.1) under its search strategies: one joint
+    20-D search, G1 + G2 + G3+G4, four independent searches (each 5 random initial points
+    and 10 x k evaluations, FP32 scoring of 16384 candidates per step, fixed rule
+    hyperparameters), and random search with the same 200 evaluations; Case 4 again with the
+    hyperparameters refitted by maximum likelihood at every step.  Values are the noise-free
+    objective at each strategy's combined best configuration (lower is better)."""
+    from paper_2403_08131_b300 import searches as S
+
+    cases, evals, secs = {}, 0, 0.0
+    for case in range(1, 6):
+        f = W.PaperSynthetic(case, 0.1, seed=case)
+        row = {"random": round(S.random_search(f, 200, seed=case)["value"], 2)}
+        for name, searches in S.STRATEGIES.items():
+            r = S.run_strategy(ctx, f, searches, seed=case, M=16384, refit=False, prec="f32")
+            row[name] = round(r["value"], 2)
+            evals += sum(s["evaluations"] for s in r["searches"])
+            secs += r["seconds"]
+        cases[f"case{case}"] = row
+    f = W.PaperSynthetic(4, 0.1, seed=4)
+    mle, mle_s = {}, {}
+    for name, searches in S.STRATEGIES.items():
+        r = S.run_strategy(ctx, f, searches, seed=4, M=16384, refit=True, prec="f32", mle_iters=20)
+        mle[name] = round(r["value"], 2)
+        mle_s[name] = round(r["seconds"], 2)
+    return {"workload": "paper synthetic Cases 1-5 (d=20, 4 routines), strategies joint / G1,G2,G3+G4 / "
+                        "independent / random, 10 x k evaluations per search, M=16384 FP32",
+            "value": round(evals / secs, 1), "unit": "BO evaluations/s (fixed hyperparameters)",
+            "minima": cases, "case4_refit_minima": mle, "case4_refit_seconds": mle_s,
+            "timing": "host wall clock around each search (objective evaluated on the host)"}
+
+
 # ---------------------------------------------------------------------------- ours
 def aggregate_timing(ms_local, steps, world, device, units_per_step=None):
     """Whole-job timing of a weakly scaled run: the slowest rank's time (max over ranks by
@@ -449,6 +483,8 @@ def run_ours(args, rank, world, local):
             out["ei_max_rel_diff_vs_plain"] = abs(r["ei_max"] - pr["ei_max"]) / max(abs(pr["ei_max"]), 1e-300)
         if not args.no_mle:
             out.setdefault("forms", {})["mle"] = mle_form(ctx, W, dev, fp64_peak)
+        if not args.no_bo:
+            out.setdefault("forms", {})["bo_synth"] = bo_form(ctx, W)
         if not args.no_surrogate and args.prec != "f32":
             out.setdefault("forms", {})["surrogate"] = surrogate_form(
                 ctx, gpbo, W, dev, out.get("plain", {}).get("value"))

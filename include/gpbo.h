@@ -213,7 +213,11 @@ typedef struct gpbo_objective {
     void *user;
 } gpbo_objective;
 
-typedef enum gpbo_screen_mode { GPBO_SCREEN_PAIRWISE = 0, GPBO_SCREEN_ROUTINE = 1 } gpbo_screen_mode;
+typedef enum gpbo_screen_mode {
+    GPBO_SCREEN_PAIRWISE = 0,
+    GPBO_SCREEN_ROUTINE = 1,
+    GPBO_SCREEN_ROUTINE_SERIES = 2
+} gpbo_screen_mode;
 /* n_base base points b_k = (1-h) u, u uniform in [0,1)^d (stream 3); step h along each axis.
  * PAIRWISE: score_ij = mean_k |f(b+he_i+he_j) - f(b+he_i) - f(b+he_j) + f(b)|
  *                      / (mean_k(|f(b+he_i) - f(b)| + |f(b+he_j) - f(b)|) + 1e-12),
@@ -227,7 +231,19 @@ typedef enum gpbo_screen_mode { GPBO_SCREEN_PAIRWISE = 0, GPBO_SCREEN_ROUTINE = 
  * Noise counters: PAIRWISE evaluation e of base k uses k*E + e, E = 1 + d + d(d-1)/2, with
  * e = 0 the base, 1+i the step along i, 1+d+p the double step of the p-th pair i<j in
  * lexicographic order.  ROUTINE output g of evaluation e (0 base, 1+i step) uses
- * (k*(1+d) + e)*R + g. */
+ * (k*(1+d) + e)*R + g.
+ * ROUTINE_SERIES: the paper's schedule for its synthetic functions (§IV-B): one baseline b
+ *           (point 0 of stream 3, in [0,1)^d) and, for each parameter i in turn, V = n_base
+ *           variations: the parameter's value in its own units, x = lo_i + (hi_i - lo_i) u,
+ *           multiplied by (1 + growth) once per variation (10% in the paper), clamped to
+ *           [lo_i, hi_i]; the other parameters stay at b.  score_gi = (1/V) sum_v
+ *           |(f_g(b) - f_g(variation v of i)) / f_g(b)|; links, merge and cap as ROUTINE.
+ *           The ranges are the built-in blocks' own domains, or lo / hi (host, d each; NULL:
+ *           [0, 1]) for a host black box.  h is not used.  Output g of evaluation e (0 the
+ *           baseline, 1 + i V + v - 1 the v-th variation of i) uses noise counter e R + g.
+ * In both ROUTINE modes a host black box may give param_owner[i] = -1 for a parameter that
+ * several routines share: it is assigned to the routine it influences most (premise 5 of
+ * §IV: the kernel with the highest impact has priority). */
 typedef struct screen_opts {
     int mode;
     int n_base;
@@ -235,6 +251,9 @@ typedef struct screen_opts {
     double cutoff;
     int max_dims;
     uint64_t seed;
+    double growth;     /* ROUTINE_SERIES */
+    const double *lo;  /* ROUTINE_SERIES, host black box: parameter ranges (may be NULL) */
+    const double *hi;
 } screen_opts;
 
 /* score: host, d x d (PAIRWISE) or R x d (ROUTINE; R = n_blocks or n_routines) FP64.

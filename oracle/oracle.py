@@ -441,3 +441,35 @@ def bo_search(fn, x_init, budget, M, seed, ls, s2, sn2, xi=0.0):
         y.append(float(fn(r["x_next"])))
     y = np.array(y)
     return np.array(X), y, int(np.argmin(y))
+
+
+# ------------------------------------------------------------------ the paper's sensitivity series
+def series_points(u0, i, V, growth, lo, hi):
+    """The V variations of parameter i from baseline u0 (§IV-B): the value in its own units
+    grown by (1 + growth) once per variation, clamped to [lo, hi], back in [0, 1]."""
+    out = np.tile(np.asarray(u0, dtype=np.float64), (V, 1))
+    x = lo + (hi - lo) * float(u0[i])
+    for v in range(V):
+        x = x * (1.0 + growth)
+        out[v, i] = (min(max(x, lo), hi) - lo) / (hi - lo)
+    return out
+
+
+def screen_routine_series(routines_fn, d, R, V, growth, seed, lo, hi, owner, cutoff, max_dims):
+    """Routine sensitivity on the paper's schedule: baseline b = point 0 of stream 3; for each
+    parameter i its V variations; S_gi = mean_v |(f_g(b) - f_g(variation)) / f_g(b)| (with
+    1e-12 added to |f_g(b)|); a shared parameter (owner -1) goes to the routine it influences
+    most; then the routine partition (links above the cut-off, merge, cap).
+    routines_fn(u) -> R outputs for one configuration u in [0,1]^d."""
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), (d,))
+    u0 = uniform_points(seed, 3, 1, d)[0]  # counters 0 .. d-1 of stream 3
+    f0 = np.asarray(routines_fn(u0), dtype=np.float64)
+    S = np.zeros((R, d))
+    for i in range(d):
+        for u in series_points(u0, i, V, growth, lo[i], hi[i]):
+            S[:, i] += np.abs((f0 - np.asarray(routines_fn(u), dtype=np.float64)) / (np.abs(f0) + 1e-12))
+    S /= V
+    own = np.array([int(np.argmax(S[:, i])) if o < 0 else int(o) for i, o in enumerate(owner)], dtype=np.int32)
+    g, ng, fx = partition_routine(S, own, cutoff, max_dims)
+    return S, g, ng, fx, own

@@ -492,8 +492,17 @@ int interdep_screen(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const scree
                     double *influence, int *group_of, int *n_groups, int *fixed)
 {
     if (!ctx || !obj || !o || !group_of || !n_groups || d < 1 || d > GPBO_MAX_D) return GPBO_EINVAL;
-    if (o->n_base < 1 || !(o->h > 0.0) || !(o->h < 0.5) || !std::isfinite(o->cutoff)) return GPBO_EINVAL;
-    if (o->mode != GPBO_SCREEN_PAIRWISE && o->mode != GPBO_SCREEN_ROUTINE) return GPBO_EINVAL;
+    if (o->mode != GPBO_SCREEN_PAIRWISE && o->mode != GPBO_SCREEN_ROUTINE && o->mode != GPBO_SCREEN_ROUTINE_SERIES)
+        return GPBO_EINVAL;
+    if (o->n_base < 1 || !std::isfinite(o->cutoff)) return GPBO_EINVAL;
+    if (o->mode == GPBO_SCREEN_ROUTINE_SERIES) {
+        if (!(o->growth > 0.0) || !std::isfinite(o->growth) || (int64_t)o->n_base * d > (1 << 24)) return GPBO_EINVAL;
+        if (obj->fn && o->lo && o->hi)
+            for (int i = 0; i < d; ++i)
+                if (!(o->lo[i] < o->hi[i]) || !std::isfinite(o->lo[i]) || !std::isfinite(o->hi[i])) return GPBO_EINVAL;
+    } else if (!(o->h > 0.0) || !(o->h < 0.5)) {
+        return GPBO_EINVAL;
+    }
     if (!(obj->noise_sd >= 0.0)) return GPBO_EINVAL;
     GPBO_TRY(set_device(ctx));
     GPBO_TRY(trace_begin(ctx, PH_SCREEN, 0.0));

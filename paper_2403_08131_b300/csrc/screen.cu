@@ -7,6 +7,11 @@
 // exceeds the cut-off links A and B (§IV-C, the DAG with parameters as edges and the
 // cut-off pruning); linked routines merge; a merged search above max_dims keeps its most
 // influential parameters (§IV-D and premise 4 of §IV).
+// ROUTINE_SERIES mode takes the paper's own schedule for the synthetic functions (§IV-B):
+// one random baseline, then V variations of each parameter in turn, each 10% (growth) above
+// the one before in the parameter's own units, clamped to its range; the same score and
+// merge.  A parameter shared by several routines (owner -1) goes to the routine it
+// influences most (§IV, premise 5).
 // PAIRWISE mode is the classical second-order screen: mixed differences over all d(d-1)/2
 // parameter pairs at the same base points.
 //
@@ -88,6 +93,60 @@ __device__ void eval_axes(int64_t e, int d, int &i, int &j)
 __device__ void base_point(uint64_t seed, int k, int d, double h, double *x)
 {
     for (int t = 0; t < d; ++t) x[t] = (1.0 - h) * uniform24d(seed, 3, (uint64_t)k * d + t);
+}
+
+// Variation v (1..V) of one coordinate in the series schedule: the baseline's value in the
+// parameter's units, grown by (1 + growth) v times in turn, clamped to [lo, hi], back in the
+// unit interval.  Host and device take the same steps.
+__host__ __device__ inline double series_value(double u0, double lo, double hi, double growth, int v)
+{
+    double x = lo + (hi - lo) * u0;
+    for (int s = 0; s < v; ++s) x *= 1.0 + growth;
+    x = fmin(fmax(x, lo), hi);
+    return (x - lo) / (hi - lo);
+}
+
+struct SeriesRange {
+    double lo[GPBO_MAX_D], hi[GPBO_MAX_D];
+};
+
+// Evaluation e = 0 is the baseline (point 0 of stream 3), e = 1 + i V + (v - 1) varies
+// parameter i for the v-th time.  Outputs f[e R + g]; the noise of output g of evaluation e
+// uses counter e R + g.
+__global__ void k_screen_eval_series(ObjSpec spec, SeriesRange rg, int d, int V, double growth, uint64_t seed,
+                                     double noise_sd, double *__restrict__ f)
+{
+    const int R = spec.nb;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 1 + (int64_t)d * V) return;
+    double x[GPBO_MAX_D];
+    for (int k = 0; k < d; ++k) x[k] = uniform24d(seed, 3, (uint64_t)k);
+    if (t > 0) {
+        const int i = (int)((t - 1) / V), v = (int)((t - 1) % V) + 1;
+        x[i] = series_value(x[i], rg.lo[i], rg.hi[i], growth, v);
+    }
+    int o = 0;
+    for (int g = 0; g < R; ++g) {
+        double val = block_value(spec.fn[g], x + o, spec.dim[g]);
+        o += spec.dim[g];
+        if (noise_sd > 0.0) val += noise_sd * normal_draw(seed, (uint64_t)(t * R + g));
+        f[t * R + g] = val;
+    }
+}
+
+// S_gi = (1/V) sum_v |(f_g(base) - f_g(variation v of i)) / f_g(base)|.
+__global__ void k_screen_score_series(const double *__restrict__ f, int R, int d, int V, double *__restrict__ S)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * d) return;
+    const int g = t / d, i = t % d;
+    const double f0 = f[g];
+    double s = 0.0;
+    for (int v = 0; v < V; ++v) {
+        const double fi = f[(1 + (int64_t)i * V + v) * R + g];
+        s += fabs((f0 - fi) / (fabs(f0) + 1e-12));
+    }
+    S[t] = s / V;
 }
 
 __global__ void k_screen_eval_pairwise(ObjSpec spec, int d, int n_base, double h, uint64_t seed, double noise_sd,
@@ -216,7 +275,8 @@ void cap_groups(int d, const int *label, const double *infl, int max_dims, int *
 int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opts *o, double *score_out,
                double *infl_out, int *group_of, int *n_groups, int *fixed_out)
 {
-    const bool routine = o->mode == GPBO_SCREEN_ROUTINE;
+    const bool series = o->mode == GPBO_SCREEN_ROUTINE_SERIES;
+    const bool routine = o->mode == GPBO_SCREEN_ROUTINE || series;
     const bool host_fn = obj->fn != nullptr;
     const int R = host_fn ? obj->n_routines : obj->n_blocks;
     if (routine && (R < 1 || R > GPBO_MAX_D)) return GPBO_EINVAL;
@@ -237,20 +297,54 @@ int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opt
     } else if (routine) {
         if (!obj->param_owner) return GPBO_EINVAL;
         for (int i = 0; i < d; ++i) {
-            owner[i] = obj->param_owner[i];
-            if (owner[i] < 0 || owner[i] >= R) return GPBO_EINVAL;
+            owner[i] = obj->param_owner[i];  // -1: shared, settled by the scores below
+            if (owner[i] < -1 || owner[i] >= R) return GPBO_EINVAL;
         }
     }
-    const int64_t E = routine ? 1 + d : 1 + d + (int64_t)d * (d - 1) / 2;
+    // the series schedule's ranges: the built-in blocks' own domains, else the caller's
+    SeriesRange rg{};
+    for (int i = 0; i < d; ++i) {
+        rg.lo[i] = host_fn && o->lo ? o->lo[i] : 0.0;
+        rg.hi[i] = host_fn && o->hi ? o->hi[i] : 1.0;
+    }
+    if (series && !host_fn) {
+        int o2 = 0;
+        for (int b = 0; b < spec.nb; ++b)
+            for (int k = 0; k < spec.dim[b]; ++k, ++o2) {
+                const double w = spec.fn[b] == GPBO_FN_ACKLEY ? 32.768 : spec.fn[b] == GPBO_FN_RASTRIGIN ? 5.12 : 2.0;
+                rg.lo[o2] = -w;
+                rg.hi[o2] = w;
+            }
+    }
+    const int64_t E = series ? 1 + (int64_t)d * o->n_base : routine ? 1 + d : 1 + d + (int64_t)d * (d - 1) / 2;
     const int per = routine ? R : 1;
-    const int64_t nf = E * o->n_base * per;
+    const int64_t nf = series ? E * R : E * o->n_base * per;
     const int srows = routine ? R : d;
     void *w = nullptr;
     GPBO_TRY(ws_reserve(ctx, sizeof(double) * (nf + (int64_t)srows * d + d), &w));
     double *f = (double *)w, *S = f + nf, *infl = S + (int64_t)srows * d;
     cudaStream_t st = ctx->stream;
 
-    if (!host_fn) {
+    if (!host_fn && series) {
+        k_screen_eval_series<<<(unsigned)cdiv64(E, 128), 128, 0, st>>>(spec, rg, d, o->n_base, o->growth, o->seed,
+                                                                         obj->noise_sd, f);
+        GPBO_LAUNCH_CHECK(ctx);
+    } else if (host_fn && series) {
+        std::vector<double> hf(nf), u0(d), x(d), fr(R);
+        for (int k = 0; k < d; ++k) u0[k] = uniform24d(o->seed, 3, (uint64_t)k);
+        for (int64_t e = 0; e < E; ++e) {
+            x = u0;
+            if (e > 0) {
+                const int i = (int)((e - 1) / o->n_base), v = (int)((e - 1) % o->n_base) + 1;
+                x[i] = series_value(u0[i], rg.lo[i], rg.hi[i], o->growth, v);
+            }
+            double ft = 0.0;
+            if (obj->fn(x.data(), d, &ft, fr.data(), obj->user) != 0) return GPBO_EINVAL;
+            for (int g = 0; g < R; ++g) hf[e * R + g] = fr[g];
+        }
+        GPBO_CUDA_TRY(cudaMemcpyAsync(f, hf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
+        GPBO_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (!host_fn) {
         const int64_t threads = E * o->n_base;
         if (routine)
             k_screen_eval_routine<<<(unsigned)cdiv64(threads, 128), 128, 0, st>>>(spec, d, o->n_base, o->h, o->seed,
@@ -287,7 +381,9 @@ int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opt
         GPBO_CUDA_TRY(cudaMemcpyAsync(f, hf.data(), sizeof(double) * nf, cudaMemcpyHostToDevice, st));
         GPBO_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if (routine)
+    if (series)
+        k_screen_score_series<<<(unsigned)cdiv64((int64_t)R * d, 128), 128, 0, st>>>(f, R, d, o->n_base, S);
+    else if (routine)
         k_screen_score_routine<<<(unsigned)cdiv64((int64_t)R * d, 128), 128, 0, st>>>(f, R, d, o->n_base, S);
     else
         k_screen_score_pairwise<<<(unsigned)cdiv64((int64_t)d * d, 128), 128, 0, st>>>(f, d, o->n_base, S, infl);
@@ -306,6 +402,14 @@ int screen_run(gpbo_ctx *ctx, const gpbo_objective *obj, int d, const screen_opt
                 if (hs[(size_t)i * d + j] > o->cutoff) ds.join(i, j);
         for (int i = 0; i < d; ++i) label[i] = ds.root(i);
     } else {
+        // a shared parameter belongs to the routine it influences most (ties: the first)
+        for (int i = 0; i < d; ++i)
+            if (owner[i] < 0) {
+                int b = 0;
+                for (int g = 1; g < R; ++g)
+                    if (hs[(size_t)g * d + i] > hs[(size_t)b * d + i]) b = g;
+                owner[i] = b;
+            }
         DisjointSets rs(R);
         for (int i = 0; i < d; ++i) {
             hinfl[i] = 0.0;

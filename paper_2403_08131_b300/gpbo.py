@@ -26,7 +26,7 @@ GPBO_OK, GPBO_EINVAL, GPBO_ENOTSPD, GPBO_ENAN, GPBO_ENOMEM, GPBO_ECUDA, GPBO_ETI
 PREC = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 HOST_PTRS = 0x1
 JITTER = 0x2
-SCREEN_PAIRWISE, SCREEN_ROUTINE = 0, 1
+SCREEN_PAIRWISE, SCREEN_ROUTINE, SCREEN_ROUTINE_SERIES = 0, 1, 2
 
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
@@ -55,7 +55,7 @@ class GpboObjective(C.Structure):
 
 class ScreenOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("n_base", C.c_int), ("h", C.c_double), ("cutoff", C.c_double),
-                ("max_dims", C.c_int), ("seed", C.c_uint64)]
+                ("max_dims", C.c_int), ("seed", C.c_uint64), ("growth", C.c_double), ("lo", _D), ("hi", _D)]
 
 
 def _sig(name, restype, argtypes):
@@ -383,9 +383,12 @@ class Context:
 
     # ------------------------------------------------------------ screen
     def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,
-               max_dims=10, mode=SCREEN_PAIRWISE, host_fn=None, d=None, n_routines=0, param_owner=None):
+               max_dims=10, mode=SCREEN_PAIRWISE, host_fn=None, d=None, n_routines=0, param_owner=None,
+               growth=0.1, lo=None, hi=None):
         """Built-in block objective (block_dim, block_fn) or a host black box
-        host_fn(x: np.ndarray) -> (f_total, routines) with d / n_routines / param_owner."""
+        host_fn(x: np.ndarray) -> (f_total, routines) with d / n_routines / param_owner
+        (-1 for a shared parameter).  mode SCREEN_ROUTINE_SERIES: n_base variations per
+        parameter, each `growth` above the last, in the ranges lo / hi of a host black box."""
         keep = []
         if host_fn is None:
             bd = np.ascontiguousarray(block_dim, dtype=np.int32)
@@ -413,7 +416,12 @@ class Context:
             obj = GpboObjective(0, C.cast(None, _I), C.cast(None, _I), 0.0, int(seed), cb, int(n_routines),
                                 ow.ctypes.data_as(_I), None)
             R = n_routines
-        opts = ScreenOpts(int(mode), int(n_base), float(h), float(cutoff), int(max_dims), int(seed))
+        lo_a = None if lo is None else np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.float64), (d,)))
+        hi_a = None if hi is None else np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.float64), (d,)))
+        keep += [lo_a, hi_a]
+        opts = ScreenOpts(int(mode), int(n_base), float(h), float(cutoff), int(max_dims), int(seed), float(growth),
+                          C.cast(None, _D) if lo_a is None else lo_a.ctypes.data_as(_D),
+                          C.cast(None, _D) if hi_a is None else hi_a.ctypes.data_as(_D))
         rows = d if mode == SCREEN_PAIRWISE else R
         score = np.zeros((rows, d))
         infl = np.zeros(d)

@@ -273,8 +273,21 @@ def bo_form(ctx, W):
     objective at each strategy's combined best configuration (lower is better)."""
     from paper_2403_08131_b300 import searches as S
 
-    cases, evals, secs = {}, 0, 0.0
+    from paper_2403_08131_b300 import gpbo
+
+    cases, evals, secs, decisions = {}, 0, 0.0, {}
     for case in range(1, 6):
+        # the methodology's first phase: the routine sensitivity on the paper's schedule
+        # (baseline from seed 1, 100 variations of 10%, raw group values), 25% cut-off
+        g = W.PaperSynthetic(case)
+        t0 = time.perf_counter()
+        scr = ctx.screen(host_fn=lambda u, g=g: (0.0, g.group_values(u)), d=20, n_routines=4,
+                         param_owner=np.repeat(np.arange(4), 5), n_base=100, cutoff=0.25, seed=1,
+                         mode=gpbo.SCREEN_ROUTINE_SERIES, growth=0.1, lo=-50.0, hi=50.0)
+        merged = bool(scr["group_of"][15] == scr["group_of"][10])
+        decisions[f"case{case}"] = {"g3_g4_merged": merged, "n_searches": scr["n_groups"],
+                                    "g3_score_from_g4_max": round(float(scr["score"][2, 15:20].max()), 4),
+                                    "screen_ms": round((time.perf_counter() - t0) * 1e3, 1)}
         f = W.PaperSynthetic(case, 0.1, seed=case)
         row = {"random": round(S.random_search(f, 200, seed=case)["value"], 2)}
         for name, searches in S.STRATEGIES.items():
@@ -282,6 +295,7 @@ def bo_form(ctx, W):
             row[name] = round(r["value"], 2)
             evals += sum(s["evaluations"] for s in r["searches"])
             secs += r["seconds"]
+        row["methodology"] = row["g1_g2_g34"] if merged else row["independent"]
         cases[f"case{case}"] = row
     f = W.PaperSynthetic(4, 0.1, seed=4)
     mle, mle_s = {}, {}
@@ -292,7 +306,7 @@ def bo_form(ctx, W):
     return {"workload": "paper synthetic Cases 1-5 (d=20, 4 routines), strategies joint / G1,G2,G3+G4 / "
                         "independent / random, 10 x k evaluations per search, M=16384 FP32",
             "value": round(evals / secs, 1), "unit": "BO evaluations/s (fixed hyperparameters)",
-            "minima": cases, "case4_refit_minima": mle, "case4_refit_seconds": mle_s,
+            "screen_decisions": decisions, "minima": cases, "case4_refit_minima": mle, "case4_refit_seconds": mle_s,
             "timing": "host wall clock around each search (objective evaluated on the host)"}
 
 

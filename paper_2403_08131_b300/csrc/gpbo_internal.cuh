@@ -161,6 +161,12 @@ size_t chol_tc_slice_bytes(int n_pad);
 int chol_tc_maps(const gp_model *m, void *map_a, void *map_b);  // two 128-byte CUtensorMap
 int64_t chol_tc_tiles(int nblk, int kb);
 int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b);
+
+// kinv_tc.cu: lower 64 x 64 tiles of K^-1 = L^-T L^-1 on the tensor cores at FP64 accuracy,
+// from Linv (n_pad x n_pad FP64; n_pad a multiple of 128).  slices: kinv_tc_slice_bytes(n_pad)
+// bytes and exps: n_pad ints of device scratch.
+size_t kinv_tc_slice_bytes(int n_pad);
+int kinv_tc(gpbo_ctx *ctx, cudaStream_t st, const double *Linv, int n_pad, void *slices, int *exps, double *C);
 bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
              float *mu);

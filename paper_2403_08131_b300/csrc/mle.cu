@@ -30,77 +30,14 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// One CTA per lower tile (I, J), J <= I, numbered p = I (I + 1) / 2 + J so that the tiles with
-// the most rows of L^-1 to reduce start first.  S = [K^-1]_{I,J} = sum_{k >= 64 I} L^-1[k, I]^T
-// L^-1[k, J] (L^-1 is lower triangular, so rows above block I are zero in both operands); each
-// thread holds a 4 x 4 piece (rows ty + 16 u, columns tx + 16 v).  Rows k of both operands are
-// contiguous 64-double segments, staged through two shared buffers (one barrier per step).
-// Epilogue, for p > q both < n (weight 1 = 2 x 1/2 by symmetry) with t = (x_p - x_q) / l,
-// r = |t|, e = exp(-sqrt5 r), G = alpha_p alpha_q - S_pq:
-//   g_k   += G s2 (5/3)(1 + sqrt5 r) e t_k^2            (k < d)
-//   g_d   += G s2 (1 + sqrt5 r + 5/3 r^2) e
-// and for p = q < n (weight 1/2): g_d += G s2 / 2, g_{d+1} += G sn2 / 2.
-// part[j * ntiles + p] receives the CTA's sum for component j (fixed order: deterministic).
-__global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Linv, const double *__restrict__ Xs,
-                                                   const double *__restrict__ alpha, int n, int d, int n_pad, int kend,
-                                                   double s2, double sn2, int ntiles, double *__restrict__ part)
+// The pair terms of one thread's 4 x 4 piece of a K^-1 tile (rows p0 + ty + 16 u, columns
+// q0 + tx + 16 v), reduced over the CTA into part[j * ntiles + p] (see k_lml_pairs).
+__device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const double *__restrict__ Xs,
+                                                  const double *__restrict__ alpha, int n, int d, int n_pad,
+                                                  double s2, double sn2, int ntiles, double *__restrict__ part, int p,
+                                                  int p0, int q0, double (*red)[GPBO_MAX_D + 2])
 {
-    __shared__ __align__(16) double As[2][LBK][LT];
-    __shared__ __align__(16) double Bs[2][LBK][LT];
-    __shared__ double red[8][GPBO_MAX_D + 2];
-    const int p = blockIdx.x;
-    int I = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((I + 1) * (I + 2) / 2 <= p) ++I;
-    while (I * (I + 1) / 2 > p) --I;
-    const int J = p - I * (I + 1) / 2;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
-    const int p0 = I * LT, q0 = J * LT;
-    const int lr = tid >> 4, lc = (tid & 15) * 4;
-
-    double acc[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-
-    double2 ra0, ra1, rb0, rb1;
-    {
-        const double *a = Linv + (int64_t)(p0 + lr) * n_pad + p0 + lc;
-        const double *b = Linv + (int64_t)(p0 + lr) * n_pad + q0 + lc;
-        ra0 = *reinterpret_cast<const double2 *>(a);
-        ra1 = *reinterpret_cast<const double2 *>(a + 2);
-        rb0 = *reinterpret_cast<const double2 *>(b);
-        rb1 = *reinterpret_cast<const double2 *>(b + 2);
-    }
-    int buf = 0;
-    for (int k0 = p0; k0 < kend; k0 += LBK) {
-        *reinterpret_cast<double2 *>(&As[buf][lr][lc]) = ra0;
-        *reinterpret_cast<double2 *>(&As[buf][lr][lc + 2]) = ra1;
-        *reinterpret_cast<double2 *>(&Bs[buf][lr][lc]) = rb0;
-        *reinterpret_cast<double2 *>(&Bs[buf][lr][lc + 2]) = rb1;
-        __syncthreads();
-        if (k0 + LBK < kend) {
-            const double *a = Linv + (int64_t)(k0 + LBK + lr) * n_pad + p0 + lc;
-            const double *b = Linv + (int64_t)(k0 + LBK + lr) * n_pad + q0 + lc;
-            ra0 = *reinterpret_cast<const double2 *>(a);
-            ra1 = *reinterpret_cast<const double2 *>(a + 2);
-            rb0 = *reinterpret_cast<const double2 *>(b);
-            rb1 = *reinterpret_cast<const double2 *>(b + 2);
-        }
-#pragma unroll
-        for (int t = 0; t < LBK; ++t) {
-            double x[4], y[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { x[u] = As[buf][t][ty + 16 * u]; y[u] = Bs[buf][t][tx + 16 * u]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
-        }
-        buf ^= 1;
-    }
-
-    // ---- epilogue
     double r2[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -175,6 +112,101 @@ __global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Li
     }
 }
 
+// One CTA per lower tile (I, J), J <= I, numbered p = I (I + 1) / 2 + J so that the tiles with
+// the most rows of L^-1 to reduce start first.  S = [K^-1]_{I,J} = sum_{k >= 64 I} L^-1[k, I]^T
+// L^-1[k, J] (L^-1 is lower triangular, so rows above block I are zero in both operands); each
+// thread holds a 4 x 4 piece (rows ty + 16 u, columns tx + 16 v).  Rows k of both operands are
+// contiguous 64-double segments, staged through two shared buffers (one barrier per step).
+// Epilogue, for p > q both < n (weight 1 = 2 x 1/2 by symmetry) with t = (x_p - x_q) / l,
+// r = |t|, e = exp(-sqrt5 r), G = alpha_p alpha_q - S_pq:
+//   g_k   += G s2 (5/3)(1 + sqrt5 r) e t_k^2            (k < d)
+//   g_d   += G s2 (1 + sqrt5 r + 5/3 r^2) e
+// and for p = q < n (weight 1/2): g_d += G s2 / 2, g_{d+1} += G sn2 / 2.
+// part[j * ntiles + p] receives the CTA's sum for component j (fixed order: deterministic).
+__global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Linv, const double *__restrict__ Xs,
+                                                   const double *__restrict__ alpha, int n, int d, int n_pad, int kend,
+                                                   double s2, double sn2, int ntiles, double *__restrict__ part)
+{
+    __shared__ __align__(16) double As[2][LBK][LT];
+    __shared__ __align__(16) double Bs[2][LBK][LT];
+    __shared__ double red[8][GPBO_MAX_D + 2];
+    const int p = blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= p) ++I;
+    while (I * (I + 1) / 2 > p) --I;
+    const int J = p - I * (I + 1) / 2;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int p0 = I * LT, q0 = J * LT;
+    const int lr = tid >> 4, lc = (tid & 15) * 4;
+
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+    double2 ra0, ra1, rb0, rb1;
+    {
+        const double *a = Linv + (int64_t)(p0 + lr) * n_pad + p0 + lc;
+        const double *b = Linv + (int64_t)(p0 + lr) * n_pad + q0 + lc;
+        ra0 = *reinterpret_cast<const double2 *>(a);
+        ra1 = *reinterpret_cast<const double2 *>(a + 2);
+        rb0 = *reinterpret_cast<const double2 *>(b);
+        rb1 = *reinterpret_cast<const double2 *>(b + 2);
+    }
+    int buf = 0;
+    for (int k0 = p0; k0 < kend; k0 += LBK) {
+        *reinterpret_cast<double2 *>(&As[buf][lr][lc]) = ra0;
+        *reinterpret_cast<double2 *>(&As[buf][lr][lc + 2]) = ra1;
+        *reinterpret_cast<double2 *>(&Bs[buf][lr][lc]) = rb0;
+        *reinterpret_cast<double2 *>(&Bs[buf][lr][lc + 2]) = rb1;
+        __syncthreads();
+        if (k0 + LBK < kend) {
+            const double *a = Linv + (int64_t)(k0 + LBK + lr) * n_pad + p0 + lc;
+            const double *b = Linv + (int64_t)(k0 + LBK + lr) * n_pad + q0 + lc;
+            ra0 = *reinterpret_cast<const double2 *>(a);
+            ra1 = *reinterpret_cast<const double2 *>(a + 2);
+            rb0 = *reinterpret_cast<const double2 *>(b);
+            rb1 = *reinterpret_cast<const double2 *>(b + 2);
+        }
+#pragma unroll
+        for (int t = 0; t < LBK; ++t) {
+            double x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { x[u] = As[buf][t][ty + 16 * u]; y[u] = Bs[buf][t][tx + 16 * u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+        }
+        buf ^= 1;
+    }
+
+    lml_pair_epilogue(acc, Xs, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+}
+
+// The same pair terms with K^-1 read from memory (the lower 64 x 64 tiles that kinv_tc forms
+// on the tensor cores), tile p = I (I + 1) / 2 + J as in k_lml_pairs.
+__global__ void __launch_bounds__(256) k_lml_pairs_kinv(const double *__restrict__ Kinv, const double *__restrict__ Xs,
+                                                        const double *__restrict__ alpha, int n, int d, int n_pad,
+                                                        double s2, double sn2, int ntiles, double *__restrict__ part)
+{
+    __shared__ double red[8][GPBO_MAX_D + 2];
+    const int p = blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= p) ++I;
+    while (I * (I + 1) / 2 > p) --I;
+    const int J = p - I * (I + 1) / 2;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int p0 = I * LT, q0 = J * LT;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = Kinv[(int64_t)(p0 + ty + 16 * u) * n_pad + q0 + tx + 16 * v];
+    lml_pair_epilogue(acc, Xs, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+}
+
 __device__ double block_sum256(double v, double *sh)
 {
     sh[threadIdx.x] = v;
@@ -221,6 +253,9 @@ struct MleState {
     double *part = nullptr;                    // (d + 2) x ntiles
     double *out = nullptr;                     // d + 3 (device)
     double *host = nullptr;                    // d + 3 (pinned)
+    void *kslices = nullptr;                   // tensor-core K^-1 (n_pad a multiple of 128): slices,
+    int *kexps = nullptr;                      //   their exponents
+    double *kinv = nullptr;                    //   and K^-1's lower tiles
     int ntiles = 0;
     int64_t evals = 0;
 };
@@ -230,7 +265,13 @@ static void mle_release(MleState &s)
     if (s.part) cudaFree(s.part);
     if (s.out) cudaFree(s.out);
     if (s.host) cudaFreeHost(s.host);
+    if (s.kslices) cudaFree(s.kslices);
+    if (s.kexps) cudaFree(s.kexps);
+    if (s.kinv) cudaFree(s.kinv);
     if (s.m) model_free(s.m);
+    s.kslices = nullptr;
+    s.kexps = nullptr;
+    s.kinv = nullptr;
     s.part = s.out = s.host = nullptr;
     s.m = nullptr;
 }
@@ -246,6 +287,12 @@ static int mle_init(MleState &s, gpbo_ctx *ctx, const double *X, const double *y
     GPBO_CUDA_TRY(cudaMalloc(&s.part, sizeof(double) * (size_t)(d + 2) * s.ntiles));
     GPBO_CUDA_TRY(cudaMalloc(&s.out, sizeof(double) * (d + 3)));
     GPBO_CUDA_TRY(cudaMallocHost(&s.host, sizeof(double) * (d + 3)));
+    const int n_pad = s.m->n_pad;
+    if (n_pad % 128 == 0 && n_pad >= 256) {
+        GPBO_CUDA_TRY(cudaMalloc(&s.kslices, kinv_tc_slice_bytes(n_pad)));
+        GPBO_CUDA_TRY(cudaMalloc(&s.kexps, sizeof(int) * n_pad));
+        GPBO_CUDA_TRY(cudaMalloc(&s.kinv, sizeof(double) * (size_t)n_pad * n_pad));
+    }
     return GPBO_OK;
 }
 
@@ -273,8 +320,15 @@ static int mle_eval(MleState &s, const double *theta, double *lml, double *grad)
     double flops = 0.0;
     for (int p = 0; p < n; ++p) flops += 2.0 * (double)(p + 1) * (double)(n - p);
     GPBO_TRY(trace_begin(ctx, PH_LML, flops));
-    k_lml_pairs<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, m->alpha64, n, d, n_pad, kend, m->s2, m->sn2,
-                                                   s.ntiles, s.part);
+    if (s.kinv) {
+        // K^-1 on the tensor cores (FP64 accuracy), then the pair terms from memory
+        GPBO_TRY(kinv_tc(ctx, ctx->stream, m->Linv64, n_pad, s.kslices, s.kexps, s.kinv));
+        k_lml_pairs_kinv<<<s.ntiles, 256, 0, ctx->stream>>>(s.kinv, m->Xs64, m->alpha64, n, d, n_pad, m->s2, m->sn2,
+                                                            s.ntiles, s.part);
+    } else {
+        k_lml_pairs<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, m->alpha64, n, d, n_pad, kend, m->s2,
+                                                       m->sn2, s.ntiles, s.part);
+    }
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_TRY(trace_end(ctx));
     k_lml_finish<<<1, 256, 0, ctx->stream>>>(s.part, s.ntiles, d + 2, s.y, m->alpha64, m->L, n, n_pad,

@@ -237,8 +237,26 @@ static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int>
     }
 }
 
+// FP64 levels of at least TRTRI_TC_MIN columns run on the tensor cores (slice products at FP64
+// accuracy); the small ones on the FP64 pipe.
+constexpr int TRTRI_TC_MIN = 256;
+
+// Scratch of the tensor-core FP64 levels (the largest level's).
+static size_t trtri_tc_scratch(int n_pad)
+{
+    std::vector<GemmProb> probs;
+    std::vector<int> first, count;
+    std::vector<int2> mm;
+    trtri_plan(n_pad, probs, first, count, mm);
+    size_t b = 0;
+    for (size_t l = 0; l < first.size(); ++l)
+        if (mm[l].y >= TRTRI_TC_MIN) b = std::max(b, dtc_scratch_bytes(count[l], std::max(mm[l].x, mm[l].y), mm[l].y));
+    return b;
+}
+
 template <typename T>
-static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev)
+static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev,
+                        void *tc_scratch = nullptr)
 {
     std::vector<GemmProb> probs;
     std::vector<int> first, count;
@@ -249,6 +267,14 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
     GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, probs.data(), sizeof(GemmProb) * probs.size(), cudaMemcpyHostToDevice,
                                   ctx->stream));
     for (size_t l = 0; l < first.size(); ++l) {
+        if (std::is_same<T, double>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN) {
+            // T = L21 X11 (X11 lower), then X21 = -X22 T (X22 lower)
+            GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Ls, (const double *)Linv, (double *)tmp, n_pad,
+                                    probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
+            GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Linv, (const double *)tmp, (double *)Linv, n_pad,
+                                    probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
+            continue;
+        }
         if (std::is_same<T, float>::value && mm[l].y >= 128) {
             // large FP32 levels: 128 x 128 tiles (the batched step uses the same rule per level)
             dim3 grid((mm[l].y + 127) / 128, (mm[l].x + 127) / 128, count[l]);
@@ -369,8 +395,9 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     const int max_probs = 2 * nblk + 2;
     const int64_t sq = (int64_t)n_pad * n_pad;
     const size_t vec = sizeof(double) * n_pad;
+    const size_t tc_bytes = m->prec == GPBO_PREC_F64 && n_pad >= 2 * TRTRI_TC_MIN ? trtri_tc_scratch(n_pad) : 0;
     const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
-                             sizeof(GemmProb) * 2 * max_probs;
+                             sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
     const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
     void *wsp = nullptr;
     GPBO_TRY(ws_reserve(ctx, vec * 6 + sync_bytes + inv_bytes, &wsp));
@@ -399,7 +426,8 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         probs = (GemmProb *)(tmp + sq);
         k_linv_init<double><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv64);
         GPBO_LAUNCH_CHECK(ctx);
-        GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs));
+        void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
+        GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs, tcs));
     } else {
         float *L32 = (float *)w2, *tmp = L32 + sq;
         probs = (GemmProb *)(tmp + sq);

@@ -10,13 +10,6 @@
 
 namespace gpbo {
 
-// Batched SIMT GEMM problem: operand offsets (elements) and shape; ld = leading dimension
-// of all three operands (the problem's n_pad).
-struct GemmProb {
-    int64_t a_off, b_off, c_off;
-    int m, n, k;
-    int ld;
-};
 
 // ------------------------------------------------------------------ inputs
 // Xs64[k][i] = X[i][k] / l_k for i < n, 0 for padding; Xs32 is its FP32 rounding.

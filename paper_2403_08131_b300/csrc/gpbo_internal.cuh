@@ -166,6 +166,19 @@ int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const vo
 // from Linv (n_pad x n_pad FP64; n_pad a multiple of 128).  slices: kinv_tc_slice_bytes(n_pad)
 // bytes and exps: n_pad ints of device scratch.
 size_t kinv_tc_slice_bytes(int n_pad);
+
+// dgemm_tc.cu: one level of the FP64 triangular inverse's products at FP64 accuracy on the
+// tensor cores: C_q = alpha A_q B_q (tri: 1 = B lower triangular, 2 = A lower triangular).
+// Batched SIMT GEMM problem: operand offsets (elements) and shape; ld = leading dimension
+// of all three operands (the problem's n_pad).
+struct GemmProb {
+    int64_t a_off, b_off, c_off;
+    int m, n, k;
+    int ld;
+};
+size_t dtc_scratch_bytes(int cnt, int mk, int nmax);
+int dgemm_tc_level(gpbo_ctx *ctx, cudaStream_t st, const double *A, const double *B, double *C, int ld,
+                   const GemmProb *probs, int cnt, double alpha, int tri, void *scratch);
 int kinv_tc(gpbo_ctx *ctx, cudaStream_t st, const double *Linv, int n_pad, void *slices, int *exps, double *C);
 bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,

@@ -105,18 +105,6 @@ __device__ __forceinline__ void tile_coords(int t, int nblk, int &i2, int &jb)
     jb = t;
 }
 
-__device__ __forceinline__ double scaled_to_double(long long x, int k)
-{
-    if (x == 0) return 0.0;
-    const unsigned long long sign = (unsigned long long)x & 0x8000000000000000ull;
-    const unsigned long long ux = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-    const int lz = __clzll((long long)ux);
-    const int ex = 1023 + 63 - lz + k;
-    if (ex <= 0 || ex >= 2047) return scalbn((double)x, k);
-    const unsigned long long m = (ux << lz) >> 11;
-    return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (m & 0x000FFFFFFFFFFFFFull)));
-}
-
 __global__ void __launch_bounds__(THREADS, 1)
     k_kinv_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, Params P)
 {

@@ -166,6 +166,22 @@ __device__ __forceinline__ void pin16(uint32_t *r)
                    "+r"(r[15]));
 }
 
+// x 2^k as a double, built on the integer pipe: normalise |x| by its leading zeros, write the
+// exponent with k folded in and the top 52 bits after the leading one (truncated: relative
+// error below 2^-52).  Values outside the normal range take scalbn.  For the FP64 results of
+// the slice-product kernels, where the FP64 pipe is the scarce one.
+__device__ __forceinline__ double scaled_to_double(long long x, int k)
+{
+    if (x == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)x & 0x8000000000000000ull;
+    const unsigned long long ux = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const int lz = __clzll((long long)ux);
+    const int ex = 1023 + 63 - lz + k;
+    if (ex <= 0 || ex >= 2047) return scalbn((double)x, k);
+    const unsigned long long m = (ux << lz) >> 11;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulate, A/B format (0 = F16, 1 = BF16), both
 // K-major, N x M.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, int N, int M)

@@ -35,6 +35,19 @@ def _check(prec, got, ref, Xc=None):
     return check_argmax(am, rei, bar)
 
 
+@pytest.mark.parametrize("n", [600, 1100])
+def test_f64_parity_with_tensor_core_inverse(ctx, orc, n):
+    """n_pad >= 512: the large levels of the FP64 L^-1 run on the tensor cores (slice
+    products at FP64 accuracy); FP64 scoring keeps the FP64 bar."""
+    w = W.config4(n=n, M=3000, prec="f64")
+    ys = (w.y - w.y.mean()) / w.y.std()
+    m = ctx.fit(to_dev(w.X), to_dev(ys), w.lengthscale, 1.0, w.noise_var, prec="f64")
+    Xc = w.candidates(3000)
+    got = _score(ctx, m, Xc, "f64", ys.min())
+    _check("f64", got, _oracle(orc, w, ys, Xc, ys.min()))
+    m.free()
+
+
 def test_f64_rosenbrock_n64_full_parity(ctx, orc):
     w = W.config1()
     ys = (w.y - w.y.mean()) / w.y.std()

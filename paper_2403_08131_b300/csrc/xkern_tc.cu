@@ -38,7 +38,7 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int KB = 128;                    // split width: [hi|hi|lo|0] x 32 for A', [hi|lo|hi|0] for B'
 constexpr int DMAX = 32;
-constexpr int STAGES = 2;
+constexpr int STAGES = 1;                  // B' copies are short next to a chunk's epilogue
 constexpr int EPI_WARPS = 16;             // 4 lane quadrants x 4 column groups of 64
 constexpr int GROUPS = EPI_WARPS / 4;
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
@@ -64,10 +64,15 @@ struct alignas(16) Shared {
     float mu_part[2][GROUPS - 1][BM]; // column groups 1..3: partial means per slot
 };
 
+// K* leaves through per-warp staging tiles of 32 rows x 32 values (2 KB), stored by TMA with
+// 64-byte swizzle: the 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3), which also
+// keeps the lanes' row-wise shared-memory writes free of bank conflicts.
+constexpr int STAGE_BYTES = 32 * 64;
+
 constexpr int ALPHA_SMEM_MAX = 4096;  // models up to this n_pad keep alpha in shared memory
 inline size_t smem_bytes(bool alpha_smem)
 {
-    return (size_t)2 * A_SLOT + (size_t)STAGES * B_STAGE + 1024 + sizeof(Shared) +
+    return (size_t)2 * A_SLOT + (size_t)STAGES * B_STAGE + (size_t)EPI_WARPS * STAGE_BYTES + 1024 + sizeof(Shared) +
            (alpha_smem ? sizeof(float) * ALPHA_SMEM_MAX : 0);
 }
 
@@ -82,7 +87,6 @@ struct Params {
     float zs[DMAX];       // 1 / lengthscale
     const float *nb;      // n_pad: |z_i|^2
     const float *alpha;   // n_pad
-    void *Kst;            // C x n_pad, 16-bit
     float *mu;            // pool-indexed
     unsigned *status;
     uint32_t idesc;
@@ -162,13 +166,15 @@ __device__ __forceinline__ float build_row(unsigned char *a, int r, int64_t t, c
 }
 
 template <typename Out, bool ALPHA_SMEM>
-__global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__ CUtensorMap map_b, const Params P)
+__global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_k,
+                                                    const Params P)
 {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *aslot = base;                       // 2 x A_SLOT
     unsigned char *bst = base + 2 * A_SLOT;            // STAGES x B_STAGE
-    Shared *sh = (Shared *)(bst + (size_t)STAGES * B_STAGE);
+    unsigned char *stg = bst + (size_t)STAGES * B_STAGE;  // EPI_WARPS x STAGE_BYTES
+    Shared *sh = (Shared *)(stg + (size_t)EPI_WARPS * STAGE_BYTES);
     float *alpha_s = (float *)(sh + 1);  // n_pad floats when ALPHA_SMEM
     if (ALPHA_SMEM)
         for (int i = threadIdx.x; i < P.n_pad; i += blockDim.x) alpha_s[i] = P.alpha[i];
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
         const bool builder = grp == 0;
         const float s2 = P.s2, c1 = P.s2 * 2.2360680f, c2 = P.s2 * 1.6666666f;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-        Out *Kst = (Out *)P.Kst;
+        uint4 *my_stage = reinterpret_cast<uint4 *>(stg + (size_t)ew * STAGE_BYTES);
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
@@ -308,6 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->a_empty[slot]);
             const int64_t cl = (int64_t)t * BM + row;
+            const int64_t row0 = (int64_t)t * BM + quad * 32;  // the warp's first row
             float mu = 0.0f;
             for (int q = 0; q < nq; ++q) {
                 const bool g = mbar_wait_inl(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
@@ -333,11 +340,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                         pk[j / 2] = Pack8<Out>::two(k0, k1);
                         pk[j / 2 + 1] = Pack8<Out>::two(k2, k3);
                     }
-                    if (cl < P.C) {
-                        uint4 *dst = reinterpret_cast<uint4 *>(Kst + cl * P.n_pad + i0);
+                    // K* out: each lane writes its row's 64 bytes into the warp's staging tile
+                    // (once the previous tile's TMA store has read it), one lane stores the
+                    // 32 x 32 tile; rows past C are clipped by the tensor map
+                    if (lane == 0) bulk_wait_read0();
+                    __syncwarp();
+                    const int sw = (lane >> 1) & 3;
 #pragma unroll
-                        for (int w4 = 0; w4 < 4; ++w4)
-                            dst[w4] = make_uint4(pk[4 * w4], pk[4 * w4 + 1], pk[4 * w4 + 2], pk[4 * w4 + 3]);
+                    for (int w4 = 0; w4 < 4; ++w4)
+                        my_stage[lane * 4 + (w4 ^ sw)] =
+                            make_uint4(pk[4 * w4], pk[4 * w4 + 1], pk[4 * w4 + 2], pk[4 * w4 + 3]);
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && row0 < P.C) {
+                        tma_store_2d(&map_k, my_stage, i0, (int)row0);
+                        bulk_commit();
                     }
                 }
                 tc_fence_before();
@@ -365,6 +382,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                 if (cl < P.C) P.mu[P.c0 + cl] = m;
             }
         }
+        if (lane == 0) bulk_wait_all0();  // the last K* tiles are written before the CTA ends
     }
     tc_fence_before();
     __syncthreads();
@@ -417,9 +435,12 @@ bool xkern_tc_usable(const gp_model *m) { return m->Zsplit != nullptr && m->d <=
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,
              float *mu)
 {
-    if (m->n_pad % xtc::BN != 0 || ((uintptr_t)Kst & 15)) return GPBO_EINVAL;
-    CUtensorMap mb;
+    if (m->n_pad % xtc::BN != 0 || !Kst || ((uintptr_t)Kst & 15) || C <= 0 || C > 0x7fffffffll) return GPBO_EINVAL;
+    CUtensorMap mb, mk;
     GPBO_TRY(encode_2d(&mb, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, m->Zsplit, (uint64_t)m->n_pad, (uint64_t)xtc::KB, xtc::BN));
+    GPBO_TRY(encode_2d_box(&mk,
+                           m->prec == GPBO_PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                           Kst, (uint64_t)C, (uint64_t)m->n_pad, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B));
     xtc::Params P;
     P.C = C;
     P.c0 = c0;
@@ -433,7 +454,6 @@ int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, i
     for (int k = 0; k < xtc::DMAX; ++k) P.zs[k] = k < m->d ? (float)(1.0 / m->ls[k]) : 0.0f;
     P.nb = m->nb32;
     P.alpha = m->alpha32;
-    P.Kst = Kst;
     P.mu = mu;
     P.status = ctx->dev_status;
     P.idesc = tcx::idesc_f16(0u, xtc::BN, xtc::BM);
@@ -442,7 +462,7 @@ int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, i
     const size_t smem = xtc::smem_bytes(as);
     auto launch = [&](auto kern) -> int {
         GPBO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, P);
+        kern<<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, mk, P);
         return GPBO_OK;
     };
     if (m->prec == GPBO_PREC_BF16) {

@@ -5,9 +5,9 @@
 // Step kb of the right-looking factorisation subtracts P P^T from the trailing lower tiles,
 // P = L[rows below, block column kb] (64 columns).  Each row r of P is written as
 //     P_r = 2^(e_r - 7) (a_1 + 2^-8 a_2 + ... + 2^-48 a_7) + rest,    |a_s| <= 128 integers,
-// with e_r the exponent that puts the row's largest |entry| just below 2^e_r, a_1 = rint(2^7 x),
-// and each later slice the rounded remainder of the one before scaled by 2^8 (|rest| <=
-// 2^(e_r - 56)).  A slice is exact in BF16, a product of two is an integer below 2^14, and up to
+// with e_r the exponent that puts the row's largest |entry| just below 2^e_r and a_1 .. a_7 the
+// balanced base-256 digits of the integer round(x 2^(55 - e_r)), taken on the integer pipe from
+// the bits of x (|rest| <= 2^(e_r - 56)).  A slice is exact in BF16, a product of two is an integer below 2^14, and up to
 // 7 x 64 of them sum below 2^23: every partial sum of a tensor-core MMA with FP32 accumulation
 // is an exact integer, whatever the order or rounding mode.  Products of slices s and t carry
 // the weight 2^(e_r + e_c - 14 - 8 (s + t - 2)); the kernel keeps the 34 pairs with
@@ -64,20 +64,17 @@ __global__ void __launch_bounds__(256) k_chol_split(const double *__restrict__ A
     if (r >= n_pad) return;
     const double *row = A + (int64_t)r * n_pad + (int64_t)kb * NB;
     const double2 v = *reinterpret_cast<const double2 *>(row + 2 * lane);
-    double mx = fmax(fabs(v.x), fabs(v.y));
+    unsigned long long mx = max(mag_bits(v.x), mag_bits(v.y));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
-    double t0 = scalbn(v.x, 7 - e), t1 = scalbn(v.y, 7 - e);  // |x| < 1, times 2^7
-    for (int s = 0; s < SLICES; ++s) {
-        const double a0 = rint(t0), a1 = rint(t1);
-        __nv_bfloat162 p;
-        p.x = __double2bfloat16(a0);
-        p.y = __double2bfloat16(a1);
-        *reinterpret_cast<__nv_bfloat162 *>(slices + ((int64_t)s * n_pad + r) * BK + 2 * lane) = p;
-        t0 = (t0 - a0) * 256.0;
-        t1 = (t1 - a1) * 256.0;
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = exp_of_mag(mx);
+    uint16_t d0[SLICES], d1[SLICES];
+    split7(fixed55(v.x, e), d0);
+    split7(fixed55(v.y, e), d1);
+#pragma unroll
+    for (int s = 0; s < SLICES; ++s)
+        *reinterpret_cast<uint32_t *>(slices + ((int64_t)s * n_pad + r) * BK + 2 * lane) =
+            (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
     if (lane == 0) exps[r] = e;
 }
 

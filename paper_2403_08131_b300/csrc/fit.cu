@@ -49,6 +49,11 @@ constexpr int SLAB_ROWS = 4;
 // Models with the tensor-core update use it while at least CHOL_TC_MIN_T block columns remain
 // after the lookahead column; the last few small updates stay on the FP64 pipe.
 constexpr int CHOL_TC_MIN_T = 4;
+// Warps per CTA of the diagonal-block inverse (one column per warp, NB / INV_WARPS CTAs).  Two
+// measured best at n = 4096 (Cholesky 8.54 ms against 8.68 with four and 9.04 with one): the
+// inverse overlaps the tensor-core updates of the main stream, and narrower CTAs share fewer SMs'
+// FP64 units with them; with one warp the load of the block dominates.
+constexpr int INV_WARPS = 2;
 // Programmatic dependent launch along the factorisation's chain (next-column update -> diagonal
 // factor -> inverse -> panel, one stream): each kernel lets the next one be scheduled as soon as
 // all of its own CTAs are running, and each waits (griddepcontrol.wait: the previous kernel has
@@ -346,7 +351,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, 0, m->Dinv));
+    GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, 0, m->Dinv));
     if (nblk > 1)
         GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((nblk - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, 0,
                             m->Dinv));
@@ -363,7 +368,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         GPBO_TRY(launch_pdl(ctx, k_chol_diag, dim3(1), dim3(DIAG_THREADS), smem1, side, m->L, n_pad, kb + 1, m->Dinv,
                             ctx->dev_status));
-        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb + 1, m->Dinv));
+        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1, m->Dinv));
         if (T > 1)
             GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((T - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, kb + 1,
                                 m->Dinv));

@@ -160,12 +160,12 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
 }
 
 // Inverse X = L_kk^-1 of diagonal block kb (after k_chol_diag_body), by forward substitution of
-// the unit columns, one warp per column (CTA bx: columns 4 bx .. 4 bx + 3), lanes owning rows
-// lane and lane + 32.  With rd_t = 1 / L_tt (the pivot's rsqrt, from Dinv's diagonal) and the
+// the unit columns, one warp per column (CTA bx: columns W bx .. W bx + W - 1 for W warps), lanes
+// owning rows lane and lane + 32.  With rd_t = 1 / L_tt (the pivot's rsqrt, from Dinv's diagonal) and the
 // scaled columns l'_it = l_it rd_t, the unscaled solution x~ takes x~_ic -= l'_it x~_tc for
 // t = c .. i - 1, and X_ic = rd_i x~_ic: one shuffle and one or two FP64 FMAs per step (on this
 // part every FP64 warp instruction holds its SMSP's FP64 unit for 64 cycles, so the step count
-// of this chain is what the factorisation waits on).  Launch: 16 CTAs of 128 threads.
+// of this chain is what the factorisation waits on).  Launch: 64 / W CTAs of 32 W threads.
 __device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, int n_pad, int kb,
                                                   double *__restrict__ Dinv, const int bx)
 {
@@ -174,14 +174,14 @@ __device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
     double *D = Dinv + (int64_t)kb * NB * NB;
-    if (tid < NB) rd[tid] = D[tid * NB + tid];
+    for (int e = tid; e < NB; e += blockDim.x) rd[e] = D[e * NB + e];
     __syncthreads();
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, t = e % NB;
         l[i][t] = t < i ? A[base + (int64_t)i * n_pad + t] * rd[t] : 0.0;
     }
     __syncthreads();
-    const int c = bx * 4 + warp;
+    const int c = bx * (int)(blockDim.x >> 5) + warp;
     double x0 = lane == c ? 1.0 : 0.0, x1 = lane + 32 == c ? 1.0 : 0.0;
     for (int t = c; t < NB; ++t) {
         const double v = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);

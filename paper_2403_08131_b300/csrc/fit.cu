@@ -242,12 +242,13 @@ static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int>
     }
 }
 
-// FP64 levels of at least TRTRI_TC_MIN columns run on the tensor cores (slice products at FP64
-// accuracy); the small ones on the FP64 pipe.
+// Levels of at least TRTRI_TC_MIN columns run on the tensor cores: slice products at FP64
+// accuracy for the FP64 inverse (7 slices), at FP32 accuracy for the FP32 one (3 slices); the
+// small levels on the FP64 / FP32 pipes.
 constexpr int TRTRI_TC_MIN = 256;
 
-// Scratch of the tensor-core FP64 levels (the largest level's).
-static size_t trtri_tc_scratch(int n_pad)
+// Scratch of the tensor-core levels (the largest level's).
+static size_t trtri_tc_scratch(int n_pad, bool f64)
 {
     std::vector<GemmProb> probs;
     std::vector<int> first, count;
@@ -255,7 +256,10 @@ static size_t trtri_tc_scratch(int n_pad)
     trtri_plan(n_pad, probs, first, count, mm);
     size_t b = 0;
     for (size_t l = 0; l < first.size(); ++l)
-        if (mm[l].y >= TRTRI_TC_MIN) b = std::max(b, dtc_scratch_bytes(count[l], std::max(mm[l].x, mm[l].y), mm[l].y));
+        if (mm[l].y >= TRTRI_TC_MIN) {
+            const int mk = std::max(mm[l].x, mm[l].y);
+            b = std::max(b, f64 ? dtc_scratch_bytes(count[l], mk, mm[l].y) : stc_scratch_bytes(count[l], mk, mm[l].y));
+        }
     return b;
 }
 
@@ -277,6 +281,14 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
             GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Ls, (const double *)Linv, (double *)tmp, n_pad,
                                     probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
             GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Linv, (const double *)tmp, (double *)Linv, n_pad,
+                                    probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
+            continue;
+        }
+        if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN) {
+            // FP32 accuracy from three slices: T = L21 X11 (X11 lower), then X21 = -X22 T
+            GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Ls, (const float *)Linv, (float *)tmp, n_pad,
+                                    probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
+            GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Linv, (const float *)tmp, (float *)Linv, n_pad,
                                     probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
             continue;
         }
@@ -400,7 +412,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     const int max_probs = 2 * nblk + 2;
     const int64_t sq = (int64_t)n_pad * n_pad;
     const size_t vec = sizeof(double) * n_pad;
-    const size_t tc_bytes = m->prec == GPBO_PREC_F64 && n_pad >= 2 * TRTRI_TC_MIN ? trtri_tc_scratch(n_pad) : 0;
+    const size_t tc_bytes = n_pad >= 2 * TRTRI_TC_MIN ? trtri_tc_scratch(n_pad, m->prec == GPBO_PREC_F64) : 0;
     const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
                              sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
     const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
@@ -440,7 +452,8 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         k_linv_init<float><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv32);
         GPBO_LAUNCH_CHECK(ctx);
-        GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs));
+        void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
+        GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs, tcs));
         if (m->prec == GPBO_PREC_BF16) {
             __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;
             k_split_bf16<<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, hi, hi + sq);

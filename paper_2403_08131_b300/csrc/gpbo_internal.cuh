@@ -179,6 +179,9 @@ struct GemmProb {
 size_t dtc_scratch_bytes(int cnt, int mk, int nmax);
 int dgemm_tc_level(gpbo_ctx *ctx, cudaStream_t st, const double *A, const double *B, double *C, int ld,
                    const GemmProb *probs, int cnt, double alpha, int tri, void *scratch);
+size_t stc_scratch_bytes(int cnt, int mk, int nmax);
+int sgemm_tc_level(gpbo_ctx *ctx, cudaStream_t st, const float *A, const float *B, float *C, int ld,
+                   const GemmProb *probs, int cnt, double alpha, int tri, void *scratch);
 int kinv_tc(gpbo_ctx *ctx, cudaStream_t st, const double *Linv, int n_pad, void *slices, int *exps, double *C);
 bool xkern_tc_usable(const gp_model *m);
 int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, int64_t c0, int64_t C, void *Kst,

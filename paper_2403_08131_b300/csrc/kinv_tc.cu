@@ -42,15 +42,15 @@ using namespace tcx;
 // 32 columns: 8 row groups, warp-coalesced reads of 32 consecutive columns.
 __global__ void __launch_bounds__(256) k_kinv_exp(const double *__restrict__ Li, int n_pad, int *__restrict__ exps)
 {
-    __shared__ double mx[8][32];
+    __shared__ unsigned long long mx[8][32];
     const int p = blockIdx.x * 32 + (threadIdx.x & 31), rg = threadIdx.x >> 5;
-    double m = 0.0;
-    for (int k = rg; k < n_pad; k += 8) m = fmax(m, fabs(Li[(int64_t)k * n_pad + p]));
+    unsigned long long m = 0;
+    for (int k = rg; k < n_pad; k += 8) m = max(m, (unsigned long long)mag_bits(Li[(int64_t)k * n_pad + p]));
     mx[rg][threadIdx.x & 31] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
-        for (int g = 1; g < 8; ++g) m = fmax(m, mx[g][threadIdx.x]);
-        exps[p] = m > 0.0 ? ilogb(m) + 1 : 0;
+        for (int g = 1; g < 8; ++g) m = max(m, mx[g][threadIdx.x]);
+        exps[p] = exp_of_mag(m);
     }
 }
 
@@ -66,12 +66,11 @@ __global__ void __launch_bounds__(256) k_kinv_split(const double *__restrict__ L
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int p = p0 + r;
-        double v = scalbn(t[tx][r], 7 - exps[p]);  // element (k0 + tx, p), |v| < 2^7
-        for (int s = 0; s < SLICES; ++s) {
-            const double a = rint(v);
-            slices[((int64_t)s * n_pad + p) * n_pad + k0 + tx] = __double2bfloat16(a);
-            v = (v - a) * 256.0;
-        }
+        uint16_t d[SLICES];
+        split7(fixed55(t[tx][r], exps[p]), d);  // element (k0 + tx, p)
+        uint16_t *out = reinterpret_cast<uint16_t *>(slices);
+#pragma unroll
+        for (int s = 0; s < SLICES; ++s) out[((int64_t)s * n_pad + p) * n_pad + k0 + tx] = d[s];
     }
 }
 

@@ -98,42 +98,64 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 }
 
 // Error-free 8-bit slicing on the integer pipe (no FP64 instruction).  For x with |x| < 2^e,
-// fixed55 returns X = round(x 2^(55 - e)) (|X| <= 2^55) from the bits of x, and split7 writes
-// X = sum_s d_s 2^(8 (6 - s)) in balanced base-256 digits, d_0 .. d_6 with |d_0| <= 128 and
-// -128 <= d_s <= 127 for s > 0, each as BF16 bits (exact: at most 8 significant bits).
-// |x - X 2^(e - 55)| <= 2^(e - 56).
-__device__ __forceinline__ int64_t fixed55(double x, int e)
+// fixed_of(x, e, P) returns X = round(x 2^(P - e)) (|X| <= 2^P) from the bits of x, and
+// split_digits<S> writes X = sum_s d_s 2^(8 (S - 1 - s)) in balanced base-256 digits, d_0 ..
+// d_(S-1) with |d_0| <= 128 (for P = 8 S - 1) and -128 <= d_s <= 127 for s > 0, each as BF16 bits
+// (exact: at most 8 significant bits).  |x - X 2^(e - P)| <= 2^(e - P - 1).
+__device__ __forceinline__ int64_t fixed_of(double x, int e, int P)
 {
     const uint64_t bits = (uint64_t)__double_as_longlong(x), mag = bits & 0x7fffffffffffffffull;
     const int E = (int)(mag >> 52);
     const uint64_t m = (mag & 0x000fffffffffffffull) | (E ? 0x0010000000000000ull : 0ull);
-    const int sh = (E ? E : 1) - 1020 - e;  // x = m 2^(E - 1075); |x| < 2^e makes sh <= 2
+    const int sh = (E ? E : 1) - 1075 + P - e;  // x = m 2^(E - 1075); |x| < 2^e makes X < 2^P
     uint64_t X;
     if (sh >= 0) X = m << sh;
     else if (sh > -64) X = (m + (1ull << (-sh - 1))) >> (-sh);
     else X = 0;
     return (bits >> 63) ? -(int64_t)X : (int64_t)X;
 }
-// the row exponent e (|x| < 2^e for every x of the row) from the largest magnitude's bits
+__device__ __forceinline__ int64_t fixed_of(float x, int e, int P)
+{
+    const uint32_t bits = __float_as_uint(x), mag = bits & 0x7fffffffu;
+    const int E = (int)(mag >> 23);
+    const uint64_t m = (uint64_t)((mag & 0x007fffffu) | (E ? 0x00800000u : 0u));
+    const int sh = (E ? E : 1) - 150 + P - e;  // x = m 2^(E - 150)
+    uint64_t X;
+    if (sh >= 0) X = m << sh;
+    else if (sh > -64) X = (m + (1ull << (-sh - 1))) >> (-sh);
+    else X = 0;
+    return (bits >> 31) ? -(int64_t)X : (int64_t)X;
+}
+__device__ __forceinline__ int64_t fixed55(double x, int e) { return fixed_of(x, e, 55); }
+// |x| as an unsigned integer that orders like |x|
 __device__ __forceinline__ uint64_t mag_bits(double x)
 {
     return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
+__device__ __forceinline__ uint64_t mag_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+// the exponent e with |x| < 2^e for the largest magnitude mx (as mag_bits), 0 for mx = 0
 __device__ __forceinline__ int exp_of_mag(uint64_t mx) { return mx ? (int)(mx >> 52 ? mx >> 52 : 1) - 1022 : 0; }
+template <typename T> __device__ __forceinline__ int exp_of_mag_t(uint64_t mx);
+template <> __device__ __forceinline__ int exp_of_mag_t<double>(uint64_t mx) { return exp_of_mag(mx); }
+template <> __device__ __forceinline__ int exp_of_mag_t<float>(uint64_t mx)
+{
+    return mx ? (int)(mx >> 23 ? mx >> 23 : 1) - 126 : 0;
+}
 __device__ __forceinline__ uint16_t bf16_of_small_int(int d)
 {
     return (uint16_t)(__float_as_uint((float)d) >> 16);  // |d| <= 128: exact in BF16
 }
-__device__ __forceinline__ void split7(int64_t X, uint16_t (&out)[7])
+template <int S> __device__ __forceinline__ void split_digits(int64_t X, uint16_t (&out)[S])
 {
 #pragma unroll
-    for (int s = 6; s >= 1; --s) {
+    for (int s = S - 1; s >= 1; --s) {
         const int64_t q = (X + 128) >> 8;
         out[s] = bf16_of_small_int((int)(X - (q << 8)));
         X = q;
     }
     out[0] = bf16_of_small_int((int)X);
 }
+__device__ __forceinline__ void split7(int64_t X, uint16_t (&out)[7]) { split_digits<7>(X, out); }
 
 // TMA tile store (shared -> global) in the calling thread's bulk async-group.
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)

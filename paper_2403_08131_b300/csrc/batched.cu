@@ -23,8 +23,9 @@ struct BProb {
     int64_t M;
     uint64_t seed;
     double s2, sn2;
-    int64_t off_X, off_y, off_xs, off_sq, off_dinv, off_vec, off_kst, off_mu, off_part;
+    int64_t off_X, off_y, off_xs, off_sq, off_dinv, off_vec, off_kst, off_mu, off_part, off_rpart;
     int part_count;
+    int chunks;  // row chunks of the refinement's X^T u
 };
 
 struct BatchPlan {
@@ -39,6 +40,7 @@ struct BatchPlan {
     std::vector<BProb> probs;
     double *dX = nullptr, *dy = nullptr, *dys = nullptr, *tau = nullptr;
     double *Xs64 = nullptr, *K = nullptr, *L = nullptr, *Dinv = nullptr, *vec = nullptr, *lsinv = nullptr;
+    double *rpart = nullptr;  // the refinement's row-chunk partial sums
     float *Xs32 = nullptr, *alpha32 = nullptr, *L32 = nullptr, *Linv32 = nullptr, *tmp = nullptr, *Kst = nullptr;
     float *mu = nullptr, *pei = nullptr;
     int64_t *pidx = nullptr;
@@ -49,7 +51,7 @@ struct BatchPlan {
     std::vector<int> lvl_first, lvl_count;
     std::vector<int2> lvl_mm;
     int64_t sum_vec = 0;
-    int max_npad = 0, max_nblk = 0, max_tiles64 = 0;
+    int max_npad = 0, max_nblk = 0, max_tiles64 = 0, max_chunks = 0;
     int64_t max_M = 0;
     int64_t max_sq = 0, max_dn = 0;
     int tile_req = 0;    // requested variance tile (0: autotune)
@@ -57,7 +59,7 @@ struct BatchPlan {
     float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 64, 128, 256
     cudaStream_t cap = nullptr;
     cudaStream_t cap2 = nullptr;     // second capture stream: lookahead column, alpha solve
-    cudaEvent_t ev[4] = {};          // fork / join events between the two capture streams
+    cudaEvent_t ev[5] = {};          // fork / join events between the two capture streams
     int64_t kernels = 0;             // kernel nodes in the captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -176,12 +178,30 @@ __global__ void b_residual(const BProb *P, const double *K, double *vec)
     k_residual_body(K + p.off_sq, v, v + p.n_pad, p.n_pad, v + 4 * (int64_t)p.n_pad, blockIdx.x, 0);
 }
 
-__global__ void b_axpy_cast(const BProb *P, double *vec, float *alpha32)
+// Refinement correction through the FP32 L^-1 (the single-problem path's arithmetic):
+// u = X r (slot 5 from slot 4), part = chunks of X^T u, alpha (slot 0) += their sum.
+__global__ void __launch_bounds__(256) b_trmv(const BProb *P, const float *Linv, double *vec)
+{
+    const BProb &p = P[blockIdx.y];
+    if ((int)(blockIdx.x * 8) >= p.n_pad) return;
+    double *v = vec + p.off_vec;
+    k_trmv_body(Linv + p.off_sq, p.n_pad, v + 4 * (int64_t)p.n_pad, v + 5 * (int64_t)p.n_pad, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) b_trmv_t_part(const BProb *P, const float *Linv, const double *vec,
+                                                     double *rpart)
+{
+    const BProb &p = P[blockIdx.z];
+    if ((int)(blockIdx.x * 32) >= p.n_pad || (int)blockIdx.y >= p.chunks) return;  // whole CTA
+    k_trmv_t_part_body(Linv + p.off_sq, p.n_pad, vec + p.off_vec + 5 * (int64_t)p.n_pad, rpart + p.off_rpart,
+                       blockIdx.x, blockIdx.y);
+}
+
+__global__ void b_trmv_t_sum(const BProb *P, const double *rpart, double *vec, float *alpha32)
 {
     const BProb &p = P[blockIdx.y];
     if ((int)(blockIdx.x * blockDim.x) >= p.n_pad) return;
-    double *v = vec + p.off_vec;
-    k_axpy_cast_body(v, v + 5 * (int64_t)p.n_pad, p.n_pad, alpha32 + p.off_vec / 6, blockIdx.x, 0);
+    k_trmv_t_sum_body(rpart + p.off_rpart, p.n_pad, p.chunks, vec + p.off_vec, alpha32 + p.off_vec / 6, blockIdx.x);
 }
 
 __global__ void b_cast_L(const BProb *P, const double *L, float *L32)
@@ -274,7 +294,7 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
 {
     const int G = pl->G;
     pl->probs.resize(G);
-    int64_t sX = 0, sy = 0, sxs = 0, ssq = 0, sdinv = 0, svec = 0, skst = 0, smu = 0, spart = 0;
+    int64_t sX = 0, sy = 0, sxs = 0, ssq = 0, sdinv = 0, svec = 0, skst = 0, smu = 0, spart = 0, srpart = 0;
     std::vector<double> lsinv((size_t)G * GPBO_MAX_D, 0.0);
     for (int g = 0; g < G; ++g) {
         BProb &p = pl->probs[g];
@@ -297,6 +317,9 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
         p.off_mu = smu;   smu += p.M;
         p.part_count = (int)cdiv64(p.M, 64);
         p.off_part = spart; spart += cdiv64(p.M, 64);  // room for the smallest variance tile
+        p.chunks = (p.n_pad + TRMV_ROWS - 1) / TRMV_ROWS;
+        p.off_rpart = srpart; srpart += (int64_t)p.chunks * p.n_pad;
+        pl->max_chunks = std::max(pl->max_chunks, p.chunks);
         pl->max_npad = std::max(pl->max_npad, p.n_pad);
         pl->max_nblk = std::max(pl->max_nblk, p.nblk);
         pl->max_tiles64 = std::max<int>(pl->max_tiles64, (int)cdiv64(p.M, 64));
@@ -317,6 +340,7 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
     GPBO_TRY(arena(pl, &pl->Dinv, sdinv));
     GPBO_TRY(arena(pl, &pl->vec, svec));
     GPBO_TRY(arena(pl, &pl->alpha32, svec / 6));
+    GPBO_TRY(arena(pl, &pl->rpart, srpart));
     GPBO_TRY(arena(pl, &pl->lsinv, (int64_t)G * GPBO_MAX_D));
     GPBO_TRY(arena(pl, &pl->L32, ssq));
     GPBO_TRY(arena(pl, &pl->Linv32, ssq));
@@ -473,22 +497,18 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     b_zero_upper<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L);
-    // alpha = K^-1 y' with one refinement step on the second stream, under the L^-1 products;
-    // vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 dlt
+    // alpha = K^-1 y' with one step of iterative refinement (as the single-problem path): the
+    // FP64 solve and residual on the second stream, under the L^-1 products, then the
+    // correction through L^-1; vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 u
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_fork, 0));
     b_pad_copy<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->dys, pl->vec);
-    for (int pass = 0; pass < 2; ++pass) {
-        b_copy_vec<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->vec, pass == 0 ? 1 : 4, 2);
-        for (int b = 0; b < NBL; ++b)
-            b_fwd_step<<<dim3(std::max(1, NBL - b - 1), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, b);
-        for (int s = 0; s < NBL; ++s)
-            b_bwd_step<<<dim3(std::max(1, NBL - 1 - s), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, s,
-                                                                        pass == 0 ? 0 : 5);
-        if (pass == 0) b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, s2>>>(P, pl->K, pl->vec);
-    }
-    b_axpy_cast<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->vec, pl->alpha32);
-    GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
+    b_copy_vec<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->vec, 1, 2);
+    for (int b = 0; b < NBL; ++b)
+        b_fwd_step<<<dim3(std::max(1, NBL - b - 1), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, b);
+    for (int s = 0; s < NBL; ++s)
+        b_bwd_step<<<dim3(std::max(1, NBL - 1 - s), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, s, 0);
+    b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, s2>>>(P, pl->K, pl->vec);
     // FP32 L^-1
     b_cast_L<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L, pl->L32);
     b_linv_init<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->Dinv, pl->Linv32);
@@ -505,6 +525,12 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         b_gemm<<<grid, 256, 0, st>>>(pl->Linv32, pl->tmp, pl->Linv32, pl->gemm_dev + pl->lvl_first[l] + pl->lvl_count[l],
                                      -1.0f, 1, 0);
     }
+    GPBO_CUDA_TRY(cudaEventRecord(pl->ev[4], st));
+    GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, pl->ev[4], 0));
+    b_trmv<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, s2>>>(P, pl->Linv32, pl->vec);
+    b_trmv_t_part<<<dim3(pl->max_npad / 32, pl->max_chunks, G), 256, 0, s2>>>(P, pl->Linv32, pl->vec, pl->rpart);
+    b_trmv_t_sum<<<dim3(gb(pl->max_npad), G), 256, 0, s2>>>(P, pl->rpart, pl->vec, pl->alpha32);
+    GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     // scoring
     b_xkern<<<dim3(pl->max_tiles64, G), 256, sizeof(float) * 64 * GPBO_MAX_D, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,

@@ -128,9 +128,25 @@ __global__ void k_residual(const double *__restrict__ K, const double *__restric
     k_residual_body(K, alpha, y, n_pad, r, blockIdx.x, blockIdx.y);
 }
 
-__global__ void k_axpy_cast(double *__restrict__ a, const double *__restrict__ dlt, int n, float *__restrict__ a32)
+// Refinement correction through L^-1 (bodies in fit_kernels.cuh).
+template <typename T>
+__global__ void __launch_bounds__(256) k_trmv(const T *__restrict__ X, int n_pad, const double *__restrict__ r,
+                                              double *__restrict__ u)
 {
-    k_axpy_cast_body(a, dlt, n, a32, blockIdx.x, blockIdx.y);
+    k_trmv_body(X, n_pad, r, u, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_trmv_t_part(const T *__restrict__ X, int n_pad, const double *__restrict__ u,
+                                                     double *__restrict__ part)
+{
+    k_trmv_t_part_body(X, n_pad, u, part, blockIdx.x, blockIdx.y);
+}
+
+__global__ void k_trmv_t_sum(const double *__restrict__ part, int n_pad, int chunks, double *__restrict__ a,
+                             float *__restrict__ a32)
+{
+    k_trmv_t_sum_body(part, n_pad, chunks, a, a32, blockIdx.x);
 }
 
 __global__ void k_pad_copy(const double *__restrict__ y, int n, int n_pad, double *__restrict__ out)
@@ -246,6 +262,9 @@ static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int>
 // accuracy for the FP64 inverse (7 slices), at FP32 accuracy for the FP32 one (3 slices); the
 // small levels on the FP64 / FP32 pipes.
 constexpr int TRTRI_TC_MIN = 256;
+// FP32 levels from 1024 columns: the batched path (n <= 1024, CUDA-core levels) then computes
+// the same FP32 inverse, bit for bit, as this path for every size it takes.
+constexpr int TRTRI_TC_MIN_F32 = 1024;
 
 // Scratch of the tensor-core levels (the largest level's).
 static size_t trtri_tc_scratch(int n_pad, bool f64)
@@ -256,7 +275,7 @@ static size_t trtri_tc_scratch(int n_pad, bool f64)
     trtri_plan(n_pad, probs, first, count, mm);
     size_t b = 0;
     for (size_t l = 0; l < first.size(); ++l)
-        if (mm[l].y >= TRTRI_TC_MIN) {
+        if (mm[l].y >= (f64 ? TRTRI_TC_MIN : TRTRI_TC_MIN_F32)) {
             const int mk = std::max(mm[l].x, mm[l].y);
             b = std::max(b, f64 ? dtc_scratch_bytes(count[l], mk, mm[l].y) : stc_scratch_bytes(count[l], mk, mm[l].y));
         }
@@ -284,7 +303,7 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
                                     probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
             continue;
         }
-        if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN) {
+        if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN_F32) {
             // FP32 accuracy from three slices: T = L21 X11 (X11 lower), then X21 = -X22 T
             GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Ls, (const float *)Linv, (float *)tmp, n_pad,
                                     probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
@@ -412,18 +431,24 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     const int max_probs = 2 * nblk + 2;
     const int64_t sq = (int64_t)n_pad * n_pad;
     const size_t vec = sizeof(double) * n_pad;
-    const size_t tc_bytes = n_pad >= 2 * TRTRI_TC_MIN ? trtri_tc_scratch(n_pad, m->prec == GPBO_PREC_F64) : 0;
+    const bool f64 = m->prec == GPBO_PREC_F64;
+    const size_t tc_bytes = n_pad >= 2 * (f64 ? TRTRI_TC_MIN : TRTRI_TC_MIN_F32) ? trtri_tc_scratch(n_pad, f64) : 0;
     const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
                              sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
     const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
+    const int chunks = (n_pad + TRMV_ROWS - 1) / TRMV_ROWS;
     void *wsp = nullptr;
-    GPBO_TRY(ws_reserve(ctx, vec * 6 + sync_bytes + inv_bytes, &wsp));
-    double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *dlt = r + n_pad;
-    int *sync = (int *)((char *)wsp + vec * 6);
-    void *w2 = (void *)((char *)wsp + vec * 6 + sync_bytes);
+    GPBO_TRY(ws_reserve(ctx, vec * (6 + chunks) + sync_bytes + inv_bytes, &wsp));
+    double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *u = r + n_pad;
+    double *part = ypad + 6 * (int64_t)n_pad;
+    int *sync = (int *)((char *)wsp + vec * (6 + chunks));
+    void *w2 = (void *)((char *)wsp + vec * (6 + chunks) + sync_bytes);
 
-    // alpha = K^-1 y with one refinement step (FP64 throughout), on the side stream: its
-    // substitution steps are latency-bound and overlap the L^-1 products on the main stream.
+    // alpha = K^-1 y with one step of iterative refinement, on the side stream: the FP64 solve
+    // (latency-bound substitutions, beside the L^-1 products on the main stream) and the FP64
+    // residual r = y - K alpha; the correction K^-1 r = X^T (X r) then goes through X = L^-1
+    // once it is ready (FP64 for FP64 models, FP32-accurate otherwise: mixed-precision
+    // refinement, whose correction only needs the precision of the correction itself).
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_pad_copy<<<blocks_for(n_pad), 256, 0, side>>>(y_dev, n, n_pad, ypad);
@@ -431,10 +456,20 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_TRY(alpha_solve(ctx, side, m, ypad, work, m->alpha64, sync));
     k_residual<<<(n_pad + 7) / 8, 256, 0, side>>>(m->K, m->alpha64, ypad, n_pad, r);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(alpha_solve(ctx, side, m, r, work, dlt, sync));
-    k_axpy_cast<<<blocks_for(n_pad), 256, 0, side>>>(m->alpha64, dlt, n_pad, m->alpha32);
-    GPBO_LAUNCH_CHECK(ctx);
-    GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
+    cudaEvent_t ev_linv = ctx->side_ev[4];
+    auto correction = [&](auto *X) -> int {
+        using T = std::remove_const_t<std::remove_pointer_t<decltype(X)>>;
+        GPBO_CUDA_TRY(cudaEventRecord(ev_linv, st));
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_linv, 0));
+        k_trmv<T><<<(n_pad + 7) / 8, 256, 0, side>>>(X, n_pad, r, u);
+        GPBO_LAUNCH_CHECK(ctx);
+        k_trmv_t_part<T><<<dim3(n_pad / 32, chunks), 256, 0, side>>>(X, n_pad, u, part);
+        GPBO_LAUNCH_CHECK(ctx);
+        k_trmv_t_sum<<<blocks_for(n_pad), 256, 0, side>>>(part, n_pad, chunks, m->alpha64, m->alpha32);
+        GPBO_LAUNCH_CHECK(ctx);
+        GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
+        return GPBO_OK;
+    };
 
     // L^-1 for scoring
     GemmProb *probs = nullptr;
@@ -445,6 +480,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
         GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs, tcs));
+        GPBO_TRY(correction(m->Linv64));
     } else {
         float *L32 = (float *)w2, *tmp = L32 + sq;
         probs = (GemmProb *)(tmp + sq);
@@ -454,6 +490,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         GPBO_LAUNCH_CHECK(ctx);
         void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
         GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs, tcs));
+        GPBO_TRY(correction(m->Linv32));
         if (m->prec == GPBO_PREC_BF16) {
             __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;
             k_split_bf16<<<blocks_for(sq), 256, 0, st>>>(m->Linv32, sq, hi, hi + sq);

@@ -505,6 +505,55 @@ __device__ __forceinline__ void k_residual_body(const double *__restrict__ K, co
     if (lane == 0) r[row] = y[row] - s;
 }
 
+// Refinement correction through X = L^-1 (lower triangular, row-major; FP64 or FP32), shared by
+// the single-problem and batched paths.  u = X r: one warp per row (row bx * 8 + warp).
+template <typename T>
+__device__ __forceinline__ void k_trmv_body(const T *__restrict__ X, int n_pad, const double *__restrict__ r,
+                                            double *__restrict__ u, const int bx)
+{
+    const int i = bx * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n_pad) return;
+    const T *row = X + (int64_t)i * n_pad;
+    T s = T(0);
+    for (int j = lane; j <= i; j += 32) s = fma(row[j], (T)r[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) u[i] = (double)s;
+}
+
+// d = X^T u in two deterministic passes: CTA (bx, by) of 256 threads sums rows
+// TRMV_ROWS by .. of columns 32 bx .. into part[by][j] (zero above the diagonal); then
+// k_trmv_t_sum_body adds the row chunks in order and applies a += d (with the FP32 copy of a).
+constexpr int TRMV_ROWS = 256;
+template <typename T>
+__device__ __forceinline__ void k_trmv_t_part_body(const T *__restrict__ X, int n_pad, const double *__restrict__ u,
+                                                   double *__restrict__ part, const int bx, const int by)
+{
+    __shared__ T red[8][32];
+    const int j = bx * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
+    const int i0 = by * TRMV_ROWS + w * (TRMV_ROWS / 8), i1 = min(i0 + TRMV_ROWS / 8, n_pad);
+    T s = T(0);
+    for (int i = max(i0, j); i < i1; ++i) s = fma(X[(int64_t)i * n_pad + j], (T)u[i], s);
+    red[w][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (w == 0) {
+        for (int g = 1; g < 8; ++g) s += red[g][threadIdx.x];
+        part[(int64_t)by * n_pad + j] = (double)s;
+    }
+}
+
+__device__ __forceinline__ void k_trmv_t_sum_body(const double *__restrict__ part, int n_pad, int chunks,
+                                                  double *__restrict__ a, float *__restrict__ a32, const int bx)
+{
+    const int j = bx * blockDim.x + threadIdx.x;
+    if (j >= n_pad) return;
+    double d = 0.0;
+    for (int c = j / TRMV_ROWS; c < chunks; ++c) d += part[(int64_t)c * n_pad + j];
+    const double v = a[j] + d;
+    a[j] = v;
+    a32[j] = (float)v;
+}
+
 __device__ __forceinline__ void k_axpy_cast_body(double *__restrict__ a, const double *__restrict__ dlt, int n, float *__restrict__ a32, const int bx, const int by)
 {
     int i = bx * blockDim.x + threadIdx.x;

@@ -86,7 +86,7 @@ struct gpbo_ctx {
     void *batch_plan = nullptr;      // captured batched step for the last set of shapes
     int batch_tile = 0;              // batched variance tile (0: autotune)
     cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
-    cudaEvent_t side_ev[4] = {};     // fork / join events between the two streams
+    cudaEvent_t side_ev[5] = {};     // fork / join events between the two streams
     gp_model *step_model = nullptr;  // search_step's model, kept for the next call of the same shape
     void *step_buf = nullptr;        // search_step's device staging
     size_t step_buf_bytes = 0;

@@ -279,8 +279,10 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
  * analysis produces in parallel (§IV-D) -- each of its own dimension d[g], size n[g] and
  * hyperparameters hyp[g], in one graph launch: every kernel of search_step covers all G
  * problems at once, with the same device code, so problem g's result equals search_step
- * on it bit for bit.  FP32 scoring only (GPBO_ENOTSUP otherwise); M[g] candidates are
- * drawn on the device from seed[g].
+ * on it bit for bit while n[g] pads to less than 1536 (search_step moves the Cholesky updates
+ * and the large levels of L^-1 to the tensor cores from there on; larger problems agree
+ * within the FP32 tolerances).  FP32 scoring only (GPBO_ENOTSUP otherwise); M[g] candidates
+ * are drawn on the device from seed[g].
  *   X, y : host arrays of G pointers; the pointed-to data are device arrays (n[g] x d[g]
  *          and n[g]) unless flags has GPBO_HOST_PTRS.
  *   x_next : host, G x 64 doubles; row g holds the d[g] coordinates of problem g's pick.

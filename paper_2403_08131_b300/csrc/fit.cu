@@ -262,9 +262,13 @@ static void trtri_plan(int n_pad, std::vector<GemmProb> &probs, std::vector<int>
 // accuracy for the FP64 inverse (7 slices), at FP32 accuracy for the FP32 one (3 slices); the
 // small levels on the FP64 / FP32 pipes.
 constexpr int TRTRI_TC_MIN = 256;
-// FP32 levels from 1024 columns: the batched path (n <= 1024, CUDA-core levels) then computes
-// the same FP32 inverse, bit for bit, as this path for every size it takes.
-constexpr int TRTRI_TC_MIN_F32 = 1024;
+// The FP32 inverse takes the tensor-core levels only in models that also take the tensor-core
+// Cholesky updates (n_pad >= CHOL_TC_MIN_NPAD): below that size this path runs the batched
+// path's CUDA-core arithmetic throughout, and the two agree bit for bit.
+static int trtri_tc_min(int n_pad, bool f64)
+{
+    return f64 || n_pad >= CHOL_TC_MIN_NPAD ? TRTRI_TC_MIN : 1 << 30;
+}
 
 // Scratch of the tensor-core levels (the largest level's).
 static size_t trtri_tc_scratch(int n_pad, bool f64)
@@ -275,7 +279,7 @@ static size_t trtri_tc_scratch(int n_pad, bool f64)
     trtri_plan(n_pad, probs, first, count, mm);
     size_t b = 0;
     for (size_t l = 0; l < first.size(); ++l)
-        if (mm[l].y >= (f64 ? TRTRI_TC_MIN : TRTRI_TC_MIN_F32)) {
+        if (mm[l].y >= trtri_tc_min(n_pad, f64)) {
             const int mk = std::max(mm[l].x, mm[l].y);
             b = std::max(b, f64 ? dtc_scratch_bytes(count[l], mk, mm[l].y) : stc_scratch_bytes(count[l], mk, mm[l].y));
         }
@@ -303,7 +307,7 @@ static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, 
                                     probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
             continue;
         }
-        if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN_F32) {
+        if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= trtri_tc_min(n_pad, false)) {
             // FP32 accuracy from three slices: T = L21 X11 (X11 lower), then X21 = -X22 T
             GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Ls, (const float *)Linv, (float *)tmp, n_pad,
                                     probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
@@ -432,7 +436,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     const int64_t sq = (int64_t)n_pad * n_pad;
     const size_t vec = sizeof(double) * n_pad;
     const bool f64 = m->prec == GPBO_PREC_F64;
-    const size_t tc_bytes = n_pad >= 2 * (f64 ? TRTRI_TC_MIN : TRTRI_TC_MIN_F32) ? trtri_tc_scratch(n_pad, f64) : 0;
+    const size_t tc_bytes = n_pad >= 2 * trtri_tc_min(n_pad, f64) ? trtri_tc_scratch(n_pad, f64) : 0;
     const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
                              sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
     const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);

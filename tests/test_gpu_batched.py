@@ -112,3 +112,35 @@ def test_batched_edge_shapes_equal_single_calls(ctx, shapes):
                               prec="f32")
         assert out["argmax"][g] == one["argmax"] and out["ei_max"][g] == one["ei_max"], (g, shapes[g])
         assert np.array_equal(out["x_next"][g], one["x_next"])
+
+
+def test_batched_large_problem_within_bars_small_one_bit_for_bit(ctx):
+    """Beside a small problem, one that pads to at least 1536 rows: search_step factors it with
+    the tensor-core Cholesky updates and L^-1 levels, the batched step on the CUDA cores, so
+    the large problem agrees within the FP32 bars (its pick's EI, rescored by the
+    single-problem path, within the bar of that path's maximum) while the small one stays
+    bit for bit."""
+    from paper_2403_08131_b300 import gpbo
+    from tests._util import to_dev
+    probs = []
+    for g, (n, d) in enumerate([(300, 6), (1600, 8)]):
+        X = W.uniform_points(7100 + g, W.STREAM_OBS, n, d)
+        y = W.Objective([d], [W.FN_ACKLEY], 0.0, 7100 + g)(X)
+        probs.append(dict(X=X, y=y, lengthscale=W.lengthscale_rule(d), signal_var=1.0, noise_var=1e-4, M=4096,
+                          seed=800 + g))
+    out = ctx.search_step_batched(probs)
+    small, large = probs
+    one = ctx.search_step(small["X"], small["y"], small["lengthscale"], 1.0, 1e-4, M=small["M"], seed=small["seed"],
+                          prec="f32")
+    assert out["argmax"][0] == one["argmax"] and out["ei_max"][0] == one["ei_max"]
+    one = ctx.search_step(large["X"], large["y"], large["lengthscale"], 1.0, 1e-4, M=large["M"], seed=large["seed"],
+                          prec="f32")
+    ys = (large["y"] - large["y"].mean()) / (large["y"].std() or 1.0)
+    m = ctx.fit(to_dev(large["X"]), to_dev(ys), large["lengthscale"], 1.0, 1e-4, prec="f32")
+    import torch
+    ei = torch.empty(large["M"], dtype=torch.float32, device="cuda")
+    ctx.posterior_ei(m, None, M=large["M"], seed=large["seed"], y_best=float(ys.min()), ei=ei)
+    ei = ei.cpu().numpy().astype(np.float64)
+    check_argmax(int(out["argmax"][1]), ei, BAR["f32"])
+    assert abs(out["ei_max"][1] - one["ei_max"]) <= BAR["f32"] * one["ei_max"]
+    m.free()

@@ -3,7 +3,8 @@ exact rational products (the error-free splitting of Ozaki, Ogita, Oishi and Rum
 kernel applies it).
 
 Each row of a Cholesky panel P (64 columns) is 2^(e-7) times 7 integer slices of at most 8
-bits; slice pairs with s + t <= 9 are multiplied exactly (integer sums below 2^23, as the FP32
+bits -- the balanced base-256 digits of X = round(x 2^(55-e)) (ties away from zero), taken from
+the least significant end as the kernels take them from the bits of x; slice pairs with s + t <= 9 are multiplied exactly (integer sums below 2^23, as the FP32
 accumulators hold them), the 8 levels are folded in int64 (hi: levels 2..5, lo: 6..9), combined
 as hi 2^16 + floor(lo / 2^16), and turned into a double by truncation.  The test checks the
 exactness conditions the kernel relies on and that the result is within 2^-52 * 64 *
@@ -19,16 +20,39 @@ from paper_2403_08131_b300 import workloads as W
 SLICES, LEVEL_MAX = 7, 9
 
 
+def _fixed(x, e, prec=55):
+    """round(x 2^(prec - e)) as an exact integer, ties away from zero."""
+    if x == 0.0:
+        return 0
+    m, ex = math.frexp(x)                      # |x| = mi 2^(ex - 53), mi a 53-bit integer
+    mi = int(math.ldexp(abs(m), 53))
+    sh = ex - 53 + prec - e
+    X = mi << sh if sh >= 0 else ((mi + (1 << (-sh - 1))) >> -sh if sh > -64 else 0)
+    return X if x > 0 else -X
+
+
+def _digits(X):
+    """X = sum_s d_s 256^(SLICES - 1 - s), balanced digits from the least significant end."""
+    d = [0] * SLICES
+    for s in range(SLICES - 1, 0, -1):
+        q = (X + 128) >> 8                     # floor division, as the kernels' arithmetic shift
+        d[s] = X - (q << 8)
+        X = q
+    d[0] = X
+    return d
+
+
 def _split(P):
     mx = np.abs(P).max(1)
     e = np.array([math.frexp(m)[1] if m > 0 else 0 for m in mx])  # m < 2^e
-    t = np.ldexp(P, (7 - e)[:, None])
-    out = []
-    for _ in range(SLICES):
-        a = np.rint(t)
-        assert np.all(np.abs(a) <= 128)
-        out.append(a.astype(np.int64))
-        t = (t - a) * 256.0
+    out = [np.zeros(P.shape, dtype=np.int64) for _ in range(SLICES)]
+    for i in range(P.shape[0]):
+        for j in range(P.shape[1]):
+            X = _fixed(float(P[i, j]), int(e[i]))
+            assert abs(X) <= 2 ** 55
+            for s, dv in enumerate(_digits(X)):
+                assert (-128 <= dv <= 128) if s == 0 else (-128 <= dv <= 127)
+                out[s][i, j] = dv
     return e, out
 
 

@@ -116,7 +116,7 @@ void model_free(gp_model *m)
     if (!m) return;
     void *ptrs[] = {m->X,       m->Xs64,    m->Xs32,   m->K,      m->L,      m->Dinv,
                     m->alpha64, m->alpha32, m->Linv64, m->Linv32, m->Linv16, m->Zsplit, m->nb32,
-                    m->cslices, m->cexps};
+                    m->cslices, m->cexps, m->xmax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -147,6 +147,7 @@ static int alloc_model(gp_model *m)
     if (m->n_pad >= CHOL_TC_MIN_NPAD) {
         GPBO_CUDA_TRY(cudaMalloc(&m->cslices, chol_tc_slice_bytes(m->n_pad)));
         GPBO_TRY(dalloc(&m->cexps, m->n_pad));
+        GPBO_TRY(dalloc(&m->xmax, 1));
     }
     if ((m->prec == GPBO_PREC_BF16 || m->prec == GPBO_PREC_F16) && m->d <= 32) {
         GPBO_CUDA_TRY(cudaMalloc(&m->Zsplit, (size_t)m->n_pad * 128 * 2));

@@ -13,6 +13,7 @@
 // Padded rows/columns of K are the identity, so L and L^-1 are the identity there, the
 // padded right-hand side is zero, and alpha is zero there.  No kernel needs a ragged tail.
 #include "fit_kernels.cuh"
+#include "tc_common.cuh"
 
 #include <utility>
 
@@ -36,6 +37,69 @@ __global__ void k_kmat(const double *__restrict__ Xs, int n, int d, int n_pad, d
                        double *__restrict__ K)
 {
     k_kmat_body(Xs, n, d, n_pad, s2, sn2, K, blockIdx.x, blockIdx.y);
+}
+
+// Kernel matrix with the distances in exact integer arithmetic (models with the tensor-core
+// updates): each coordinate x / l as the integer q = round(x / l 2^(58 - e)) (|x / l| < 2^e
+// over the model, from k_xs_max; |q| <= 2^58), so every difference q_i - q_j and the sum of
+// its d squares (below 2^125) are exact in 128 bits, rounded once to FP64 and scaled by
+// 2^(2 (e - 58)).  Against the FP64 loop (one rounding per subtraction and per FMA) the
+// distance is exact up to the inputs' quantisation (2^-59 of the largest |x / l|), and the
+// 2 d FP64 operations per pair move to the integer pipe.  The Matern factor stays FP64.
+__global__ void k_xs_max(const double *__restrict__ Xs, int64_t count, unsigned long long *__restrict__ xmax)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long m = t < count ? (unsigned long long)tcx::mag_bits(Xs[t]) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(xmax, m);
+}
+
+__global__ void k_kmat_fixed(const double *__restrict__ Xs, const unsigned long long *__restrict__ xmax, int n,
+                             int d, int n_pad, double s2, double sn2, double *__restrict__ K)
+{
+    constexpr int P = 58;
+    const int tj = blockIdx.x, ti = blockIdx.y;
+    if (tj > ti) return;
+    __shared__ long long qi[GPBO_MAX_D][32], qj[GPBO_MAX_D][32];
+    __shared__ double tile[32][33];
+    const int e = tcx::exp_of_mag(*xmax);
+    for (int idx = threadIdx.y * 32 + threadIdx.x; idx < d * 32; idx += 32 * blockDim.y) {
+        const int k = idx / 32, c = idx % 32;
+        qi[k][c] = tcx::fixed_of(Xs[(int64_t)k * n_pad + ti * 32 + c], e, P);
+        qj[k][c] = tcx::fixed_of(Xs[(int64_t)k * n_pad + tj * 32 + c], e, P);
+    }
+    __syncthreads();
+    const int sh = 2 * (e - P);
+    const bool fast = sh > -1000 && sh < 1000;
+    const double scale = fast ? ldexp(1.0, sh) : 0.0;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = ti * 32 + r, j = tj * 32 + threadIdx.x;
+        double v;
+        if (i < n && j < n) {
+            unsigned long long lo = 0, hi = 0;
+            for (int k = 0; k < d; ++k) {
+                const long long t = qi[k][r] - qj[k][threadIdx.x];
+                const unsigned long long a = (unsigned long long)(t < 0 ? -t : t);
+                const unsigned long long pl = a * a;
+                lo += pl;
+                hi += __umul64hi(a, a) + (lo < pl ? 1ull : 0ull);
+            }
+            const double S = (double)hi * 18446744073709551616.0 + (double)lo;  // hi 2^64 + lo
+            const double r2 = fast ? S * scale : ldexp(S, sh);
+            v = s2 * matern52_r2(r2) + (i == j ? sn2 : 0.0);
+        } else {
+            v = i == j ? 1.0 : 0.0;
+        }
+        K[(int64_t)i * n_pad + j] = v;
+        tile[r][threadIdx.x] = v;
+    }
+    if (ti == tj) return;
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = tj * 32 + r, i = ti * 32 + threadIdx.x;
+        K[(int64_t)j * n_pad + i] = tile[threadIdx.x][r];
+    }
 }
 
 // Diagonal factor: warp 0 takes the pivots, 31 warps share each column's updates (the
@@ -367,7 +431,14 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     if (m->Zsplit) GPBO_TRY(xkern_tc_prepare(ctx, m));
     {
         dim3 grid(n_pad / 32, n_pad / 32);
-        k_kmat<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, n, d, n_pad, m->s2, m->sn2, m->K);
+        if (m->xmax) {
+            GPBO_CUDA_TRY(cudaMemsetAsync(m->xmax, 0, sizeof(unsigned long long), st));
+            k_xs_max<<<blocks_for((int64_t)d * n_pad), 256, 0, st>>>(m->Xs64, (int64_t)d * n_pad, m->xmax);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_kmat_fixed<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, m->xmax, n, d, n_pad, m->s2, m->sn2, m->K);
+        } else {
+            k_kmat<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, n, d, n_pad, m->s2, m->sn2, m->K);
+        }
         GPBO_LAUNCH_CHECK(ctx);
     }
     GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));

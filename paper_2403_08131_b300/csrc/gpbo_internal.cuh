@@ -115,6 +115,7 @@ struct gp_model {
     float *nb32 = nullptr;      // 16-bit models: |(x_i - 1/2) / l|^2
     void *cslices = nullptr;    // n_pad >= CHOL_TC_MIN_NPAD: 7 BF16 slices of a Cholesky panel, slice-major
     int *cexps = nullptr;       // their per-row exponents
+    unsigned long long *xmax = nullptr;  // n_pad >= CHOL_TC_MIN_NPAD: largest |x / l| as magnitude bits
 };
 
 namespace gpbo {

@@ -147,7 +147,7 @@ __global__ void k_xs_max(const double *__restrict__ Xs, int64_t count, unsigned 
 }
 
 __global__ void k_kmat_fixed(const double *__restrict__ Xs, const unsigned long long *__restrict__ xmax, int n,
-                             int d, int n_pad, double s2, double sn2, double *__restrict__ K)
+                             int d, int n_pad, double s2, double sn2, double *__restrict__ K, double *__restrict__ L)
 {
     constexpr int P = 58;
     const int tj = blockIdx.x, ti = blockIdx.y;
@@ -183,6 +183,7 @@ __global__ void k_kmat_fixed(const double *__restrict__ Xs, const unsigned long 
             v = i == j ? 1.0 : 0.0;
         }
         K[(int64_t)i * n_pad + j] = v;
+        L[(int64_t)i * n_pad + j] = v;  // the factorisation's working copy (its lower triangle)
         tile[r][threadIdx.x] = v;
     }
     if (ti == tj) return;
@@ -527,13 +528,14 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
             GPBO_CUDA_TRY(cudaMemsetAsync(m->xmax, 0, sizeof(unsigned long long), st));
             k_xs_max<<<blocks_for((int64_t)d * n_pad), 256, 0, st>>>(m->Xs64, (int64_t)d * n_pad, m->xmax);
             GPBO_LAUNCH_CHECK(ctx);
-            k_kmat_fixed<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, m->xmax, n, d, n_pad, m->s2, m->sn2, m->K);
+            k_kmat_fixed<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, m->xmax, n, d, n_pad, m->s2, m->sn2, m->K, m->L);
         } else {
             k_kmat<<<grid, dim3(32, 8), 0, st>>>(m->Xs64, n, d, n_pad, m->s2, m->sn2, m->K);
         }
         GPBO_LAUNCH_CHECK(ctx);
     }
-    GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
+    // the factorisation works in L (k_kmat_fixed writes its lower triangle with K)
+    if (!m->xmax) GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
     const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
     // Right-looking blocked factorisation with a lookahead of one block column: the update
     // of block column kb+1 by panel kb, the factorisation of its diagonal block, its inverse

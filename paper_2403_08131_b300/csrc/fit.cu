@@ -154,7 +154,10 @@ __global__ void k_kmat_fixed(const double *__restrict__ Xs, const unsigned long 
     if (tj > ti) return;
     __shared__ long long qi[GPBO_MAX_D][32], qj[GPBO_MAX_D][32];
     __shared__ double tile[32][33];
-    const int e = tcx::exp_of_mag(*xmax);
+    // a NaN or infinite coordinate makes the FP64 loop's K NaN (and the factorisation report
+    // it); the fixed-point form would hide it, so it writes NaN entries instead
+    const bool finite = *xmax < 0x7ff0000000000000ull;
+    const int e = finite ? tcx::exp_of_mag(*xmax) : 0;
     for (int idx = threadIdx.y * 32 + threadIdx.x; idx < d * 32; idx += 32 * blockDim.y) {
         const int k = idx / 32, c = idx % 32;
         qi[k][c] = tcx::fixed_of(Xs[(int64_t)k * n_pad + ti * 32 + c], e, P);
@@ -178,7 +181,7 @@ __global__ void k_kmat_fixed(const double *__restrict__ Xs, const unsigned long 
             }
             const double S = (double)hi * 18446744073709551616.0 + (double)lo;  // hi 2^64 + lo
             const double r2 = fast ? S * scale : ldexp(S, sh);
-            v = s2 * matern52_r2_int(r2) + (i == j ? sn2 : 0.0);
+            v = finite ? s2 * matern52_r2_int(r2) + (i == j ? sn2 : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
         } else {
             v = i == j ? 1.0 : 0.0;
         }

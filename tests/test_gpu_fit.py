@@ -97,3 +97,16 @@ def test_trace_phases_nest(ctx):
     assert 0 < tr["chol_update"]["ms"] < tr["fit"]["ms"]
     assert tr["variance"]["intervals"] >= 1 and tr["xkern"]["intervals"] >= 1
     assert tr["chol_update"]["flops"] == sum(T * (T - 1) // 2 for T in range(2, 8)) * 2 * 64 ** 3
+
+
+@pytest.mark.parametrize("n", [100, 1600])
+def test_fit_nan_in_device_inputs_fails_the_same_way(ctx, n):
+    """A NaN coordinate in device-resident X makes K NaN and the factorisation fail, with the
+    same error whether the distances are FP64 (n = 100) or exact integers (n = 1600)."""
+    from paper_2403_08131_b300 import gpbo
+    from tests._util import to_dev
+    X, y = _obs(n, 6, 4000 + n)
+    X[n // 2, 3] = np.nan
+    with pytest.raises(gpbo.GpboError) as e:
+        ctx.fit(to_dev(X), to_dev(y), W.lengthscale_rule(6), 1.0, 1e-4, prec="f32")
+    assert e.value.code == gpbo.GPBO_ENOTSPD

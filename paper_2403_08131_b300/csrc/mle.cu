@@ -9,6 +9,7 @@
 // L^-1) is the FP64 fit of gp_fit; one fused kernel forms each 64 x 64 tile of K^-1 and, without
 // writing it out, folds it into the d + 2 gradient sums.
 
+#include "int_math.cuh"
 #include "gpbo_internal.cuh"
 #include "gpbo.h"
 
@@ -73,8 +74,10 @@ __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const dou
                     gs += 0.5 * G * s2;
                     gn += 0.5 * G * sn2;
                 } else if (pp > qq) {
-                    const double r = sqrt(r2[u][v]);
-                    const double e = exp(-sq5 * r);
+                    // square root and exponential on the integer pipe (int_math.cuh): this
+                    // epilogue is bound by the FP64 pipe
+                    const double r = r2[u][v] > 0.0 ? r2[u][v] * rsqrt_int(r2[u][v]) : 0.0;
+                    const double e = exp_neg_int(sq5 * r);
                     gs += G * s2 * (1.0 + sq5 * r + (5.0 / 3.0) * r2[u][v]) * e;
                     w = G * s2 * (5.0 / 3.0) * (1.0 + sq5 * r) * e;
                 }

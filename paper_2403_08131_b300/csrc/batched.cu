@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128) b_chol_inv(const BProb *P, const double *
     k_chol_inv_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) b_chol_panel(const BProb *P, double *L, const double *Dinv, int kb)
+__global__ void __launch_bounds__(128) b_chol_panel(const BProb *P, double *L, const double *Dinv, int kb)
 {
     const BProb &p = P[blockIdx.y];
     const int T = p.nblk - kb - 1;
@@ -478,7 +478,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_fork, 0));
     b_chol_diag<<<dim3(1, G), 256, smem1, s2>>>(P, pl->L, pl->Dinv, 0, ctx->dev_status);
     b_chol_inv<<<dim3(NB / 4, G), 128, 0, s2>>>(P, pl->L, pl->Dinv, 0);
-    if (NBL > 1) b_chol_panel<<<dim3((NBL - 1) * (NB / 4), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, 0);
+    if (NBL > 1) b_chol_panel<<<dim3((NBL - 1) * (NB / 4), G), 128, 0, s2>>>(P, pl->L, pl->Dinv, 0);
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
     for (int kb = 0; kb + 1 < NBL; ++kb) {
         const int T = NBL - kb - 1;
@@ -487,7 +487,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         b_chol_update<<<dim3((unsigned)T, G), 256, smem2, s2>>>(P, pl->L, kb, 1);
         b_chol_diag<<<dim3(1, G), 256, smem1, s2>>>(P, pl->L, pl->Dinv, kb + 1, ctx->dev_status);
         b_chol_inv<<<dim3(NB / 4, G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
-        if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
+        if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
         if (T > 1) {
             b_chol_update<<<dim3((unsigned)((int64_t)T * (T - 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb, 2);

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(128) k_chol_inv(const double *__restrict__ A, 
     k_chol_inv_body(A, n_pad, kb, Dinv, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(256) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
+__global__ void __launch_bounds__(128) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv)
 {
     pdl_wait();
@@ -476,7 +476,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, 0, m->Dinv));
     if (nblk > 1)
-        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((nblk - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, 0,
+        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((nblk - 1) * (NB / 4)), dim3(128), 0, side, m->L, n_pad, 0,
                             m->Dinv));
     GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
     // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
@@ -493,7 +493,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
                             ctx->dev_status));
         GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1, m->Dinv));
         if (T > 1)
-            GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((T - 1) * (NB / 4)), dim3(256), 0, side, m->L, n_pad, kb + 1,
+            GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((T - 1) * (NB / 4)), dim3(128), 0, side, m->L, n_pad, kb + 1,
                                 m->Dinv));
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
         if (T > 1) {

@@ -235,22 +235,36 @@ __device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, 
     for (int u = 0; u < SR / 4; ++u) A[(r0 + ty + 4 * u) * n_pad + (int64_t)jb * NB + tx] -= acc[u];
 }
 
-// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, four rows per CTA (thread = row ty,
-// column tx; L_kk^-T is lower, so t <= tx), so that short panels still spread over many SMs.
+// Panel: L_ik = A_ik L_kk^-T for the block rows i > k, four rows per CTA of 128 threads, so that
+// short panels still spread over many SMs.  Output column c is the triangular dot product
+// sum_{t <= c} a_t Dinv[c][t] (L_kk^-T is lower); thread (row ty, lane tx) takes columns tx and
+// 63 - tx in one loop of 65 steps -- every lane issues one FMA per step (a warp issues 65 FP64
+// instructions per row instead of 96 when a lane takes one column) -- and each column keeps
+// its t = 0 .. c accumulation order.
 __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv, const int bx, const int by)
 {
     __shared__ double a[4][NB + 1];
     __shared__ double dv[NB][NB + 1];
     const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)bx * 4;
-    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < 4 * NB; e += blockDim.x) a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
     for (int e = tid; e < NB * NB; e += blockDim.x) dv[e / NB][e % NB] = D[e];
     __syncthreads();
-    double acc = 0.0;
-    for (int t = 0; t <= tx; ++t) acc = fma(a[ty][t], dv[tx][t], acc);
-    A[(row0 + ty) * n_pad + (int64_t)kb * NB + tx] = acc;
+    const int c1 = tx, c2 = NB - 1 - tx;
+    double acc = 0.0, out1 = 0.0;
+    for (int s = 0; s <= NB; ++s) {
+        const bool first = s <= c1;
+        const int t = first ? s : s - c1 - 1, c = first ? c1 : c2;
+        acc = fma(a[ty][t], dv[c][t], acc);
+        if (s == c1) {
+            out1 = acc;
+            acc = 0.0;
+        }
+    }
+    A[(row0 + ty) * n_pad + (int64_t)kb * NB + c1] = out1;
+    A[(row0 + ty) * n_pad + (int64_t)kb * NB + c2] = acc;
 }
 
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.

@@ -44,7 +44,8 @@ __device__ __forceinline__ double rsqrt_int(double p)
 // exp(-t) = 2^(1-f) 2^(-n-1) with 2^h = sum_k (h ln2)^k / k! (k <= 18, Horner in Q62 with h = 1 - f
 // in Q63), rounded to 53 bits.  Constants from the definitions: ln2 = sum_k 1 / (k 2^k),
 // EXP_C[k] = round((ln2)^k / k! 2^62).  Within 0.52 ulp of exp(-t) (checked on 4e6 arguments
-// against long double); 0 from t >= 708 (below the normal range).
+// against long double); 0 from t >= 708 (below the normal range).  Meant for t >= 0: a NaN or
+// negative t takes the library exp.
 static __constant__ uint64_t EXP_C[19] = {
     0x4000000000000000ull, 0x2c5c85fdf473de6bull, 0x0f5fdeffc162c754ull, 0x038d611ae09417f1ull,
     0x009d955b7dd273b9ull, 0x0015d87fe78a6731ull, 0x0002861225f0d8f1ull, 0x00003ff97f8b1162ull,
@@ -54,7 +55,7 @@ static __constant__ uint64_t EXP_C[19] = {
 };
 __device__ __forceinline__ double exp_neg_int(double t)
 {
-    if (!(t > 0.0)) return 1.0;
+    if (!(t > 0.0)) return t == 0.0 ? 1.0 : exp(-t);  // NaN stays NaN; t < 0 by the library
     if (t >= 708.0) return 0.0;
     const uint64_t b = (uint64_t)__double_as_longlong(t);
     const int E = (int)(b >> 52);

@@ -1,0 +1,150 @@
+"""The integer-pipe FP64 functions of the kernel matrix and the likelihood epilogue
+(paper_2403_08131_b300/csrc/int_math.cuh), emulated exactly with Python integers.
+
+exp(-t): x = t / ln2 in 128-bit fixed point, 2^h = e^(h ln2) by its Taylor series in Q62,
+rounded to 53 bits.  1/sqrt(p): an FP32 seed and two Newton-Raphson steps in Q63.  The tests
+re-derive the header's constants from their definitions (ln2 = sum 1 / (k 2^k); the series
+coefficients (ln2)^k / k!; 2^126 / ln2), check the stated error bounds (0.52 and 0.51 ulp)
+against 60-digit references, and check that planted mistakes fall outside them."""
+import math
+import re
+import struct
+from decimal import Decimal, getcontext
+from fractions import Fraction
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+HEADER = Path(__file__).resolve().parents[1] / "paper_2403_08131_b300" / "csrc" / "int_math.cuh"
+M64 = (1 << 64) - 1
+getcontext().prec = 60
+
+
+def _ln2():
+    return sum(Fraction(1, k * 2 ** k) for k in range(1, 300))
+
+
+def _header_constants():
+    src = HEADER.read_text()
+    chi = int(re.search(r"CHI = (0x[0-9a-f]+)ull", src).group(1), 16)
+    clo = int(re.search(r"CLO = (0x[0-9a-f]+)ull", src).group(1), 16)
+    body = re.search(r"EXP_C\[19\] = \{(.*?)\};", src, re.S).group(1)
+    coef = [int(h, 16) for h in re.findall(r"0x([0-9a-f]+)ull", body)]
+    return chi, clo, coef
+
+
+def _bits(x):
+    return struct.unpack("<Q", struct.pack("<d", x))[0]
+
+
+def _dbl(b):
+    return struct.unpack("<d", struct.pack("<Q", b))[0]
+
+
+def _exp_neg(t, chi, clo, coef, shift=0):
+    """Bit-for-bit model of exp_neg_int for t > 0 (shift plants a wrong fraction shift)."""
+    if t >= 708.0:
+        return 0.0
+    b = _bits(t)
+    E = b >> 52
+    m = (b & ((1 << 52) - 1)) | (1 << 52)
+    sc = 63 if t < 1.0 else 52
+    sh = E - 1075 + sc
+    T = (m << sh) if sh >= 0 else (((m + (1 << (-sh - 1))) >> -sh) if sh > -64 else 0)
+    c = (T * clo) >> 64
+    slo = (T * chi + c) & M64
+    shi = ((T * chi) >> 64) + (1 if slo < c else 0)
+    r = sc - 2 + shift
+    n = shi >> r
+    fq = ((shi << (64 - r)) | (slo >> r)) & M64
+    h = (1 << 63) - (fq >> 1)
+    p = coef[18]
+    for k in range(17, -1, -1):
+        p = coef[k] + ((h * p) >> 63)
+    ex = 1022 - n
+    if p >= 1 << 63:
+        mm, ex = 0, ex + 1
+    else:
+        mm = (p >> 10) + ((p >> 9) & 1)
+        if mm >> 53:
+            mm >>= 1
+            ex += 1
+        mm &= (1 << 52) - 1
+    return 0.0 if ex < 1 else _dbl((ex << 52) | mm)
+
+
+def _rsqrt(p, seed_rel=0.0, steps=2):
+    """Bit-for-bit model of rsqrt_int with an FP32 seed of relative error seed_rel."""
+    b = _bits(p)
+    E = b >> 52
+    f = b & ((1 << 52) - 1)
+    u = E - 1023
+    odd = u & 1
+    k = (u - odd) // 2
+    Mq = (f | (1 << 52)) << (10 + odd)
+    Mf = struct.unpack("<f", struct.pack("<I", ((127 + odd) << 23) | (f >> 29)))[0]
+    yf = np.float32(np.float32(1.0) / np.sqrt(np.float32(Mf)) * np.float32(1.0 + seed_rel))
+    yb = struct.unpack("<I", struct.pack("<f", float(yf)))[0]
+    yq = ((yb & 0x7FFFFF) | 0x800000) << (40 - (127 - (yb >> 23)))
+    for _ in range(steps):
+        t = (Mq * ((yq * yq) >> 64)) >> 64
+        e = (0x3000000000000000 - t) & M64
+        yq = ((yq * e) >> 61) & M64
+    if yq >= 1 << 63:
+        return _dbl((1023 - k) << 52)
+    m = (yq >> 10) + ((yq >> 9) & 1)
+    ex = 1022 - k
+    if m >> 53:
+        m >>= 1
+        ex += 1
+    return _dbl((ex << 52) | (m & ((1 << 52) - 1)))
+
+
+def _ulp_err(got, exact):
+    ulp = 2.0 ** (math.frexp(float(exact))[1] - 53)
+    return abs(Decimal(got) - exact) / Decimal(ulp)
+
+
+def test_exp_constants_follow_from_their_definitions():
+    ln2 = _ln2()
+    chi, clo, coef = _header_constants()
+    assert (chi << 64) | clo == round(Fraction(2 ** 126) / ln2)
+    want, term = [], Fraction(1)
+    for k in range(19):
+        if k:
+            term = term * ln2 / k
+        want.append(round(term * 2 ** 62))
+    assert coef == want
+
+
+def test_exp_neg_within_its_bound():
+    chi, clo, coef = _header_constants()
+    rng = np.random.default_rng(5)
+    ts = np.concatenate([rng.uniform(0, 700, 400), rng.uniform(0, 20, 400), np.ldexp(rng.uniform(0.5, 1, 200),
+                         -rng.integers(1, 60, 200)), [1.0, 2.0, 0.5, 1e-300, math.nextafter(1.0, 0.0)]])
+    worst = max(_ulp_err(_exp_neg(float(t), chi, clo, coef), (-Decimal(float(t))).exp()) for t in ts)
+    assert worst <= Decimal("0.52"), worst
+
+
+def test_rsqrt_within_its_bound_for_seed_errors():
+    rng = np.random.default_rng(6)
+    ps = np.ldexp(rng.uniform(1, 2, 300), rng.integers(-900, 900, 300))
+    worst = Decimal(0)
+    for seed_rel in (0.0, 3e-7, -3e-7):
+        for p in ps:
+            exact = 1 / Decimal(float(p)).sqrt()
+            worst = max(worst, _ulp_err(_rsqrt(float(p), seed_rel), exact))
+    assert worst <= Decimal("0.51"), worst
+
+
+def test_planted_mistakes_fall_outside_the_bounds():
+    chi, clo, coef = _header_constants()
+    t = 3.7
+    exact = (-Decimal(t)).exp()
+    bad = list(coef)
+    bad[3] += 1 << 20
+    assert _ulp_err(_exp_neg(t, chi, clo, bad), exact) > 1
+    assert _ulp_err(_exp_neg(t, chi ^ (1 << 40), clo, coef), exact) > 1
+    assert _ulp_err(_exp_neg(t, chi, clo, coef, shift=1), exact) > 1
+    assert _ulp_err(_rsqrt(7.25, 3e-7, steps=1), 1 / Decimal(7.25).sqrt()) > 1

@@ -5,7 +5,10 @@ exp(-t): x = t / ln2 in 128-bit fixed point, 2^h = e^(h ln2) by its Taylor serie
 rounded to 53 bits.  1/sqrt(p): an FP32 seed and two Newton-Raphson steps in Q63.  The tests
 re-derive the header's constants from their definitions (ln2 = sum 1 / (k 2^k); the series
 coefficients (ln2)^k / k!; 2^126 / ln2), check the stated error bounds (0.52 and 0.51 ulp)
-against 60-digit references, and check that planted mistakes fall outside them."""
+against 60-digit references, and check that planted mistakes fall outside them.  The kernel
+matrix's fixed-point squared distances (k_kmat_fixed: coordinates quantised to 2^(e - 58),
+exact 128-bit sums, one two-part rounding) are checked against exact rational distances.
+These pins need no GPU."""
 import math
 import re
 import struct
@@ -148,3 +151,42 @@ def test_planted_mistakes_fall_outside_the_bounds():
     assert _ulp_err(_exp_neg(t, chi ^ (1 << 40), clo, coef), exact) > 1
     assert _ulp_err(_exp_neg(t, chi, clo, coef, shift=1), exact) > 1
     assert _ulp_err(_rsqrt(7.25, 3e-7, steps=1), 1 / Decimal(7.25).sqrt()) > 1
+
+
+def _fixed(x, e, prec=58):
+    """round(x 2^(prec - e)) with ties away from zero, as the kernels take it from the bits of x."""
+    if x == 0.0:
+        return 0
+    m, ex = math.frexp(x)
+    mi = int(math.ldexp(abs(m), 53))
+    sh = ex - 53 + prec - e
+    X = mi << sh if sh >= 0 else ((mi + (1 << (-sh - 1))) >> -sh if sh > -64 else 0)
+    return X if x > 0 else -X
+
+
+def _r2_fixed(a, b, e, scale_bias=0):
+    """Bit-for-bit model of k_kmat_fixed's squared distance between rows a and b."""
+    S = sum((_fixed(x, e) - _fixed(y, e)) ** 2 for x, y in zip(a, b))
+    hi, lo = S >> 64, S & M64
+    return (float(hi) * 18446744073709551616.0 + float(lo)) * 2.0 ** (2 * (e - 58) + scale_bias)
+
+
+def test_fixed_point_distances_within_their_bound():
+    """Exact integer squares and sums, one two-part rounding: within 2 ulp of the exact distance
+    of the quantised coordinates, which move by at most 2^(e - 59) each."""
+    rng = np.random.default_rng(7)
+    Xs = rng.uniform(-0.5, 0.5, (40, 20)) / rng.uniform(0.2, 2.0, 20)
+    Xs[3] = Xs[4] + 1e-9 * rng.standard_normal(20)            # a near pair
+    mx = np.abs(Xs).max()
+    e = math.frexp(mx)[1]                                       # |x| < 2^e
+    for i in range(40):
+        for j in range(i):
+            got = _r2_fixed(Xs[i], Xs[j], e)
+            exact = sum((Fraction(x) - Fraction(y)) ** 2 for x, y in zip(Xs[i], Xs[j]))
+            quant = sum(2 * abs(Fraction(x) - Fraction(y)) * Fraction(2) ** (e - 58) + Fraction(2) ** (2 * (e - 58))
+                        for x, y in zip(Xs[i], Xs[j]))
+            bound = Fraction(2) * Fraction(2) ** -52 * exact + quant
+            assert abs(Fraction(got) - exact) <= bound, (i, j)
+    # a wrong power of two in the scaling lands far outside
+    assert abs(_r2_fixed(Xs[1], Xs[0], e, scale_bias=1) - float(sum((Fraction(x) - Fraction(y)) ** 2
+               for x, y in zip(Xs[1], Xs[0])))) > 0.1 * float(sum((x - y) ** 2 for x, y in zip(Xs[1], Xs[0])))

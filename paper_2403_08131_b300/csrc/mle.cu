@@ -10,6 +10,7 @@
 // writing it out, folds it into the d + 2 gradient sums.
 
 #include "int_math.cuh"
+#include "tc_common.cuh"
 #include "gpbo_internal.cuh"
 #include "gpbo.h"
 
@@ -31,9 +32,26 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Fixed-point coordinates for the pair terms of models whose kernel matrix takes its squared
+// distances in integers (n_pad >= 1536, k_kmat_fixed): Qx = round(Xs 2^(58 - e)) with the
+// same e (from the fit's largest |x / l|), so each pair's r^2 is the one K was built from.
+__global__ void k_lml_fixed_coords(const double *__restrict__ Xs, const unsigned long long *__restrict__ xmax,
+                                   int64_t count, long long *__restrict__ Qx)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const bool finite = *xmax < 0x7ff0000000000000ull;  // else the fit has failed already
+    Qx[t] = finite ? tcx::fixed_of(Xs[t], tcx::exp_of_mag(*xmax), 58) : 0;
+}
+
 // The pair terms of one thread's 4 x 4 piece of a K^-1 tile (rows p0 + ty + 16 u, columns
-// q0 + tx + 16 v), reduced over the CTA into part[j * ntiles + p] (see k_lml_pairs).
+// q0 + tx + 16 v), reduced over the CTA into part[j * ntiles + p] (see k_lml_pairs).  FIXED:
+// the squared distances are exact 128-bit sums over the fixed-point coordinates Qx, rounded
+// once (as in k_kmat_fixed, bit for bit), in two halves of 8 pairs to bound the registers.
+template <bool FIXED>
 __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const double *__restrict__ Xs,
+                                                  const long long *__restrict__ Qx,
+                                                  const unsigned long long *__restrict__ xmax,
                                                   const double *__restrict__ alpha, int n, int d, int n_pad,
                                                   double s2, double sn2, int ntiles, double *__restrict__ part, int p,
                                                   int p0, int q0, double (*red)[GPBO_MAX_D + 2])
@@ -44,7 +62,45 @@ __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const dou
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) r2[u][v] = 0.0;
-    for (int k = 0; k < d; ++k) {
+    if constexpr (FIXED) {
+        const int sh = 2 * (tcx::exp_of_mag(*xmax) - 58);
+        const bool fast = sh > -1000 && sh < 1000;
+        const double scale = fast ? ldexp(1.0, sh) : 0.0;
+#pragma unroll
+        for (int uh = 0; uh < 4; uh += 2) {
+            unsigned long long lo[2][4], hi[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) lo[u][v] = hi[u][v] = 0ull;
+            for (int k = 0; k < d; ++k) {
+                const long long *row = Qx + (int64_t)k * n_pad;
+                long long qp[2], qq[4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) qp[u] = __ldg(row + p0 + ty + 16 * (uh + u));
+#pragma unroll
+                for (int v = 0; v < 4; ++v) qq[v] = __ldg(row + q0 + tx + 16 * v);
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const long long t = qp[u] - qq[v];
+                        const unsigned long long a = (unsigned long long)(t < 0 ? -t : t);
+                        const unsigned long long pl = a * a;
+                        lo[u][v] += pl;
+                        hi[u][v] += __umul64hi(a, a) + (lo[u][v] < pl ? 1ull : 0ull);
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const double S = (double)hi[u][v] * 18446744073709551616.0 + (double)lo[u][v];
+                    r2[uh + u][v] = fast ? S * scale : ldexp(S, sh);
+                }
+        }
+    }
+    for (int k = 0; !FIXED && k < d; ++k) {
         const double *row = Xs + (int64_t)k * n_pad;
         double xp[4], xq[4];
 #pragma unroll
@@ -126,7 +182,10 @@ __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const dou
 //   g_d   += G s2 (1 + sqrt5 r + 5/3 r^2) e
 // and for p = q < n (weight 1/2): g_d += G s2 / 2, g_{d+1} += G sn2 / 2.
 // part[j * ntiles + p] receives the CTA's sum for component j (fixed order: deterministic).
+template <bool FIXED>
 __global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Linv, const double *__restrict__ Xs,
+                                                   const long long *__restrict__ Qx,
+                                                   const unsigned long long *__restrict__ xmax,
                                                    const double *__restrict__ alpha, int n, int d, int n_pad, int kend,
                                                    double s2, double sn2, int ntiles, double *__restrict__ part)
 {
@@ -185,12 +244,15 @@ __global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Li
         buf ^= 1;
     }
 
-    lml_pair_epilogue(acc, Xs, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
 }
 
 // The same pair terms with K^-1 read from memory (the lower 64 x 64 tiles that kinv_tc forms
 // on the tensor cores), tile p = I (I + 1) / 2 + J as in k_lml_pairs.
+template <bool FIXED>
 __global__ void __launch_bounds__(256) k_lml_pairs_kinv(const double *__restrict__ Kinv, const double *__restrict__ Xs,
+                                                        const long long *__restrict__ Qx,
+                                                        const unsigned long long *__restrict__ xmax,
                                                         const double *__restrict__ alpha, int n, int d, int n_pad,
                                                         double s2, double sn2, int ntiles, double *__restrict__ part)
 {
@@ -207,7 +269,7 @@ __global__ void __launch_bounds__(256) k_lml_pairs_kinv(const double *__restrict
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = Kinv[(int64_t)(p0 + ty + 16 * u) * n_pad + q0 + tx + 16 * v];
-    lml_pair_epilogue(acc, Xs, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
 }
 
 __device__ double block_sum256(double v, double *sh)
@@ -259,6 +321,7 @@ struct MleState {
     void *kslices = nullptr;                   // tensor-core K^-1 (n_pad a multiple of 128): slices,
     int *kexps = nullptr;                      //   their exponents
     double *kinv = nullptr;                    //   and K^-1's lower tiles
+    long long *qx = nullptr;                   // fixed-point coordinates, d x n_pad (models with xmax)
     int ntiles = 0;
     int64_t evals = 0;
 };
@@ -271,10 +334,12 @@ static void mle_release(MleState &s)
     if (s.kslices) cudaFree(s.kslices);
     if (s.kexps) cudaFree(s.kexps);
     if (s.kinv) cudaFree(s.kinv);
+    if (s.qx) cudaFree(s.qx);
     if (s.m) model_free(s.m);
     s.kslices = nullptr;
     s.kexps = nullptr;
     s.kinv = nullptr;
+    s.qx = nullptr;
     s.part = s.out = s.host = nullptr;
     s.m = nullptr;
 }
@@ -291,6 +356,7 @@ static int mle_init(MleState &s, gpbo_ctx *ctx, const double *X, const double *y
     GPBO_CUDA_TRY(cudaMalloc(&s.out, sizeof(double) * (d + 3)));
     GPBO_CUDA_TRY(cudaMallocHost(&s.host, sizeof(double) * (d + 3)));
     const int n_pad = s.m->n_pad;
+    if (s.m->xmax) GPBO_CUDA_TRY(cudaMalloc(&s.qx, sizeof(long long) * (size_t)d * n_pad));
     if (n_pad % 128 == 0 && n_pad >= 256) {
         GPBO_CUDA_TRY(cudaMalloc(&s.kslices, kinv_tc_slice_bytes(n_pad)));
         GPBO_CUDA_TRY(cudaMalloc(&s.kexps, sizeof(int) * n_pad));
@@ -323,14 +389,20 @@ static int mle_eval(MleState &s, const double *theta, double *lml, double *grad)
     double flops = 0.0;
     for (int p = 0; p < n; ++p) flops += 2.0 * (double)(p + 1) * (double)(n - p);
     GPBO_TRY(trace_begin(ctx, PH_LML, flops));
+    if (s.qx) {
+        const int64_t cnt = (int64_t)d * n_pad;
+        k_lml_fixed_coords<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(m->Xs64, m->xmax, cnt, s.qx);
+    }
     if (s.kinv) {
         // K^-1 on the tensor cores (FP64 accuracy), then the pair terms from memory
         GPBO_TRY(kinv_tc(ctx, ctx->stream, m->Linv64, n_pad, s.kslices, s.kexps, s.kinv));
-        k_lml_pairs_kinv<<<s.ntiles, 256, 0, ctx->stream>>>(s.kinv, m->Xs64, m->alpha64, n, d, n_pad, m->s2, m->sn2,
-                                                            s.ntiles, s.part);
+        auto k = s.qx ? k_lml_pairs_kinv<true> : k_lml_pairs_kinv<false>;
+        k<<<s.ntiles, 256, 0, ctx->stream>>>(s.kinv, m->Xs64, s.qx, m->xmax, m->alpha64, n, d, n_pad, m->s2, m->sn2,
+                                             s.ntiles, s.part);
     } else {
-        k_lml_pairs<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, m->alpha64, n, d, n_pad, kend, m->s2,
-                                                       m->sn2, s.ntiles, s.part);
+        auto k = s.qx ? k_lml_pairs<true> : k_lml_pairs<false>;
+        k<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, s.qx, m->xmax, m->alpha64, n, d, n_pad, kend, m->s2,
+                                             m->sn2, s.ntiles, s.part);
     }
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_TRY(trace_end(ctx));

@@ -32,16 +32,58 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Largest |x_k / l_k| of each dimension as magnitude bits (dmax zeroed before).  n_pad is a
+// multiple of 64, so a warp's 32 elements lie in one dimension.
+__global__ void k_lml_dim_max(const double *__restrict__ Xs, int n_pad, int64_t count,
+                              unsigned long long *__restrict__ dmax)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    unsigned long long m = t < count ? (unsigned long long)tcx::mag_bits(Xs[t]) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m && t < count) atomicMax(&dmax[t / n_pad], m);
+}
+
 // Fixed-point coordinates for the pair terms of models whose kernel matrix takes its squared
-// distances in integers (n_pad >= 1536, k_kmat_fixed): Qx = round(Xs 2^(58 - e)) with the
-// same e (from the fit's largest |x / l|), so each pair's r^2 is the one K was built from.
+// distances in integers (n_pad >= 1536, k_kmat_fixed).  Qx = round(Xs 2^(58 - e)) with the
+// fit's e (from the largest |x / l| over all dimensions), so each pair's r^2 is the one K was
+// built from.  Qg = round(Xs 2^(58 - e_k)) with each dimension's own e_k, for the gradient's
+// (x_pk - x_qk)^2: a dimension with a long lengthscale keeps its own 58 bits (its FP64
+// coordinates carry 53).
 __global__ void k_lml_fixed_coords(const double *__restrict__ Xs, const unsigned long long *__restrict__ xmax,
-                                   int64_t count, long long *__restrict__ Qx)
+                                   const unsigned long long *__restrict__ dmax, int n_pad, int64_t count,
+                                   long long *__restrict__ Qx, long long *__restrict__ Qg)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= count) return;
     const bool finite = *xmax < 0x7ff0000000000000ull;  // else the fit has failed already
     Qx[t] = finite ? tcx::fixed_of(Xs[t], tcx::exp_of_mag(*xmax), 58) : 0;
+    Qg[t] = finite ? tcx::fixed_of(Xs[t], tcx::exp_of_mag(dmax[t / n_pad]), 58) : 0;
+}
+
+// t^2 as a double for an exact integer t, on the integer pipe: |t| normalised by its leading
+// zeros, the leading 64 bits of its 128-bit square, 53 of them rounded to nearest with ties
+// away from zero (the bits below the leading 64 are not looked at: a tie rounds up, so the
+// result is within 0.5 ulp of t^2 either way).  |t| < 2^61, so the exponent (at most 121) is
+// always normal.
+__device__ __forceinline__ double sq_to_double(long long t)
+{
+    if (t == 0) return 0.0;
+    const unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+    const int lz = __clzll((long long)a);
+    const unsigned long long top = a << lz;  // [2^63, 2^64); a^2 = top^2 2^(-2 lz)
+    unsigned long long h = __umul64hi(top, top);
+    int ex = 1023 + 127 - 2 * lz;
+    if (!(h >> 63)) {
+        h = (h << 1) | ((top * top) >> 63);
+        --ex;
+    }
+    unsigned long long m = (h >> 11) + ((h >> 10) & 1ull);
+    if (m >> 53) {
+        m >>= 1;
+        ++ex;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)ex << 52) | (m & 0x000FFFFFFFFFFFFFull)));
 }
 
 // The pair terms of one thread's 4 x 4 piece of a K^-1 tile (rows p0 + ty + 16 u, columns
@@ -52,6 +94,8 @@ template <bool FIXED>
 __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const double *__restrict__ Xs,
                                                   const long long *__restrict__ Qx,
                                                   const unsigned long long *__restrict__ xmax,
+                                                  const long long *__restrict__ Qg,
+                                                  const unsigned long long *__restrict__ dmax,
                                                   const double *__restrict__ alpha, int n, int d, int n_pad,
                                                   double s2, double sn2, int ntiles, double *__restrict__ part, int p,
                                                   int p0, int q0, double (*red)[GPBO_MAX_D + 2])
@@ -141,18 +185,32 @@ __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const dou
             acc[u][v] = w;
         }
     for (int k = 0; k < d; ++k) {
-        const double *row = Xs + (int64_t)k * n_pad;
-        double xp[4], xq[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { xp[u] = __ldg(row + p0 + ty + 16 * u); xq[u] = __ldg(row + q0 + tx + 16 * u); }
         double g = 0.0;
+        if constexpr (FIXED) {
+            // (x_pk - x_qk)^2 2^(116 - 2 e_k) exactly from the per-dimension fixed-point
+            // coordinates, rounded once on the integer pipe; 2^(2 e_k - 116) is applied to the
+            // CTA's sum below
+            const long long *row = Qg + (int64_t)k * n_pad;
+            long long qp[4], qq[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 4; ++u) { qp[u] = __ldg(row + p0 + ty + 16 * u); qq[u] = __ldg(row + q0 + tx + 16 * u); }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const double t = xp[u] - xq[v];
-                g = fma(acc[u][v], t * t, g);
-            }
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) g = fma(acc[u][v], sq_to_double(qp[u] - qq[v]), g);
+        } else {
+            const double *row = Xs + (int64_t)k * n_pad;
+            double xp[4], xq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { xp[u] = __ldg(row + p0 + ty + 16 * u); xq[u] = __ldg(row + q0 + tx + 16 * u); }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const double t = xp[u] - xq[v];
+                    g = fma(acc[u][v], t * t, g);
+                }
+        }
         g = warp_sum(g);
         if (lane == 0) red[warp][k] = g;
     }
@@ -167,6 +225,7 @@ __device__ __forceinline__ void lml_pair_epilogue(double (&acc)[4][4], const dou
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) s += red[w][tid];
+        if (FIXED && tid < d) s = ldexp(s, 2 * (tcx::exp_of_mag(dmax[tid]) - 58));
         part[(int64_t)tid * ntiles + p] = s;
     }
 }
@@ -186,6 +245,8 @@ template <bool FIXED>
 __global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Linv, const double *__restrict__ Xs,
                                                    const long long *__restrict__ Qx,
                                                    const unsigned long long *__restrict__ xmax,
+                                                   const long long *__restrict__ Qg,
+                                                   const unsigned long long *__restrict__ dmax,
                                                    const double *__restrict__ alpha, int n, int d, int n_pad, int kend,
                                                    double s2, double sn2, int ntiles, double *__restrict__ part)
 {
@@ -244,7 +305,7 @@ __global__ void __launch_bounds__(256) k_lml_pairs(const double *__restrict__ Li
         buf ^= 1;
     }
 
-    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, Qg, dmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
 }
 
 // The same pair terms with K^-1 read from memory (the lower 64 x 64 tiles that kinv_tc forms
@@ -253,6 +314,8 @@ template <bool FIXED>
 __global__ void __launch_bounds__(256) k_lml_pairs_kinv(const double *__restrict__ Kinv, const double *__restrict__ Xs,
                                                         const long long *__restrict__ Qx,
                                                         const unsigned long long *__restrict__ xmax,
+                                                        const long long *__restrict__ Qg,
+                                                        const unsigned long long *__restrict__ dmax,
                                                         const double *__restrict__ alpha, int n, int d, int n_pad,
                                                         double s2, double sn2, int ntiles, double *__restrict__ part)
 {
@@ -269,7 +332,7 @@ __global__ void __launch_bounds__(256) k_lml_pairs_kinv(const double *__restrict
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = Kinv[(int64_t)(p0 + ty + 16 * u) * n_pad + q0 + tx + 16 * v];
-    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
+    lml_pair_epilogue<FIXED>(acc, Xs, Qx, xmax, Qg, dmax, alpha, n, d, n_pad, s2, sn2, ntiles, part, p, p0, q0, red);
 }
 
 __device__ double block_sum256(double v, double *sh)
@@ -321,7 +384,8 @@ struct MleState {
     void *kslices = nullptr;                   // tensor-core K^-1 (n_pad a multiple of 128): slices,
     int *kexps = nullptr;                      //   their exponents
     double *kinv = nullptr;                    //   and K^-1's lower tiles
-    long long *qx = nullptr;                   // fixed-point coordinates, d x n_pad (models with xmax)
+    long long *qx = nullptr;                   // fixed-point coordinates, 2 x d x n_pad (models with
+    unsigned long long *dmax = nullptr;        //   xmax): common and per-dimension exponents; d maxima
     int ntiles = 0;
     int64_t evals = 0;
 };
@@ -335,11 +399,13 @@ static void mle_release(MleState &s)
     if (s.kexps) cudaFree(s.kexps);
     if (s.kinv) cudaFree(s.kinv);
     if (s.qx) cudaFree(s.qx);
+    if (s.dmax) cudaFree(s.dmax);
     if (s.m) model_free(s.m);
     s.kslices = nullptr;
     s.kexps = nullptr;
     s.kinv = nullptr;
     s.qx = nullptr;
+    s.dmax = nullptr;
     s.part = s.out = s.host = nullptr;
     s.m = nullptr;
 }
@@ -356,7 +422,10 @@ static int mle_init(MleState &s, gpbo_ctx *ctx, const double *X, const double *y
     GPBO_CUDA_TRY(cudaMalloc(&s.out, sizeof(double) * (d + 3)));
     GPBO_CUDA_TRY(cudaMallocHost(&s.host, sizeof(double) * (d + 3)));
     const int n_pad = s.m->n_pad;
-    if (s.m->xmax) GPBO_CUDA_TRY(cudaMalloc(&s.qx, sizeof(long long) * (size_t)d * n_pad));
+    if (s.m->xmax) {
+        GPBO_CUDA_TRY(cudaMalloc(&s.qx, sizeof(long long) * 2 * (size_t)d * n_pad));
+        GPBO_CUDA_TRY(cudaMalloc(&s.dmax, sizeof(unsigned long long) * d));
+    }
     if (n_pad % 128 == 0 && n_pad >= 256) {
         GPBO_CUDA_TRY(cudaMalloc(&s.kslices, kinv_tc_slice_bytes(n_pad)));
         GPBO_CUDA_TRY(cudaMalloc(&s.kexps, sizeof(int) * n_pad));
@@ -389,19 +458,23 @@ static int mle_eval(MleState &s, const double *theta, double *lml, double *grad)
     double flops = 0.0;
     for (int p = 0; p < n; ++p) flops += 2.0 * (double)(p + 1) * (double)(n - p);
     GPBO_TRY(trace_begin(ctx, PH_LML, flops));
+    long long *qg = s.qx ? s.qx + (int64_t)d * n_pad : nullptr;
     if (s.qx) {
         const int64_t cnt = (int64_t)d * n_pad;
-        k_lml_fixed_coords<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(m->Xs64, m->xmax, cnt, s.qx);
+        const unsigned blocks = (unsigned)((cnt + 255) / 256);
+        GPBO_CUDA_TRY(cudaMemsetAsync(s.dmax, 0, sizeof(unsigned long long) * d, ctx->stream));
+        k_lml_dim_max<<<blocks, 256, 0, ctx->stream>>>(m->Xs64, n_pad, cnt, s.dmax);
+        k_lml_fixed_coords<<<blocks, 256, 0, ctx->stream>>>(m->Xs64, m->xmax, s.dmax, n_pad, cnt, s.qx, qg);
     }
     if (s.kinv) {
         // K^-1 on the tensor cores (FP64 accuracy), then the pair terms from memory
         GPBO_TRY(kinv_tc(ctx, ctx->stream, m->Linv64, n_pad, s.kslices, s.kexps, s.kinv));
         auto k = s.qx ? k_lml_pairs_kinv<true> : k_lml_pairs_kinv<false>;
-        k<<<s.ntiles, 256, 0, ctx->stream>>>(s.kinv, m->Xs64, s.qx, m->xmax, m->alpha64, n, d, n_pad, m->s2, m->sn2,
+        k<<<s.ntiles, 256, 0, ctx->stream>>>(s.kinv, m->Xs64, s.qx, m->xmax, qg, s.dmax, m->alpha64, n, d, n_pad, m->s2, m->sn2,
                                              s.ntiles, s.part);
     } else {
         auto k = s.qx ? k_lml_pairs<true> : k_lml_pairs<false>;
-        k<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, s.qx, m->xmax, m->alpha64, n, d, n_pad, kend, m->s2,
+        k<<<s.ntiles, 256, 0, ctx->stream>>>(m->Linv64, m->Xs64, s.qx, m->xmax, qg, s.dmax, m->alpha64, n, d, n_pad, kend, m->s2,
                                              m->sn2, s.ntiles, s.part);
     }
     GPBO_LAUNCH_CHECK(ctx);

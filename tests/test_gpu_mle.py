@@ -47,15 +47,19 @@ def test_lml_and_gradient_match_oracle(ctx, orc, n, d):
     _check(orc, X, y, ls, 0.9, 2e-3, lml, g)
 
 
-@pytest.mark.parametrize("n,d", [(1600, 7), (1530, 20), (1560, 64)])
-def test_lml_fixed_point_distances_match_oracle(ctx, orc, n, d):
+@pytest.mark.parametrize("n,d,stretch", [(1600, 7, 1.0), (1530, 20, 1.0), (1560, 64, 1.0), (1600, 6, 3e4)])
+def test_lml_fixed_point_distances_match_oracle(ctx, orc, n, d, stretch):
     """Models with n_pad >= 1536 take the pair terms' squared distances in fixed point (exact
-    128-bit sums over the quantised scaled coordinates, as their kernel matrix does): n_pad
-    1600 takes K^-1 as FP64 tiles, 1536 (ragged, n = 1530) from the tensor cores, d = 64 the
-    widest input."""
+    128-bit sums over the quantised scaled coordinates, as their kernel matrix does) and the
+    gradient's per-dimension squares from coordinates quantised per dimension: n_pad 1600 takes
+    K^-1 as FP64 tiles, 1536 (ragged, n = 1530) from the tensor cores, d = 64 the widest input;
+    stretch gives dimension 2 a lengthscale 3e4 times the others', so its scaled coordinates
+    sit 15 binary orders below the largest and its gradient component is checked against its
+    own, much smaller scale."""
     from tests._util import to_dev
     X, y = _obs(n, d, 5000 + n, noise=0.01)
     ls = 1.1 * np.asarray(W.lengthscale_rule(d))
+    ls[2] *= stretch
     lml, g = ctx.lml(to_dev(X), to_dev(y), ls, 0.8, 3e-3)
     _check(orc, X, y, ls, 0.8, 3e-3, lml, g)
 

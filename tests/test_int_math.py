@@ -190,3 +190,46 @@ def test_fixed_point_distances_within_their_bound():
     # a wrong power of two in the scaling lands far outside
     assert abs(_r2_fixed(Xs[1], Xs[0], e, scale_bias=1) - float(sum((Fraction(x) - Fraction(y)) ** 2
                for x, y in zip(Xs[1], Xs[0])))) > 0.1 * float(sum((x - y) ** 2 for x, y in zip(Xs[1], Xs[0])))
+
+
+def _sq_to_double(t, shift=11):
+    """Bit-for-bit model of sq_to_double (mle.cu): t^2 for an exact integer t, its leading 64
+    bits rounded to 53 with ties away from zero (shift plants a wrong mantissa shift)."""
+    if t == 0:
+        return 0.0
+    a = abs(t)
+    lz = 64 - a.bit_length()
+    top = a << lz
+    h = (top * top) >> 64
+    ex = 1023 + 127 - 2 * lz
+    if not h >> 63:
+        h = ((h << 1) | (((top * top) & M64) >> 63)) & M64
+        ex -= 1
+    m = (h >> shift) + ((h >> (shift - 1)) & 1)
+    if m >> 53:
+        m >>= 1
+        ex += 1
+    return _dbl((ex << 52) | (m & ((1 << 52) - 1)))
+
+
+def test_integer_square_within_half_an_ulp():
+    """The likelihood gradient's (x_p - x_q)^2 from fixed-point differences |t| <= 2^59: within
+    0.5 ulp of the exact square (rounding to nearest, the tie away from zero), on random
+    magnitudes, powers of two and their neighbours, and values whose square sits at a tie."""
+    rng = np.random.default_rng(8)
+    ts = [int(v) for v in rng.integers(1, 1 << 59, 3000, dtype=np.int64)]
+    ts += [int(rng.integers(1, 1 << int(b))) for b in rng.integers(1, 59, 2000)]
+    ts += [(1 << k) + o for k in range(0, 59) for o in (-1, 0, 1) if (1 << k) + o > 0]
+    ts += [(1 << 27) + 1, (1 << 40) + 3, -(1 << 33) - 7]     # squares wider than 53 bits
+    worst = Fraction(0)
+    for t in ts:
+        got = Fraction(_sq_to_double(t))
+        exact = Fraction(t * t)
+        ulp = Fraction(2) ** ((t * t).bit_length() - 53)
+        worst = max(worst, abs(got - exact) / ulp)
+        assert abs(got - exact) <= ulp / 2, t
+    assert _sq_to_double(-12345) == _sq_to_double(12345) == 12345.0 ** 2
+    assert _sq_to_double(1) == 1.0 and _sq_to_double(1 << 59) == 2.0 ** 118
+    # a mantissa taken one bit too low is off by a factor near 2
+    t = (1 << 40) + 12345
+    assert abs(_sq_to_double(t, shift=10) / (t * t) - 1) > 0.4

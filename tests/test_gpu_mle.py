@@ -35,7 +35,8 @@ def _check(orc, X, y, ls, s2, sn2, lml, g):
     assert abs(lml - lo) <= bar * lscale, (lml, lo, bar * lscale)
     err = np.abs(g - go)
     assert np.all(err <= bar * gscale + 1e-300), (err / gscale, bar)
-    return float(np.max(err / gscale)), bar
+    pos = gscale > 0                         # a constant dimension has gscale = err = 0
+    return float(np.max(err[pos] / gscale[pos])) if pos.any() else 0.0, bar
 
 
 @pytest.mark.parametrize("n,d", [(2, 3), (63, 4), (64, 5), (65, 6), (200, 20), (700, 8), (300, 64)])
@@ -62,6 +63,37 @@ def test_lml_fixed_point_distances_match_oracle(ctx, orc, n, d, stretch):
     ls[2] *= stretch
     lml, g = ctx.lml(to_dev(X), to_dev(y), ls, 0.8, 3e-3)
     _check(orc, X, y, ls, 0.8, 3e-3, lml, g)
+
+
+def test_lml_fixed_point_constant_dimension_has_zero_gradient(ctx, orc):
+    """A dimension on which every observation agrees: each (x_pk - x_qk)^2 is exactly zero, so
+    its gradient component is exactly 0.0 on both sides (the per-dimension quantisation of a
+    constant column gives equal integers); the other components stay within the bar."""
+    from tests._util import to_dev
+    n, d = 1600, 5
+    X, y = _obs(n, d, 6100, noise=0.01)
+    X[:, 3] = 0.37
+    ls = W.lengthscale_rule(d)
+    lml, g = ctx.lml(to_dev(X), to_dev(y), ls, 1.0, 2e-3)
+    assert g[3] == 0.0
+    _check(orc, X, y, ls, 1.0, 2e-3, lml, g)
+
+
+@pytest.mark.parametrize("n", [300, 1600])
+def test_lml_nan_coordinate_fails_like_the_fit(ctx, n):
+    """A NaN coordinate fails the evaluation with the fit's error, whether the distances are
+    FP64 (n = 300) or fixed point (n = 1600: the coordinate kernels write zeros instead of
+    converting the NaN)."""
+    from paper_2403_08131_b300 import gpbo
+    from tests._util import to_dev
+    X, y = _obs(n, 4, 6200 + n)
+    X[n // 3, 1] = np.nan
+    with pytest.raises(gpbo.GpboError) as e:
+        ctx.lml(to_dev(X), to_dev(y), W.lengthscale_rule(4), 1.0, 1e-3)
+    assert e.value.code == gpbo.GPBO_ENOTSPD
+    X[n // 3, 1] = 0.5                      # the context stays usable
+    lml, g = ctx.lml(to_dev(X), to_dev(y), W.lengthscale_rule(4), 1.0, 1e-3)
+    assert np.isfinite(lml) and np.all(np.isfinite(g))
 
 
 def test_lml_single_observation_closed_form(ctx):

@@ -115,6 +115,20 @@ int gpbo_trace_read(gpbo_ctx *ctx, int nphase, double *ms, int64_t *intervals, d
  * kind 0 = FP64 DFMA, 1 = FP32 FFMA.  Runs a short in-bounds FMA-chain kernel (about 50 ms)
  * and writes TFLOP/s (2 flops per FMA) to *tflops.  Synchronises. */
 int gpbo_probe_fma(gpbo_ctx *ctx, int kind, double *tflops);
+/* Bounded device waits.  Every wait inside the library's kernels that can give up (the
+ * producer / consumer waits of the tensor-core kernels, the flag waits of the wavefront
+ * substitutions) does so after `cycles` SM clock cycles; 0 restores the default, about 2 s.
+ * A kernel whose wait gives up sets an error bit, leaves its loops, lets the copies and MMAs it
+ * issued finish (those drains always allow the default limit, so shared and tensor memory are
+ * never released under an asynchronous operation), frees its tensor memory and exits; the call
+ * then returns GPBO_ETIMEOUT and the context stays usable.  A short limit can make ordinary
+ * calls time out: it is meant for tests of that error path.  Synchronises. */
+int gpbo_set_wait_limit(gpbo_ctx *ctx, int64_t cycles);
+/* Failure injection for tests of the error path above, with no fault and no unbounded wait:
+ * with stall = 1 the epilogue warps of the tensor-core variance kernel (16-bit models) first
+ * wait on a barrier that nothing arrives at, so that the wait runs out after the wait limit and
+ * the scoring call returns GPBO_ETIMEOUT.  stall = 0 turns it off.  Synchronises. */
+int gpbo_inject_wait_stall(gpbo_ctx *ctx, int stall);
 /* Upper bound, in bytes, of the scratch arena the context may grow to (default 2 GiB).
  * Candidate scoring works through the pool in chunks that fit in this bound. */
 int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes);
@@ -173,6 +187,8 @@ int gp_posterior_ei(gpbo_ctx *ctx, const gp_model *model, const float *Xc, int64
  *     is rejected with GPBO_ESCRATCH before any work is queued.
  *   - The first call on a device looks up the scratch array's device address (once per
  *     device, with that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process: after cudaDeviceReset on that device
+ *     it is stale, so do not call this entry point on a device that has been reset.
  *   - All calls share the one array and it keeps the last call's contents; each call
  *     clears what it needs.  Calls that overlap on the GPU (several streams or host
  *     threads at once on one device) race on the scratch: order them on one stream.

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 namespace gpbo {
@@ -17,6 +20,21 @@ int probe_fma(gpbo_ctx *ctx, int kind, double *tflops);
 void note_cuda_error(cudaError_t e, const char *what, const char *file, int line)
 {
     if (getenv("GPBO_VERBOSE")) fprintf(stderr, "gpbo: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
+
+namespace {
+std::mutex g_smem_mu;
+std::map<std::pair<const void *, int>, int> g_smem_set;
+}  // namespace
+
+int ensure_smem(const void *fn, int device, int bytes)
+{
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int &have = g_smem_set[std::make_pair(fn, device)];
+    if (have >= bytes) return GPBO_OK;
+    GPBO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    have = bytes;
+    return GPBO_OK;
 }
 
 int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
@@ -367,6 +385,26 @@ int gpbo_probe_fma(gpbo_ctx *ctx, int kind, double *tflops)
     if (!ctx || !tflops || (kind != 0 && kind != 1)) return GPBO_EINVAL;
     GPBO_TRY(set_device(ctx));
     return probe_fma(ctx, kind, tflops);
+}
+
+int gpbo_set_wait_limit(gpbo_ctx *ctx, int64_t cycles)
+{
+    if (!ctx || cycles < 0) return GPBO_EINVAL;
+    GPBO_TRY(set_device(ctx));
+    const long long v = (long long)cycles;
+    GPBO_CUDA_TRY(cudaMemcpyAsync((char *)ctx->dev_status + 8, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GPBO_OK;
+}
+
+int gpbo_inject_wait_stall(gpbo_ctx *ctx, int stall)
+{
+    if (!ctx || (stall != 0 && stall != 1)) return GPBO_EINVAL;
+    GPBO_TRY(set_device(ctx));
+    const unsigned v = (unsigned)stall;
+    GPBO_CUDA_TRY(cudaMemcpyAsync((char *)ctx->dev_status + 4, &v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GPBO_OK;
 }
 
 int gpbo_set_workspace_limit(gpbo_ctx *ctx, int64_t bytes)

@@ -282,12 +282,7 @@ int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const vo
 {
     const int n_pad = m->n_pad, nblk = n_pad / NB;
     if (kb + 2 >= nblk) return GPBO_OK;
-    static bool attr = false;
-    if (!attr) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(ctc::k_chol_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ctc::SMEM_BYTES));
-        attr = true;
-    }
+    GPBO_TRY(ensure_smem((const void *)ctc::k_chol_update_tc, ctx->device, (int)ctc::SMEM_BYTES));
     const int r0 = (kb + 2) * NB, rows = n_pad - r0;
     ctc::k_chol_split<<<(unsigned)cdiv64((int64_t)rows * 32, 256), 256, 0, st>>>(
         m->L, n_pad, kb, r0, (__nv_bfloat16 *)m->cslices, m->cexps);

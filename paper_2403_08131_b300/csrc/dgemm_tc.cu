@@ -391,12 +391,7 @@ static int gemm_level(gpbo_ctx *ctx, cudaStream_t st, const T *A, const T *B, T 
     }
     // from pageable memory the copy is staged before the call returns, so hp may go at return
     GPBO_CUDA_TRY(cudaMemcpyAsync(dp, hp.data(), sizeof(dtc::Prob) * cnt, cudaMemcpyHostToDevice, st));
-    static bool attr = false;
-    if (!attr) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(dtc::k_dtc_gemm<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)dtc::Cfg<S>::SMEM_BYTES));
-        attr = true;
-    }
+    GPBO_TRY(ensure_smem((const void *)dtc::k_dtc_gemm<T, S>, ctx->device, (int)dtc::Cfg<S>::SMEM_BYTES));
     dtc::k_dtc_split_rows<T, S><<<dim3((mk + 7) / 8, cnt), 256, 0, st>>>(A, ld, dp, KA, RA, Sa, exa);
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_CUDA_TRY(cudaMemsetAsync(mxb, 0, sizeof(unsigned long long) * RB, st));

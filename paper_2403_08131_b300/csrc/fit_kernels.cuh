@@ -403,8 +403,9 @@ __device__ __forceinline__ void k_bwd_step_body(const double *__restrict__ L, co
 // fences, and reads the solution past L1.  flags (nblk) and ticket must be zero at launch.
 __device__ __forceinline__ bool wave_wait(const int *flag, unsigned *status)
 {
+    const long long t0 = clock64(), limit = wait_limit(status);
     for (long it = 0; *(volatile const int *)flag == 0; ++it)
-        if (it == (1l << 26)) {  // ~seconds: set the error and give up rather than hang
+        if ((it & 255) == 255 && clock64() - t0 > limit) {  // set the error and give up rather than hang
             atomicOr(status, DEV_TIMEOUT);
             return false;
         }

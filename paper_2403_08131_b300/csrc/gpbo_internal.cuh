@@ -55,6 +55,17 @@ enum : unsigned {
     DEV_NAN = 4u,
 };
 
+// Default limit of a bounded device wait: about 2 s of SM clock.
+constexpr long long WAIT_DEFAULT_CYCLES = 4000000000ll;
+
+// Limit of a wait that may give up: the context's wait limit, a count of SM clock cycles kept as
+// a 64-bit word at byte 8 of its status buffer (gpbo_set_wait_limit; 0 means the default).
+__device__ __forceinline__ long long wait_limit(const unsigned *status)
+{
+    const long long v = *(const volatile long long *)(status + 2);
+    return v > 0 ? v : WAIT_DEFAULT_CYCLES;
+}
+
 }  // namespace gpbo
 
 namespace gpbo {
@@ -76,7 +87,8 @@ struct gpbo_ctx {
     int64_t ws_limit = (int64_t)2 << 30;
     void *ws = nullptr;              // grow-only scratch arena
     size_t ws_size = 0;
-    unsigned *dev_status = nullptr;  // device error word (cleared by each call)
+    unsigned *dev_status = nullptr;  // 64 device bytes: [0] error bits (cleared by each call),
+                                     // [4] injected faults, [8] wait limit in cycles (int64)
     void *pinned = nullptr;          // small pinned host staging buffer
     bool trace = false;              // per-phase event timing (gpbo_trace_enable)
     gpbo::TraceRec *trace_recs = nullptr;
@@ -122,6 +134,10 @@ namespace gpbo {
 
 // capi.cu
 int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out);
+// Raise kernel fn's dynamic shared-memory limit on `device` (which must be current) to at least
+// `bytes`.  The attribute belongs to the device, so what was set is remembered per (kernel,
+// device) under a lock: contexts on several devices, or on several host threads, each get it.
+int ensure_smem(const void *fn, int device, int bytes);
 // The context's high-priority side stream (created on first use).  Every call that forks
 // work onto it joins back into ctx->stream before returning.
 int side_stream(gpbo_ctx *ctx, cudaStream_t *out);

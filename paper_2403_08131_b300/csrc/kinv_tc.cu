@@ -292,12 +292,7 @@ size_t kinv_tc_slice_bytes(int n_pad) { return (size_t)ktc::SLICES * n_pad * n_p
 int kinv_tc(gpbo_ctx *ctx, cudaStream_t st, const double *Linv, int n_pad, void *slices, int *exps, double *C)
 {
     if (n_pad % 128 != 0) return GPBO_EINVAL;
-    static bool attr = false;
-    if (!attr) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(ktc::k_kinv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ktc::SMEM_BYTES));
-        attr = true;
-    }
+    GPBO_TRY(ensure_smem((const void *)ktc::k_kinv_tc, ctx->device, (int)ktc::SMEM_BYTES));
     ktc::k_kinv_exp<<<n_pad / 32, 256, 0, st>>>(Linv, n_pad, exps);
     GPBO_LAUNCH_CHECK(ctx);
     ktc::k_kinv_split<<<dim3(n_pad / 32, n_pad / 32), 256, 0, st>>>(Linv, n_pad, exps, (__nv_bfloat16 *)slices);

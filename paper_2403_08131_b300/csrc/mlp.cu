@@ -746,19 +746,35 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
     const int d = net->d;
     float *ei = ei_pool;
     float *own = nullptr;
-    if (!ei) {
-        GPBO_CUDA_TRY(cudaMalloc(&own, sizeof(float) * (size_t)M));
-        ei = own;
-    }
     int64_t *idx = nullptr;
     uint32_t *hist = nullptr;
     float *Xk = nullptr;
-    GPBO_CUDA_TRY(cudaMalloc(&idx, sizeof(int64_t) * (size_t)k));
-    GPBO_CUDA_TRY(cudaMalloc(&hist, sizeof(uint32_t) * (4096 + 4)));
-    GPBO_CUDA_TRY(cudaMalloc(&Xk, sizeof(float) * (size_t)k * d));
+    int rc = GPBO_OK;
+    auto dalloc = [&](void **p, size_t bytes) {
+        if (rc != GPBO_OK) return;
+        const cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            note_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+            rc = e == cudaErrorMemoryAllocation ? GPBO_ENOMEM : GPBO_ECUDA;
+        }
+    };
+    if (!ei) {
+        dalloc((void **)&own, sizeof(float) * (size_t)M);
+        ei = own;
+    }
+    dalloc((void **)&idx, sizeof(int64_t) * (size_t)k);
+    dalloc((void **)&hist, sizeof(uint32_t) * (4096 + 4));
+    dalloc((void **)&Xk, sizeof(float) * (size_t)k * d);
     uint32_t *sel = hist + 4096, *counters = hist + 4098;
     const int prec = mlp_tc_usable(d, net->H, net->E) ? GPBO_PREC_F16 : GPBO_PREC_F32;
-    int rc = score_pool(ctx, net, nullptr, M, seed, y_best, xi, prec, ei, nullptr, nullptr);
+    if (rc == GPBO_OK) rc = score_pool(ctx, net, nullptr, M, seed, y_best, xi, prec, ei, nullptr, nullptr);
+    if (rc == GPBO_OK) {
+        // a bounded wait that gave up in the network's forward leaves part of the pool unscored:
+        // report it here rather than select from it (or leave the bit for a later call)
+        unsigned bits = 0;
+        rc = take_device_status(ctx, &bits);
+        if (rc == GPBO_OK && (bits & DEV_TIMEOUT)) rc = GPBO_ETIMEOUT;
+    }
     // top k by the surrogate's EI
     if (rc == GPBO_OK) {
         uint32_t init[8] = {0, (uint32_t)k, 0, 0, 0, 0, 0, 0};
@@ -788,9 +804,9 @@ int surrogate_screen(gpbo_ctx *ctx, const gp_model *model, gpbo_mlp *net, int64_
         *ei_max = em;
     }
     cudaStreamSynchronize(st);
-    cudaFree(idx);
-    cudaFree(hist);
-    cudaFree(Xk);
+    if (idx) cudaFree(idx);
+    if (hist) cudaFree(hist);
+    if (Xk) cudaFree(Xk);
     if (own) cudaFree(own);
     return rc;
 }

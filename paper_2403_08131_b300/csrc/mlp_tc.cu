@@ -467,7 +467,7 @@ int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, 
     P.status = ctx->dev_status;
     P.idesc = tcx::idesc_f16(0u, mtc::HID, mtc::BM);  // FP16 A and B
     const size_t smem = mtc::smem_bytes();
-    GPBO_CUDA_TRY(cudaFuncSetAttribute(mtc::k_mlp_screen_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GPBO_TRY(ensure_smem((const void *)mtc::k_mlp_screen_tc, ctx->device, (int)smem));
     const int grid = std::min(P.num_tiles, ctx->sm_count);
     mtc::k_mlp_screen_tc<<<grid, mtc::THREADS, smem, ctx->stream>>>(mw, P);
     GPBO_LAUNCH_CHECK(ctx);

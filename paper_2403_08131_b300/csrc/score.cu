@@ -100,11 +100,7 @@ static int launch_xkern(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint6
         return GPBO_OK;
     }
     const size_t smem = sizeof(Acc) * ((size_t)32 * m->d + (size_t)m->d * 128 + 128);
-    static int attr_bytes = 0;  // one per template instance
-    if ((int)smem > attr_bytes) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(k_xkern<Acc, Out>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_bytes = (int)smem;
-    }
+    GPBO_TRY(ensure_smem((const void *)k_xkern<Acc, Out>, ctx->device, (int)smem));
     k_xkern<Acc, Out><<<(unsigned)cdiv64(C, 32), 256, smem, ctx->stream>>>(Xc, seed, c0, C, m->d, Xs, alpha, m->n,
                                                                           m->n_pad, (Acc)m->s2, ls, Kst, mu);
     GPBO_LAUNCH_CHECK(ctx);

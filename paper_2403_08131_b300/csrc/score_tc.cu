@@ -22,10 +22,12 @@
 // K loop then runs twice (hi, then lo) into the same accumulator, so only K*'s rounding
 // remains (twice the MMA work).  FP16 models run a single pass.
 //
-// Every mbarrier wait is bounded (about 2 s of SM clock).  On timeout the kernel sets
-// DEV_TIMEOUT in the context's status word, every role leaves its loop, the producer
-// waits (bounded) for copies it issued, the MMA issuer drains its MMAs, and the
-// allocating warp frees TMEM before the CTA exits.
+// Every mbarrier wait is bounded (the context's wait limit, about 2 s of SM clock by
+// default).  On timeout the kernel sets DEV_TIMEOUT in the context's status word, every
+// role leaves its loop, the producer waits (bounded by the default limit) for copies it
+// issued, the MMA issuer drains its MMAs, and the allocating warp frees TMEM before the
+// CTA exits.  gpbo_inject_wait_stall makes the epilogue wait on a barrier that nothing
+// arrives at, so that tests can run this path without a fault.
 #include "tc_common.cuh"
 
 #include <cuda.h>
@@ -56,6 +58,7 @@ struct Shared {
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t drain;
+    uint64_t never;    // failure injection: a barrier that nothing arrives at
     uint32_t tmem_base;
     int abort;
     float best_v[4];
@@ -106,6 +109,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&sh->acc_empty[a], 4);
         }
         mbar_init(&sh->drain, 1);
+        mbar_init(&sh->never, 1);
         sh->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -202,6 +206,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
+        if (injected_faults(P.status) & 1u) {
+            // failure injection for tests of this error path: the wait runs out after the
+            // context's wait limit, and every role leaves as on a real timeout
+            const bool got = mbar_wait_inl(&sh->never, 0, abort_flag, P.status);
+            ok = __all_sync(0xffffffffu, got);
+        }
         for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
             float ss = 0.0f;
             for (int q = 0; q < nq; ++q) {
@@ -313,12 +323,7 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
     GPBO_TRY(encode_2d(&ml, dt, m->Linv16, (uint64_t)m->n_pad, (uint64_t)m->n_pad, tc::BN));
     GPBO_TRY(encode_2d(&ml2, dt, (const uint16_t *)m->Linv16 + (split ? sq : 0), (uint64_t)m->n_pad,
                        (uint64_t)m->n_pad, tc::BN));
-    static bool attr = false;
-    if (!attr) {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(tc::k_var_ei_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)tc::SMEM_BYTES));
-        attr = true;
-    }
+    GPBO_TRY(ensure_smem((const void *)tc::k_var_ei_tc, ctx->device, (int)tc::SMEM_BYTES));
     tc::Params P;
     P.C = C;
     P.c0 = c0;

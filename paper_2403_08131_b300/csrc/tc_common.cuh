@@ -9,7 +9,7 @@
 namespace gpbo {
 namespace tcx {
 
-constexpr long long TIMEOUT_CYCLES = 4000000000ll;  // bounded waits: about 2 s of SM clock
+constexpr long long TIMEOUT_CYCLES = WAIT_DEFAULT_CYCLES;  // bounded waits: about 2 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -41,17 +41,30 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait.  Gives up (returning false) when another role has aborted, or after
-// TIMEOUT_CYCLES, in which case it raises the abort flag and the device status bit.
+// A wait that honours the abort flag gives up after the context's wait limit (wait_limit).
+// The waits with which a CTA drains its own copies and MMAs before it exits always allow
+// TIMEOUT_CYCLES, so that a short limit never releases shared or tensor memory that an
+// asynchronous operation still uses.
+
+// Failure injection word (byte 4 of the status buffer, gpbo_inject_wait_stall): bit 0 makes the
+// tensor-core variance kernel's epilogue wait on a barrier that nothing arrives at.
+__device__ __forceinline__ unsigned injected_faults(const unsigned *status)
+{
+    return *(const volatile unsigned *)(status + 1);
+}
+
+// Bounded wait.  Gives up (returning false) when another role has aborted, or after the wait
+// limit, in which case it raises the abort flag and the device status bit.
 static __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, unsigned *status,
                                        bool honour_abort = true)
 {
     long long t0 = clock64();
+    const long long limit = honour_abort ? wait_limit(status) : TIMEOUT_CYCLES;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 255u) {
             if (honour_abort && *abort_flag) return false;
-            if (clock64() - t0 > TIMEOUT_CYCLES) {
+            if (clock64() - t0 > limit) {
                 *abort_flag = 1;
                 atomicOr(status, DEV_TIMEOUT);
                 return false;
@@ -70,7 +83,7 @@ __device__ __forceinline__ bool mbar_wait_inl(uint64_t *bar, uint32_t parity, vo
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > TIMEOUT_CYCLES) {
+            if (clock64() - t0 > wait_limit(status)) {
                 *abort_flag = 1;
                 atomicOr(status, DEV_TIMEOUT);
                 return false;

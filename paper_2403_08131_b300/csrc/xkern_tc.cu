@@ -461,7 +461,7 @@ int xkern_tc(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint64_t seed, i
     const bool as = m->n_pad <= xtc::ALPHA_SMEM_MAX;
     const size_t smem = xtc::smem_bytes(as);
     auto launch = [&](auto kern) -> int {
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GPBO_TRY(ensure_smem((const void *)kern, ctx->device, (int)smem));
         kern<<<grid, xtc::THREADS, smem, ctx->stream>>>(mb, mk, P);
         return GPBO_OK;
     };

@@ -75,6 +75,8 @@ _trace_en = _sig("gpbo_trace_enable", C.c_int, [_P, C.c_int])
 _trace_rd = _sig("gpbo_trace_read", C.c_int, [_P, C.c_int, _D, _L, _D])
 PHASES = ("fit", "xkern", "variance", "screen", "chol_update", "lml")
 _probe = _sig("gpbo_probe_fma", C.c_int, [_P, C.c_int, _D])
+_wait_limit = _sig("gpbo_set_wait_limit", C.c_int, [_P, C.c_int64])
+_inject_stall = _sig("gpbo_inject_wait_stall", C.c_int, [_P, C.c_int])
 _fit = _sig("gp_fit", C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.POINTER(GpHyper), C.c_int, C.c_uint,
                                  C.POINTER(_P)])
 _model_free = _sig("gp_model_free", C.c_int, [_P])
@@ -191,6 +193,15 @@ class Context:
         v = C.c_double(0.0)
         check(_probe(self._h, 0 if kind == "f64" else 1, C.byref(v)), "gpbo_probe_fma")
         return float(v.value)
+
+    def set_wait_limit(self, cycles: int):
+        """Limit, in SM clock cycles, of the library's bounded device waits (0 = default)."""
+        check(_wait_limit(self._h, int(cycles)), "gpbo_set_wait_limit")
+
+    def inject_wait_stall(self, on):
+        """Failure injection for tests: the tensor-core variance epilogue waits on a barrier
+        that nothing arrives at, so the scoring call returns GPBO_ETIMEOUT."""
+        check(_inject_stall(self._h, int(on)), "gpbo_inject_wait_stall")
 
     def trace_read(self):
         n = len(PHASES)

@@ -31,3 +31,14 @@ def ctx():
     c = gpbo.Context(0, torch.cuda.current_stream())
     yield c
     c.close()
+
+
+@pytest.fixture(scope="session")
+def full_size(orc):
+    """n = 4096, d = 20, M = 2^20: the bench's workload (five-block function, standardised y);
+    the oracle fit is done once per session."""
+    from paper_2403_08131_b300 import workloads as W
+    w = W.config4()
+    ys = (w.y - w.y.mean()) / w.y.std()
+    _, Lo, ao = orc.gp_fit(w.X, ys, w.lengthscale, 1.0, w.noise_var)
+    return w, ys, Lo, ao

@@ -45,6 +45,21 @@ def test_fit_tensor_core_update_matches_oracle(ctx, orc, n, d, prec):
     m.free()
 
 
+@pytest.mark.parametrize("prec", ["f16", "bf16", "f32", "f64"])
+def test_fit_full_size_matches_oracle(ctx, full_size, prec):
+    """The bench's fit (n = 4096, d = 20, 64 block columns, the lookahead chain and every
+    tensor-core update level) in each scoring precision: L and alpha against the textbook
+    FP64 Cholesky and solves at the same bars as the smaller fits."""
+    from tests._util import to_dev
+    w, ys, Lo, ao = full_size
+    m = ctx.fit(to_dev(w.X), to_dev(ys), w.lengthscale, 1.0, w.noise_var, prec=prec)
+    Lg, ag = m.read()
+    m.free()
+    assert np.abs(Lg - Lo).max() <= 1e-11 * np.abs(Lo).max(), np.abs(Lg - Lo).max()
+    assert np.abs(ag - ao).max() <= 1e-9 * (np.abs(ao).max() + 1), np.abs(ag - ao).max()
+    assert not np.triu(Lg, 1).any()
+
+
 def test_fit_host_pointers_equal_device(ctx):
     from tests._util import to_dev
     X, y = _obs(200, 5, 7)

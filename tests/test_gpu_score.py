@@ -113,15 +113,6 @@ def test_chunked_pool_equals_single_pass(ctx):
     c2.close()
 
 
-@pytest.fixture(scope="module")
-def full_size(orc):
-    """n = 4096, d = 20, M = 2^20: the bench's workload; the oracle fit is done once."""
-    w = W.config4()
-    ys = (w.y - w.y.mean()) / w.y.std()
-    _, Lo, ao = orc.gp_fit(w.X, ys, w.lengthscale, 1.0, w.noise_var)
-    return w, ys, Lo, ao
-
-
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 def test_full_size_sampled_parity(ctx, orc, full_size, prec):
     w, ys, Lo, ao = full_size
@@ -145,3 +136,44 @@ def test_full_size_sampled_parity(ctx, orc, full_size, prec):
     best_ref = max(rei[pos[int(i)]] for i in top)
     assert rei[pos[am]] >= best_ref * (1 - bar)
     m.free()
+
+
+@pytest.fixture(scope="module")
+def full_pool(ctx, orc, full_size):
+    """Every scoring path on the bench's whole pool (n = 4096, M = 2^20): each path's pick and
+    its top 1024 by EI, and the oracle's EI on the union of those sets and 512 random pool
+    indices.  The FP64 path's top 1024 is within the FP64 bar of the oracle's ranking, so the
+    union holds the oracle's best candidates of the whole pool."""
+    w, ys, Lo, ao = full_size
+    tau = float(ys.min())
+    picks, tops = {}, {}
+    for prec in ("f16", "bf16", "f32", "f64"):
+        m = ctx.fit(to_dev(w.X), to_dev(ys), w.lengthscale, 1.0, w.noise_var, prec=prec)
+        am, em, _, _, ei = _score(ctx, m, None, prec, tau, seed=w.seed, M=w.M)
+        m.free()
+        picks[prec] = am
+        tops[prec] = np.argsort(-ei, kind="stable")[:1024]
+        assert tops[prec][0] == am or ei[tops[prec][0]] == ei[am]
+    rng = np.random.default_rng(1)
+    union = np.unique(np.concatenate(list(tops.values()) + [rng.choice(w.M, 512, replace=False)]))
+    cnt = union.astype(np.uint64)[:, None] * np.uint64(w.d) + np.arange(w.d, dtype=np.uint64)[None, :]
+    Xs = W.uniform24(w.seed, W.STREAM_CAND, cnt)
+    rmu, rsg = orc.posterior(w.X, w.lengthscale, 1.0, Lo, ao, Xs)
+    return picks, tops, union, orc.ei_batch(rmu, rsg, tau)
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16", "f32", "f64"])
+def test_full_pool_argmax_against_oracle(full_pool, prec):
+    """The pick over all 2^20 candidates obeys the argmax rule against the oracle's best over
+    the union (exact when the oracle's margin exceeds the path's bar), and no oracle-scored
+    candidate that the path ranked outside its top 1024 beats the pick."""
+    picks, tops, union, rei = full_pool
+    pos = {int(i): k for k, i in enumerate(union)}
+    bar = BAR[prec]
+    am = picks[prec]
+    rule = check_argmax(pos[am], rei, bar)
+    outside = ~np.isin(union, tops[prec])
+    assert rei[outside].max() <= rei[pos[am]] * (1 + bar), (prec, float(rei[outside].max()), float(rei[pos[am]]))
+    order = np.argsort(-rei, kind="stable")
+    print(f"{prec}: pick {am}, oracle best {int(union[order[0]])}, margin "
+          f"{(rei[order[0]] - rei[order[1]]) / rei[order[0]]:.3g}, rule {rule}")

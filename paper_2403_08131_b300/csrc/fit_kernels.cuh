@@ -69,22 +69,19 @@ __device__ __forceinline__ void k_kmat_body(const double *__restrict__ Xs, int n
 // the flag and store them scaled, so one barrier per column suffices.  The factor's arithmetic
 // per element is that of a plain right-looking loop.  The reciprocal pivots go to the diagonal
 // of Dinv_kb; k_chol_inv builds the rest of the inverse for the panel.
-__device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_pad, int kb,
-                                                   double *__restrict__ Dinv, unsigned *status, const int bx, const int by)
+constexpr int DIAG_TRI = NB * (NB + 1) / 2;
+
+// The factorisation of one 64 x 64 diagonal block held in shared memory (a: the block, rows of
+// NB + 1 doubles; tab: DIAG_TRI entries of scratch; rdiag: NB doubles; ready: one int), by the
+// CTA's threads (a multiple of 128).  On return (after a barrier) a holds L_kk in its lower
+// triangle and rdiag the reciprocal pivots.
+__device__ __forceinline__ void chol_diag_factor_smem(double (*a)[NB + 1], uint16_t *tab, double *rdiag, int *ready_p,
+                                                      unsigned *status)
 {
-    extern __shared__ double sm[];
-    double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
-    constexpr int TRI = NB * (NB + 1) / 2;
-    __shared__ double rdiag[NB];
-    __shared__ uint16_t tab[TRI];  // lower triangle, column-major: row | col << 8
-    __shared__ int ready;          // highest column whose pivot is published
+    constexpr int TRI = DIAG_TRI;
+    int &ready = *ready_p;         // highest column whose pivot is published
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
     auto coff = [](int c) { return c * NB - c * (c - 1) / 2; };  // first entry of column c
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-        const int r = e / NB, c = e % NB;
-        a[r][c] = A[base + (int64_t)r * n_pad + c];
-    }
     for (int e = tid; e < TRI; e += blockDim.x) {
         // column c: the largest with coff(c) <= e (closed form, then exact integer fix-up)
         int c = (int)((129.0f - sqrtf(16641.0f - 8.0f * (float)e)) * 0.5f);
@@ -128,17 +125,39 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
         }
         // workers: the warps on schedulers 1-3, so that the pivot's FP64 instructions have
         // scheduler 0's FP64 unit to themselves (each FP64 warp instruction holds it 64 cycles)
+        // Each worker thread takes at most one element of column j+1 below its diagonal (final
+        // after this pass: updated now, stored scaled once the pivot is published) and elements
+        // e, e + W, ... of the trailing triangle, four independent ones per pass so that the
+        // shared-memory loads and FMAs of a warp overlap (each FP64 warp instruction holds its
+        // scheduler's FP64 unit 64 cycles: the passes keep that unit, not latency, the limit).
         const int warp = tid >> 5, nw = (int)(blockDim.x >> 5), workers = nw - (nw + 3) / 4;
         const int wid = warp - warp / 4 - 1;
-        for (int e = wid * 32 + (tid & 31); e < nT; e += workers * 32) {
-            if ((warp & 3) == 0) break;
-            if (e < nF) {
-                const int t = tab[coff(j + 2) + e], i = t & 255, c = t >> 8;
+        if ((warp & 3) != 0) {
+            const int W = workers * 32, w0 = wid * 32 + (tid & 31);
+            const uint16_t *tj = tab + coff(j + 2);
+            const bool has_col = w0 < m - 1;
+            double vcol = 0.0;
+            if (has_col) vcol = fma(-a[j + 2 + w0][j], a[j + 1][j], a[j + 2 + w0][j + 1]);
+            int e = w0;
+            for (; e + 3 * W < nF; e += 4 * W) {
+                int ii[4], cc[4];
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int t = tj[e + u * W];
+                    ii[u] = t & 255;
+                    cc[u] = t >> 8;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = fma(-a[ii[u]][j], a[cc[u]][j], a[ii[u]][cc[u]]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[ii[u]][cc[u]] = v[u];
+            }
+            for (; e < nF; e += W) {
+                const int t = tj[e], i = t & 255, c = t >> 8;
                 a[i][c] = fma(-a[i][j], a[c][j], a[i][c]);
-            } else {
-                // last: column j+1 below its diagonal, final after this pass; stored scaled
-                const int q = e - nF;
-                const double v = fma(-a[j + 2 + q][j], a[j + 1][j], a[j + 2 + q][j + 1]);
+            }
+            if (has_col) {
                 for (int it = 0; *vready < j + 1; ++it) {
                     if (it == (1 << 24)) {  // cannot happen: warp 0 publishes unconditionally
                         atomicOr(status, DEV_TIMEOUT);
@@ -146,11 +165,30 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
                     }
                 }
                 __threadfence_block();
-                a[j + 2 + q][j + 1] = v * vrdiag[j + 1];
+                a[j + 2 + w0][j + 1] = vcol * vrdiag[j + 1];
             }
         }
         __syncthreads();
     }
+}
+
+// Diagonal block kb of A (global): load, factor (chol_diag_factor_smem), store L_kk with zeros
+// above its diagonal and the reciprocal pivots on Dinv_kb's diagonal.
+__device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_pad, int kb,
+                                                   double *__restrict__ Dinv, unsigned *status, const int bx, const int by)
+{
+    extern __shared__ double sm[];
+    double(*a)[NB + 1] = reinterpret_cast<double(*)[NB + 1]>(sm);
+    __shared__ double rdiag[NB];
+    __shared__ uint16_t tab[DIAG_TRI];  // lower triangle, column-major: row | col << 8
+    __shared__ int ready;
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        a[r][c] = A[base + (int64_t)r * n_pad + c];
+    }
+    chol_diag_factor_smem(a, tab, rdiag, &ready, status);
     double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < NB * NB; e += blockDim.x) {
         const int i = e / NB, c = e % NB;
@@ -166,6 +204,21 @@ __device__ __forceinline__ void k_chol_diag_body(double *__restrict__ A, int n_p
 // t = c .. i - 1, and X_ic = rd_i x~_ic: one shuffle and one or two FP64 FMAs per step (on this
 // part every FP64 warp instruction holds its SMSP's FP64 unit for 64 cycles, so the step count
 // of this chain is what the factorisation waits on).  Launch: 64 / W CTAs of 32 W threads.
+// Column c of the inverse, by one warp, from the scaled block l (l_it rd_t below the diagonal,
+// zero elsewhere) and the reciprocal pivots rd in shared memory; written to D (row-major 64 x 64).
+__device__ __forceinline__ void chol_inv_column(const double (*l)[NB + 1], const double *rd, int c, int lane,
+                                                double *__restrict__ D)
+{
+    double x0 = lane == c ? 1.0 : 0.0, x1 = lane + 32 == c ? 1.0 : 0.0;
+    for (int t = c; t < NB; ++t) {
+        const double v = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
+        if (t < 31 && lane > t) x0 = fma(-l[lane][t], v, x0);
+        if (lane + 32 > t) x1 = fma(-l[lane + 32][t], v, x1);
+    }
+    D[lane * NB + c] = x0 * rd[lane];   // zero above the diagonal (rows < c never change)
+    D[(lane + 32) * NB + c] = x1 * rd[lane + 32];
+}
+
 __device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, int n_pad, int kb,
                                                   double *__restrict__ Dinv, const int bx)
 {
@@ -182,14 +235,7 @@ __device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, in
     }
     __syncthreads();
     const int c = bx * (int)(blockDim.x >> 5) + warp;
-    double x0 = lane == c ? 1.0 : 0.0, x1 = lane + 32 == c ? 1.0 : 0.0;
-    for (int t = c; t < NB; ++t) {
-        const double v = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
-        if (t < 31 && lane > t) x0 = fma(-l[lane][t], v, x0);
-        if (lane + 32 > t) x1 = fma(-l[lane + 32][t], v, x1);
-    }
-    D[lane * NB + c] = x0 * rd[lane];   // zero above the diagonal (rows < c never change)
-    D[(lane + 32) * NB + c] = x1 * rd[lane + 32];
+    chol_inv_column(l, rd, c, lane, D);
 }
 
 // Trailing update in slabs of SR rows (64 / SR CTAs per 64x64 tile), for launches too small to
@@ -241,6 +287,26 @@ __device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, 
 // 63 - tx in one loop of 65 steps -- every lane issues one FMA per step (a warp issues 65 FP64
 // instructions per row instead of 96 when a lane takes one column) -- and each column keeps
 // its t = 0 .. c accumulation order.
+// Output columns tx and 63 - tx of one panel row a (shared, NB values) times L_kk^-T, from the
+// inverse dv (shared, rows of NB + 1), each column summed over t = 0 .. c in order.
+__device__ __forceinline__ void chol_panel_pair(const double *a, const double (*dv)[NB + 1], int tx, double &out1,
+                                                double &out2)
+{
+    const int c1 = tx, c2 = NB - 1 - tx;
+    double acc = 0.0;
+    out1 = 0.0;
+    for (int s = 0; s <= NB; ++s) {
+        const bool first = s <= c1;
+        const int t = first ? s : s - c1 - 1, c = first ? c1 : c2;
+        acc = fma(a[t], dv[c][t], acc);
+        if (s == c1) {
+            out1 = acc;
+            acc = 0.0;
+        }
+    }
+    out2 = acc;
+}
+
 __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_pad, int kb,
                                                     const double *__restrict__ Dinv, const int bx, const int by)
 {
@@ -252,19 +318,10 @@ __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_
     for (int e = tid; e < 4 * NB; e += blockDim.x) a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];
     for (int e = tid; e < NB * NB; e += blockDim.x) dv[e / NB][e % NB] = D[e];
     __syncthreads();
-    const int c1 = tx, c2 = NB - 1 - tx;
-    double acc = 0.0, out1 = 0.0;
-    for (int s = 0; s <= NB; ++s) {
-        const bool first = s <= c1;
-        const int t = first ? s : s - c1 - 1, c = first ? c1 : c2;
-        acc = fma(a[ty][t], dv[c][t], acc);
-        if (s == c1) {
-            out1 = acc;
-            acc = 0.0;
-        }
-    }
-    A[(row0 + ty) * n_pad + (int64_t)kb * NB + c1] = out1;
-    A[(row0 + ty) * n_pad + (int64_t)kb * NB + c2] = acc;
+    double out1, out2;
+    chol_panel_pair(a[ty], dv, tx, out1, out2);
+    A[(row0 + ty) * n_pad + (int64_t)kb * NB + tx] = out1;
+    A[(row0 + ty) * n_pad + (int64_t)kb * NB + NB - 1 - tx] = out2;
 }
 
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.

@@ -8,16 +8,22 @@
 // Williams 2006, Alg. 2.1) written as a GEMM with many right-hand sides, so that it is a
 // dense contraction and belongs on the tensor cores.
 //
-// Kernel shape (one CTA per SM, persistent over 128-candidate tiles):
-//   warp 0      TMA producer: K* tile (128 x 64) and L^-1 tile (256 x 64) per stage,
-//               128-byte swizzle, 4 stages of 48 KiB in shared memory
-//   warp 1      allocates 512 TMEM columns; one lane issues tcgen05.mma (M=128, N=256,
-//               K=16, FP32 accumulate) into one of two 256-column accumulators
-//   warps 2..5  epilogue: tcgen05.ld the accumulator, square and sum into the candidate's
-//               running |v|^2 (one TMEM lane = one candidate = one thread), then sigma,
-//               EI and the per-CTA argmax
+// Kernel shape: clusters of two CTAs (one per SM), persistent over tiles of 256 candidates, the
+// pair running one tensor-core MMA of M = 256 (cta_group::2): each CTA holds its own 128
+// candidates (its TMEM lanes) and half of the 256 L^-1 rows of the output chunk, so a CTA stages
+// 32 KiB per 64 of K instead of 48 KiB for the same MMA time.
+//   warp 0      TMA producer (both CTAs): K* tile (128 x 128) and half the L^-1 tile (128 x 128)
+//               per stage as 64-wide sub-tiles, 128-byte swizzle, 3 stages of 64 KiB
+//   warp 1      both CTAs allocate 512 TMEM columns together; in the first CTA one lane issues
+//               the pair's tcgen05.mma (M=256, N=256, K=16, FP32 accumulate) into one of two
+//               256-column accumulators once both CTAs' copies of a stage have landed; in the
+//               second CTA one lane forwards each landed stage to the first CTA's barrier
+//   warps 2..5  epilogue (both CTAs): tcgen05.ld the accumulator, square and sum into the
+//               candidate's running |v|^2 (one TMEM lane = one candidate = one thread), then
+//               sigma, EI and the per-CTA argmax
 // For output chunk q (L^-1 rows 256q .. 256q+255) only K columns < 256(q+1) are read:
-// the triangle's zero blocks are never loaded or multiplied.
+// the triangle's zero blocks are never loaded or multiplied.  Successive passes over K run in
+// opposite directions, so a pass starts on the K* columns the previous one read last (in L2).
 // BF16 models carry a compensated inverse, hi = bf16(L^-1) and lo = bf16(L^-1 - hi); the
 // K loop then runs twice (hi, then lo) into the same accumulator, so only K*'s rounding
 // remains (twice the MMA work).  FP16 models run a single pass.
@@ -25,9 +31,9 @@
 // Every mbarrier wait is bounded (the context's wait limit, about 2 s of SM clock by
 // default).  On timeout the kernel sets DEV_TIMEOUT in the context's status word, every
 // role leaves its loop, the producer waits (bounded by the default limit) for copies it
-// issued, the MMA issuer drains its MMAs, and the allocating warp frees TMEM before the
-// CTA exits.  gpbo_inject_wait_stall makes the epilogue wait on a barrier that nothing
-// arrives at, so that tests can run this path without a fault.
+// issued, the MMA issuer drains its MMAs (and both CTAs wait for that), and the allocating
+// warps free TMEM before the CTAs exit.  gpbo_inject_wait_stall makes the epilogue wait on a
+// barrier that nothing arrives at, so that tests can run this path without a fault.
 #include "tc_common.cuh"
 
 #include <cuda.h>
@@ -36,45 +42,52 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace gpbo {
 
 namespace tc {
 
-constexpr int BM = 128;        // candidates per tile (MMA M, TMEM lanes)
+constexpr int BM = 128;        // candidates per CTA (TMEM lanes); a pair covers 2 BM
 constexpr int BN = TC_NCHUNK;  // L^-1 rows per output chunk (MMA N)
-constexpr int BK = 64;         // K elements per stage (128 bytes of 16-bit values)
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
+constexpr int BNH = BN / 2;    // rows of the chunk each CTA of the pair stages
+constexpr int BK = 128;        // K elements per stage
+constexpr int KSUB = BK / 64;  // sub-tiles of 64 (128 bytes of 16-bit values: the swizzle span)
+constexpr int STAGES = 3;
+constexpr int A_SUB = BM * 64 * 2;
+constexpr int B_SUB = BNH * 64 * 2;
+constexpr int A_BYTES = KSUB * A_SUB;
+constexpr int B_BYTES = KSUB * B_SUB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 512;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
 
 struct Shared {
-    uint64_t full[STAGES];
-    uint64_t empty[STAGES];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
-    uint64_t drain;
-    uint64_t never;    // failure injection: a barrier that nothing arrives at
+    uint64_t full[STAGES];   // this CTA's copies of the stage have landed
+    uint64_t pfull[STAGES];  // first CTA: the second CTA's copies of the stage have landed
+    uint64_t empty[STAGES];  // the pair's MMAs are done with the stage (both CTAs)
+    uint64_t acc_full[2];    // accumulator a is complete (both CTAs)
+    uint64_t acc_empty[2];   // first CTA: both CTAs' epilogues have read accumulator a
+    uint64_t drain;          // every MMA of the pair is complete (both CTAs)
+    uint64_t never;          // failure injection: a barrier that nothing arrives at
     uint32_t tmem_base;
     int abort;
     float best_v[4];
     int64_t best_i[4];
 };
+static_assert(sizeof(Shared) <= 512, "barrier area");
 
 using namespace tcx;
 
-// Instruction descriptor for this kernel's MMA: N = 256, M = 128.
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) { return idesc_f16(fmt, BN, BM); }
+// Instruction descriptor for this kernel's MMA: N = 256, M = 256 (the pair's two halves).
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) { return idesc_f16(fmt, BN, 2 * BM); }
 
 struct Params {
     int64_t C;        // candidates in this chunk
     int64_t c0;       // pool index of the chunk's first candidate
     int n_pad;
-    int num_tiles;
+    int num_tiles;    // tiles of 2 BM candidates
     float s2;
     float xi;
     double y_best;
@@ -89,7 +102,7 @@ struct Params {
     int split;        // 1: V = K* hi^T + K* lo^T (compensated BF16 inverse), 0: single pass
 };
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     k_var_ei_tc(const __grid_constant__ CUtensorMap map_k, const __grid_constant__ CUtensorMap map_l,
                 const __grid_constant__ CUtensorMap map_l2, Params P)
 {
@@ -98,15 +111,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     Shared *sh = (Shared *)(tiles + (size_t)STAGES * STAGE_BYTES);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nq = P.n_pad / BN;
+    const uint32_t rank = cluster_rank();  // 0: issues the pair's MMAs
+    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+    const int passes = 1 + P.split;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->pfull[s], 1);
             mbar_init(&sh->empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&sh->acc_full[a], 1);
-            mbar_init(&sh->acc_empty[a], 4);
+            mbar_init(&sh->acc_empty[a], 8);
         }
         mbar_init(&sh->drain, 1);
         mbar_init(&sh->never, 1);
@@ -115,13 +132,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+        // one warp of each CTA of the pair allocates, together, the same columns in both
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
                      "r"(TMEM_COLS)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before either signals the other
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort_flag = &sh->abort;
@@ -138,21 +157,29 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t armed_par[STAGES];
             for (int s = 0; s < STAGES; ++s) armed[s] = 0, armed_par[s] = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+            for (int t = pair; ok && t < P.num_tiles; t += npairs) {
+                const int arow = t * (2 * BM) + (int)rank * BM;
                 for (int q = 0; ok && q < nq; ++q) {
                     const int ksteps = (q + 1) * (BN / BK);
-                    // the compensated form runs the K loop twice: hi operand, then lo
-                    for (int ks2 = 0; ks2 < ksteps * (1 + P.split); ++ks2) {
-                        const int ks = ks2 < ksteps ? ks2 : ks2 - ksteps;
-                        if (!mbar_wait_fast(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
-                        unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
-                        unsigned char *b = a + A_BYTES;
-                        mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
-                        armed[stage] = 1;
-                        armed_par[stage] = phase;
-                        tma_load_2d(a, &map_k, ks * BK, t * BM, &sh->full[stage]);
-                        tma_load_2d(b, ks2 < ksteps ? &map_l : &map_l2, ks * BK, q * BN, &sh->full[stage]);
-                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    const int brow = q * BN + (int)rank * BNH;
+                    for (int h = 0; ok && h < passes; ++h) {
+                        const bool down = ((q * passes + h) & 1) != 0;
+                        const CUtensorMap *mb = h ? &map_l2 : &map_l;
+                        for (int i = 0; i < ksteps; ++i) {
+                            const int ks = down ? ksteps - 1 - i : i;
+                            if (!mbar_wait_fast(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                            unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
+                            unsigned char *b = a + A_BYTES;
+                            mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
+                            armed[stage] = 1;
+                            armed_par[stage] = phase;
+#pragma unroll
+                            for (int u = 0; u < KSUB; ++u) {
+                                tma_load_2d(a + u * A_SUB, &map_k, ks * BK + 64 * u, arow, &sh->full[stage]);
+                                tma_load_2d(b + u * B_SUB, mb, ks * BK + 64 * u, brow, &sh->full[stage]);
+                            }
+                            if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                        }
                     }
                 }
             }
@@ -161,38 +188,60 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (armed[s]) mbar_wait(&sh->full[s], armed_par[s], abort_flag, P.status, false);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------- MMA issuer
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer of the pair
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+            for (int t = pair; ok && t < P.num_tiles; t += npairs) {
                 for (int q = 0; ok && q < nq; ++q) {
-                    if (!mbar_wait_fast(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (!mbar_wait_cluster(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-                    const int ksteps = (q + 1) * (BN / BK) * (1 + P.split);
+                    const int ksteps = (q + 1) * (BN / BK) * passes;
                     for (int ks = 0; ks < ksteps; ++ks) {
                         if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_try_cluster(&sh->pfull[stage], phase) &&
+                            !mbar_wait_cluster(&sh->pfull[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                         const unsigned char *b = a + A_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
-                            mma_f16(d_tmem, smem_desc(a + kk * 32), smem_desc(b + kk * 32), P.idesc,
-                                    (ks > 0 || kk > 0) ? 1u : 0u);
-                        mma_commit(&sh->empty[stage]);
+                            mma_f16_pair(d_tmem, smem_desc(a + (kk >> 2) * A_SUB + (kk & 3) * 32),
+                                         smem_desc(b + (kk >> 2) * B_SUB + (kk & 3) * 32), P.idesc,
+                                         (ks > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit_pair(&sh->empty[stage], 3);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
-                    mma_commit(&sh->acc_full[acc]);
+                    mma_commit_pair(&sh->acc_full[acc], 3);
                     if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
                 }
             }
-            // drain every MMA this thread issued before TMEM is released
-            mma_commit(&sh->drain);
+            // every MMA this thread issued completes before either CTA releases TMEM or exits
+            mma_commit_pair(&sh->drain, 3);
+            mbar_wait(&sh->drain, 0, abort_flag, P.status, false);
+        } else if (lane == 0) {
+            // ---------------- the second CTA: forward each landed stage to the first CTA
+            const uint32_t pfull0 = cluster_addr(&sh->pfull[0], 0);
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = pair; ok && t < P.num_tiles; t += npairs) {
+                for (int q = 0; ok && q < nq; ++q) {
+                    const int ksteps = (q + 1) * (BN / BK) * passes;
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        // the copies have landed in this CTA's shared memory (this wait saw them);
+                        // the signal itself publishes nothing, so it needs no release fence
+                        mbar_arrive_cluster_relaxed(pfull0 + (uint32_t)(stage * sizeof(uint64_t)));
+                        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
             mbar_wait(&sh->drain, 0, abort_flag, P.status, false);
         }
     } else {
@@ -200,6 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        const uint32_t acc_empty0 = cluster_addr(&sh->acc_empty[0], 0);
         const float tau = P.tau_dev ? (float)*P.tau_dev : (float)P.y_best;
         float best_v = -1.0f;
         int64_t best_i = INT64_MAX;
@@ -212,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const bool got = mbar_wait_inl(&sh->never, 0, abort_flag, P.status);
             ok = __all_sync(0xffffffffu, got);
         }
-        for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
+        for (int t = pair; ok && t < P.num_tiles; t += npairs) {
             float ss = 0.0f;
             for (int q = 0; q < nq; ++q) {
                 // every lane waits; the warp leaves together so tcgen05.ld stays warp-uniform
@@ -228,11 +278,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->acc_empty[acc]);
+                if (lane == 0) mbar_arrive_cluster(acc_empty0 + (uint32_t)(acc * sizeof(uint64_t)));
                 if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
             }
             if (!ok) break;
-            const int64_t cl = (int64_t)t * BM + row;
+            const int64_t cl = (int64_t)t * (2 * BM) + (int64_t)rank * BM + row;
             if (cl < P.C) {
                 const int64_t c = P.c0 + cl;
                 const float var = P.s2 - ss;
@@ -255,7 +305,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    tc_fence_after();
     if (threadIdx.x == 0) {
         float bv = sh->best_v[0];
         int64_t bi = sh->best_i[0];
@@ -264,8 +313,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         P.part_ei[blockIdx.x] = bv;
         P.part_idx[blockIdx.x] = bi;
     }
+    // neither CTA leaves while the other may still signal its barriers
+    cluster_sync();
+    tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
@@ -320,15 +372,15 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
     const int split = m->prec == GPBO_PREC_BF16 ? 1 : 0;
     const size_t sq = (size_t)m->n_pad * m->n_pad;
     GPBO_TRY(encode_2d(&mk, dt, Kstar, (uint64_t)C, (uint64_t)m->n_pad, tc::BM));
-    GPBO_TRY(encode_2d(&ml, dt, m->Linv16, (uint64_t)m->n_pad, (uint64_t)m->n_pad, tc::BN));
+    GPBO_TRY(encode_2d(&ml, dt, m->Linv16, (uint64_t)m->n_pad, (uint64_t)m->n_pad, tc::BNH));
     GPBO_TRY(encode_2d(&ml2, dt, (const uint16_t *)m->Linv16 + (split ? sq : 0), (uint64_t)m->n_pad,
-                       (uint64_t)m->n_pad, tc::BN));
+                       (uint64_t)m->n_pad, tc::BNH));
     GPBO_TRY(ensure_smem((const void *)tc::k_var_ei_tc, ctx->device, (int)tc::SMEM_BYTES));
     tc::Params P;
     P.C = C;
     P.c0 = c0;
     P.n_pad = m->n_pad;
-    P.num_tiles = (int)cdiv64(C, tc::BM);
+    P.num_tiles = (int)cdiv64(C, 2 * tc::BM);
     P.s2 = (float)m->s2;
     P.xi = (float)xi;
     P.y_best = y_best;
@@ -341,7 +393,33 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
     P.status = ctx->dev_status;
     P.idesc = tc::instr_desc(m->prec == GPBO_PREC_BF16 ? 1u : 0u);
     P.split = split;
-    const int grid = std::min(P.num_tiles, ctx->sm_count);
+    // clusters of two CTAs, one per SM: as many pairs as can be resident at once (a pair must
+    // sit in one GPC, so this can be below half the SMs)
+    int pairs = 0;
+    {
+        static std::mutex mu;
+        static int cached[64] = {};
+        std::lock_guard<std::mutex> lk(mu);
+        if (ctx->device >= 0 && ctx->device < 64 && cached[ctx->device] > 0) {
+            pairs = cached[ctx->device];
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * (ctx->sm_count / 2));
+            cfg.blockDim = dim3(tc::THREADS);
+            cfg.dynamicSmemBytes = tc::SMEM_BYTES;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            GPBO_CUDA_TRY(cudaOccupancyMaxActiveClusters(&pairs, (const void *)tc::k_var_ei_tc, &cfg));
+            if (pairs < 1) return GPBO_ENOTSUP;
+            if (ctx->device >= 0 && ctx->device < 64) cached[ctx->device] = pairs;
+        }
+    }
+    const int grid = 2 * std::max(1, std::min(P.num_tiles, pairs));
     tc::k_var_ei_tc<<<grid, tc::THREADS, tc::SMEM_BYTES, ctx->stream>>>(mk, ml, ml2, P);
     GPBO_LAUNCH_CHECK(ctx);
     *n_parts = grid;

@@ -268,6 +268,85 @@ __device__ __forceinline__ double scaled_to_double(long long x, int k)
     return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (m & 0x000FFFFFFFFFFFFFull)));
 }
 
+// ---- CTA pairs (clusters of two CTAs whose tensor cores run one MMA together, cta_group::2)
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives, then waits for all the others.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the variable at local shared address p in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+// Arrive (release, cluster scope) on an mbarrier given by its shared::cluster address.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+// Relaxed arrive (no release fence) on an mbarrier given by its shared::cluster address: for a
+// signal that publishes no memory writes of the arriving thread (a stage whose copies another
+// barrier has already seen land).
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+// try_wait with cluster-scope acquire, for barriers that the peer CTA arrives on.
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+static __device__ __noinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                                      unsigned *status)
+{
+    const long long t0 = clock64(), limit = wait_limit(status);
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_cluster(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                *abort_flag = 1;
+                atomicOr(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+// One MMA of the CTA pair, issued by one thread of the pair's first CTA: D (128 lanes of each
+// CTA's tensor memory) += A (each CTA's own 128 rows) x B (N rows: the first half from this
+// CTA's shared memory, the second from the peer's, at the same offsets).
+__device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// Arrive on the mbarrier at this offset in each CTA of `mask` once the pair's MMAs issued so far
+// by this thread are complete.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulate, A/B format (0 = F16, 1 = BF16), both
 // K-major, N x M.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, int N, int M)

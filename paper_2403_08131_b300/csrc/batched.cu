@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) b_xkern(const BProb *P, const float *Xs32
 }
 
 template <int BM>
-__global__ void __launch_bounds__(256) b_var(const BProb *P, const float *Kst, const float *Linv, const float *mu,
+__global__ void __launch_bounds__(256, BM == 256 ? 1 : 2) b_var(const BProb *P, const float *Kst, const float *Linv, const float *mu,
                                              const double *tau, float xi, float *pei, int64_t *pidx)
 {
     const BProb &p = P[blockIdx.y];

@@ -62,7 +62,7 @@ constexpr int VAR_BM32 = 128;
 template <typename T> constexpr int var_bm() { return sizeof(T) == 4 ? VAR_BM32 : 64; }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_var_simt(const T *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
+__global__ void __launch_bounds__(256, 2) k_var_simt(const T *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
                                                   const T *__restrict__ Linv, const T *__restrict__ mu, T s2,
                                                   double y_best, const double *__restrict__ tau_dev, T xi,
                                                   T *__restrict__ sigma_out, T *__restrict__ ei_out,

@@ -296,11 +296,17 @@ __device__ __forceinline__ void k_var_simt_body(const T *__restrict__ Kst, int64
 }
 
 // FP32 variance, EI and per-CTA argmax on CUDA cores, BM = 64, 128 or 256 candidates per CTA.
-// Thread (ty, tx) of 16 x 16 owns candidates ty*TM .. ty*TM+TM-1 (TM = BM/16) and, in each
-// 64-row output chunk of L^-1, rows tx*4 .. tx*4+3, so its shared-memory reads are 128-bit;
-// K steps of 16 through transposed shared tiles, with the next step's global loads held in
-// registers while the current one is multiplied.  Every candidate's sums run in the same order
-// for every BM, so the tile changes no result.
+// The output is worked through in chunks of 128 rows of L^-1 (chunk q needs K columns below
+// 128 (q + 1) only: the triangle's zero blocks are skipped).  Thread (ty, tx) of 16 x 16 owns
+// candidates ty*TM .. ty*TM+TM-1 (TM = BM/16) and rows tx*4 .. tx*4+3 and 64+tx*4 .. 64+tx*4+3
+// of each chunk: an 8 x TM register tile, so each K step reads 8 + TM floats from shared
+// memory (128-bit reads, conflict-free) for 8 TM FMAs, within the shared-memory port at the
+// FMA rate.  K* is read in 64-byte row segments (four lanes per candidate) and L^-1 likewise;
+// both go through transposed shared tiles in K steps of 8, the next step's global loads held
+// in registers while the current one is multiplied (short steps keep the register count at
+// 128, so that two CTAs share an SM and hide each other's latencies).  Successive chunks run over K in opposite
+// directions, so a chunk starts on the K* columns the previous one read last (still in L2).
+// Every candidate's sums run in the same order for every BM, so the tile changes no result.
 template <int BM>
 __device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, int64_t C, int64_t c0, int n_pad,
                                                const float *__restrict__ Linv, const float *__restrict__ mu, float s2,
@@ -310,75 +316,90 @@ __device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, in
                                                int part_base, const int bx)
 {
     static_assert(BM == 64 || BM == 128 || BM == 256, "tile");
-    constexpr int BN = 64, BK = 16, TM = BM / 16, PAD = 4;
-    constexpr int AE = BM * BK / 256;  // K* elements each thread loads per K step
-    constexpr int AQ = AE / 4;         // ... as float4s
+    constexpr int BN = 128, BK = 8, TM = BM / 16, PAD = 4;
+    constexpr int LPR = BK / 4;              // lanes per row segment (float4 each)
+    constexpr int RPP = 256 / LPR;           // rows covered by one pass of the CTA's threads
+    constexpr int AQ = (BM + RPP - 1) / RPP; // K* float4s per thread per K step (some idle if BM < RPP)
+    constexpr int BQ = BN / RPP;             // L^-1 float4s per thread per K step
     __shared__ __align__(16) float As[2][BK][BM + PAD];
     __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     __shared__ float red_v[BM];
     __shared__ int64_t red_i[BM];
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
     const int64_t cb = bx * (int64_t)BM;
-    const int ra = tid / (BK / AE), ka = (tid % (BK / AE)) * AE;  // K* loader: candidate, first k
-    const int rb = tid / 4, kb = (tid % 4) * 4;                    // L^-1 loader: row, first k
-    const bool a_ok = cb + ra < C;
-    const float *arow = Kst + (cb + ra) * n_pad + ka;
-    float4 pa[AQ], pb;
+    const int lr = tid / LPR, lk = (tid % LPR) * 4;  // loader: row within a pass, first k
+    float4 pa[AQ], pb[BQ];
     auto fetch = [&](int k0, int i0) {
 #pragma unroll
-        for (int q = 0; q < AQ; ++q)
-            pa[q] = a_ok ? *reinterpret_cast<const float4 *>(arow + k0 + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-        pb = *reinterpret_cast<const float4 *>(Linv + (int64_t)(i0 + rb) * n_pad + k0 + kb);
+        for (int q = 0; q < AQ; ++q) {
+            const int64_t c = cb + lr + q * RPP;
+            pa[q] = c < C && (BM >= RPP || lr + q * RPP < BM) ? *reinterpret_cast<const float4 *>(Kst + c * n_pad + k0 + lk)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < BQ; ++q) {
+            const int i = i0 + lr + q * RPP;
+            pb[q] = i < n_pad ? *reinterpret_cast<const float4 *>(Linv + (int64_t)i * n_pad + k0 + lk)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
     auto stash = [&](int buf) {
 #pragma unroll
         for (int q = 0; q < AQ; ++q) {
-            As[buf][ka + 4 * q + 0][ra] = pa[q].x;
-            As[buf][ka + 4 * q + 1][ra] = pa[q].y;
-            As[buf][ka + 4 * q + 2][ra] = pa[q].z;
-            As[buf][ka + 4 * q + 3][ra] = pa[q].w;
+            const int r = lr + q * RPP;
+            if (BM < RPP && r >= BM) break;
+            As[buf][lk + 0][r] = pa[q].x;
+            As[buf][lk + 1][r] = pa[q].y;
+            As[buf][lk + 2][r] = pa[q].z;
+            As[buf][lk + 3][r] = pa[q].w;
         }
-        Bs[buf][kb + 0][rb] = pb.x;
-        Bs[buf][kb + 1][rb] = pb.y;
-        Bs[buf][kb + 2][rb] = pb.z;
-        Bs[buf][kb + 3][rb] = pb.w;
+#pragma unroll
+        for (int q = 0; q < BQ; ++q) {
+            const int r = lr + q * RPP;
+            Bs[buf][lk + 0][r] = pb[q].x;
+            Bs[buf][lk + 1][r] = pb[q].y;
+            Bs[buf][lk + 2][r] = pb[q].z;
+            Bs[buf][lk + 3][r] = pb[q].w;
+        }
     };
     float sig2[TM];
 #pragma unroll
     for (int u = 0; u < TM; ++u) sig2[u] = 0.f;
     int buf = 0;
-    for (int i0 = 0; i0 < n_pad; i0 += BN) {
-        float acc[TM][4];
+    for (int i0 = 0, q = 0; i0 < n_pad; i0 += BN, ++q) {
+        float acc[TM][8];
 #pragma unroll
         for (int u = 0; u < TM; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        const int kend = i0 + BN;
-        fetch(0, i0);
+            for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+        const int ksteps = (min(i0 + BN, n_pad) + BK - 1) / BK;
+        const bool down = (q & 1) != 0;
+        fetch(down ? (ksteps - 1) * BK : 0, i0);
         stash(buf);
         __syncthreads();
-        for (int k0 = 0; k0 < kend; k0 += BK) {
-            const bool more = k0 + BK < kend;
-            if (more) fetch(k0 + BK, i0);
+        for (int s = 0; s < ksteps; ++s) {
+            const bool more = s + 1 < ksteps;
+            if (more) fetch((down ? ksteps - 2 - s : s + 1) * BK, i0);
 #pragma unroll
-            for (int t = 0; t < BK; ++t) {
-                float a[TM];
+            for (int t0 = 0; t0 < BK; ++t0) {
+                const int t = down ? BK - 1 - t0 : t0;  // K fully descending on those chunks
+                float a[TM], b[8];
 #pragma unroll
-                for (int q = 0; q < TM / 4; ++q) {
-                    const float4 f = *reinterpret_cast<const float4 *>(&As[buf][t][ty * TM + 4 * q]);
-                    a[4 * q] = f.x;
-                    a[4 * q + 1] = f.y;
-                    a[4 * q + 2] = f.z;
-                    a[4 * q + 3] = f.w;
+                for (int g = 0; g < TM / 4; ++g) {
+                    const float4 f = *reinterpret_cast<const float4 *>(&As[buf][t][ty * TM + 4 * g]);
+                    a[4 * g] = f.x;
+                    a[4 * g + 1] = f.y;
+                    a[4 * g + 2] = f.z;
+                    a[4 * g + 3] = f.w;
                 }
-                const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][t][tx * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][t][tx * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][t][64 + tx * 4]);
+                b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+                b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
-                for (int u = 0; u < TM; ++u) {
-                    acc[u][0] = fmaf(a[u], b.x, acc[u][0]);
-                    acc[u][1] = fmaf(a[u], b.y, acc[u][1]);
-                    acc[u][2] = fmaf(a[u], b.z, acc[u][2]);
-                    acc[u][3] = fmaf(a[u], b.w, acc[u][3]);
-                }
+                for (int u = 0; u < TM; ++u)
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
             }
             if (more) stash(buf ^ 1);
             __syncthreads();
@@ -387,7 +408,7 @@ __device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, in
 #pragma unroll
         for (int u = 0; u < TM; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) sig2[u] = fmaf(acc[u][v], acc[u][v], sig2[u]);
+            for (int v = 0; v < 8; ++v) sig2[u] = fmaf(acc[u][v], acc[u][v], sig2[u]);
     }
 #pragma unroll
     for (int u = 0; u < TM; ++u)

@@ -120,6 +120,12 @@ static int score_simt(gpbo_ctx *ctx, const gp_model *m, const float *Xc, int64_t
     const int64_t per_cand = (int64_t)n_pad * sizeof(T);
     const int64_t budget = std::max<int64_t>(ctx->ws_limit / 2, 64 * per_cand);
     int64_t C = std::min<int64_t>(M, std::max<int64_t>(64, budget / per_cand / 64 * 64));
+    if constexpr (sizeof(T) == 4) {
+        // whole waves of the FP32 variance kernel (two CTAs of VAR_BM32 candidates per SM), so
+        // that no chunk ends on a partly filled wave
+        const int64_t wave = (int64_t)2 * ctx->sm_count * VAR_BM32;
+        if (C < M && C >= wave) C = C / wave * wave;
+    }
     const int64_t nchunks = cdiv64(M, C);
     const int64_t parts_per_chunk = cdiv64(C, 64);
     const int64_t np = parts_per_chunk * nchunks;

@@ -12,6 +12,8 @@
 #include "fit_kernels.cuh"
 #include "score_kernels.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -48,6 +50,13 @@ struct BatchPlan {
     int64_t *best_idx = nullptr;
     float *xnext = nullptr;
     GemmProb *gemm_dev = nullptr;
+    // tensor-core trailing updates (problems with n_pad >= CHOL_TC_UPDATE_MIN_NPAD): every such
+    // problem's 7 BF16 slices of a panel in one arena, one pair of tensor maps over it
+    CholTcProb *tc_probs = nullptr;
+    std::vector<CholTcProb> tc_host;
+    void *tc_slices = nullptr;
+    int *tc_exps = nullptr;
+    alignas(64) unsigned char tc_maps[2][128];
     std::vector<int> lvl_first, lvl_count;
     std::vector<int2> lvl_mm;
     int64_t sum_vec = 0;
@@ -125,6 +134,7 @@ __global__ void __launch_bounds__(256) b_chol_update(const BProb *P, double *L, 
     const int T = p.nblk - kb - 1;
     const int64_t tiles = part == 1 ? T : (int64_t)T * (T - 1) / 2;
     if (T <= 0 || (int64_t)blockIdx.x >= tiles) return;
+    if (part == 2 && chol_tc_step(p.n_pad, p.nblk, kb)) return;  // on the tensor cores instead
     k_chol_update_body(L + p.off_sq, p.n_pad, kb, p.nblk, blockIdx.x, 0, part);
 }
 
@@ -353,6 +363,34 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
     GPBO_TRY(arena(pl, &pl->best_idx, G));
     GPBO_TRY(arena(pl, &pl->xnext, (int64_t)G * GPBO_MAX_D));
     GPBO_CUDA_TRY(cudaMemcpy(pl->lsinv, lsinv.data(), sizeof(double) * lsinv.size(), cudaMemcpyHostToDevice));
+    // the tensor-core updates' slice arena (the single-problem path's rule, per problem)
+    {
+        int64_t rows = 0, nexp = 0;
+        pl->tc_host.assign(G, CholTcProb{});
+        for (int g = 0; g < G; ++g) {
+            const BProb &p = pl->probs[g];
+            CholTcProb &t = pl->tc_host[g];
+            t.n_pad = p.n_pad;
+            t.nblk = p.nblk;
+            if (p.n_pad < CHOL_TC_UPDATE_MIN_NPAD) continue;
+            t.row_off = rows;
+            rows += (int64_t)chol_tc_slice_bytes(p.n_pad) / (2 * NB);
+            t.exps = (int *)(intptr_t)nexp;  // offset for now
+            nexp += p.n_pad;
+        }
+        if (rows > 0) {
+            GPBO_TRY(arena(pl, (__nv_bfloat16 **)&pl->tc_slices, rows * NB));
+            GPBO_TRY(arena(pl, &pl->tc_exps, nexp));
+            GPBO_TRY(arena(pl, &pl->tc_probs, G));
+            for (int g = 0; g < G; ++g) {
+                CholTcProb &t = pl->tc_host[g];
+                t.A = pl->L + pl->probs[g].off_sq;
+                t.exps = t.n_pad >= CHOL_TC_UPDATE_MIN_NPAD ? pl->tc_exps + (intptr_t)t.exps : nullptr;
+            }
+            GPBO_CUDA_TRY(cudaMemcpy(pl->tc_probs, pl->tc_host.data(), sizeof(CholTcProb) * G, cudaMemcpyHostToDevice));
+            GPBO_TRY(chol_tc_arena_maps(pl->tc_slices, rows, pl->tc_maps[0], pl->tc_maps[1]));
+        }
+    }
     // merged triangular-inverse plan: level l gathers every problem's runs of 2^l blocks
     std::vector<GemmProb> all;
     for (int run = 1; run < pl->max_nblk; run *= 2) {
@@ -490,6 +528,19 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
         if (T > 1) {
+            // problems with a tensor-core update at this step (the single-problem rule), then
+            // the FP64 update of the others
+            int max_rows = 0;
+            int64_t max_tiles = 0;
+            if (pl->tc_probs)
+                for (int g = 0; g < G; ++g) {
+                    const CholTcProb &t = pl->tc_host[g];
+                    if (!chol_tc_step(t.n_pad, t.nblk, kb)) continue;
+                    max_rows = std::max(max_rows, t.n_pad - (kb + 2) * NB);
+                    max_tiles = std::max(max_tiles, chol_tc_tiles(t.nblk, kb));
+                }
+            GPBO_TRY(chol_tc_update_batched(ctx, st, pl->tc_probs, G, kb, max_rows, max_tiles, pl->tc_slices,
+                                            pl->tc_maps[0], pl->tc_maps[1]));
             b_chol_update<<<dim3((unsigned)((int64_t)T * (T - 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb, 2);
             GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }

@@ -162,9 +162,11 @@ static int alloc_model(gp_model *m)
     else GPBO_TRY(dalloc(&m->Linv32, sq));
     if (m->prec == GPBO_PREC_F16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 2));
     if (m->prec == GPBO_PREC_BF16) GPBO_CUDA_TRY(cudaMalloc(&m->Linv16, sq * 4));  // hi then lo
-    if (m->n_pad >= CHOL_TC_MIN_NPAD) {
+    if (m->n_pad >= CHOL_TC_UPDATE_MIN_NPAD) {
         GPBO_CUDA_TRY(cudaMalloc(&m->cslices, chol_tc_slice_bytes(m->n_pad)));
         GPBO_TRY(dalloc(&m->cexps, m->n_pad));
+    }
+    if (m->n_pad >= CHOL_TC_MIN_NPAD) {
         GPBO_TRY(dalloc(&m->xmax, 1));
     }
     if ((m->prec == GPBO_PREC_BF16 || m->prec == GPBO_PREC_F16) && m->d <= 32) {

@@ -56,11 +56,12 @@ struct Shared {
 
 using namespace tcx;
 
-__global__ void __launch_bounds__(256) k_chol_split(const double *__restrict__ A, int n_pad, int kb, int r0,
-                                                    __nv_bfloat16 *__restrict__ slices, int *__restrict__ exps)
+// Rows r0 .. n_pad - 1 of panel kb of A: one warp per row (warp index w = r - r0).
+__device__ __forceinline__ void chol_split_row(const double *__restrict__ A, int n_pad, int kb, int r0, int w,
+                                               __nv_bfloat16 *__restrict__ slices, int *__restrict__ exps)
 {
-    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    const int r = r0 + warp;
+    const int lane = threadIdx.x & 31;
+    const int r = r0 + w;
     if (r >= n_pad) return;
     const double *row = A + (int64_t)r * n_pad + (int64_t)kb * NB;
     const double2 v = *reinterpret_cast<const double2 *>(row + 2 * lane);
@@ -78,6 +79,22 @@ __global__ void __launch_bounds__(256) k_chol_split(const double *__restrict__ A
     if (lane == 0) exps[r] = e;
 }
 
+__global__ void __launch_bounds__(256) k_chol_split(const double *__restrict__ A, int n_pad, int kb, int r0,
+                                                    __nv_bfloat16 *__restrict__ slices, int *__restrict__ exps)
+{
+    chol_split_row(A, n_pad, kb, r0, (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), slices, exps);
+}
+
+// The batched form: problem blockIdx.y, its slices at row row_off of the arena.
+__global__ void __launch_bounds__(256) k_chol_split_batched(const CholTcProb *__restrict__ probs, int kb,
+                                                            __nv_bfloat16 *__restrict__ arena)
+{
+    const CholTcProb p = probs[blockIdx.y];
+    if (!chol_tc_step(p.n_pad, p.nblk, kb)) return;
+    chol_split_row(p.A, p.n_pad, kb, (kb + 2) * NB, (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5),
+                   arena + p.row_off * BK, p.exps);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile(
@@ -89,10 +106,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 }
 
 struct Params {
-    double *A;
-    const int *exps;
+    CholTcProb one;            // the problem of a single launch
+    const CholTcProb *probs;   // or, batched: problem blockIdx.y (device)
     unsigned *status;
-    int n_pad, nblk, b0;  // b0 = kb + 2: first block row / column of the update
+    int kb;                    // step: block rows / columns kb + 2 .. are updated by panel kb
     uint32_t idesc;
 };
 
@@ -119,9 +136,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned char *sb = tiles + (size_t)SLICES * A_BYTES;      // SLICES x B_BYTES
     Shared *sh = (Shared *)(sb + (size_t)SLICES * B_BYTES);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const CholTcProb pr = P.probs ? P.probs[blockIdx.y] : P.one;
+    // a problem without a tensor-core update at this step, or a tile beyond its count, leaves
+    // before any barrier or tensor memory is touched
+    if (!chol_tc_step(pr.n_pad, pr.nblk, P.kb) || (int64_t)blockIdx.x >= chol_tc_tiles(pr.nblk, P.kb)) return;
+    const int n_pad = pr.n_pad, b0 = P.kb + 2;
     int i2, jb;
-    tile_coords(blockIdx.x, P.b0, P.nblk, i2, jb);
-    const int row0 = (P.b0 + 2 * i2) * NB;  // first row of the strip
+    tile_coords(blockIdx.x, b0, pr.nblk, i2, jb);
+    const int row0 = (b0 + 2 * i2) * NB;  // first row of the strip
     const int col0 = jb * NB;
 
     if (threadIdx.x == 0) {
@@ -131,8 +153,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < BM; i += THREADS) sh->er[i] = row0 + i < P.n_pad ? P.exps[row0 + i] : 0;
-    for (int i = threadIdx.x; i < BN; i += THREADS) sh->ec[i] = P.exps[col0 + i];
+    for (int i = threadIdx.x; i < BM; i += THREADS) sh->er[i] = row0 + i < n_pad ? pr.exps[row0 + i] : 0;
+    for (int i = threadIdx.x; i < BN; i += THREADS) sh->ec[i] = pr.exps[col0 + i];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
                      "r"(TMEM_COLS)
@@ -151,8 +173,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_b) : "memory");
         mbar_arrive_expect_tx(&sh->full, SLICES * (A_BYTES + B_BYTES));
         for (int s = 0; s < SLICES; ++s) {
-            tma_load_2d(sa + (size_t)s * A_BYTES, &map_a, 0, s * P.n_pad + row0, &sh->full);
-            tma_load_2d(sb + (size_t)s * B_BYTES, &map_b, 0, s * P.n_pad + col0, &sh->full);
+            const int base = (int)(pr.row_off + (int64_t)s * n_pad);
+            tma_load_2d(sa + (size_t)s * A_BYTES, &map_a, 0, base + row0, &sh->full);
+            tma_load_2d(sb + (size_t)s * B_BYTES, &map_b, 0, base + col0, &sh->full);
         }
         if (mbar_wait(&sh->full, 0, abort_flag, P.status)) {
             tc_fence_after();
@@ -190,12 +213,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = quad * 32 + lane;
         const int r = row0 + row;
         const int ib = r / NB;
-        const bool live = r < P.n_pad && ib >= jb;
+        const bool live = r < n_pad && ib >= jb;
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16);
         // this thread's 32 values of A, loaded while the copies and MMAs are in flight
         double2 pre[2][8];
         {
-            const double *src = P.A + (int64_t)r * P.n_pad + col0 + half * 32;
+            const double *src = pr.A + (int64_t)r * n_pad + col0 + half * 32;
 #pragma unroll
             for (int g = 0; g < 2; ++g)
 #pragma unroll
@@ -230,7 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int j = 0; j < 16; ++j) lo[j] = lo[j] * 256 + __float2int_rn(__uint_as_float(v[j]));
                 }
                 if (live) {
-                    double *dst = P.A + (int64_t)r * P.n_pad + col0 + c0;
+                    double *dst = pr.A + (int64_t)r * n_pad + col0 + c0;
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         double2 a = pre[g][j / 2];
@@ -269,14 +292,6 @@ int chol_tc_maps(const gp_model *m, void *map_a, void *map_b)
     return GPBO_OK;
 }
 
-int64_t chol_tc_tiles(int nblk, int kb)
-{
-    const int T2 = nblk - (kb + 2);
-    int64_t t = 0;
-    for (int i2 = 0; 2 * i2 < T2; ++i2) t += std::min(2 * i2 + 2, T2);
-    return t;
-}
-
 // Split panel kb (rows of block rows kb+2 ..) and update block columns kb+2 .. on stream st.
 int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b)
 {
@@ -288,15 +303,47 @@ int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const vo
         m->L, n_pad, kb, r0, (__nv_bfloat16 *)m->cslices, m->cexps);
     GPBO_LAUNCH_CHECK(ctx);
     ctc::Params P;
-    P.A = m->L;
-    P.exps = m->cexps;
+    P.one.A = m->L;
+    P.one.exps = m->cexps;
+    P.one.n_pad = n_pad;
+    P.one.nblk = nblk;
+    P.one.row_off = 0;
+    P.probs = nullptr;
     P.status = ctx->dev_status;
-    P.n_pad = n_pad;
-    P.nblk = nblk;
-    P.b0 = kb + 2;
+    P.kb = kb;
     P.idesc = tcx::idesc_f16(1u, ctc::BN, ctc::BM);
     const int64_t tiles = chol_tc_tiles(nblk, kb);
     ctc::k_chol_update_tc<<<(unsigned)tiles, ctc::THREADS, ctc::SMEM_BYTES, st>>>(
+        *(const CUtensorMap *)map_a, *(const CUtensorMap *)map_b, P);
+    GPBO_LAUNCH_CHECK(ctx);
+    return GPBO_OK;
+}
+
+int chol_tc_arena_maps(const void *slices, int64_t rows, void *map_a, void *map_b)
+{
+    GPBO_TRY(encode_2d_box((CUtensorMap *)map_a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, slices, (uint64_t)rows, ctc::BK,
+                           ctc::BM, ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
+    GPBO_TRY(encode_2d_box((CUtensorMap *)map_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, slices, (uint64_t)rows, ctc::BK,
+                           ctc::BN, ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
+    return GPBO_OK;
+}
+
+// Step kb of every problem that takes a tensor-core update there: split its panel kb, then
+// update its block columns kb + 2 .. (one launch each, blockIdx.y = problem).
+int chol_tc_update_batched(gpbo_ctx *ctx, cudaStream_t st, const CholTcProb *probs, int G, int kb, int max_rows,
+                           int64_t max_tiles, void *slices, const void *map_a, const void *map_b)
+{
+    if (max_rows <= 0 || max_tiles <= 0) return GPBO_OK;
+    GPBO_TRY(ensure_smem((const void *)ctc::k_chol_update_tc, ctx->device, (int)ctc::SMEM_BYTES));
+    ctc::k_chol_split_batched<<<dim3((unsigned)cdiv64((int64_t)max_rows * 32, 256), G), 256, 0, st>>>(
+        probs, kb, (__nv_bfloat16 *)slices);
+    GPBO_LAUNCH_CHECK(ctx);
+    ctc::Params P = {};
+    P.probs = probs;
+    P.status = ctx->dev_status;
+    P.kb = kb;
+    P.idesc = tcx::idesc_f16(1u, ctc::BN, ctc::BM);
+    ctc::k_chol_update_tc<<<dim3((unsigned)max_tiles, G), ctc::THREADS, ctc::SMEM_BYTES, st>>>(
         *(const CUtensorMap *)map_a, *(const CUtensorMap *)map_b, P);
     GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;

@@ -125,9 +125,6 @@ constexpr int DIAG_THREADS = 1024;
 // step): the update is FP64-bound, not wave-bound.
 constexpr int SLAB_BELOW = 6;
 constexpr int SLAB_ROWS = 4;
-// Models with the tensor-core update use it while at least CHOL_TC_MIN_T block columns remain
-// after the lookahead column; the last few small updates stay on the FP64 pipe.
-constexpr int CHOL_TC_MIN_T = 4;
 // Warps per CTA of the diagonal-block inverse (one column per warp, NB / INV_WARPS CTAs).  Two
 // measured best at n = 4096 (Cholesky 8.54 ms against 8.68 with four and 9.04 with one): the
 // inverse overlaps the tensor-core updates of the main stream, and narrower CTAs share fewer SMs'
@@ -499,7 +496,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            if (tc && T - 1 >= CHOL_TC_MIN_T) {
+            if (tc && chol_tc_step(n_pad, nblk, kb)) {
                 GPBO_TRY(chol_tc_update(ctx, m, kb, st, tc_maps[0], tc_maps[1]));
             } else {
                 if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)

@@ -110,7 +110,6 @@ __device__ __forceinline__ void chol_diag_factor_smem(double (*a)[NB + 1], uint1
     for (int j = 0; j + 1 < NB; ++j) {
         const int m = NB - 1 - j;           // rows below j
         const int nF = TRI - coff(j + 2);   // triangle, columns >= j+2
-        const int nT = nF + (m - 1);        // + column j+1 below its diagonal
         if (tid == 0) {
             double p = fma(-a[j + 1][j], a[j + 1][j], a[j + 1][j + 1]);
             if (!(p > 0.0)) {

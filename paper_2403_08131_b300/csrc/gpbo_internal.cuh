@@ -125,7 +125,7 @@ struct gp_model {
     void *Linv16 = nullptr;     // F16: L^-1 rounded; BF16: hi = bf16(L^-1) then lo = bf16(L^-1 - hi)
     void *Zsplit = nullptr;     // 16-bit models, d <= 32: n_pad x 128 FP16 [hi | lo | hi | 0] of (x - 1/2) / l
     float *nb32 = nullptr;      // 16-bit models: |(x_i - 1/2) / l|^2
-    void *cslices = nullptr;    // n_pad >= CHOL_TC_MIN_NPAD: 7 BF16 slices of a Cholesky panel, slice-major
+    void *cslices = nullptr;    // n_pad >= CHOL_TC_UPDATE_MIN_NPAD: 7 BF16 slices of a Cholesky panel, slice-major
     int *cexps = nullptr;       // their per-row exponents
     unsigned long long *xmax = nullptr;  // n_pad >= CHOL_TC_MIN_NPAD: largest |x / l| as magnitude bits
 };
@@ -171,13 +171,45 @@ int tc_variance_ei(gpbo_ctx *ctx, const gp_model *m, const void *Kstar, int64_t 
 int xkern_tc_prepare(gpbo_ctx *ctx, gp_model *m);
 
 // chol_tc.cu: trailing updates of the Cholesky factorisation on the tensor cores at FP64
-// accuracy (exact 8-bit slice products), for models with n_pad >= CHOL_TC_MIN_NPAD.
+// accuracy (exact 8-bit slice products).  Models with n_pad >= CHOL_TC_MIN_NPAD also compute
+// their kernel matrix distances in integers and the large levels of L^-1 on the tensor cores;
+// models with n_pad >= CHOL_TC_UPDATE_MIN_NPAD take the tensor-core update at every step that
+// leaves at least CHOL_TC_MIN_T block columns after the lookahead column (the last few small
+// updates stay on the FP64 pipe).  The batched step applies the same rule per problem.
 constexpr int CHOL_TC_MIN_NPAD = 1536;
+constexpr int CHOL_TC_UPDATE_MIN_NPAD = 384;
+constexpr int CHOL_TC_MIN_T = 4;
+__host__ __device__ inline bool chol_tc_step(int n_pad, int nblk, int kb)
+{
+    return n_pad >= CHOL_TC_UPDATE_MIN_NPAD && nblk - kb - 2 >= CHOL_TC_MIN_T;
+}
+// One problem of a tensor-core update: its factor (n_pad x n_pad), its per-row exponents, and the
+// first row of its slices in the slice arena (7 n_pad rows of 64 BF16 values, slice-major).
+struct CholTcProb {
+    double *A;
+    int *exps;
+    int n_pad, nblk;
+    int64_t row_off;
+};
 bool chol_tc_enabled(const gp_model *m);
 size_t chol_tc_slice_bytes(int n_pad);
 int chol_tc_maps(const gp_model *m, void *map_a, void *map_b);  // two 128-byte CUtensorMap
-int64_t chol_tc_tiles(int nblk, int kb);
+// Output tiles (128 x 64) of step kb's tensor-core update: strips of two block rows from block
+// row kb + 2 on, each meeting the block columns kb + 2 .. up to its own.
+__host__ __device__ inline int64_t chol_tc_tiles(int nblk, int kb)
+{
+    const int T2 = nblk - (kb + 2);
+    int64_t t = 0;
+    for (int i2 = 0; 2 * i2 < T2; ++i2) t += 2 * i2 + 2 < T2 ? 2 * i2 + 2 : T2;
+    return t;
+}
 int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b);
+// The batched form: tensor maps over a slice arena of `rows` rows, and step kb for every problem
+// of probs (device, G entries) with chol_tc_step true (blockIdx.y = problem; max_rows and
+// max_tiles bound the problems' rows below block row kb + 2 and their tiles).
+int chol_tc_arena_maps(const void *slices, int64_t rows, void *map_a, void *map_b);
+int chol_tc_update_batched(gpbo_ctx *ctx, cudaStream_t st, const CholTcProb *probs, int G, int kb, int max_rows,
+                           int64_t max_tiles, void *slices, const void *map_a, const void *map_b);
 
 // kinv_tc.cu: lower 64 x 64 tiles of K^-1 = L^-T L^-1 on the tensor cores at FP64 accuracy,
 // from Linv (n_pad x n_pad FP64; n_pad a multiple of 128).  slices: kinv_tc_slice_bytes(n_pad)

@@ -127,15 +127,20 @@ __global__ void __launch_bounds__(128) b_chol_panel(const BProb *P, double *L, c
     k_chol_panel_body(L + p.off_sq, p.n_pad, kb, Dinv + p.off_dinv, blockIdx.x, 0);
 }
 
-// part 1: block column kb+1 (T tiles); part 2: block columns kb+2 .. (T(T-1)/2 tiles).
-__global__ void __launch_bounds__(256) b_chol_update(const BProb *P, double *L, int kb, int part)
+// The FP64 trailing updates in slabs of B_SLAB_ROWS rows (16 CTAs per 64 x 64 tile), as the
+// single-problem path's next-column and small updates: the same arithmetic per element as a
+// whole tile, without one CTA per tile holding a late, small step to 64^3 FP64 FMAs on one SM.
+// part 1: block column kb+1 (T tiles); part 2: block columns kb+2 .. (T(T-1)/2 tiles), except
+// problems whose step kb runs on the tensor cores.
+constexpr int B_SLAB_ROWS = 4;
+__global__ void __launch_bounds__(256) b_chol_update_slab(const BProb *P, double *L, int kb, int part)
 {
     const BProb &p = P[blockIdx.y];
     const int T = p.nblk - kb - 1;
     const int64_t tiles = part == 1 ? T : (int64_t)T * (T - 1) / 2;
-    if (T <= 0 || (int64_t)blockIdx.x >= tiles) return;
-    if (part == 2 && chol_tc_step(p.n_pad, p.nblk, kb)) return;  // on the tensor cores instead
-    k_chol_update_body(L + p.off_sq, p.n_pad, kb, p.nblk, blockIdx.x, 0, part);
+    if (T <= 0 || (int64_t)(blockIdx.x / (NB / B_SLAB_ROWS)) >= tiles) return;
+    if (part == 2 && chol_tc_step(p.n_pad, p.nblk, kb)) return;
+    k_chol_update_slab_body<B_SLAB_ROWS>(L + p.off_sq, p.n_pad, kb, blockIdx.x, part, 0);
 }
 
 __global__ void b_zero_upper(const BProb *P, double *L)
@@ -500,7 +505,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
 {
     const int G = pl->G;
     const BProb *P = pl->probs_dev;
-    const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
+    const size_t smem1 = sizeof(double) * NB * (NB + 1);
     b_standardize<<<G, 1024, 0, st>>>(P, pl->dy, pl->dys, pl->tau);
     b_scale_x<<<dim3(gb(pl->max_dn), G), 256, 0, st>>>(P, pl->dX, pl->lsinv, pl->Xs64, pl->Xs32);
     b_kmat<<<dim3(pl->max_npad / 32, pl->max_npad / 32, G), dim3(32, 8), 0, st>>>(P, pl->Xs64, pl->K);
@@ -522,7 +527,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         const int T = NBL - kb - 1;
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(s2, ev_rest, 0));
-        b_chol_update<<<dim3((unsigned)T, G), 256, smem2, s2>>>(P, pl->L, kb, 1);
+        b_chol_update_slab<<<dim3((unsigned)T * (NB / B_SLAB_ROWS), G), 256, 0, s2>>>(P, pl->L, kb, 1);
         b_chol_diag<<<dim3(1, G), 256, smem1, s2>>>(P, pl->L, pl->Dinv, kb + 1, ctx->dev_status);
         b_chol_inv<<<dim3(NB / 4, G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
         if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
@@ -541,7 +546,8 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
                 }
             GPBO_TRY(chol_tc_update_batched(ctx, st, pl->tc_probs, G, kb, max_rows, max_tiles, pl->tc_slices,
                                             pl->tc_maps[0], pl->tc_maps[1]));
-            b_chol_update<<<dim3((unsigned)((int64_t)T * (T - 1) / 2), G), 256, smem2, st>>>(P, pl->L, kb, 2);
+            b_chol_update_slab<<<dim3((unsigned)((int64_t)T * (T - 1) / 2 * (NB / B_SLAB_ROWS)), G), 256, 0, st>>>(
+                P, pl->L, kb, 2);
             GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }
     }
@@ -684,8 +690,6 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
         // capture the step once; the probe table and arenas keep their addresses from here on
         GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
         GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(double) * 2 * NB * (NB + 1))));
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(sizeof(double) * 2 * NB * (NB + 1))));
         GPBO_CUDA_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
         int st = enqueue_step(ctx, pl, pl->cap, (float)xi);

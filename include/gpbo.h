@@ -103,7 +103,9 @@ int64_t gpbo_launch_count(const gpbo_ctx *ctx);
 /* Per-phase device timing with CUDA events recorded on the context's stream around each
  * phase's kernels (phases: 0 fit, 1 cross-kernel + mean, 2 variance + EI + argmax,
  * 3 screen, 4 Cholesky trailing updates, 5 the K^-1 tiles of the likelihood gradient:
- * 2 (p + 1)(n - p) flops for row p of the lower triangle of L^-T L^-1).
+ * 2 (p + 1)(n - p) flops for row p of the lower triangle of L^-T L^-1, 6 the fit's kernel
+ * matrix and factorisation, 7 the fit's L^-1 and the solve for alpha after it; 6 and 7
+ * lie inside 0, and 4 inside 6).
  * gpbo_trace_enable(ctx, 1) clears and starts collection, 0 stops it.
  * gpbo_trace_read synchronises, then writes for each of the first nphase phases the total
  * milliseconds, the number of timed intervals, and the algorithmic flops the phase's

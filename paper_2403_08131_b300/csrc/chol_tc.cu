@@ -276,6 +276,332 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The persistent form of the update (single model).  Same slice pairs, levels and per-element
+// arithmetic as k_chol_update_tc, so the two give the same bits; what changes is the schedule
+// and the shape of the MMAs.  A tcgen05 MMA of M = 128 costs the tensor pipe about as much to
+// read its operands as a product of N = 128 takes to compute, so the 34 pairs are not issued
+// as 34 narrow products.  For each row slice s, one MMA multiplies a_s by the tile's column
+// slices t = 1 .. n_s stacked along N (n_s = min(7, 9 - s)); the product of pair (s, t) lands
+// in columns 32 (s + t - 2) .. of the accumulator, the block of level s + t, so each level's
+// pairs still sum in their own FP32 accumulator, exactly.  Per K step of 16: 7 MMAs of
+// N = 32 n_s (1088 columns in all, the 34 pairs and nothing else).  The first MMA of a tile
+// (s = 1, first K step) overwrites the accumulator: it also covers level 9's block, with a
+// zero block kept after each stage's seventh slice as its B rows.
+// One CTA per SM walks work items: an item is up to PCH tiles of 128 rows x 32 columns in one
+// strip, whose 7 row slices (112 KiB) are loaded once for the item while the column slices
+// (28 KiB per tile) stream through PSTAGES stages.  Two accumulators of 8 levels x 32 columns
+// fill the 512 TMEM columns: the epilogue of one tile overlaps the MMAs of the next.
+//   warp 0       TMA producer
+//   warp 1       allocates 512 TMEM columns; one lane issues the 28 MMAs of each tile and
+//                commits them to the stage, accumulator and item barriers
+//   warps 2..17  epilogue: TMEM lane quadrant warp % 4, columns 8 ((warp - 2) / 4) .. of the tile
+// The launch leaves CHAIN_SMS SMs free for the 64 x 64 kernels of the factorisation's chain.
+constexpr int PBN = 32;                         // output columns per tile
+constexpr int PCH = 8;                          // tiles per work item, at most
+constexpr int PSTAGES = 3;
+constexpr int CHAIN_SMS = 8;                    // SMs left to the factorisation's chain
+constexpr int PB_SLICE = PBN * BK * 2;          // one slice of a tile's column rows (4 KiB)
+constexpr int PB_STAGE = (SLICES + 1) * PB_SLICE;  // 7 slices and the zero block
+constexpr int PA_BYTES = SLICES * A_BYTES;
+constexpr int PEPI_WARPS = 16;
+constexpr int PCOLS = PBN / (PEPI_WARPS / 4);   // columns per epilogue thread
+static_assert(PCOLS == 8, "the epilogue reads 8 column exponents as two int4");
+constexpr int PTHREADS = 32 * (2 + PEPI_WARPS);
+constexpr int ACC_COLS = (LEVEL_MAX - 1) * PBN; // one accumulator: levels 2 .. 9
+static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
+constexpr size_t PSMEM_BYTES = 1024 + (size_t)PA_BYTES + (size_t)PSTAGES * PB_STAGE + 256;
+
+struct PShared {
+    uint64_t a_full;      // the item's row slices have landed
+    uint64_t a_empty;     // the item's MMAs are complete (the row-slice buffer may be refilled)
+    uint64_t b_full[PSTAGES], b_empty[PSTAGES];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+static_assert(sizeof(PShared) <= 256, "barrier area");
+
+struct PItem {
+    int row0;   // first row of the strip
+    int tile0;  // first tile, in units of PBN columns
+    int nt;     // tiles
+};
+
+// Work items of one step: strips of two block rows from block row b0 (the last may hold one),
+// strip i2 meeting block columns c0 .. min(b0 + 2 i2 + 1, nblk - 1), each cut into items of at
+// most PCH tiles; the strips that meet the most columns come first.
+__host__ __device__ inline int p_strip_tiles(int i2, int b0, int c0, int nblk)
+{
+    const int last = b0 + 2 * i2 + 1 < nblk - 1 ? b0 + 2 * i2 + 1 : nblk - 1;
+    return (NB / PBN) * (last - c0 + 1);
+}
+__host__ __device__ inline int p_items(int b0, int c0, int nblk)
+{
+    int n = 0;
+    for (int i2 = 0; b0 + 2 * i2 < nblk; ++i2) n += (p_strip_tiles(i2, b0, c0, nblk) + PCH - 1) / PCH;
+    return n;
+}
+__device__ inline bool p_item(int it, int b0, int c0, int nblk, PItem &out)
+{
+    const int S = (nblk - b0 + 1) / 2;
+    for (int i2 = S - 1; i2 >= 0; --i2) {
+        const int nt = p_strip_tiles(i2, b0, c0, nblk), ch = (nt + PCH - 1) / PCH;
+        if (it < ch) {
+            out.row0 = (b0 + 2 * i2) * NB;
+            out.tile0 = (NB / PBN) * c0 + it * PCH;
+            out.nt = nt - it * PCH < PCH ? nt - it * PCH : PCH;
+            return true;
+        }
+        it -= ch;
+    }
+    return false;
+}
+
+struct PParams {
+    double *A;
+    const int *exps;
+    unsigned *status;
+    int n_pad, nblk, kb;
+    int b0, c0;        // first block row / block column updated
+    int items;
+};
+
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void pin8(uint32_t *r)
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+
+// An exact integer |x| <= 2^22 held in FP32, as an int: x + 1.5 2^23 lies in [2^23, 2^24], where
+// FP32 steps by 1, so the sum is exact and its low bits are x + 2^22 (one FP32 add and one
+// integer subtract instead of a conversion).  Levels 2 .. 5 stay within this range: at most
+// 4 pairs x 64 products of |a_s a_t| <= 2^14.
+__device__ __forceinline__ int small_int_of(uint32_t bits)
+{
+    return (int)(__float_as_uint(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000u);
+}
+
+__global__ void __launch_bounds__(PTHREADS, 1)
+    k_chol_update_tcp(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, PParams P)
+{
+    extern __shared__ unsigned char smraw[];
+    unsigned char *sa = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);  // SLICES x A_BYTES
+    unsigned char *sb = sa + PA_BYTES;                                                      // PSTAGES x PB_STAGE
+    PShared *sh = (PShared *)(sb + (size_t)PSTAGES * PB_STAGE);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int n_pad = P.n_pad;
+
+    // the zero block after each stage's seventh slice (never written by the copies)
+    for (int i = threadIdx.x; i < PSTAGES * PB_SLICE / 16; i += PTHREADS) {
+        const int st = i / (PB_SLICE / 16), o = i % (PB_SLICE / 16);
+        *reinterpret_cast<uint4 *>(sb + (size_t)st * PB_STAGE + (size_t)SLICES * PB_SLICE + (size_t)o * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        mbar_init(&sh->a_full, 1);
+        mbar_init(&sh->a_empty, 1);
+        for (int s = 0; s < PSTAGES; ++s) {
+            mbar_init(&sh->b_full[s], 1);
+            mbar_init(&sh->b_empty[s], 1);
+        }
+        for (int u = 0; u < 2; ++u) {
+            mbar_init(&sh->acc_full[u], 1);
+            mbar_init(&sh->acc_empty[u], PEPI_WARPS);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort_flag = &sh->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_a) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_b) : "memory");
+            int a_armed = 0, b_armed = 0;
+            bool ok = true;
+            for (int it = blockIdx.x; ok && it < P.items; it += gridDim.x) {
+                PItem w;
+                p_item(it, P.b0, P.c0, P.nblk, w);
+                // the row-slice buffer is free once the previous item's MMAs are complete
+                if (a_armed > 0 && !mbar_wait(&sh->a_empty, (a_armed - 1) & 1, abort_flag, P.status)) break;
+                mbar_arrive_expect_tx(&sh->a_full, PA_BYTES);
+                ++a_armed;
+                for (int s = 0; s < SLICES; ++s)
+                    tma_load_2d(sa + (size_t)s * A_BYTES, &map_a, 0, s * n_pad + w.row0, &sh->a_full);
+                for (int t = 0; t < w.nt; ++t) {
+                    const int st = b_armed % PSTAGES, use = b_armed / PSTAGES;
+                    if (use > 0 && !mbar_wait(&sh->b_empty[st], (use - 1) & 1, abort_flag, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sh->b_full[st], SLICES * PB_SLICE);
+                    ++b_armed;
+                    const int col = (w.tile0 + t) * PBN;
+                    for (int s = 0; s < SLICES; ++s)
+                        tma_load_2d(sb + (size_t)st * PB_STAGE + (size_t)s * PB_SLICE, &map_b, 0, s * n_pad + col,
+                                    &sh->b_full[st]);
+                }
+            }
+            // every copy issued has landed before the CTA may exit (a no-op unless aborted)
+            if (a_armed > 0) mbar_wait(&sh->a_full, (a_armed - 1) & 1, abort_flag, P.status, false);
+            for (int st = 0; st < PSTAGES; ++st) {
+                const int uses = (b_armed - st + PSTAGES - 1) / PSTAGES;
+                if (uses > 0) mbar_wait(&sh->b_full[st], (uses - 1) & 1, abort_flag, P.status, false);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int ia = 0, bc = 0, tcount = 0;
+            bool ok = true, issued = false;
+            for (int it = blockIdx.x; ok && it < P.items; it += gridDim.x, ++ia) {
+                PItem w;
+                p_item(it, P.b0, P.c0, P.nblk, w);
+                if (!mbar_wait(&sh->a_full, ia & 1, abort_flag, P.status)) break;
+                tc_fence_after();
+                for (int t = 0; t < w.nt; ++t, ++bc, ++tcount) {
+                    const int st = bc % PSTAGES, u = tcount & 1;
+                    if (tcount >= 2 && !mbar_wait(&sh->acc_empty[u], ((tcount >> 1) - 1) & 1, abort_flag, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait(&sh->b_full[st], (bc / PSTAGES) & 1, abort_flag, P.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d0 = tmem + (uint32_t)(u * ACC_COLS);
+                    const unsigned char *bst = sb + (size_t)st * PB_STAGE;
+#pragma unroll 1
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t bdesc = smem_desc(bst + kk * 32);
+#pragma unroll
+                        for (int s = 1; s <= SLICES; ++s) {
+                            const bool init = kk == 0 && s == 1;
+                            const int nt = init ? LEVEL_MAX - 1 : (SLICES < LEVEL_MAX - s ? SLICES : LEVEL_MAX - s);
+                            mma_f16(d0 + (uint32_t)((s - 1) * PBN), smem_desc(sa + (size_t)(s - 1) * A_BYTES + kk * 32),
+                                    bdesc, idesc_f16(1u, nt * PBN, BM), init ? 0u : 1u);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(&sh->b_empty[st]);
+                    mma_commit(&sh->acc_full[u]);
+                }
+                mma_commit(&sh->a_empty);
+            }
+            if (issued) {
+                mma_commit(&sh->drain);
+                mbar_wait(&sh->drain, 0, abort_flag, P.status, false);  // every MMA complete
+            }
+        }
+    } else {
+        // epilogue: the sums of k_chol_update_tc's fold (the same integers: the four levels of
+        // each half combined as two int32 pairs, (L_l 256 + L_l+1) 2^16 + (L_l+2 256 + L_l+3)),
+        // then the same FP64 build, for PCOLS columns of one row per thread
+        const int q = warp & 3, g = (warp - 2) >> 2;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        int tcount = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; ok && it < P.items; it += gridDim.x) {
+            PItem w;
+            p_item(it, P.b0, P.c0, P.nblk, w);
+            const int r = w.row0 + q * 32 + lane;
+            const bool rin = r < n_pad;
+            const int er = rin ? P.exps[r] : 0;
+            for (int t = 0; t < w.nt; ++t, ++tcount) {
+                const int u = tcount & 1;
+                const int c0 = (w.tile0 + t) * PBN + PCOLS * g;
+                const bool live = rin && r / NB >= c0 / NB;
+                double *dst = P.A + (int64_t)r * n_pad + c0;
+                double2 pre[PCOLS / 2];
+#pragma unroll
+                for (int j = 0; j < PCOLS / 2; ++j)
+                    pre[j] = live ? *reinterpret_cast<const double2 *>(dst + 2 * j) : make_double2(0.0, 0.0);
+                const int4 e0 = *reinterpret_cast<const int4 *>(P.exps + c0);
+                const int4 e1 = *reinterpret_cast<const int4 *>(P.exps + c0 + 4);
+                const bool got = mbar_wait_inl(&sh->acc_full[u], (tcount >> 1) & 1, abort_flag, P.status);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tl + (uint32_t)(u * ACC_COLS + PCOLS * g);
+                long long hi[PCOLS], lo[PCOLS];
+                {
+                    uint32_t v[4][PCOLS];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_ld8_nw(ta + (uint32_t)(k * PBN), v[k]);  // levels 2..5
+                    tmem_wait();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pin8(v[k]);
+#pragma unroll
+                    for (int j = 0; j < PCOLS; ++j) {
+                        const int t0 = small_int_of(v[0][j]) * 256 + small_int_of(v[1][j]);
+                        const int t1 = small_int_of(v[2][j]) * 256 + small_int_of(v[3][j]);
+                        hi[j] = (long long)t0 * 65536 + t1;
+                    }
+                }
+                {
+                    uint32_t v[4][PCOLS];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_ld8_nw(ta + (uint32_t)((4 + k) * PBN), v[k]);  // levels 6..9
+                    tmem_wait();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pin8(v[k]);
+                    // this warp is done with the accumulator
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->acc_empty[u]);
+#pragma unroll
+                    for (int j = 0; j < PCOLS; ++j) {
+                        const int t0 =
+                            __float2int_rn(__uint_as_float(v[0][j])) * 256 + __float2int_rn(__uint_as_float(v[1][j]));
+                        const int t1 =
+                            __float2int_rn(__uint_as_float(v[2][j])) * 256 + __float2int_rn(__uint_as_float(v[3][j]));
+                        lo[j] = (long long)t0 * 65536 + t1;
+                    }
+                }
+                if (live) {
+                    const int ec[PCOLS] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+#pragma unroll
+                    for (int j = 0; j < PCOLS; j += 2) {
+                        double2 a = pre[j / 2];
+                        const long long C0 = hi[j] * 65536 + (lo[j] >> 16), C1 = hi[j + 1] * 65536 + (lo[j + 1] >> 16);
+                        a.x -= scaled_to_double(C0, er + ec[j] - 54);
+                        a.y -= scaled_to_double(C1, er + ec[j + 1] - 54);
+                        *reinterpret_cast<double2 *>(dst + j) = a;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 }  // namespace ctc
 
 bool chol_tc_enabled(const gp_model *m) { return m->cslices != nullptr; }
@@ -287,33 +613,35 @@ int chol_tc_maps(const gp_model *m, void *map_a, void *map_b)
     const uint64_t rows = (uint64_t)ctc::SLICES * m->n_pad;
     GPBO_TRY(encode_2d_box((CUtensorMap *)map_a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->cslices, rows, ctc::BK, ctc::BM,
                            ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
-    GPBO_TRY(encode_2d_box((CUtensorMap *)map_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->cslices, rows, ctc::BK, ctc::BN,
+    GPBO_TRY(encode_2d_box((CUtensorMap *)map_b, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, m->cslices, rows, ctc::BK, ctc::PBN,
                            ctc::BK, CU_TENSOR_MAP_SWIZZLE_128B));
     return GPBO_OK;
 }
 
-// Split panel kb (rows of block rows kb+2 ..) and update block columns kb+2 .. on stream st.
-int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b)
+// Split panel kb (rows of block rows min(c0, kb + 2) ..), then update block columns c0 .. of the
+// rows of block rows kb + 2 .. on stream st with the persistent kernel.
+int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, int c0, cudaStream_t st, const void *map_a, const void *map_b)
 {
-    const int n_pad = m->n_pad, nblk = n_pad / NB;
-    if (kb + 2 >= nblk) return GPBO_OK;
-    GPBO_TRY(ensure_smem((const void *)ctc::k_chol_update_tc, ctx->device, (int)ctc::SMEM_BYTES));
-    const int r0 = (kb + 2) * NB, rows = n_pad - r0;
+    const int n_pad = m->n_pad, nblk = n_pad / NB, b0 = kb + 2;
+    if (b0 >= nblk) return GPBO_OK;
+    GPBO_TRY(ensure_smem((const void *)ctc::k_chol_update_tcp, ctx->device, (int)ctc::PSMEM_BYTES));
+    const int r0 = (c0 < b0 ? c0 : b0) * NB, rows = n_pad - r0;
     ctc::k_chol_split<<<(unsigned)cdiv64((int64_t)rows * 32, 256), 256, 0, st>>>(
         m->L, n_pad, kb, r0, (__nv_bfloat16 *)m->cslices, m->cexps);
     GPBO_LAUNCH_CHECK(ctx);
-    ctc::Params P;
-    P.one.A = m->L;
-    P.one.exps = m->cexps;
-    P.one.n_pad = n_pad;
-    P.one.nblk = nblk;
-    P.one.row_off = 0;
-    P.probs = nullptr;
+    ctc::PParams P;
+    P.A = m->L;
+    P.exps = m->cexps;
     P.status = ctx->dev_status;
+    P.n_pad = n_pad;
+    P.nblk = nblk;
     P.kb = kb;
-    P.idesc = tcx::idesc_f16(1u, ctc::BN, ctc::BM);
-    const int64_t tiles = chol_tc_tiles(nblk, kb);
-    ctc::k_chol_update_tc<<<(unsigned)tiles, ctc::THREADS, ctc::SMEM_BYTES, st>>>(
+    P.b0 = b0;
+    P.c0 = c0;
+    P.items = ctc::p_items(b0, c0, nblk);
+    const int sms = ctx->sm_count > 2 * ctc::CHAIN_SMS ? ctx->sm_count - ctc::CHAIN_SMS : ctx->sm_count;
+    const int grid = P.items < sms ? P.items : sms;
+    ctc::k_chol_update_tcp<<<(unsigned)grid, ctc::PTHREADS, ctc::PSMEM_BYTES, st>>>(
         *(const CUtensorMap *)map_a, *(const CUtensorMap *)map_b, P);
     GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;

@@ -175,10 +175,10 @@ __global__ void __launch_bounds__(128) k_chol_inv(const double *__restrict__ A, 
 }
 
 __global__ void __launch_bounds__(128) k_chol_panel(double *__restrict__ A, int n_pad, int kb,
-                                                    const double *__restrict__ Dinv)
+                                                    const double *__restrict__ Dinv, int boff)
 {
     pdl_wait();
-    k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y);
+    k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y, boff);
 }
 
 __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int n_pad, int kb, int nblk, int part)
@@ -438,6 +438,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     cudaStream_t st = ctx->stream;
     Lengthscales_inv ls;
     for (int k = 0; k < d; ++k) ls.inv[k] = 1.0 / m->ls[k];
+    GPBO_TRY(trace_begin(ctx, PH_FACTOR, (double)n * n * n / 3.0));
     GPBO_CUDA_TRY(cudaMemcpyAsync(m->X, X_dev, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, st));
     k_scale_x<<<blocks_for((int64_t)d * n_pad), 256, 0, st>>>(m->X, n, d, n_pad, ls, m->Xs64, m->Xs32);
     GPBO_LAUNCH_CHECK(ctx);
@@ -457,47 +458,55 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     // the factorisation works in L (k_kmat_fixed writes its lower triangle with K)
     if (!m->xmax) GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
     const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
-    // Right-looking blocked factorisation with a lookahead of one block column: the update
-    // of block column kb+1 by panel kb, the factorisation of its diagonal block, its inverse
-    // and its panel run on the high-priority side stream (the chain every step waits on)
-    // while the rest of step kb's trailing update runs on the main stream.  The two touch
-    // disjoint tiles; column kb+2 is updated by the side stream only after the main stream's
-    // step-kb update (event ev_rest).
+    // Right-looking blocked factorisation with a lookahead of one block column.  The chain that
+    // every step waits on runs on the high-priority side stream and holds only 64 x 64 blocks:
+    // the panel's first block row L_{kb+1,kb}, the update of diagonal block kb+1 by it, the
+    // factorisation of that block and its inverse.  The main stream takes the rest of each
+    // step: the panel's other block rows, the update of the rest of block column kb+1 (which
+    // the next step's first panel row waits for), then the trailing update of block columns
+    // kb+2 .. .  Each element gets the same arithmetic, in the same order, as in one launch per
+    // part; the streams only reorder independent tiles.
     cudaStream_t side = nullptr;
     GPBO_TRY(side_stream(ctx, &side));
-    cudaEvent_t ev_fork = ctx->side_ev[0], ev_panel = ctx->side_ev[1], ev_rest = ctx->side_ev[2],
-                ev_join = ctx->side_ev[3];
+    cudaEvent_t ev_fork = ctx->side_ev[0], ev_pf = ctx->side_ev[1], ev_rest = ctx->side_ev[2],
+                ev_join = ctx->side_ev[3], ev_col = ctx->side_ev[5];
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, 0, m->Dinv));
-    if (nblk > 1)
-        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((nblk - 1) * (NB / 4)), dim3(128), 0, side, m->L, n_pad, 0,
-                            m->Dinv));
-    GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
     // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
     alignas(64) unsigned char tc_maps[2][128];
     const bool tc = chol_tc_enabled(m);
     if (tc) GPBO_TRY(chol_tc_maps(m, tc_maps[0], tc_maps[1]));
     for (int kb = 0; kb + 1 < nblk; ++kb) {
-        const int T = nblk - kb - 1;
-        GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_panel, 0));  // panel kb
-        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));  // step kb-1 done with column kb+1
-        k_chol_update_slab<<<T * (NB / SLAB_ROWS), 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
+        const int T = nblk - kb - 1;  // block rows below block kb
+        // side: L_{kb+1,kb} (needs block column kb final: the main stream's step kb-1), then
+        // diagonal block kb+1 (needs the main stream's trailing update of step kb-1)
+        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_col, 0));
+        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
+        GPBO_CUDA_TRY(cudaEventRecord(ev_pf, side));
+        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));
+        k_chol_update_slab<<<NB / SLAB_ROWS, 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
         GPBO_LAUNCH_CHECK(ctx);
         GPBO_TRY(launch_pdl(ctx, k_chol_diag, dim3(1), dim3(DIAG_THREADS), smem1, side, m->L, n_pad, kb + 1, m->Dinv,
                             ctx->dev_status));
-        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1, m->Dinv));
-        if (T > 1)
-            GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3((T - 1) * (NB / 4)), dim3(128), 0, side, m->L, n_pad, kb + 1,
-                                m->Dinv));
-        GPBO_CUDA_TRY(cudaEventRecord(ev_panel, side));
+        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1,
+                            m->Dinv));
+        // main: the rest of panel kb and of block column kb+1, then block columns kb+2 ..
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_pf, 0));
+        if (T > 1) {
+            k_chol_panel<<<(T - 1) * (NB / 4), 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_chol_update_slab<<<(T - 1) * (NB / SLAB_ROWS), 256, 0, st>>>(m->L, n_pad, kb, 1, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+        }
+        GPBO_CUDA_TRY(cudaEventRecord(ev_col, st));
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
             if (tc && chol_tc_step(n_pad, nblk, kb)) {
-                GPBO_TRY(chol_tc_update(ctx, m, kb, st, tc_maps[0], tc_maps[1]));
+                GPBO_TRY(chol_tc_update(ctx, m, kb, kb + 2, st, tc_maps[0], tc_maps[1]));
             } else {
                 if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
                     k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
@@ -506,13 +515,15 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
                 GPBO_LAUNCH_CHECK(ctx);
             }
             GPBO_TRY(trace_end(ctx));
-            GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }
+        GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     k_zero_upper_blocks<<<blocks_for((int64_t)n_pad * n_pad), 256, 0, st>>>(m->L, n_pad);
     GPBO_LAUNCH_CHECK(ctx);
+    GPBO_TRY(trace_end(ctx));
+    GPBO_TRY(trace_begin(ctx, PH_INVERSE, (double)n * n * n / 3.0));
     // A pivot that was not positive is reported by the status check at the end (the factor
     // carries on with 1 in its place, so what follows stays finite): no host round trip here.
 
@@ -602,6 +613,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         }
     }
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
+    GPBO_TRY(trace_end(ctx));
     unsigned bits = 0;
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;

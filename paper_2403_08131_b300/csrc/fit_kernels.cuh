@@ -285,7 +285,9 @@ __device__ __forceinline__ void k_chol_update_slab_body(double *__restrict__ A, 
 // sum_{t <= c} a_t Dinv[c][t] (L_kk^-T is lower); thread (row ty, lane tx) takes columns tx and
 // 63 - tx in one loop of 65 steps -- every lane issues one FMA per step (a warp issues 65 FP64
 // instructions per row instead of 96 when a lane takes one column) -- and each column keeps
-// its t = 0 .. c accumulation order.
+// its t = 0 .. c accumulation order.  CTA bx takes rows 4 bx .. of block rows kb + 1 + boff ..
+// (the factorisation launches the first block row, boff = 0, on its critical path and the
+// rest, boff = 1, beside it).
 // Output columns tx and 63 - tx of one panel row a (shared, NB values) times L_kk^-T, from the
 // inverse dv (shared, rows of NB + 1), each column summed over t = 0 .. c in order.
 __device__ __forceinline__ void chol_panel_pair(const double *a, const double (*dv)[NB + 1], int tx, double &out1,
@@ -307,11 +309,12 @@ __device__ __forceinline__ void chol_panel_pair(const double *a, const double (*
 }
 
 __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_pad, int kb,
-                                                    const double *__restrict__ Dinv, const int bx, const int by)
+                                                    const double *__restrict__ Dinv, const int bx, const int by,
+                                                    int boff = 0)
 {
     __shared__ double a[4][NB + 1];
     __shared__ double dv[NB][NB + 1];
-    const int64_t row0 = (int64_t)(kb + 1) * NB + (int64_t)bx * 4;
+    const int64_t row0 = (int64_t)(kb + 1 + boff) * NB + (int64_t)bx * 4;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const double *D = Dinv + (int64_t)kb * NB * NB;
     for (int e = tid; e < 4 * NB; e += blockDim.x) a[e / NB][e % NB] = A[(row0 + e / NB) * n_pad + (int64_t)kb * NB + e % NB];

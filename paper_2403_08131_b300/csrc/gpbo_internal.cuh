@@ -70,7 +70,7 @@ __device__ __forceinline__ long long wait_limit(const unsigned *status)
 
 namespace gpbo {
 constexpr int TRACE_PHASES = 6;
-enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3, PH_CHOL_UPDATE = 4, PH_LML = 5 };
+enum { PH_FIT = 0, PH_XKERN = 1, PH_VAR = 2, PH_SCREEN = 3, PH_CHOL_UPDATE = 4, PH_LML = 5, PH_FACTOR = 6, PH_INVERSE = 7 };
 struct TraceRec {
     int phase;
     cudaEvent_t a, b;
@@ -98,7 +98,7 @@ struct gpbo_ctx {
     void *batch_plan = nullptr;      // captured batched step for the last set of shapes
     int batch_tile = 0;              // batched variance tile (0: autotune)
     cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
-    cudaEvent_t side_ev[5] = {};     // fork / join events between the two streams
+    cudaEvent_t side_ev[6] = {};     // fork / join events between the two streams
     gp_model *step_model = nullptr;  // search_step's model, kept for the next call of the same shape
     void *step_buf = nullptr;        // search_step's device staging
     size_t step_buf_bytes = 0;
@@ -203,7 +203,9 @@ __host__ __device__ inline int64_t chol_tc_tiles(int nblk, int kb)
     for (int i2 = 0; 2 * i2 < T2; ++i2) t += 2 * i2 + 2 < T2 ? 2 * i2 + 2 : T2;
     return t;
 }
-int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, cudaStream_t st, const void *map_a, const void *map_b);
+// Step kb of a single model: block columns c0 .. (c0 = kb + 1 or kb + 2) of block rows kb + 2 ..,
+// with the maps of chol_tc_maps (row strips of 128, column tiles of 32).
+int chol_tc_update(gpbo_ctx *ctx, gp_model *m, int kb, int c0, cudaStream_t st, const void *map_a, const void *map_b);
 // The batched form: tensor maps over a slice arena of `rows` rows, and step kb for every problem
 // of probs (device, G entries) with chol_tc_step true (blockIdx.y = problem; max_rows and
 // max_tiles bound the problems' rows below block row kb + 2 and their tiles).

@@ -73,7 +73,7 @@ _launches = _sig("gpbo_launch_count", C.c_int64, [_P])
 _ws_limit = _sig("gpbo_set_workspace_limit", C.c_int, [_P, C.c_int64])
 _trace_en = _sig("gpbo_trace_enable", C.c_int, [_P, C.c_int])
 _trace_rd = _sig("gpbo_trace_read", C.c_int, [_P, C.c_int, _D, _L, _D])
-PHASES = ("fit", "xkern", "variance", "screen", "chol_update", "lml")
+PHASES = ("fit", "xkern", "variance", "screen", "chol_update", "lml", "factor", "inverse")
 _probe = _sig("gpbo_probe_fma", C.c_int, [_P, C.c_int, _D])
 _wait_limit = _sig("gpbo_set_wait_limit", C.c_int, [_P, C.c_int64])
 _inject_stall = _sig("gpbo_inject_wait_stall", C.c_int, [_P, C.c_int])

@@ -98,7 +98,8 @@ def test_fit_rejects_bad_arguments(ctx):
 
 
 def test_trace_phases_nest(ctx):
-    """The Cholesky-update intervals nest inside the fit interval; both are recorded."""
+    """The Cholesky-update intervals nest inside the factorisation, which with the inverse
+    splits the fit interval; all are recorded."""
     import torch
     w = W.config2()
     ys = (w.y - w.y.mean()) / w.y.std()
@@ -112,6 +113,10 @@ def test_trace_phases_nest(ctx):
     assert 0 < tr["chol_update"]["ms"] < tr["fit"]["ms"]
     assert tr["variance"]["intervals"] >= 1 and tr["xkern"]["intervals"] >= 1
     assert tr["chol_update"]["flops"] == sum(T * (T - 1) // 2 for T in range(2, 8)) * 2 * 64 ** 3
+    # the factorisation and the inverse split the fit, in that order, inside its interval
+    assert tr["factor"]["intervals"] == 1 and tr["inverse"]["intervals"] == 1
+    assert tr["chol_update"]["ms"] < tr["factor"]["ms"]
+    assert tr["factor"]["ms"] + tr["inverse"]["ms"] <= tr["fit"]["ms"] * 1.001
 
 
 @pytest.mark.parametrize("n", [100, 1600])

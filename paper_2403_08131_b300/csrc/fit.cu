@@ -493,20 +493,25 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
                             ctx->dev_status));
         GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1,
                             m->Dinv));
-        // main: the rest of panel kb and of block column kb+1, then block columns kb+2 ..
+        // main: the rest of panel kb and of block column kb+1, then block columns kb+2 ..; large
+        // models take block column kb+1 into the tensor-core update of the step
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_pf, 0));
+        const bool tc_step = tc && chol_tc_step(n_pad, nblk, kb);
+        const bool tc_col = tc_step && n_pad >= CHOL_TC_MIN_NPAD;
         if (T > 1) {
             k_chol_panel<<<(T - 1) * (NB / 4), 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
             GPBO_LAUNCH_CHECK(ctx);
-            k_chol_update_slab<<<(T - 1) * (NB / SLAB_ROWS), 256, 0, st>>>(m->L, n_pad, kb, 1, 1);
-            GPBO_LAUNCH_CHECK(ctx);
+            if (!tc_col) {
+                k_chol_update_slab<<<(T - 1) * (NB / SLAB_ROWS), 256, 0, st>>>(m->L, n_pad, kb, 1, 1);
+                GPBO_LAUNCH_CHECK(ctx);
+            }
         }
-        GPBO_CUDA_TRY(cudaEventRecord(ev_col, st));
+        if (!tc_col) GPBO_CUDA_TRY(cudaEventRecord(ev_col, st));
         if (T > 1) {
             const int64_t tiles = (int64_t)T * (T - 1) / 2;
             GPBO_TRY(trace_begin(ctx, PH_CHOL_UPDATE, (double)tiles * 2.0 * NB * NB * NB));
-            if (tc && chol_tc_step(n_pad, nblk, kb)) {
-                GPBO_TRY(chol_tc_update(ctx, m, kb, kb + 2, st, tc_maps[0], tc_maps[1]));
+            if (tc_step) {
+                GPBO_TRY(chol_tc_update(ctx, m, kb, tc_col ? kb + 1 : kb + 2, st, tc_maps[0], tc_maps[1]));
             } else {
                 if (tiles >= SLAB_BELOW * (int64_t)ctx->sm_count)
                     k_chol_update<<<(unsigned)tiles, 256, smem2, st>>>(m->L, n_pad, kb, nblk, 2);
@@ -516,6 +521,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
             }
             GPBO_TRY(trace_end(ctx));
         }
+        if (tc_col) GPBO_CUDA_TRY(cudaEventRecord(ev_col, st));
         GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));

@@ -181,6 +181,21 @@ __global__ void __launch_bounds__(128) k_chol_panel(double *__restrict__ A, int 
     k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y, boff);
 }
 
+__global__ void __launch_bounds__(128) k_chol_panel_row(double *__restrict__ A, int n_pad, int kb,
+                                                        const double *__restrict__ Dinv, int boff)
+{
+    pdl_wait();
+    pdl_trigger();
+    k_chol_panel_row_body(A, n_pad, kb, Dinv, boff, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(128) k_chol_update_diagblk(double *__restrict__ A, int n_pad, int kb)
+{
+    pdl_wait();
+    pdl_trigger();
+    k_chol_update_diagblk_body(A, n_pad, kb, blockIdx.x);
+}
+
 __global__ void __launch_bounds__(256) k_chol_update(double *__restrict__ A, int n_pad, int kb, int nblk, int part)
 {
     k_chol_update_body(A, n_pad, kb, nblk, blockIdx.x, blockIdx.y, part);
@@ -478,17 +493,30 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
     alignas(64) unsigned char tc_maps[2][128];
     const bool tc = chol_tc_enabled(m);
+    // models of n_pad >= CHOL_TC_MIN_NPAD take the latency-shaped panel and diagonal-block
+    // kernels (smaller ones keep the batched step's arithmetic, bit for bit)
+    const bool large = n_pad >= CHOL_TC_MIN_NPAD;
     if (tc) GPBO_TRY(chol_tc_maps(m, tc_maps[0], tc_maps[1]));
     for (int kb = 0; kb + 1 < nblk; ++kb) {
         const int T = nblk - kb - 1;  // block rows below block kb
         // side: L_{kb+1,kb} (needs block column kb final: the main stream's step kb-1), then
         // diagonal block kb+1 (needs the main stream's trailing update of step kb-1)
-        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_col, 0));
-        GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
+        // (where the step before updated block column kb+1 on the tensor cores, ev_col and
+        // ev_rest mark the same point: one wait, so the next two launches chain without a gap)
+        const bool one_wait = kb > 0 && tc && n_pad >= CHOL_TC_MIN_NPAD && chol_tc_step(n_pad, nblk, kb - 1);
+        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, one_wait ? ev_rest : ev_col, 0));
+        if (large)
+            GPBO_TRY(launch_pdl(ctx, k_chol_panel_row, dim3(NB), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
+        else
+            GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
         GPBO_CUDA_TRY(cudaEventRecord(ev_pf, side));
-        if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));
-        k_chol_update_slab<<<NB / SLAB_ROWS, 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
-        GPBO_LAUNCH_CHECK(ctx);
+        if (kb > 0 && !one_wait) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_rest, 0));
+        if (large) {
+            GPBO_TRY(launch_pdl(ctx, k_chol_update_diagblk, dim3(NB), dim3(128), 0, side, m->L, n_pad, kb));
+        } else {
+            k_chol_update_slab<<<NB / SLAB_ROWS, 256, 0, side>>>(m->L, n_pad, kb, 1, 0);
+            GPBO_LAUNCH_CHECK(ctx);
+        }
         GPBO_TRY(launch_pdl(ctx, k_chol_diag, dim3(1), dim3(DIAG_THREADS), smem1, side, m->L, n_pad, kb + 1, m->Dinv,
                             ctx->dev_status));
         GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1,
@@ -499,7 +527,10 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         const bool tc_step = tc && chol_tc_step(n_pad, nblk, kb);
         const bool tc_col = tc_step && n_pad >= CHOL_TC_MIN_NPAD;
         if (T > 1) {
-            k_chol_panel<<<(T - 1) * (NB / 4), 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
+            if (large)
+                k_chol_panel_row<<<(T - 1) * NB, 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
+            else
+                k_chol_panel<<<(T - 1) * (NB / 4), 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
             GPBO_LAUNCH_CHECK(ctx);
             if (!tc_col) {
                 k_chol_update_slab<<<(T - 1) * (NB / SLAB_ROWS), 256, 0, st>>>(m->L, n_pad, kb, 1, 1);

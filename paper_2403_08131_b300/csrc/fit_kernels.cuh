@@ -326,6 +326,67 @@ __device__ __forceinline__ void k_chol_panel_body(double *__restrict__ A, int n_
     A[(row0 + ty) * n_pad + (int64_t)kb * NB + NB - 1 - tx] = out2;
 }
 
+// The same two products for models with n_pad >= CHOL_TC_MIN_NPAD, shaped for latency: one CTA
+// of 4 warps per output row, warp w summing t in [16 w, 16 w + 16) for two columns a lane, and the
+// four partial sums added in a fixed order.  On this part every dependent FP64 operation costs
+// a warp about 64 cycles, so the 64- and 65-term chains of the kernels above, not their FP64
+// work, set the latency of the factorisation's 64 x 64 steps; here each chain is 16 terms and
+// each row's work has an SM to itself.
+// Panel row: L_{r,kb} = A_{r,kb} L_kk^-T (L_kk^-T from Dinv_kb, lower), row r = 64 (kb + 1 + boff) + blockIdx.x.
+__device__ __forceinline__ void k_chol_panel_row_body(double *__restrict__ A, int n_pad, int kb,
+                                                      const double *__restrict__ Dinv, int boff, const int bx)
+{
+    __shared__ double part[4][NB];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *ar = A + ((int64_t)(kb + 1 + boff) * NB + bx) * n_pad + (int64_t)kb * NB;
+    const double *D = Dinv + (int64_t)kb * NB * NB;
+    double x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = ar[16 * w + k];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        const double *dc = D + (int64_t)c * NB + 16 * w;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (16 * w + k <= c) acc = fma(x[k], dc[k], acc);
+        part[w][c] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < NB) {
+        const int c = threadIdx.x;
+        ar[c] = ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
+    }
+}
+// Diagonal block kb+1, lower triangle: A_{kb+1,kb+1} -= L_{kb+1,kb} L_{kb+1,kb}^T, row blockIdx.x.
+__device__ __forceinline__ void k_chol_update_diagblk_body(double *__restrict__ A, int n_pad, int kb, const int r)
+{
+    __shared__ double part[4][NB];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t rowb = (int64_t)(kb + 1) * NB;
+    const double *Pn = A + rowb * n_pad + (int64_t)kb * NB;  // panel rows of block kb+1
+    double x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = Pn[(int64_t)r * n_pad + 16 * w + k];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        double acc = 0.0;
+        if (c <= r) {
+            const double *pc = Pn + (int64_t)c * n_pad + 16 * w;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc = fma(x[k], pc[k], acc);
+        }
+        part[w][c] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x <= r) {
+        const int c = threadIdx.x;
+        A[(rowb + r) * n_pad + rowb + c] -= ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
+    }
+}
+
 // Trailing update of the lower tiles: A_ij -= L_ik L_jk^T for k < j <= i.
 // part 0: every tile of the trailing lower triangle (T(T+1)/2 CTAs, T = nblk - kb - 1);
 // part 1: block column kb+1 only (T CTAs); part 2: block columns kb+2 .. (T(T-1)/2 CTAs).

@@ -47,6 +47,7 @@ int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
             // stream-ordered users of the old arena must finish before it is released
             GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
             if (ctx->side) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side));
+            if (ctx->side2) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side2));
             GPBO_CUDA_TRY(cudaFree(ctx->ws));
             ctx->ws = nullptr;
             ctx->ws_size = 0;
@@ -64,6 +65,7 @@ int side_stream(gpbo_ctx *ctx, cudaStream_t *out)
         int lo = 0, hi = 0;
         GPBO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
+        GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, hi));
         for (cudaEvent_t &e : ctx->side_ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     *out = ctx->side;
@@ -319,6 +321,10 @@ int gpbo_destroy(gpbo_ctx *ctx)
     if (ctx->side) {
         cudaStreamSynchronize(ctx->side);
         cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->side2) {
+        cudaStreamSynchronize(ctx->side2);
+        cudaStreamDestroy(ctx->side2);
     }
     for (cudaEvent_t e : ctx->side_ev)
         if (e) cudaEventDestroy(e);

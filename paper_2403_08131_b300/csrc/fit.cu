@@ -181,6 +181,14 @@ __global__ void __launch_bounds__(128) k_chol_panel(double *__restrict__ A, int 
     k_chol_panel_body(A, n_pad, kb, Dinv, blockIdx.x, blockIdx.y, boff);
 }
 
+__global__ void __launch_bounds__(128) k_chol_panel_subst(double *__restrict__ A, int n_pad, int kb,
+                                                          const double *__restrict__ Dinv)
+{
+    pdl_wait();
+    pdl_trigger();
+    k_chol_panel_subst_body(A, n_pad, kb, Dinv, blockIdx.x);
+}
+
 __global__ void __launch_bounds__(128) k_chol_panel_row(double *__restrict__ A, int n_pad, int kb,
                                                         const double *__restrict__ Dinv, int boff)
 {
@@ -481,21 +489,35 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     // the next step's first panel row waits for), then the trailing update of block columns
     // kb+2 .. .  Each element gets the same arithmetic, in the same order, as in one launch per
     // part; the streams only reorder independent tiles.
+    // Models of n_pad >= CHOL_TC_MIN_NPAD take latency-shaped kernels (smaller ones keep the
+    // batched step's arithmetic, bit for bit): the first panel row by substitution against the
+    // diagonal factor, so the chain no longer waits for the block's inverse, which runs on a
+    // second side stream for the main stream's rows of the panel.
+    const bool large = n_pad >= CHOL_TC_MIN_NPAD;
     cudaStream_t side = nullptr;
     GPBO_TRY(side_stream(ctx, &side));
+    cudaStream_t side2 = ctx->side2;
     cudaEvent_t ev_fork = ctx->side_ev[0], ev_pf = ctx->side_ev[1], ev_rest = ctx->side_ev[2],
-                ev_join = ctx->side_ev[3], ev_col = ctx->side_ev[5];
+                ev_join = ctx->side_ev[3], ev_col = ctx->side_ev[5], ev_d = ctx->side_ev[6], ev_inv = ctx->side_ev[7];
     GPBO_CUDA_TRY(cudaEventRecord(ev_fork, st));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(side, ev_fork, 0));
     k_chol_diag<<<1, DIAG_THREADS, smem1, side>>>(m->L, n_pad, 0, m->Dinv, ctx->dev_status);
     GPBO_LAUNCH_CHECK(ctx);
-    GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, 0, m->Dinv));
+    auto inverse_on_side2 = [&](int jb) -> int {
+        GPBO_CUDA_TRY(cudaEventRecord(ev_d, side));
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(side2, ev_d, 0));
+        k_chol_inv<<<NB / INV_WARPS, 32 * INV_WARPS, 0, side2>>>(m->L, n_pad, jb, m->Dinv);
+        GPBO_LAUNCH_CHECK(ctx);
+        GPBO_CUDA_TRY(cudaEventRecord(ev_inv, side2));
+        return GPBO_OK;
+    };
+    if (large) GPBO_TRY(inverse_on_side2(0));
+    else
+        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, 0,
+                            m->Dinv));
     // tensor-core trailing updates (FP64 accuracy by exact slice products) for large models
     alignas(64) unsigned char tc_maps[2][128];
     const bool tc = chol_tc_enabled(m);
-    // models of n_pad >= CHOL_TC_MIN_NPAD take the latency-shaped panel and diagonal-block
-    // kernels (smaller ones keep the batched step's arithmetic, bit for bit)
-    const bool large = n_pad >= CHOL_TC_MIN_NPAD;
     if (tc) GPBO_TRY(chol_tc_maps(m, tc_maps[0], tc_maps[1]));
     for (int kb = 0; kb + 1 < nblk; ++kb) {
         const int T = nblk - kb - 1;  // block rows below block kb
@@ -506,7 +528,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         const bool one_wait = kb > 0 && tc && n_pad >= CHOL_TC_MIN_NPAD && chol_tc_step(n_pad, nblk, kb - 1);
         if (kb > 0) GPBO_CUDA_TRY(cudaStreamWaitEvent(side, one_wait ? ev_rest : ev_col, 0));
         if (large)
-            GPBO_TRY(launch_pdl(ctx, k_chol_panel_row, dim3(NB), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
+            GPBO_TRY(launch_pdl(ctx, k_chol_panel_subst, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv));
         else
             GPBO_TRY(launch_pdl(ctx, k_chol_panel, dim3(NB / 4), dim3(128), 0, side, m->L, n_pad, kb, m->Dinv, 0));
         GPBO_CUDA_TRY(cudaEventRecord(ev_pf, side));
@@ -519,11 +541,13 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         }
         GPBO_TRY(launch_pdl(ctx, k_chol_diag, dim3(1), dim3(DIAG_THREADS), smem1, side, m->L, n_pad, kb + 1, m->Dinv,
                             ctx->dev_status));
-        GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad, kb + 1,
-                            m->Dinv));
+        if (!large)
+            GPBO_TRY(launch_pdl(ctx, k_chol_inv, dim3(NB / INV_WARPS), dim3(32 * INV_WARPS), 0, side, m->L, n_pad,
+                                kb + 1, m->Dinv));
         // main: the rest of panel kb and of block column kb+1, then block columns kb+2 ..; large
         // models take block column kb+1 into the tensor-core update of the step
         GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_pf, 0));
+        if (large) GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_inv, 0));  // the inverse of block kb
         const bool tc_step = tc && chol_tc_step(n_pad, nblk, kb);
         const bool tc_col = tc_step && n_pad >= CHOL_TC_MIN_NPAD;
         if (T > 1) {
@@ -554,9 +578,11 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         }
         if (tc_col) GPBO_CUDA_TRY(cudaEventRecord(ev_col, st));
         GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
+        if (large) GPBO_TRY(inverse_on_side2(kb + 1));  // after the main stream's wait for block kb's
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, side));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
+    if (large) GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_inv, 0));
     k_zero_upper_blocks<<<blocks_for((int64_t)n_pad * n_pad), 256, 0, st>>>(m->L, n_pad);
     GPBO_LAUNCH_CHECK(ctx);
     GPBO_TRY(trace_end(ctx));

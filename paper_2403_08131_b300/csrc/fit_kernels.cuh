@@ -237,6 +237,39 @@ __device__ __forceinline__ void k_chol_inv_body(const double *__restrict__ A, in
     chol_inv_column(l, rd, c, lane, D);
 }
 
+// First block row of panel kb by substitution against L_kk (models of n_pad >= CHOL_TC_MIN_NPAD):
+// row i of L_{kb+1,kb} solves x L_kk^T = A_{kb+1,kb}[i], by forward substitution with the
+// column-scaled block (l'_it = l_it / l_tt, the inverse column's steps above: one shuffle and one
+// or two FP64 FMAs per step), then x_t = x~_t / l_tt.  It needs only the factor of block kb, not
+// its inverse, so the inverse leaves the factorisation's chain.  One warp per row; launch
+// NB / W CTAs of 32 W threads.
+__device__ __forceinline__ void k_chol_panel_subst_body(double *__restrict__ A, int n_pad, int kb,
+                                                        const double *__restrict__ Dinv, const int bx)
+{
+    __shared__ double l[NB][NB + 1];
+    __shared__ double rd[NB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)kb * NB * n_pad + (int64_t)kb * NB;
+    const double *D = Dinv + (int64_t)kb * NB * NB;
+    for (int e = tid; e < NB; e += blockDim.x) rd[e] = D[e * NB + e];
+    __syncthreads();
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, t = e % NB;
+        l[i][t] = t < i ? A[base + (int64_t)i * n_pad + t] * rd[t] : 0.0;
+    }
+    __syncthreads();
+    const int i = bx * (int)(blockDim.x >> 5) + warp;
+    double *row = A + ((int64_t)(kb + 1) * NB + i) * n_pad + (int64_t)kb * NB;
+    double x0 = row[lane], x1 = row[lane + 32];
+    for (int t = 0; t < NB; ++t) {
+        const double v = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
+        if (lane > t) x0 = fma(-l[lane][t], v, x0);
+        if (lane + 32 > t) x1 = fma(-l[lane + 32][t], v, x1);
+    }
+    row[lane] = x0 * rd[lane];
+    row[lane + 32] = x1 * rd[lane + 32];
+}
+
 // Trailing update in slabs of SR rows (64 / SR CTAs per 64x64 tile), for launches too small to
 // fill the GPU with whole tiles: on this part a CTA's FP64 work sets its latency, so short
 // slabs keep the late, small updates short.  part 1: block column kb+1 from tile t0 on (CTA bx

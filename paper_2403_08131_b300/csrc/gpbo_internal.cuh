@@ -97,8 +97,9 @@ struct gpbo_ctx {
     int trace_depth = 0;
     void *batch_plan = nullptr;      // captured batched step for the last set of shapes
     int batch_tile = 0;              // batched variance tile (0: autotune)
-    cudaStream_t side = nullptr;     // high-priority stream for work overlapped inside a call
-    cudaEvent_t side_ev[6] = {};     // fork / join events between the two streams
+    cudaStream_t side = nullptr;     // high-priority streams for work overlapped inside a call
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t side_ev[8] = {};     // fork / join events between the streams
     gp_model *step_model = nullptr;  // search_step's model, kept for the next call of the same shape
     void *step_buf = nullptr;        // search_step's device staging
     size_t step_buf_bytes = 0;

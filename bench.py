@@ -463,7 +463,7 @@ def run_ours(args, rank, world, local):
         # counts those BF16 flops, with the FP64-equivalent rate against the FP64 pipe beside it
         cu = tr["chol_update"]
         if cu["ms"] > 0:
-            e = entry("chol_update", "k_chol_update_tc", "tensor", tensor_burst, burst_src, None, scale=34.0)
+            e = entry("chol_update", "k_chol_update_tcp", "tensor", tensor_burst, burst_src, None, scale=34.0)
             f64 = cu["flops"] / (cu["ms"] / 1e3) / 1e12
             e.update({"fp64_equivalent_tflops": round(f64, 3), "fp64_pipe_peak": round(fp64_peak, 3),
                       "fp64_equivalent_frac": round(f64 / fp64_peak, 3),

@@ -63,6 +63,7 @@ struct BatchPlan {
     int max_npad = 0, max_nblk = 0, max_tiles64 = 0, max_chunks = 0;
     int64_t max_M = 0;
     int64_t max_sq = 0, max_dn = 0;
+    int max_d = 1;                        // the widest problem's d
     int tile_req = 0;    // requested variance tile (0: autotune)
     int var_bm = 128;    // variance tile in use: candidates per CTA
     float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 64, 128, 256
@@ -341,6 +342,7 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
         pl->max_M = std::max<int64_t>(pl->max_M, p.M);
         pl->max_sq = std::max<int64_t>(pl->max_sq, (int64_t)p.n_pad * p.n_pad);
         pl->max_dn = std::max<int64_t>(pl->max_dn, (int64_t)p.d * p.n_pad);
+        pl->max_d = std::max(pl->max_d, p.d);
     }
     // alpha32 shares the vec offsets divided by 6 (one float per padded row)
     GPBO_TRY(arena(pl, &pl->probs_dev, G));
@@ -590,7 +592,9 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
     // scoring
-    b_xkern<<<dim3(pl->max_tiles64, G), 256, sizeof(float) * 64 * GPBO_MAX_D, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,
+    const size_t xkern_smem = sizeof(float) * (192 * (size_t)pl->max_d + 128);
+    GPBO_TRY(ensure_smem((const void *)b_xkern, ctx->device, (int)xkern_smem));
+    b_xkern<<<dim3(pl->max_tiles64, G), 256, xkern_smem, st>>>(P, pl->Xs32, pl->alpha32, pl->lsinv,
                                                                                     pl->Kst, pl->mu);
     GPBO_TRY(launch_var(pl, st, xi));
     b_argmax<<<G, 1024, 0, st>>>(P, pl->pei, pl->pidx, pl->best_ei, pl->best_idx);

@@ -93,7 +93,8 @@ static int launch_xkern(gpbo_ctx *ctx, const gp_model *m, const float *Xc, uint6
     for (int k = 0; k < m->d; ++k) ls.inv[k] = 1.0 / m->ls[k];
     if constexpr (sizeof(Acc) == 4) {
         // FP32 models: the register-tiled kernel (n_pad is a multiple of 64, so every float4 is in bounds)
-        const size_t smem = sizeof(float) * 64 * (size_t)m->d;
+        const size_t smem = sizeof(float) * (192 * (size_t)m->d + 128);
+        GPBO_TRY(ensure_smem((const void *)k_xkern32<Out>, ctx->device, (int)smem));
         k_xkern32<Out><<<(unsigned)cdiv64(C, 64), 256, smem, ctx->stream>>>(Xc, seed, c0, C, m->d, Xs, alpha, m->n,
                                                                              m->n_pad, (float)m->s2, ls, Kst, mu);
         GPBO_LAUNCH_CHECK(ctx);

@@ -134,6 +134,8 @@ __device__ __forceinline__ float matern_fast(float r2, float s2)
     return s2 * fmaf(1.6666666f, r2, fmaf(2.2360680f, r, 1.0f)) * e;
 }
 
+// Cross-kernel and mean for FP32 scoring: CTA = 256 threads = 64 candidates (8 per warp) x
+// blocks of 128 observations (4 per lane).  Dynamic shared memory: sizeof(float) (192 d + 128).
 template <typename Out>
 __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
                                                  int d, const float *__restrict__ Xs, const float *__restrict__ alpha,
@@ -141,7 +143,9 @@ __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uin
                                                  float *__restrict__ mu, const int bx, const int by, const int gx)
 {
     constexpr int CW = 8;                 // candidates per warp
-    extern __shared__ float cs[];         // [64][d]
+    extern __shared__ float cs[];         // [64][d] candidates, [d][128] observations, [128] alpha
+    float *xo = cs + 64 * d;
+    float *al = xo + 128 * d;
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
     const int64_t cbase = bx * 64ll;
     for (int e = tid; e < 64 * d; e += 256) {
@@ -150,19 +154,27 @@ __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uin
         const float x = Xc ? (cbase + r < C ? Xc[c * d + k] : 0.0f) : uniform24f(seed, 2, (uint64_t)(c * d + k));
         cs[e] = x * (float)ls.inv[k];
     }
-    __syncthreads();
     const float *cw = cs + warp * CW * d;
     float mp[CW];
 #pragma unroll
     for (int a = 0; a < CW; ++a) mp[a] = 0.0f;
     for (int i0 = 0; i0 < n_pad; i0 += 128) {
+        // the block's observations and alpha, staged once for the CTA (the previous block's
+        // reads are done first): the d-step loop below then never waits on a global load
+        __syncthreads();
+        for (int e = tid; e < d * 128; e += 256) {
+            const int k = e >> 7, q = e & 127;
+            xo[e] = i0 + q < n_pad ? Xs[(size_t)k * n_pad + i0 + q] : 0.0f;
+        }
+        if (tid < 128) al[tid] = i0 + tid < n_pad ? alpha[i0 + tid] : 0.0f;
+        __syncthreads();
         const int i = i0 + 4 * lane;
-        if (i >= n_pad) break;
+        if (i >= n_pad) continue;  // n_pad is a multiple of 64: whole float4s or none
         float r2[CW][4];
 #pragma unroll
         for (int a = 0; a < CW; ++a) r2[a][0] = r2[a][1] = r2[a][2] = r2[a][3] = 0.0f;
         for (int k = 0; k < d; ++k) {
-            const float4 o = *reinterpret_cast<const float4 *>(Xs + (size_t)k * n_pad + i);
+            const float4 o = *reinterpret_cast<const float4 *>(xo + k * 128 + 4 * lane);
 #pragma unroll
             for (int a = 0; a < CW; ++a) {
                 const float cv = cw[a * d + k];
@@ -173,7 +185,7 @@ __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uin
                 r2[a][3] = fmaf(t3, t3, r2[a][3]);
             }
         }
-        const float4 al = *reinterpret_cast<const float4 *>(alpha + i);
+        const float4 alv = *reinterpret_cast<const float4 *>(al + 4 * lane);
         const bool v0 = i < n, v1 = i + 1 < n, v2 = i + 2 < n, v3 = i + 3 < n;
 #pragma unroll
         for (int a = 0; a < CW; ++a) {
@@ -181,7 +193,7 @@ __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uin
             const float k1 = v1 ? matern_fast(r2[a][1], s2) : 0.0f;
             const float k2 = v2 ? matern_fast(r2[a][2], s2) : 0.0f;
             const float k3 = v3 ? matern_fast(r2[a][3], s2) : 0.0f;
-            mp[a] = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mp[a]))));
+            mp[a] = fmaf(k0, alv.x, fmaf(k1, alv.y, fmaf(k2, alv.z, fmaf(k3, alv.w, mp[a]))));
             const int64_t cl = cbase + warp * CW + a;
             if (cl < C)
                 *reinterpret_cast<typename Pack4<Out>::T *>(Kst + cl * n_pad + i) = Pack4<Out>::make(k0, k1, k2, k3);

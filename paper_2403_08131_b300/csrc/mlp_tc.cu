@@ -277,57 +277,59 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->x_full);
                 }
-#pragma unroll 1
-                for (int qb = 0; qb < 4; qb += 2) {
-                    uint32_t v[2][16];
+                // K tile q's 16 columns are processed while tile q+1's load is in flight
+                uint32_t va[16], vb[16];
+                tmem_ld16_nw(tmem + lane_addr + (uint32_t)(grp * 16), va);
+                tmem_wait();
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) tmem_ld16_nw(tmem + lane_addr + (uint32_t)((qb + u) * KT + grp * 16), v[u]);
-                    tmem_wait();
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t *cur = (q & 1) ? vb : va;
+                    uint32_t *nxt = (q & 1) ? va : vb;
+                    if (q < 3) tmem_ld16_nw(tmem + lane_addr + (uint32_t)((q + 1) * KT + grp * 16), nxt);
+                    pin16(cur);
+                    uint32_t w[8];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int q = qb + u;
-                        pin16(v[u]);
-                        uint32_t w[8];
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2)
-                            w[j / 2] = pack_f16(gelu2_tanh(__uint_as_float(v[u][j])), gelu2_tanh(__uint_as_float(v[u][j + 1])));
-                        unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
-                        const int j0 = 2 * grp, j1 = 2 * grp + 1;
-                        *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-                        *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-                        fence_async_smem();
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh->h_full[q]);
-                    }
+                    for (int j = 0; j < 16; j += 2)
+                        w[j / 2] = pack_f16(gelu2_tanh(__uint_as_float(cur[j])), gelu2_tanh(__uint_as_float(cur[j + 1])));
+                    unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
+                    const int j0 = 2 * grp, j1 = 2 * grp + 1;
+                    *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->h_full[q]);
+                    if (q < 3) tmem_wait();
                 }
                 // ---- layer-2 epilogue and layer 3
                 g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
                 float o0 = 0.f, o1 = 0.f;
-#pragma unroll 1
-                for (int qb = 0; qb < 4; qb += 2) {
-                    uint32_t v[2][16];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64 + (qb + u) * 16), v[u]);
+                {
+                    uint32_t va[16], vb[16];
+                    tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64), va);
                     tmem_wait();
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        pin16(v[u]);
-                        const int j0 = grp * 64 + (qb + u) * 16;
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t *cur = (q & 1) ? vb : va;
+                        uint32_t *nxt = (q & 1) ? va : vb;
+                        if (q < 3) tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64 + (q + 1) * 16), nxt);
+                        pin16(cur);
+                        const int j0 = grp * 64 + q * 16;
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
                             const float4 b = *reinterpret_cast<const float4 *>(aux + j0 + j);
                             const float4 wa = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
                             const float4 wb = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4);
-                            const float h0 = gelu2_tanh(__uint_as_float(v[u][j]) + b.x);
-                            const float h1v = gelu2_tanh(__uint_as_float(v[u][j + 1]) + b.y);
-                            const float h2 = gelu2_tanh(__uint_as_float(v[u][j + 2]) + b.z);
-                            const float h3 = gelu2_tanh(__uint_as_float(v[u][j + 3]) + b.w);
+                            const float h0 = gelu2_tanh(__uint_as_float(cur[j]) + b.x);
+                            const float h1v = gelu2_tanh(__uint_as_float(cur[j + 1]) + b.y);
+                            const float h2 = gelu2_tanh(__uint_as_float(cur[j + 2]) + b.z);
+                            const float h3 = gelu2_tanh(__uint_as_float(cur[j + 3]) + b.w);
                             o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
                             o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
                         }
+                        if (q < 3) tmem_wait();
                     }
                 }
                 tc_fence_before();

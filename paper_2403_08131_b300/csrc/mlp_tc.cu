@@ -107,10 +107,12 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b)
 
 // Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in FP16, 128-byte swizzled
 // (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
-__device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const Params &P)
+// The fields come by value: a reference to the kernel's parameters would copy them to local memory.
+__device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, int64_t C, int64_t c0, int d,
+                                     const float *Xc, uint64_t seed)
 {
     const int64_t cl = t * BM + r;
-    const int64_t c = P.c0 + cl;
+    const int64_t c = c0 + cl;
     uint32_t w[16];
 #pragma unroll
     for (int k = 0; k < 32; k += 2) {
@@ -119,10 +121,10 @@ __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, const 
         for (int u = 0; u < 2; ++u) {
             const int kk = k + u;
             float x = 0.0f;
-            if (kk < P.d) {
-                if (P.Xc) x = cl < P.C ? P.Xc[c * P.d + kk] : 0.5f;
-                else x = uniform24f(P.seed, 2, (uint64_t)(c * P.d + kk));
-            } else if (kk == P.d) {
+            if (kk < d) {
+                if (Xc) x = cl < C ? Xc[c * d + kk] : 0.5f;
+                else x = uniform24f(seed, 2, (uint64_t)(c * d + kk));
+            } else if (kk == d) {
                 x = 1.0f;
             }
             v[u] = x;
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         const float invE = 1.0f / (float)P.E;
         float mu_shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;  // ensemble state (group 0)
         if (builder && (int)blockIdx.x < P.num_tiles) {
-            build_x(xs, row, blockIdx.x, P);
+            build_x(xs, row, blockIdx.x, P.C, P.c0, P.d, P.Xc, P.seed);
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->x_full);
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 tc_fence_after();
                 if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
                     // the last network's layer-1 MMAs are complete: the x tile is free
-                    build_x(xs, row, t + gridDim.x, P);
+                    build_x(xs, row, t + gridDim.x, P.C, P.c0, P.d, P.Xc, P.seed);
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->x_full);

@@ -153,9 +153,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             if (P.split) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l2) : "memory");
             int stage = 0;
             uint32_t phase = 0;
-            int armed[STAGES];
-            uint32_t armed_par[STAGES];
-            for (int s = 0; s < STAGES; ++s) armed[s] = 0, armed_par[s] = 0;
+            uint32_t armed = 0, armed_par = 0;  // bit s: stage s has a copy issued, and its phase
             bool ok = true;
             for (int t = pair; ok && t < P.num_tiles; t += npairs) {
                 const int arow = t * (2 * BM) + (int)rank * BM;
@@ -171,8 +169,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                             unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                             unsigned char *b = a + A_BYTES;
                             mbar_arrive_expect_tx(&sh->full[stage], STAGE_BYTES);
-                            armed[stage] = 1;
-                            armed_par[stage] = phase;
+                            armed |= 1u << stage;
+                            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
 #pragma unroll
                             for (int u = 0; u < KSUB; ++u) {
                                 tma_load_2d(a + u * A_SUB, &map_k, ks * BK + 64 * u, arow, &sh->full[stage]);
@@ -185,7 +183,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             }
             // leave no copy in flight: wait for the last arming of every stage
             for (int s = 0; s < STAGES; ++s)
-                if (armed[s]) mbar_wait(&sh->full[s], armed_par[s], abort_flag, P.status, false);
+                if ((armed >> s) & 1u) mbar_wait(&sh->full[s], (armed_par >> s) & 1u, abort_flag, P.status, false);
         }
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {

@@ -4,8 +4,10 @@
 // For a tile of 128 candidates and each network e of the ensemble (d -> 256 -> 256 -> 2):
 //   Z1 = [x | 1] [W1 ; b1]         tcgen05.mma, K = 32 (d <= 31 inputs, then the constant 1)
 //   H1 = fp16(gelu(Z1))            epilogue; written to shared memory as the next A operand
-//   Z2 = H1 W2                     tcgen05.mma, K = 256 in four 64-column K tiles
-//   o  = gelu(Z2 + b2) W3 + b3     epilogue, FP32 on the CUDA cores (two outputs)
+//   Z2 = b2 + H1 W2                tcgen05.mma: the bias as [1 1] [b2_hi ; b2_lo] (one K = 16 step,
+//                                  b2 = b2_hi + b2_lo to 2^-22 relative), then K = 256 in four
+//                                  64-column K tiles
+//   o  = gelu(Z2) W3 + b3          epilogue, FP32 on the CUDA cores (two outputs)
 // then mu_e = o_0 sd_mu + mean_mu and sigma_e = exp(o_1 sd_ls + mean_ls); after the last
 // network mu_bar = mean_e mu_e, sigma_bar^2 = mean_e sigma_e^2 + var_e mu_e and
 // EI(mu_bar, sigma_bar) for minimisation.
@@ -15,10 +17,10 @@
 // tensor rate, 11 significant bits instead of 8.
 //
 // Roles (one CTA per SM, persistent over tiles; 576 threads):
-//   warp 0      TMA: per network, [W1 ; b1]^T (256 x 64, zero padded) then W2^T in four
-//               256 x 64 K chunks; 3 stages of 32 KiB.  The packed ensemble (8 networks,
-//               1.3 MB) is read from L2 for every tile; b2, W3 and b3 of every network
-//               (E <= 8) stay in shared memory.
+//   warp 0      TMA: per network, [W1 ; b1 | b2 split]^T (256 x 64, zero padded) then W2^T in
+//               four 256 x 64 K chunks; 3 stages of 32 KiB (the first chunk's stage is held
+//               until layer 2's bias MMA).  The packed ensemble (8 networks, 1.3 MB) is read
+//               from L2 for every tile; W3 and b3 of every network (E <= 8) stay in shared memory.
 //   warp 1      TMEM (512 columns: Z1 in 0..255, Z2 in 256..511); one lane issues the MMAs
 //   warps 2-17  epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4;
 //               warps 2-5 (group 0) also build the x tile and own the ensemble state of
@@ -105,7 +107,8 @@ __device__ __forceinline__ uint32_t pack_f16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ...] in FP16, 128-byte swizzled
+// Row r of the x tile of tile t: [x_0 .. x_{d-1}, 1, 0 ... | 1, 1, 0 ...] in FP16 (the second part
+// from K column 32: the A operand of layer 2's bias), 128-byte swizzled
 // (16-byte chunk j of row r at r * 128 + ((j ^ (r & 7)) * 16)).
 // The fields come by value: a reference to the kernel's parameters would copy them to local memory.
 __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, int64_t C, int64_t c0, int d,
@@ -134,7 +137,8 @@ __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, int64_
     unsigned char *row = xs + r * 128;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint4 val = j < 4 ? make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]) : make_uint4(0, 0, 0, 0);
+        const uint4 val = j < 4 ? make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3])
+                                : make_uint4(j == 4 ? pack_f16(1.0f, 1.0f) : 0u, 0u, 0u, 0u);
         *reinterpret_cast<uint4 *>(row + ((j ^ (r & 7)) * 16)) = val;
     }
 }
@@ -216,16 +220,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     if (e == 0 && !mbar_wait_fast(&sh->x_full, ti & 1u, abort_flag, P.status)) { ok = false; break; }
                     if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
-                    {
-                        const unsigned char *w = wst + (size_t)stage * W_BYTES;
-                        for (int kk = 0; kk < P.nk1; ++kk)
-                            mma_f16(tmem, smem_desc(xs + kk * 32), smem_desc(w + kk * 32), P.idesc, kk ? 1u : 0u);
-                    }
-                    mma_commit(&sh->empty[stage]);
+                    const unsigned char *w0 = wst + (size_t)stage * W_BYTES;
+                    for (int kk = 0; kk < P.nk1; ++kk)
+                        mma_f16(tmem, smem_desc(xs + kk * 32), smem_desc(w0 + kk * 32), P.idesc, kk ? 1u : 0u);
                     mma_commit(&sh->z1_full);
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                    // layer 2, K tile by K tile as H1 fills
+                    // layer 2 starts with its bias: Z2 = [1 1] [b2_hi ; b2_lo] (K columns 32..47
+                    // of the x tile and of chunk 0), then accumulates H1 W2 K tile by K tile as H1 fills
                     if (!mbar_wait_fast(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    mma_f16(tmem + HID, smem_desc(xs + 64), smem_desc(w0 + 64), P.idesc, 0u);
+                    mma_commit(&sh->empty[stage]);
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     for (int q = 0; q < 4; ++q) {
                         if (!mbar_wait_fast(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
                         if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
@@ -234,8 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                         const unsigned char *a = h1 + q * TILE_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_f16(tmem + HID, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc,
-                                    (q | kk) ? 1u : 0u);
+                            mma_f16(tmem + HID, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc, 1u);
                         mma_commit(&sh->empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
@@ -272,13 +275,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
-                if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
-                    // the last network's layer-1 MMAs are complete: the x tile is free
-                    build_x(xs, row, t + gridDim.x, P.C, P.c0, P.d, P.Xc, P.seed);
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->x_full);
-                }
                 // K tile q's 16 columns are processed while tile q+1's load is in flight
                 uint32_t va[16], vb[16];
                 tmem_ld16_nw(tmem + lane_addr + (uint32_t)(grp * 16), va);
@@ -307,6 +303,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
+                if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
+                    // every MMA of the tile that reads the x tile (the last network's layer 1 and
+                    // layer-2 bias) is complete: build the next tile's
+                    build_x(xs, row, t + gridDim.x, P.C, P.c0, P.d, P.Xc, P.seed);
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->x_full);
+                }
                 float o0 = 0.f, o1 = 0.f;
                 {
                     uint32_t va[16], vb[16];
@@ -321,13 +325,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                         const int j0 = grp * 64 + q * 16;
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
-                            const float4 b = *reinterpret_cast<const float4 *>(aux + j0 + j);
                             const float4 wa = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
                             const float4 wb = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4);
-                            const float h0 = gelu2_tanh(__uint_as_float(cur[j]) + b.x);
-                            const float h1v = gelu2_tanh(__uint_as_float(cur[j + 1]) + b.y);
-                            const float h2 = gelu2_tanh(__uint_as_float(cur[j + 2]) + b.z);
-                            const float h3 = gelu2_tanh(__uint_as_float(cur[j + 3]) + b.w);
+                            const float h0 = gelu2_tanh(__uint_as_float(cur[j]));
+                            const float h1v = gelu2_tanh(__uint_as_float(cur[j + 1]));
+                            const float h2 = gelu2_tanh(__uint_as_float(cur[j + 2]));
+                            const float h3 = gelu2_tanh(__uint_as_float(cur[j + 3]));
                             o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
                             o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
                         }
@@ -390,9 +393,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
 
 // Pack one network's FP32 parameters (layout W1 [d x H], b1, W2 [H x H], b2, W3 [H x 2], b3)
 // into the kernel's operands: wt = E x 5 chunks of 256 x 64 FP16, K-major
-//   chunk 0: row j = [W1[0][j] .. W1[d-1][j], b1[j], 0 ...]
+//   chunk 0: row j = [W1[0][j] .. W1[d-1][j], b1[j], 0 ... | b2_hi[j], b2_lo[j], 0 ...] (the second
+//            part from K column 32: b2_hi = fp16(b2[j]), b2_lo = fp16(b2[j] - b2_hi))
 //   chunk c = 1..4: row j = W2[64(c-1) .. 64c-1][j] / 2
-// and aux = E x AUX FP32: b2 [256], W3 [256 x 2] / 2 (row j = the two outputs), b3 [2], zeros.
+// and aux = E x AUX FP32: b2 [256] (not read by the forward, which takes b2 from chunk 0),
+// W3 [256 x 2] / 2 (row j = the two outputs), b3 [2], zeros.
 // The halves absorb gelu's factor 1/2 (the epilogues produce 2 gelu).
 __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P, int64_t oW1, int64_t ob1,
                        int64_t oW2, int64_t ob2, int64_t oW3, int64_t ob3, __half *__restrict__ wt,
@@ -408,9 +413,17 @@ __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P,
         const int kk = (int)(r % KT);
         const float *th = theta + e * P;
         float v;
-        if (c == 0) v = kk < d ? th[oW1 + (int64_t)kk * HID + j] : (kk == d ? th[ob1 + j] : 0.0f);
-        else v = 0.5f * th[oW2 + (int64_t)(64 * (c - 1) + kk) * HID + j];
-        wt[t] = __float2half_rn(v);
+        __half hv;
+        if (c == 0) {
+            const float b2 = th[ob2 + j];
+            const __half b2_hi = __float2half_rn(b2);
+            if (kk == 32) hv = b2_hi;
+            else if (kk == 33) hv = __float2half_rn(b2 - __half2float(b2_hi));
+            else hv = __float2half_rn(kk < d ? th[oW1 + (int64_t)kk * HID + j] : (kk == d ? th[ob1 + j] : 0.0f));
+        } else {
+            hv = __float2half_rn(0.5f * th[oW2 + (int64_t)(64 * (c - 1) + kk) * HID + j]);
+        }
+        wt[t] = hv;
     }
     if (t < (int64_t)E * AUX) {
         const int e = (int)(t / AUX);

@@ -93,12 +93,38 @@ struct Params {
 };
 
 // 2 gelu(z) in the tanh form: z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
-__device__ __forceinline__ float gelu2_tanh(float z)
+// Two FP32 lanes per instruction (fma.rn.f32x2, mul.rn.f32x2): each lane is the IEEE
+// round-to-nearest FMA or product of its own operands, as the scalar instructions.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
 {
-    const float u = z * fmaf(0.0356774081f, z * z, 0.7978845608f);
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
-    return fmaf(z, t, z);
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// 2 gelu(z) of two elements: z (1 + tanh(z (c0 + c1 z^2))), c0 = sqrt(2/pi), c1 = 0.044715 c0
+__device__ __forceinline__ float2 gelu2_tanh_x2(float2 z)
+{
+    const float2 u = mul2(z, fma2(mul2(z, z), make_float2(0.0356774081f, 0.0356774081f),
+                                  make_float2(0.7978845608f, 0.7978845608f)));
+    float2 t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t.x) : "f"(u.x));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t.y) : "f"(u.y));
+    return fma2(z, t, z);
 }
 
 __device__ __forceinline__ uint32_t pack_f16(float a, float b)
@@ -287,8 +313,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     pin16(cur);
                     uint32_t w[8];
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2)
-                        w[j / 2] = pack_f16(gelu2_tanh(__uint_as_float(cur[j])), gelu2_tanh(__uint_as_float(cur[j + 1])));
+                    for (int j = 0; j < 16; j += 2) {
+                        const float2 h = gelu2_tanh_x2(make_float2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])));
+                        w[j / 2] = pack_f16(h.x, h.y);
+                    }
                     unsigned char *dst = h1 + q * TILE_BYTES + row * 128;
                     const int j0 = 2 * grp, j1 = 2 * grp + 1;
                     *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -311,7 +339,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->x_full);
                 }
-                float o0 = 0.f, o1 = 0.f;
+                // layer 3 on pairs of hidden units: a0 = (even, odd) partial sums of output 0, a1 of output 1
+                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
                 {
                     uint32_t va[16], vb[16];
                     tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64), va);
@@ -324,15 +353,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                         pin16(cur);
                         const int j0 = grp * 64 + q * 16;
 #pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            const float4 wa = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
-                            const float4 wb = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j) + 4);
-                            const float h0 = gelu2_tanh(__uint_as_float(cur[j]));
-                            const float h1v = gelu2_tanh(__uint_as_float(cur[j + 1]));
-                            const float h2 = gelu2_tanh(__uint_as_float(cur[j + 2]));
-                            const float h3 = gelu2_tanh(__uint_as_float(cur[j + 3]));
-                            o0 = fmaf(h0, wa.x, fmaf(h1v, wa.z, fmaf(h2, wb.x, fmaf(h3, wb.z, o0))));
-                            o1 = fmaf(h0, wa.y, fmaf(h1v, wa.w, fmaf(h2, wb.y, fmaf(h3, wb.w, o1))));
+                        for (int j = 0; j < 16; j += 2) {
+                            // W3 rows j, j+1 as (w[j][0], w[j+1][0], w[j][1], w[j+1][1])
+                            const float4 wv = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
+                            const float2 h = gelu2_tanh_x2(make_float2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])));
+                            a0 = fma2(h, make_float2(wv.x, wv.y), a0);
+                            a1 = fma2(h, make_float2(wv.z, wv.w), a1);
                         }
                         if (q < 3) tmem_wait();
                     }
@@ -340,6 +366,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->z2_empty);
+                float o0 = a0.x + a0.y, o1 = a1.x + a1.y;
                 // ---- combine the column groups; group 0 updates the ensemble state
                 const int par = k & 1;
                 const uint32_t use = (k >> 1) & 1u;
@@ -397,7 +424,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
 //            part from K column 32: b2_hi = fp16(b2[j]), b2_lo = fp16(b2[j] - b2_hi))
 //   chunk c = 1..4: row j = W2[64(c-1) .. 64c-1][j] / 2
 // and aux = E x AUX FP32: b2 [256] (not read by the forward, which takes b2 from chunk 0),
-// W3 [256 x 2] / 2 (row j = the two outputs), b3 [2], zeros.
+// W3 [256 x 2] / 2 in pairs of rows (w[2p][0], w[2p+1][0], w[2p][1], w[2p+1][1]), b3 [2], zeros.
 // The halves absorb gelu's factor 1/2 (the epilogues produce 2 gelu).
 __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P, int64_t oW1, int64_t ob1,
                        int64_t oW2, int64_t ob2, int64_t oW3, int64_t ob3, __half *__restrict__ wt,
@@ -431,7 +458,11 @@ __global__ void k_pack(const float *__restrict__ theta, int E, int d, int64_t P,
         const float *th = theta + e * P;
         float v = 0.0f;
         if (i < HID) v = th[ob2 + i];
-        else if (i < 3 * HID) v = 0.5f * th[oW3 + (i - HID)];
+        else if (i < 3 * HID) {
+            // rows 2p and 2p+1 of W3 as (w[2p][0], w[2p+1][0], w[2p][1], w[2p+1][1])
+            const int r = i - HID, pr = r / 4, o = (r / 2) & 1, sub = r & 1;
+            v = 0.5f * th[oW3 + (int64_t)(2 * pr + sub) * 2 + o];
+        }
         else if (i < 3 * HID + 2) v = th[ob3 + (i - 3 * HID)];
         aux[t] = v;
     }

@@ -16,15 +16,17 @@
 // compute h' = z (1 + t) = 2 gelu(z) with one FMA.  FP16 rather than BF16 operands: the same
 // tensor rate, 11 significant bits instead of 8.
 //
-// Roles (one CTA per SM, persistent over tiles; 576 threads):
+// Roles (one CTA per SM, persistent over tiles; 608 threads):
 //   warp 0      TMA: per network, [W1 ; b1 | b2 split]^T (256 x 64, zero padded) then W2^T in
 //               four 256 x 64 K chunks; 3 stages of 32 KiB (the first chunk's stage is held
 //               until layer 2's bias MMA).  The packed ensemble (8 networks, 1.3 MB) is read
 //               from L2 for every tile; W3 and b3 of every network (E <= 8) stay in shared memory.
 //   warp 1      TMEM (512 columns: Z1 in 0..255, Z2 in 256..511); one lane issues the MMAs
 //   warps 2-17  epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4;
-//               warps 2-5 (group 0) also build the x tile and own the ensemble state of
-//               their rows (one thread = one candidate)
+//               warps 2-5 (group 0) also own the ensemble state of their rows (one thread =
+//               one candidate)
+//   warp 18     builds the x tiles (four rows a lane) into two buffers, up to one tile ahead:
+//               the counter-RNG draws stay off the epilogue's path
 // H1 is written K tile by K tile (every warp does its 16 columns of tile q, then of q+1), and
 // the second layer's MMAs on K tile q start once tile q is complete, so layer 2 runs under
 // the first-layer epilogue; layer 1 of the next network runs under the second-layer one.
@@ -49,7 +51,8 @@ constexpr int CHUNKS = 5;                // per network: [W1;b1]^T, then W2^T in
 constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 16;
 constexpr int GROUPS = EPI_WARPS / 4;    // column groups
-constexpr int THREADS = (2 + EPI_WARPS) * 32;
+constexpr int BUILDER_WARP = 2 + EPI_WARPS;
+constexpr int THREADS = (3 + EPI_WARPS) * 32;
 constexpr int TMEM_COLS = 512;
 constexpr int TILE_BYTES = BM * 128;     // one 128 x 64 BF16 K tile
 constexpr int H1_BYTES = 4 * TILE_BYTES; // 128 x 256
@@ -64,7 +67,7 @@ struct alignas(16) Shared {
     uint64_t empty[STAGES];
     uint64_t z1_full, z2_full, z2_empty;
     uint64_t h_full[4];
-    uint64_t x_full;
+    uint64_t x_full[2], x_empty[2];
     uint64_t part_ready[2], part_free[2];
     uint64_t drain;
     uint32_t tmem_base;
@@ -74,7 +77,7 @@ struct alignas(16) Shared {
 
 inline size_t smem_bytes()
 {
-    return (size_t)H1_BYTES + X_BYTES + (size_t)STAGES * W_BYTES + 1024 + sizeof(Shared) + sizeof(float) * EMAX * AUX;
+    return (size_t)H1_BYTES + 2 * X_BYTES + (size_t)STAGES * W_BYTES + 1024 + sizeof(Shared) + sizeof(float) * EMAX * AUX;
 }
 
 struct Params {
@@ -174,8 +177,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *h1 = base;                       // 4 K tiles
-    unsigned char *xs = base + H1_BYTES;            // 1 K tile
-    unsigned char *wst = xs + X_BYTES;              // STAGES x W_BYTES
+    unsigned char *xs = base + H1_BYTES;            // 2 x tiles (tile ti in buffer ti & 1)
+    unsigned char *wst = xs + 2 * X_BYTES;          // STAGES x W_BYTES
     Shared *sh = (Shared *)(wst + (size_t)STAGES * W_BYTES);
     float *aux_s = (float *)(sh + 1);               // E x AUX (16-byte aligned: Shared is)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -190,7 +193,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         mbar_init(&sh->z2_full, 1);
         mbar_init(&sh->z2_empty, EPI_WARPS);
         for (int q = 0; q < 4; ++q) mbar_init(&sh->h_full[q], EPI_WARPS);
-        mbar_init(&sh->x_full, 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->x_full[b], 1);
+            mbar_init(&sh->x_empty[b], 1);
+        }
         for (int p = 0; p < 2; ++p) {
             mbar_init(&sh->part_ready[p], 4 * (GROUPS - 1));
             mbar_init(&sh->part_free[p], 4);
@@ -243,18 +249,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x, ++ti) {
                 for (int e = 0; ok && e < P.E; ++e, ++k) {
                     // layer 1 (Z1 is free: layer 2 of the previous network waited for all of H1)
-                    if (e == 0 && !mbar_wait_fast(&sh->x_full, ti & 1u, abort_flag, P.status)) { ok = false; break; }
+                    const int xb = (int)(ti & 1u);
+                    const unsigned char *xt = xs + xb * X_BYTES;
+                    if (e == 0 && !mbar_wait_fast(&sh->x_full[xb], (ti >> 1) & 1u, abort_flag, P.status)) { ok = false; break; }
                     if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const unsigned char *w0 = wst + (size_t)stage * W_BYTES;
                     for (int kk = 0; kk < P.nk1; ++kk)
-                        mma_f16(tmem, smem_desc(xs + kk * 32), smem_desc(w0 + kk * 32), P.idesc, kk ? 1u : 0u);
+                        mma_f16(tmem, smem_desc(xt + kk * 32), smem_desc(w0 + kk * 32), P.idesc, kk ? 1u : 0u);
                     mma_commit(&sh->z1_full);
                     // layer 2 starts with its bias: Z2 = [1 1] [b2_hi ; b2_lo] (K columns 32..47
                     // of the x tile and of chunk 0), then accumulates H1 W2 K tile by K tile as H1 fills
                     if (!mbar_wait_fast(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
-                    mma_f16(tmem + HID, smem_desc(xs + 64), smem_desc(w0 + 64), P.idesc, 0u);
+                    mma_f16(tmem + HID, smem_desc(xt + 64), smem_desc(w0 + 64), P.idesc, 0u);
                     mma_commit(&sh->empty[stage]);
+                    if (e == P.E - 1) mma_commit(&sh->x_empty[xb]);  // the tile's last read of its x tile
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     for (int q = 0; q < 4; ++q) {
                         if (!mbar_wait_fast(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
@@ -275,22 +284,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             mma_commit(&sh->drain);
             mbar_wait(&sh->drain, 0, abort_flag, P.status, false);
         }
+    } else if (warp == BUILDER_WARP) {
+        // ---------------- x tiles, up to one tile ahead of the MMAs (two buffers)
+        uint32_t ti = 0;
+        for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x, ++ti) {
+            const int b = (int)(ti & 1u);
+            const bool g = mbar_wait_inl(&sh->x_empty[b], ((ti >> 1) & 1u) ^ 1u, abort_flag, P.status);
+            if (!__all_sync(0xffffffffu, g)) break;
+            for (int r = lane; r < BM; r += 32) build_x(xs + b * X_BYTES, r, t, P.C, P.c0, P.d, P.Xc, P.seed);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->x_full[b]);
+        }
     } else {
         // ---------------- epilogue
         const int ew = warp - 2;
         const int quad = warp & 3;
         const int grp = ew >> 2;
         const int row = quad * 32 + lane;
-        const bool builder = grp == 0;
+        const bool owner = grp == 0;  // owns its rows' ensemble state
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const float invE = 1.0f / (float)P.E;
         float mu_shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;  // ensemble state (group 0)
-        if (builder && (int)blockIdx.x < P.num_tiles) {
-            build_x(xs, row, blockIdx.x, P.C, P.c0, P.d, P.Xc, P.seed);
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh->x_full);
-        }
         uint32_t k = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
@@ -331,14 +346,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
-                if (builder && e == P.E - 1 && t + (int)gridDim.x < P.num_tiles) {
-                    // every MMA of the tile that reads the x tile (the last network's layer 1 and
-                    // layer-2 bias) is complete: build the next tile's
-                    build_x(xs, row, t + gridDim.x, P.C, P.c0, P.d, P.Xc, P.seed);
-                    fence_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->x_full);
-                }
                 // layer 3 on pairs of hidden units: a0 = (even, odd) partial sums of output 0, a1 of output 1
                 float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
                 {
@@ -370,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 // ---- combine the column groups; group 0 updates the ensemble state
                 const int par = k & 1;
                 const uint32_t use = (k >> 1) & 1u;
-                if (!builder) {
+                if (!owner) {
                     g = mbar_wait_inl(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                     sh->part[par][grp - 1][row] = make_float2(o0, o1);

@@ -306,6 +306,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const float invE = 1.0f / (float)P.E;
         float mu_shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;  // ensemble state (group 0)
+        // group 0: network k's own layer-3 sums, combined during network k + 1
+        struct Pending {
+            float o0, o1;
+            uint32_t k;
+            int e;
+            int64_t cl;
+        };
+        Pending pend{0.f, 0.f, 0u, 0, 0};
+        bool has_pend = false;
+        auto combine = [&](const Pending &p) -> bool {
+            const int par = p.k & 1;
+            const bool got = mbar_wait_inl(&sh->part_ready[par], (p.k >> 1) & 1u, abort_flag, P.status);
+            if (!__all_sync(0xffffffffu, got)) return false;
+            float o0 = p.o0, o1 = p.o1;
+#pragma unroll
+            for (int gg = 0; gg < GROUPS - 1; ++gg) {
+                const float2 v = sh->part[par][gg][row];
+                o0 += v.x;
+                o1 += v.y;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->part_free[par]);
+            const float *aux = aux_s + p.e * AUX;
+            const float m = (o0 + aux[3 * HID]) * P.n1 + P.n0;
+            const float s = expf((o1 + aux[3 * HID + 1]) * P.n3 + P.n2);
+            if (p.e == 0) {
+                mu_shift = m;
+                sm = sm2 = sv = 0.f;
+            }
+            const float dm = m - mu_shift;
+            sm += dm;
+            sm2 = fmaf(dm, dm, sm2);
+            sv = fmaf(s, s, sv);
+            if (p.e == P.E - 1 && p.cl < P.C) {
+                const float mm = sm * invE;
+                const float mbar = mu_shift + mm;
+                const float sbar = sqrtf(sv * invE + fmaxf(sm2 * invE - mm * mm, 0.f));
+                const int64_t c = P.c0 + p.cl;
+                P.ei[c] = ei_minf(mbar, sbar, P.tau, P.xi);
+                if (P.mu) P.mu[c] = mbar;
+                if (P.sigma) P.sigma[c] = sbar;
+            }
+            return true;
+        };
         uint32_t k = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
@@ -342,6 +386,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     if (lane == 0) mbar_arrive(&sh->h_full[q]);
                     if (q < 3) tmem_wait();
                 }
+                if (has_pend) {
+                    has_pend = false;
+                    if (!combine(pend)) { ok = false; break; }
+                }
                 // ---- layer-2 epilogue and layer 3
                 g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
@@ -373,49 +421,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->z2_empty);
-                float o0 = a0.x + a0.y, o1 = a1.x + a1.y;
-                // ---- combine the column groups; group 0 updates the ensemble state
-                const int par = k & 1;
-                const uint32_t use = (k >> 1) & 1u;
+                const float o0 = a0.x + a0.y, o1 = a1.x + a1.y;
+                // ---- combine the column groups: groups 1..3 hand their sums to group 0 now;
+                // group 0 combines after its next layer-1 epilogue (in the wait for Z2), so
+                // that it starts that epilogue with the other groups
                 if (!owner) {
-                    g = mbar_wait_inl(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
+                    const int par = k & 1;
+                    g = mbar_wait_inl(&sh->part_free[par], ((k >> 1) & 1u) ^ 1u, abort_flag, P.status);
                     if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                     sh->part[par][grp - 1][row] = make_float2(o0, o1);
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->part_ready[par]);
                 } else {
-                    g = mbar_wait_inl(&sh->part_ready[par], use, abort_flag, P.status);
-                    if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
-#pragma unroll
-                    for (int gg = 0; gg < GROUPS - 1; ++gg) {
-                        const float2 p = sh->part[par][gg][row];
-                        o0 += p.x;
-                        o1 += p.y;
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->part_free[par]);
-                    const float m = (o0 + aux[3 * HID]) * P.n1 + P.n0;
-                    const float s = expf((o1 + aux[3 * HID + 1]) * P.n3 + P.n2);
-                    if (e == 0) {
-                        mu_shift = m;
-                        sm = sm2 = sv = 0.f;
-                    }
-                    const float dm = m - mu_shift;
-                    sm += dm;
-                    sm2 = fmaf(dm, dm, sm2);
-                    sv = fmaf(s, s, sv);
-                    if (e == P.E - 1 && cl < P.C) {
-                        const float mm = sm * invE;
-                        const float mbar = mu_shift + mm;
-                        const float sbar = sqrtf(sv * invE + fmaxf(sm2 * invE - mm * mm, 0.f));
-                        const int64_t c = P.c0 + cl;
-                        P.ei[c] = ei_minf(mbar, sbar, P.tau, P.xi);
-                        if (P.mu) P.mu[c] = mbar;
-                        if (P.sigma) P.sigma[c] = sbar;
-                    }
+                    pend = Pending{o0, o1, k, e, cl};
+                    has_pend = true;
                 }
             }
         }
+        if (ok && has_pend) combine(pend);
     }
     tc_fence_before();
     __syncthreads();

@@ -65,8 +65,9 @@ constexpr int DMAX = 31;
 struct alignas(16) Shared {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t z1_full, z2_full, z2_empty;
-    uint64_t h_full[4];
+    uint64_t z1_full;
+    uint64_t h_full;           // the epilogue has read Z1 and written all of H1
+    uint64_t z2_full[2], z2_empty[2];  // per TMEM region
     uint64_t x_full[2], x_empty[2];
     uint64_t part_ready[2], part_free[2];
     uint64_t drain;
@@ -190,9 +191,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             mbar_init(&sh->empty[s], 1);
         }
         mbar_init(&sh->z1_full, 1);
-        mbar_init(&sh->z2_full, 1);
-        mbar_init(&sh->z2_empty, EPI_WARPS);
-        for (int q = 0; q < 4; ++q) mbar_init(&sh->h_full[q], EPI_WARPS);
+        mbar_init(&sh->h_full, EPI_WARPS);
+        for (int r = 0; r < 2; ++r) {
+            mbar_init(&sh->z2_full[r], 1);
+            mbar_init(&sh->z2_empty[r], EPI_WARPS);
+        }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->x_full[b], 1);
             mbar_init(&sh->x_empty[b], 1);
@@ -248,37 +251,43 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             bool ok = true;
             for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x, ++ti) {
                 for (int e = 0; ok && e < P.E; ++e, ++k) {
-                    // layer 1 (Z1 is free: layer 2 of the previous network waited for all of H1)
+                    // Network k holds Z1 and then Z2 in TMEM region k & 1 (256 columns each): layer
+                    // 1 waits until the epilogue has read Z2 of network k - 2 from that region
+                    const uint32_t r = k & 1u;
+                    const uint32_t rk = tmem + r * (uint32_t)HID;
                     const int xb = (int)(ti & 1u);
                     const unsigned char *xt = xs + xb * X_BYTES;
                     if (e == 0 && !mbar_wait_fast(&sh->x_full[xb], (ti >> 1) & 1u, abort_flag, P.status)) { ok = false; break; }
+                    if (k >= 2 && !mbar_wait_fast(&sh->z2_empty[r], ((k >> 1) & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const unsigned char *w0 = wst + (size_t)stage * W_BYTES;
                     for (int kk = 0; kk < P.nk1; ++kk)
-                        mma_f16(tmem, smem_desc(xt + kk * 32), smem_desc(w0 + kk * 32), P.idesc, kk ? 1u : 0u);
+                        mma_f16(rk, smem_desc(xt + kk * 32), smem_desc(w0 + kk * 32), P.idesc, kk ? 1u : 0u);
                     mma_commit(&sh->z1_full);
-                    // layer 2 starts with its bias: Z2 = [1 1] [b2_hi ; b2_lo] (K columns 32..47
-                    // of the x tile and of chunk 0), then accumulates H1 W2 K tile by K tile as H1 fills
-                    if (!mbar_wait_fast(&sh->z2_empty, (k & 1u) ^ 1u, abort_flag, P.status)) { ok = false; break; }
-                    mma_f16(tmem + HID, smem_desc(xt + 64), smem_desc(w0 + 64), P.idesc, 0u);
+                    // layer 2 into the same region once the epilogue has read all of Z1 and written
+                    // H1: first the bias, Z2 = [1 1] [b2_hi ; b2_lo] (K columns 32..47 of the x tile
+                    // and of chunk 0), then H1 W2 K tile by K tile.  These MMAs run while the
+                    // epilogue works on layer 2 of network k - 1.
+                    if (!mbar_wait_fast(&sh->h_full, k & 1u, abort_flag, P.status)) { ok = false; break; }
+                    tc_fence_after();
+                    mma_f16(rk, smem_desc(xt + 64), smem_desc(w0 + 64), P.idesc, 0u);
                     mma_commit(&sh->empty[stage]);
                     if (e == P.E - 1) mma_commit(&sh->x_empty[xb]);  // the tile's last read of its x tile
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     for (int q = 0; q < 4; ++q) {
-                        if (!mbar_wait_fast(&sh->h_full[q], k & 1u, abort_flag, P.status)) { ok = false; break; }
                         if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned char *w = wst + (size_t)stage * W_BYTES;
                         const unsigned char *a = h1 + q * TILE_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_f16(tmem + HID, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc, 1u);
+                            mma_f16(rk, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc, 1u);
                         mma_commit(&sh->empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
-                    mma_commit(&sh->z2_full);
+                    mma_commit(&sh->z2_full[r]);
                 }
             }
             mma_commit(&sh->drain);
@@ -298,6 +307,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         }
     } else {
         // ---------------- epilogue
+        // Per network k: the layer-1 epilogue of k, then the layer-2 epilogue of k - 1 (whose
+        // MMAs ran under the first).
         const int ew = warp - 2;
         const int quad = warp & 3;
         const int grp = ew >> 2;
@@ -306,20 +317,56 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const float invE = 1.0f / (float)P.E;
         float mu_shift = 0.f, sm = 0.f, sm2 = 0.f, sv = 0.f;  // ensemble state (group 0)
-        // group 0: network k's own layer-3 sums, combined during network k + 1
-        struct Pending {
-            float o0, o1;
-            uint32_t k;
-            int e;
-            int64_t cl;
-        };
-        Pending pend{0.f, 0.f, 0u, 0, 0};
-        bool has_pend = false;
-        auto combine = [&](const Pending &p) -> bool {
-            const int par = p.k & 1;
-            const bool got = mbar_wait_inl(&sh->part_ready[par], (p.k >> 1) & 1u, abort_flag, P.status);
+        // layer-2 epilogue, layer 3 and the column-group combine of network kk (network ee of
+        // its tile; ccl: this thread's candidate)
+        auto layer2 = [&](uint32_t kk, int ee, int64_t ccl) -> bool {
+            const uint32_t r = kk & 1u;
+            const bool got = mbar_wait_inl(&sh->z2_full[r], (kk >> 1) & 1u, abort_flag, P.status);
             if (!__all_sync(0xffffffffu, got)) return false;
-            float o0 = p.o0, o1 = p.o1;
+            tc_fence_after();
+            const float *aux = aux_s + ee * AUX;
+            const uint32_t zc = tmem + lane_addr + r * (uint32_t)HID + (uint32_t)(grp * 64);
+            // layer 3 on pairs of hidden units: a0 = (even, odd) partial sums of output 0, a1 of output 1
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            {
+                uint32_t va[16], vb[16];
+                tmem_ld16_nw(zc, va);
+                tmem_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t *cur = (q & 1) ? vb : va;
+                    uint32_t *nxt = (q & 1) ? va : vb;
+                    if (q < 3) tmem_ld16_nw(zc + (uint32_t)((q + 1) * 16), nxt);
+                    pin16(cur);
+                    const int j0 = grp * 64 + q * 16;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        // W3 rows j, j+1 as (w[j][0], w[j+1][0], w[j][1], w[j+1][1])
+                        const float4 wv = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
+                        const float2 h = gelu2_tanh_x2(make_float2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])));
+                        a0 = fma2(h, make_float2(wv.x, wv.y), a0);
+                        a1 = fma2(h, make_float2(wv.z, wv.w), a1);
+                    }
+                    if (q < 3) tmem_wait();
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->z2_empty[r]);
+            float o0 = a0.x + a0.y, o1 = a1.x + a1.y;
+            // groups 1..3 hand their sums to group 0, which updates the ensemble state
+            const int par = kk & 1;
+            const uint32_t use = (kk >> 1) & 1u;
+            if (!owner) {
+                const bool g = mbar_wait_inl(&sh->part_free[par], use ^ 1u, abort_flag, P.status);
+                if (!__all_sync(0xffffffffu, g)) return false;
+                sh->part[par][grp - 1][row] = make_float2(o0, o1);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->part_ready[par]);
+                return true;
+            }
+            const bool g = mbar_wait_inl(&sh->part_ready[par], use, abort_flag, P.status);
+            if (!__all_sync(0xffffffffu, g)) return false;
 #pragma unroll
             for (int gg = 0; gg < GROUPS - 1; ++gg) {
                 const float2 v = sh->part[par][gg][row];
@@ -328,10 +375,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->part_free[par]);
-            const float *aux = aux_s + p.e * AUX;
             const float m = (o0 + aux[3 * HID]) * P.n1 + P.n0;
             const float s = expf((o1 + aux[3 * HID + 1]) * P.n3 + P.n2);
-            if (p.e == 0) {
+            if (ee == 0) {
                 mu_shift = m;
                 sm = sm2 = sv = 0.f;
             }
@@ -339,11 +385,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             sm += dm;
             sm2 = fmaf(dm, dm, sm2);
             sv = fmaf(s, s, sv);
-            if (p.e == P.E - 1 && p.cl < P.C) {
+            if (ee == P.E - 1 && ccl < P.C) {
                 const float mm = sm * invE;
                 const float mbar = mu_shift + mm;
                 const float sbar = sqrtf(sv * invE + fmaxf(sm2 * invE - mm * mm, 0.f));
-                const int64_t c = P.c0 + p.cl;
+                const int64_t c = P.c0 + ccl;
                 P.ei[c] = ei_minf(mbar, sbar, P.tau, P.xi);
                 if (P.mu) P.mu[c] = mbar;
                 if (P.sigma) P.sigma[c] = sbar;
@@ -352,23 +398,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         };
         uint32_t k = 0;
         bool ok = true;
+        bool has_prev = false;  // network k - 1 waits for its layer-2 epilogue
+        int prev_e = 0;
+        int64_t prev_cl = 0;
         for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
             const int64_t cl = (int64_t)t * BM + row;
             for (int e = 0; e < P.E; ++e, ++k) {
-                const float *aux = aux_s + e * AUX;
                 // ---- layer-1 epilogue: H1 = fp16(2 gelu(Z1)), K tile by K tile
-                bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
+                const bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
                 tc_fence_after();
+                const uint32_t z1c = tmem + lane_addr + (k & 1u) * (uint32_t)HID + (uint32_t)(grp * 16);
                 // K tile q's 16 columns are processed while tile q+1's load is in flight
                 uint32_t va[16], vb[16];
-                tmem_ld16_nw(tmem + lane_addr + (uint32_t)(grp * 16), va);
+                tmem_ld16_nw(z1c, va);
                 tmem_wait();
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     uint32_t *cur = (q & 1) ? vb : va;
                     uint32_t *nxt = (q & 1) ? va : vb;
-                    if (q < 3) tmem_ld16_nw(tmem + lane_addr + (uint32_t)((q + 1) * KT + grp * 16), nxt);
+                    if (q < 3) tmem_ld16_nw(z1c + (uint32_t)((q + 1) * KT), nxt);
                     pin16(cur);
                     uint32_t w[8];
 #pragma unroll
@@ -380,65 +429,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     const int j0 = 2 * grp, j1 = 2 * grp + 1;
                     *reinterpret_cast<uint4 *>(dst + ((j0 ^ (row & 7)) * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
                     *reinterpret_cast<uint4 *>(dst + ((j1 ^ (row & 7)) * 16)) = make_uint4(w[4], w[5], w[6], w[7]);
-                    fence_async_smem();
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->h_full[q]);
                     if (q < 3) tmem_wait();
                 }
-                if (has_pend) {
-                    has_pend = false;
-                    if (!combine(pend)) { ok = false; break; }
-                }
-                // ---- layer-2 epilogue and layer 3
-                g = mbar_wait_inl(&sh->z2_full, k & 1u, abort_flag, P.status);
-                if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
-                tc_fence_after();
-                // layer 3 on pairs of hidden units: a0 = (even, odd) partial sums of output 0, a1 of output 1
-                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-                {
-                    uint32_t va[16], vb[16];
-                    tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64), va);
-                    tmem_wait();
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t *cur = (q & 1) ? vb : va;
-                        uint32_t *nxt = (q & 1) ? va : vb;
-                        if (q < 3) tmem_ld16_nw(tmem + lane_addr + (uint32_t)(HID + grp * 64 + (q + 1) * 16), nxt);
-                        pin16(cur);
-                        const int j0 = grp * 64 + q * 16;
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            // W3 rows j, j+1 as (w[j][0], w[j+1][0], w[j][1], w[j+1][1])
-                            const float4 wv = *reinterpret_cast<const float4 *>(aux + HID + 2 * (j0 + j));
-                            const float2 h = gelu2_tanh_x2(make_float2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])));
-                            a0 = fma2(h, make_float2(wv.x, wv.y), a0);
-                            a1 = fma2(h, make_float2(wv.z, wv.w), a1);
-                        }
-                        if (q < 3) tmem_wait();
-                    }
-                }
+                // all of Z1 read (the region takes Z2 next) and all of H1 written
+                fence_async_smem();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->z2_empty);
-                const float o0 = a0.x + a0.y, o1 = a1.x + a1.y;
-                // ---- combine the column groups: groups 1..3 hand their sums to group 0 now;
-                // group 0 combines after its next layer-1 epilogue (in the wait for Z2), so
-                // that it starts that epilogue with the other groups
-                if (!owner) {
-                    const int par = k & 1;
-                    g = mbar_wait_inl(&sh->part_free[par], ((k >> 1) & 1u) ^ 1u, abort_flag, P.status);
-                    if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
-                    sh->part[par][grp - 1][row] = make_float2(o0, o1);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->part_ready[par]);
-                } else {
-                    pend = Pending{o0, o1, k, e, cl};
-                    has_pend = true;
-                }
+                if (lane == 0) mbar_arrive(&sh->h_full);
+                // ---- layer 2 of the previous network, whose MMAs ran under this epilogue
+                if (has_prev && !layer2(k - 1, prev_e, prev_cl)) { ok = false; break; }
+                has_prev = true;
+                prev_e = e;
+                prev_cl = cl;
             }
         }
-        if (ok && has_pend) combine(pend);
+        if (ok && has_prev) layer2(k - 1, prev_e, prev_cl);
     }
     tc_fence_before();
     __syncthreads();

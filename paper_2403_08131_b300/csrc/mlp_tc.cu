@@ -38,6 +38,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace gpbo {
 namespace mtc {
@@ -57,7 +58,9 @@ constexpr int TMEM_COLS = 512;
 constexpr int TILE_BYTES = BM * 128;     // one 128 x 64 BF16 K tile
 constexpr int H1_BYTES = 4 * TILE_BYTES; // 128 x 256
 constexpr int X_BYTES = TILE_BYTES;
-constexpr int W_BYTES = HID * 128;       // one 256 x 64 BF16 chunk
+constexpr int W_BYTES = HID * 128;       // one 256 x 64 FP16 chunk (a stage)
+constexpr int W_HROWS = HID / 2;         // the half of a chunk's rows that each CTA of a pair loads
+constexpr int W_HBYTES = W_BYTES / 2;
 constexpr int AUX = 772;                 // per network FP32: b2 [256], W3 [256 x 2], b3 [2], pad 2
 constexpr int EMAX = 8;                  // networks whose AUX rows stay in shared memory
 constexpr int DMAX = 31;
@@ -85,6 +88,7 @@ struct Params {
     int64_t C;          // candidates
     int64_t c0;         // pool index of the first
     int num_tiles;
+    int num_ptiles;     // pair tiles: tiles 2 pt and 2 pt + 1 (the second past the end when num_tiles is odd)
     int E, d, nk1;      // networks, inputs, layer-1 MMA K steps (16 each)
     uint64_t seed;
     const float *Xc;    // pool-indexed rows of d, or null: drawn from seed (stream 2)
@@ -173,7 +177,8 @@ __device__ __noinline__ void build_x(unsigned char *xs, int r, int64_t t, int64_
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_constant__ CUtensorMap map_w, const Params P)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    k_mlp_screen_tc(const __grid_constant__ CUtensorMap map_w, const Params P)
 {
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -183,12 +188,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     Shared *sh = (Shared *)(wst + (size_t)STAGES * W_BYTES);
     float *aux_s = (float *)(sh + 1);               // E x AUX (16-byte aligned: Shared is)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t rank = cluster_rank();
+    const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
     for (int i = threadIdx.x; i < P.E * AUX; i += blockDim.x) aux_s[i] = P.aux[i];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            mbar_init(&sh->empty[s], 2);  // both CTAs' MMAs are done with the stage
         }
         mbar_init(&sh->z1_full, 1);
         mbar_init(&sh->h_full, EPI_WARPS);
@@ -217,26 +224,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before either signals the other
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort_flag = &sh->abort;
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer: the same chunk sequence for every tile
+            // ---------------- TMA producer: the same chunk sequence for every tile.  The CTAs of
+            // a pair run the same sequence; each loads half of every chunk's rows and multicasts
+            // it to both, so L2 serves each chunk once per pair
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_w) : "memory");
             int stage = 0;
             uint32_t phase = 0;
             uint32_t armed = 0, armed_par = 0;  // bit s: stage s has a copy issued, and its phase
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x)
+            for (int pt = pair; ok && pt < P.num_ptiles; pt += npairs)
                 for (int e = 0; ok && e < P.E; ++e)
                     for (int c = 0; c < CHUNKS; ++c) {
                         if (!mbar_wait_fast(&sh->empty[stage], phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                         mbar_arrive_expect_tx(&sh->full[stage], W_BYTES);
                         armed |= 1u << stage;
                         armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-                        tma_load_2d(wst + (size_t)stage * W_BYTES, &map_w, 0, (e * CHUNKS + c) * HID, &sh->full[stage]);
+                        tma_load_2d_mc(wst + (size_t)stage * W_BYTES + (size_t)rank * W_HBYTES, &map_w, 0,
+                                       (e * CHUNKS + c) * HID + (int)rank * W_HROWS, &sh->full[stage], 3);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
             for (int s = 0; s < STAGES; ++s)
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
             uint32_t phase = 0;
             uint32_t k = 0, ti = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x, ++ti) {
+            for (int pt = pair; ok && pt < P.num_ptiles; pt += npairs, ++ti) {
                 for (int e = 0; ok && e < P.E; ++e, ++k) {
                     // Network k holds Z1 and then Z2 in TMEM region k & 1 (256 columns each): layer
                     // 1 waits until the epilogue has read Z2 of network k - 2 from that region
@@ -272,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
                     if (!mbar_wait_fast(&sh->h_full, k & 1u, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     mma_f16(rk, smem_desc(xt + 64), smem_desc(w0 + 64), P.idesc, 0u);
-                    mma_commit(&sh->empty[stage]);
+                    mma_commit_mc(&sh->empty[stage], 3);
                     if (e == P.E - 1) mma_commit(&sh->x_empty[xb]);  // the tile's last read of its x tile
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     for (int q = 0; q < 4; ++q) {
@@ -283,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
                             mma_f16(rk, smem_desc(a + kk * 32), smem_desc(w + kk * 32), P.idesc, 1u);
-                        mma_commit(&sh->empty[stage]);
+                        mma_commit_mc(&sh->empty[stage], 3);
                         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                     }
                     if (!ok) break;
@@ -296,7 +307,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     } else if (warp == BUILDER_WARP) {
         // ---------------- x tiles, up to one tile ahead of the MMAs (two buffers)
         uint32_t ti = 0;
-        for (int t = blockIdx.x; t < P.num_tiles; t += gridDim.x, ++ti) {
+        for (int pt = pair; pt < P.num_ptiles; pt += npairs, ++ti) {
+            const int64_t t = 2 * (int64_t)pt + rank;
             const int b = (int)(ti & 1u);
             const bool g = mbar_wait_inl(&sh->x_empty[b], ((ti >> 1) & 1u) ^ 1u, abort_flag, P.status);
             if (!__all_sync(0xffffffffu, g)) break;
@@ -401,8 +413,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
         bool has_prev = false;  // network k - 1 waits for its layer-2 epilogue
         int prev_e = 0;
         int64_t prev_cl = 0;
-        for (int t = blockIdx.x; ok && t < P.num_tiles; t += gridDim.x) {
-            const int64_t cl = (int64_t)t * BM + row;
+        for (int pt = pair; ok && pt < P.num_ptiles; pt += npairs) {
+            const int64_t cl = (2 * (int64_t)pt + rank) * BM + row;
             for (int e = 0; e < P.E; ++e, ++k) {
                 // ---- layer-1 epilogue: H1 = fp16(2 gelu(Z1)), K tile by K tile
                 const bool g = mbar_wait_inl(&sh->z1_full, k & 1u, abort_flag, P.status);
@@ -447,6 +459,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_screen_tc(const __grid_const
     }
     tc_fence_before();
     __syncthreads();
+    // neither CTA leaves while the other may still write its stages or signal its barriers
+    cluster_sync();
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -527,11 +541,12 @@ int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, 
     if (cdiv64(C, mtc::BM) > 0x7fffffffll) return GPBO_EINVAL;
     CUtensorMap mw;
     GPBO_TRY(encode_2d(&mw, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, wt, (uint64_t)E * mtc::CHUNKS * mtc::HID, mtc::KT,
-                       mtc::HID));
+                       mtc::W_HROWS));
     mtc::Params P;
     P.C = C;
     P.c0 = c0;
     P.num_tiles = (int)cdiv64(C, mtc::BM);
+    P.num_ptiles = (P.num_tiles + 1) / 2;
     P.E = E;
     P.d = d;
     P.nk1 = (d + 1 + 15) / 16;
@@ -551,7 +566,31 @@ int mlp_tc_score(gpbo_ctx *ctx, const void *wt, const float *aux, int E, int d, 
     P.idesc = tcx::idesc_f16(0u, mtc::HID, mtc::BM);  // FP16 A and B
     const size_t smem = mtc::smem_bytes();
     GPBO_TRY(ensure_smem((const void *)mtc::k_mlp_screen_tc, ctx->device, (int)smem));
-    const int grid = std::min(P.num_tiles, ctx->sm_count);
+    int pairs = 0;
+    {
+        static std::mutex mu;
+        static int cached[64] = {};
+        std::lock_guard<std::mutex> lk(mu);
+        if (ctx->device >= 0 && ctx->device < 64 && cached[ctx->device] > 0) {
+            pairs = cached[ctx->device];
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * (ctx->sm_count / 2));
+            cfg.blockDim = dim3(mtc::THREADS);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            GPBO_CUDA_TRY(cudaOccupancyMaxActiveClusters(&pairs, (const void *)mtc::k_mlp_screen_tc, &cfg));
+            if (pairs < 1) return GPBO_ENOTSUP;
+            if (ctx->device >= 0 && ctx->device < 64) cached[ctx->device] = pairs;
+        }
+    }
+    const int grid = 2 * std::min(P.num_ptiles, pairs);
     mtc::k_mlp_screen_tc<<<grid, mtc::THREADS, smem, ctx->stream>>>(mw, P);
     GPBO_LAUNCH_CHECK(ctx);
     return GPBO_OK;

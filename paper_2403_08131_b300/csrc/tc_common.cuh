@@ -101,6 +101,18 @@ __device__ __forceinline__ bool mbar_wait_fast(uint64_t *bar, uint32_t parity, v
     return mbar_wait(bar, parity, abort_flag, status, honour_abort);
 }
 
+// The same, multicast: the box lands at dst's offset in every CTA of `mask` (this GPU's own
+// memory only), and each of them counts its bytes on the mbarrier at bar's offset.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
     asm volatile(
@@ -342,6 +354,16 @@ __device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t a, uint64
 __device__ __forceinline__ void mma_commit_pair(uint64_t *bar, uint16_t mask)
 {
     asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+
+// Arrive on the mbarrier at this offset in each CTA of `mask` once the (one-CTA) MMAs issued so
+// far by this thread are complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
                      smem_u32(bar)),
                  "h"(mask)
                  : "memory");

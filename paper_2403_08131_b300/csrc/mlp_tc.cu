@@ -16,20 +16,24 @@
 // compute h' = z (1 + t) = 2 gelu(z) with one FMA.  FP16 rather than BF16 operands: the same
 // tensor rate, 11 significant bits instead of 8.
 //
-// Roles (one CTA per SM, persistent over tiles; 608 threads):
-//   warp 0      TMA: per network, [W1 ; b1 | b2 split]^T (256 x 64, zero padded) then W2^T in
-//               four 256 x 64 K chunks; 3 stages of 32 KiB (the first chunk's stage is held
-//               until layer 2's bias MMA).  The packed ensemble (8 networks, 1.3 MB) is read
-//               from L2 for every tile; W3 and b3 of every network (E <= 8) stay in shared memory.
-//   warp 1      TMEM (512 columns: Z1 in 0..255, Z2 in 256..511); one lane issues the MMAs
+// Roles (clusters of two CTAs, one CTA per SM, persistent over pairs of tiles; 608 threads):
+//   warp 0      TMA: per network, [W1 ; b1 ; b2 split]^T (256 x 64, zero padded) then W2^T in
+//               four 256 x 64 K chunks, through 3 stages of 32 KiB (the first chunk's stage is
+//               held until layer 2's bias MMA).  Each CTA of a pair loads half of every chunk's
+//               rows and multicasts it to both, and a stage is refilled once both CTAs' MMAs
+//               are done with it, so L2 serves each chunk once per pair.  The packed ensemble
+//               (8 networks, 1.3 MB) is read from L2 for every pair of tiles; W3 and b3 of
+//               every network (E <= 8) stay in shared memory.
+//   warp 1      TMEM (512 columns): network k keeps Z1 and then Z2 in region k mod 2 (256
+//               columns each); one lane issues the MMAs
 //   warps 2-17  epilogue: warp w reads TMEM lane quadrant w % 4 and column group (w-2) / 4;
 //               warps 2-5 (group 0) also own the ensemble state of their rows (one thread =
 //               one candidate)
 //   warp 18     builds the x tiles (four rows a lane) into two buffers, up to one tile ahead:
 //               the counter-RNG draws stay off the epilogue's path
-// H1 is written K tile by K tile (every warp does its 16 columns of tile q, then of q+1), and
-// the second layer's MMAs on K tile q start once tile q is complete, so layer 2 runs under
-// the first-layer epilogue; layer 1 of the next network runs under the second-layer one.
+// Per network k the epilogue writes H1 from Z1(k), then runs layer 2 of network k - 1: layer
+// 2's MMAs of network k (into region k mod 2, once Z1(k) is read) run under that second part,
+// and layer 1 of network k + 1 waits only for region (k + 1) mod 2, which Z2(k - 1) frees.
 // Every wait is bounded (about 2 s of SM clock); on timeout the kernel raises DEV_TIMEOUT,
 // every role leaves its loop, the producer waits (bounded) for its copies in flight, the MMA
 // issuer drains, and the allocating warp frees TMEM.

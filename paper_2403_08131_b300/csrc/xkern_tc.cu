@@ -117,6 +117,19 @@ __device__ __forceinline__ float matern_folded(float r2, float s2, float c1, flo
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-3.2259460f * r));  // -sqrt5 / ln 2
     return fmaf(c2, r2, fmaf(c1, r, s2)) * e;
 }
+// The same for two squared distances, the FP32 arithmetic on paired lanes (each lane's result
+// is the scalar form's, bit for bit).
+__device__ __forceinline__ float2 matern_folded2(float2 r2, float s2, float c1, float c2)
+{
+    float2 r, e;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(r2.x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(r2.y));
+    const float2 a = mul2(make_float2(-3.2259460f, -3.2259460f), r);  // -sqrt5 / ln 2
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(a.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(a.y));
+    const float2 p = fma2(make_float2(c2, c2), r2, fma2(make_float2(c1, c1), r, make_float2(s2, s2)));
+    return mul2(p, e);
+}
 
 // Build A' row `r` of tile `t` into slot base `a` (128B-swizzled K-major, two 64-column tiles).
 __device__ __forceinline__ float build_row(unsigned char *a, int r, int64_t t, const Params &P)
@@ -315,7 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
             if (lane == 0) mbar_arrive(&sh->a_empty[slot]);
             const int64_t cl = (int64_t)t * BM + row;
             const int64_t row0 = (int64_t)t * BM + quad * 32;  // the warp's first row
-            float mu = 0.0f;
+            float2 mu2 = make_float2(0.0f, 0.0f);  // mu as even- and odd-observation partial sums
             for (int q = 0; q < nq; ++q) {
                 const bool g = mbar_wait_inl(&sh->acc_full[acc], acc_phase, abort_flag, P.status);
                 if (!__all_sync(0xffffffffu, g)) { ok = false; break; }
@@ -332,13 +345,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                                                      : *reinterpret_cast<const float4 *>(P.alpha + i0 + j);
                         // padded observations: alpha = 0 and the 16-bit L^-1 rows are zero there,
                         // so their (finite) K* values never reach mu or sigma
-                        const float k0 = matern_folded(fmaxf(v[j] + na, 0.0f), s2, c1, c2);
-                        const float k1 = matern_folded(fmaxf(v[j + 1] + na, 0.0f), s2, c1, c2);
-                        const float k2 = matern_folded(fmaxf(v[j + 2] + na, 0.0f), s2, c1, c2);
-                        const float k3 = matern_folded(fmaxf(v[j + 3] + na, 0.0f), s2, c1, c2);
-                        mu = fmaf(k0, al.x, fmaf(k1, al.y, fmaf(k2, al.z, fmaf(k3, al.w, mu))));
-                        pk[j / 2] = Pack8<Out>::two(k0, k1);
-                        pk[j / 2 + 1] = Pack8<Out>::two(k2, k3);
+                        const float2 d01 = add2(make_float2(v[j], v[j + 1]), make_float2(na, na));
+                        const float2 d23 = add2(make_float2(v[j + 2], v[j + 3]), make_float2(na, na));
+                        const float2 k01 = matern_folded2(make_float2(fmaxf(d01.x, 0.0f), fmaxf(d01.y, 0.0f)), s2, c1, c2);
+                        const float2 k23 = matern_folded2(make_float2(fmaxf(d23.x, 0.0f), fmaxf(d23.y, 0.0f)), s2, c1, c2);
+                        mu2 = fma2(k01, make_float2(al.x, al.y), mu2);
+                        mu2 = fma2(k23, make_float2(al.z, al.w), mu2);
+                        pk[j / 2] = Pack8<Out>::two(k01.x, k01.y);
+                        pk[j / 2 + 1] = Pack8<Out>::two(k23.x, k23.y);
                     }
                     // K* out: each lane writes its row's 64 bytes into the warp's staging tile
                     // (once the previous tile's TMA store has read it), one lane stores the
@@ -363,6 +377,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_xkern_tc(const __grid_constant__
                 if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
             }
             if (!ok) break;
+            const float mu = mu2.x + mu2.y;
             // combine the column groups' partial means (group 0 writes the result)
             const uint32_t use = (uint32_t)(k >> 1) & 1u;
             if (!builder) {

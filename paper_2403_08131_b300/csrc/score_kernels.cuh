@@ -379,11 +379,13 @@ __device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, in
     for (int u = 0; u < TM; ++u) sig2[u] = 0.f;
     int buf = 0;
     for (int i0 = 0, q = 0; i0 < n_pad; i0 += BN, ++q) {
-        float acc[TM][8];
+        // acc[u2][v] = the products of candidates 2 u2 and 2 u2 + 1 with row v, on paired FP32
+        // lanes: each lane runs the scalar FMA sequence, so the sums are those of one lane each
+        float2 acc[TM / 2][8];
 #pragma unroll
-        for (int u = 0; u < TM; ++u)
+        for (int u = 0; u < TM / 2; ++u)
 #pragma unroll
-            for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+            for (int v = 0; v < 8; ++v) acc[u][v] = make_float2(0.f, 0.f);
         const int ksteps = (min(i0 + BN, n_pad) + BK - 1) / BK;
         const bool down = (q & 1) != 0;
         fetch(down ? (ksteps - 1) * BK : 0, i0);
@@ -409,18 +411,24 @@ __device__ __forceinline__ void k_var_f32_body(const float *__restrict__ Kst, in
                 b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
                 b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
 #pragma unroll
-                for (int u = 0; u < TM; ++u)
+                for (int v = 0; v < 8; ++v) {
+                    const float2 bb = make_float2(b[v], b[v]);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+                    for (int u = 0; u < TM / 2; ++u) acc[u][v] = fma2(make_float2(a[2 * u], a[2 * u + 1]), bb, acc[u][v]);
+                }
             }
             if (more) stash(buf ^ 1);
             __syncthreads();
             buf ^= 1;
         }
 #pragma unroll
-        for (int u = 0; u < TM; ++u)
+        for (int u = 0; u < TM / 2; ++u) {
+            float2 s = make_float2(sig2[2 * u], sig2[2 * u + 1]);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) sig2[u] = fmaf(acc[u][v], acc[u][v], sig2[u]);
+            for (int v = 0; v < 8; ++v) s = fma2(acc[u][v], acc[u][v], s);
+            sig2[2 * u] = s.x;
+            sig2[2 * u + 1] = s.y;
+        }
     }
 #pragma unroll
     for (int u = 0; u < TM; ++u)

@@ -451,9 +451,9 @@ def run_ours(args, rank, world, local):
             return e
 
         var_kernel = "k_var_ei_tc" if args.prec != "f32" else "k_var_simt"
-        # DRAM bytes of k_var_ei_tc from the ncu capture of 65536 candidates (18.2 KB per candidate),
+        # DRAM bytes of k_var_ei_tc from the ncu capture of 65536 candidates (17.7 KB per candidate),
         # scaled to one launch of this run (131072 candidates per chunk)
-        var_traffic = round(1.1952e9 / 65536 * 131072) if args.prec == "f16" else None
+        var_traffic = round(1.1585e9 / 65536 * 131072) if args.prec == "f16" else None
         if args.prec != "f32":
             rl = [entry("variance", var_kernel, "tensor", tensor_burst, burst_src, var_traffic)]
         else:

@@ -195,14 +195,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int t = pair; ok && t < P.num_tiles; t += npairs) {
                 for (int q = 0; ok && q < nq; ++q) {
-                    if (!mbar_wait_cluster(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
+                    // CTA-scope acquire on the barriers that the second CTA signals: a cluster-scope
+                    // poll costs about as much as a K step's MMAs, and each signal covers work that
+                    // the signalling CTA completed on its own side (its TMEM reads; its copies, which
+                    // its own wait saw land) before signalling
+                    if (!mbar_wait_fast(&sh->acc_empty[acc], acc_phase ^ 1u, abort_flag, P.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
                     const int ksteps = (q + 1) * (BN / BK) * passes;
                     for (int ks = 0; ks < ksteps; ++ks) {
                         if (!mbar_wait_fast(&sh->full[stage], phase, abort_flag, P.status)) { ok = false; break; }
-                        if (!mbar_try_cluster(&sh->pfull[stage], phase) &&
-                            !mbar_wait_cluster(&sh->pfull[stage], phase, abort_flag, P.status)) { ok = false; break; }
+                        if (!mbar_wait_fast(&sh->pfull[stage], phase, abort_flag, P.status)) { ok = false; break; }
                         tc_fence_after();
                         const unsigned char *a = tiles + (size_t)stage * STAGE_BYTES;
                         const unsigned char *b = a + A_BYTES;

@@ -162,6 +162,24 @@ def test_tc_forward_matches_oracle_within_f16_tolerance(ctx, orc, M):
     assert np.max(np.abs(fm - rm) / (np.abs(rm) + 1)) <= 1e-4 and np.max(np.abs(fs - rs) / rs) <= 1e-4
 
 
+@pytest.mark.parametrize("E,d,M", [(1, 7, 60013), (3, 31, 57000), (5, 20, 40129)])
+def test_tc_forward_many_tiles_per_cta(ctx, orc, E, d, M):
+    """Several tiles per CTA pair (M / 256 pair tiles over at most 74 pairs), so that the
+    per-network TMEM regions, the barrier phases and the one-network-behind layer 2 cross tile
+    boundaries: a single network, odd ensembles, a one-step (d = 7) and a full (d = 31) layer-1
+    K width, ragged tails.  The tensor-core outputs against the FP64 oracle within the FP16
+    tolerance."""
+    import torch
+    H = 256
+    net = _net(ctx, E, d, H, seed=20 + E)
+    th = _rand_biases(net, d, H, 30 + E)
+    X = np.random.default_rng(M).random((M, d)).astype(np.float32)
+    ei, mu, sg = (torch.empty(M, dtype=torch.float32, device="cuda") for _ in range(3))
+    net.score(ei, X=to_dev(X), y_best=0.1, prec="f16", mu=mu, sigma=sg)
+    r = _check_tc(orc, th, X, ei, mu, sg, (0.0, 1.0, 0.0, 1.0), 0.1, d, H)
+    print(f"E={E} d={d} M={M}: worst error / tolerance (mu_bar, sigma_bar, ei) = {r[0]:.3f}, {r[1]:.3f}, {r[2]:.3f}")
+
+
 def test_tc_trained_ensemble_seeded_equals_explicit(ctx, orc, trained):
     """Trained 8-member ensemble: seeded candidates equal the same rows passed explicitly
     (bit for bit), and both agree with the oracle within the FP16 tolerance."""

@@ -48,6 +48,7 @@ int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
             GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
             if (ctx->side) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side));
             if (ctx->side2) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side2));
+            if (ctx->side3) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side3));
             GPBO_CUDA_TRY(cudaFree(ctx->ws));
             ctx->ws = nullptr;
             ctx->ws_size = 0;
@@ -66,6 +67,7 @@ int side_stream(gpbo_ctx *ctx, cudaStream_t *out)
         GPBO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, hi));
+        GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side3, cudaStreamNonBlocking, lo));
         for (cudaEvent_t &e : ctx->side_ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     *out = ctx->side;
@@ -325,6 +327,10 @@ int gpbo_destroy(gpbo_ctx *ctx)
     if (ctx->side2) {
         cudaStreamSynchronize(ctx->side2);
         cudaStreamDestroy(ctx->side2);
+    }
+    if (ctx->side3) {
+        cudaStreamSynchronize(ctx->side3);
+        cudaStreamDestroy(ctx->side3);
     }
     for (cudaEvent_t e : ctx->side_ev)
         if (e) cudaEventDestroy(e);

@@ -7,7 +7,9 @@
 //   K      = L L^T                      k_chol_*          (blocked, right-looking, NB = 64,
 //                                                          lookahead of one block column)
 //   alpha  = L^-T L^-1 y, refined once  k_fwd_wave/k_bwd_wave/k_residual (one launch per substitution)
-//   L^-1                                k_gemm_batched, k_gemm128 (level-by-level block recursion)
+//   L^-1                                k_gemm_batched, k_gemm128, tensor-core slice products
+//                                       (level-by-level block recursion; for large models the
+//                                       leading half under the factorisation's last steps)
 //
 // Padding: n is padded to n_pad (a multiple of 64, or of 256 for tensor-core models).
 // Padded rows/columns of K are the identity, so L and L^-1 are the identity there, the
@@ -295,6 +297,43 @@ __global__ void k_cast(const Tin *__restrict__ in, int64_t count, Tout *__restri
     k_cast_body<Tin, Tout>(in, count, out, blockIdx.x, blockIdx.y);
 }
 
+// The column band [c0, c1) of a block lower triangular n_pad x n_pad matrix in another type,
+// with the blocks above the block diagonal written as zeros (they are not read).
+template <typename Tin, typename Tout>
+__global__ void k_cast_cols(const Tin *__restrict__ in, int n_pad, int c0, int c1, Tout *__restrict__ out)
+{
+    const int w = c1 - c0;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_pad * w) return;
+    const int i = (int)(t / w), j = c0 + (int)(t % w);
+    const int64_t o = (int64_t)i * n_pad + j;
+    out[o] = j / NB > i / NB ? Tout(0) : convert_to<Tout>((double)in[o]);
+}
+
+// Linv's start for the inverse in two halves: part 1 writes every element except the diagonal
+// blocks from b_split on (zeros, and the inverses of blocks 0 .. b_split - 1 from Dinv); part 2
+// writes those remaining diagonal blocks.
+template <typename T>
+__global__ void k_linv_init_part(const double *__restrict__ Dinv, int n_pad, T *__restrict__ Linv, int b_split, int part)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (part == 2) {
+        const int64_t per = (int64_t)NB * NB;
+        if (t >= (int64_t)(n_pad / NB - b_split) * per) return;
+        const int b = b_split + (int)(t / per), r = (int)(t % per / NB), c = (int)(t % NB);
+        Linv[(int64_t)(b * NB + r) * n_pad + b * NB + c] = (T)Dinv[b * per + r * NB + c];
+        return;
+    }
+    if (t >= (int64_t)n_pad * n_pad) return;
+    const int i = (int)(t / n_pad), j = (int)(t % n_pad), b = i / NB;
+    if (b == j / NB) {
+        if (b >= b_split) return;
+        Linv[t] = (T)Dinv[(int64_t)b * NB * NB + (i % NB) * NB + (j % NB)];
+    } else {
+        Linv[t] = T(0);
+    }
+}
+
 __global__ void k_split_bf16(const float *__restrict__ in, int64_t count, __nv_bfloat16 *__restrict__ hi,
                              __nv_bfloat16 *__restrict__ lo)
 {
@@ -386,53 +425,88 @@ static size_t trtri_tc_scratch(int n_pad, bool f64)
     return b;
 }
 
+// part 0: every level on stream s.  With n_pad / NB a power of two, part 1 takes the pairs
+// inside the leading half (rows < n_pad / 2) and the top level's T = L21 X11, which need only
+// the leading half of L (final once block column n_pad / (2 NB) - 1 is), and part 2 the rest:
+// the trailing half's pairs and the top level's X21 = -X22 T.  The parts write disjoint
+// regions of tmp and Linv, and each problem gets the arithmetic it gets in part 0.
 template <typename T>
-static int trtri_levels(gpbo_ctx *ctx, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev,
-                        void *tc_scratch = nullptr)
+static int trtri_levels(gpbo_ctx *ctx, cudaStream_t s, const T *Ls, T *Linv, T *tmp, int n_pad, GemmProb *probs_dev,
+                        void *tc_scratch = nullptr, int part = 0)
 {
-    std::vector<GemmProb> probs;
-    std::vector<int> first, count;
+    std::vector<GemmProb> plan;
+    std::vector<int> first0, count0;
     std::vector<int2> mm;
-    trtri_plan(n_pad, probs, first, count, mm);
+    trtri_plan(n_pad, plan, first0, count0, mm);
+    if (plan.empty()) return GPBO_OK;
+    // each level's problems for this part: its T = L21 X11 products, then its X21 = -X22 T
+    const int64_t half = n_pad / 2;
+    std::vector<GemmProb> probs;
+    std::vector<int> first(first0.size()), count(first0.size()), count2(first0.size());
+    for (size_t l = 0; l < first0.size(); ++l) {
+        std::vector<GemmProb> g1, g2;
+        for (int q = 0; q < count0[l]; ++q) {
+            const GemmProb &p1 = plan[first0[l] + q], &p2 = plan[first0[l] + count0[l] + q];
+            const int64_t r0 = p1.c_off / n_pad;                // first row of the pair's lower block
+            const bool lead = r0 + p1.m <= half;                // the pair lies in the leading half
+            const bool top = r0 == half && p1.c_off % n_pad == 0 && (int64_t)p1.n == half;
+            if (part == 0 || (part == 1) == (lead || top)) g1.push_back(p1);
+            if (part == 0 || (part == 1) == lead) g2.push_back(p2);
+        }
+        first[l] = (int)probs.size();
+        count[l] = (int)g1.size();
+        count2[l] = (int)g2.size();
+        probs.insert(probs.end(), g1.begin(), g1.end());
+        probs.insert(probs.end(), g2.begin(), g2.end());
+    }
     if (probs.empty()) return GPBO_OK;
     // the host vector dies at return: copy synchronously with respect to it (pageable memory)
-    GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, probs.data(), sizeof(GemmProb) * probs.size(), cudaMemcpyHostToDevice,
-                                  ctx->stream));
+    GPBO_CUDA_TRY(cudaMemcpyAsync(probs_dev, probs.data(), sizeof(GemmProb) * probs.size(), cudaMemcpyHostToDevice, s));
     for (size_t l = 0; l < first.size(); ++l) {
+        const int c1 = count[l], c2 = count2[l];
+        const int f1 = first[l], f2 = first[l] + c1;
         if (std::is_same<T, double>::value && tc_scratch && mm[l].y >= TRTRI_TC_MIN) {
             // T = L21 X11 (X11 lower), then X21 = -X22 T (X22 lower)
-            GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Ls, (const double *)Linv, (double *)tmp, n_pad,
-                                    probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
-            GPBO_TRY(dgemm_tc_level(ctx, ctx->stream, (const double *)Linv, (const double *)tmp, (double *)Linv, n_pad,
-                                    probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
+            GPBO_TRY(dgemm_tc_level(ctx, s, (const double *)Ls, (const double *)Linv, (double *)tmp, n_pad,
+                                    probs.data() + f1, c1, 1.0, 1, tc_scratch));
+            GPBO_TRY(dgemm_tc_level(ctx, s, (const double *)Linv, (const double *)tmp, (double *)Linv, n_pad,
+                                    probs.data() + f2, c2, -1.0, 2, tc_scratch));
             continue;
         }
         if (std::is_same<T, float>::value && tc_scratch && mm[l].y >= trtri_tc_min(n_pad, false)) {
             // FP32 accuracy from three slices: T = L21 X11 (X11 lower), then X21 = -X22 T
-            GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Ls, (const float *)Linv, (float *)tmp, n_pad,
-                                    probs.data() + first[l], count[l], 1.0, 1, tc_scratch));
-            GPBO_TRY(sgemm_tc_level(ctx, ctx->stream, (const float *)Linv, (const float *)tmp, (float *)Linv, n_pad,
-                                    probs.data() + first[l] + count[l], count[l], -1.0, 2, tc_scratch));
+            GPBO_TRY(sgemm_tc_level(ctx, s, (const float *)Ls, (const float *)Linv, (float *)tmp, n_pad,
+                                    probs.data() + f1, c1, 1.0, 1, tc_scratch));
+            GPBO_TRY(sgemm_tc_level(ctx, s, (const float *)Linv, (const float *)tmp, (float *)Linv, n_pad,
+                                    probs.data() + f2, c2, -1.0, 2, tc_scratch));
             continue;
         }
         if (std::is_same<T, float>::value && mm[l].y >= 128) {
             // large FP32 levels: 128 x 128 tiles (the batched step uses the same rule per level)
-            dim3 grid((mm[l].y + 127) / 128, (mm[l].x + 127) / 128, count[l]);
-            k_gemm128<<<grid, 256, 0, ctx->stream>>>((const float *)Ls, (const float *)Linv, (float *)tmp,
-                                                     probs_dev + first[l], 1.0f, 0, 1);
-            GPBO_LAUNCH_CHECK(ctx);
-            k_gemm128<<<grid, 256, 0, ctx->stream>>>((const float *)Linv, (const float *)tmp, (float *)Linv,
-                                                     probs_dev + first[l] + count[l], -1.0f, 1, 0);
-            GPBO_LAUNCH_CHECK(ctx);
+            if (c1) {
+                dim3 grid((mm[l].y + 127) / 128, (mm[l].x + 127) / 128, c1);
+                k_gemm128<<<grid, 256, 0, s>>>((const float *)Ls, (const float *)Linv, (float *)tmp, probs_dev + f1, 1.0f,
+                                               0, 1);
+                GPBO_LAUNCH_CHECK(ctx);
+            }
+            if (c2) {
+                dim3 grid((mm[l].y + 127) / 128, (mm[l].x + 127) / 128, c2);
+                k_gemm128<<<grid, 256, 0, s>>>((const float *)Linv, (const float *)tmp, (float *)Linv, probs_dev + f2,
+                                               -1.0f, 1, 0);
+                GPBO_LAUNCH_CHECK(ctx);
+            }
             continue;
         }
-        dim3 grid((mm[l].y + 63) / 64, (mm[l].x + 63) / 64, count[l]);
-        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Ls, Linv, tmp, n_pad, n_pad, n_pad, probs_dev + first[l],
-                                                         T(1), 0, 1);
-        GPBO_LAUNCH_CHECK(ctx);
-        k_gemm_batched<T><<<grid, 256, 0, ctx->stream>>>(Linv, tmp, Linv, n_pad, n_pad, n_pad,
-                                                         probs_dev + first[l] + count[l], T(-1), 1, 0);
-        GPBO_LAUNCH_CHECK(ctx);
+        if (c1) {
+            dim3 grid((mm[l].y + 63) / 64, (mm[l].x + 63) / 64, c1);
+            k_gemm_batched<T><<<grid, 256, 0, s>>>(Ls, Linv, tmp, n_pad, n_pad, n_pad, probs_dev + f1, T(1), 0, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+        }
+        if (c2) {
+            dim3 grid((mm[l].y + 63) / 64, (mm[l].x + 63) / 64, c2);
+            k_gemm_batched<T><<<grid, 256, 0, s>>>(Linv, tmp, Linv, n_pad, n_pad, n_pad, probs_dev + f2, T(-1), 1, 0);
+            GPBO_LAUNCH_CHECK(ctx);
+        }
     }
     return GPBO_OK;
 }
@@ -481,6 +555,24 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     // the factorisation works in L (k_kmat_fixed writes its lower triangle with K)
     if (!m->xmax) GPBO_CUDA_TRY(cudaMemcpyAsync(m->L, m->K, sizeof(double) * n_pad * n_pad, cudaMemcpyDeviceToDevice, st));
     const size_t smem2 = sizeof(double) * 2 * NB * (NB + 1), smem1 = sizeof(double) * NB * (NB + 1);
+    // One workspace reservation, before any launch on the side streams, for the solve and the
+    // inverse (they run concurrently).
+    const int max_probs = 2 * nblk + 2;
+    const int64_t sq = (int64_t)n_pad * n_pad;
+    const size_t vec = sizeof(double) * n_pad;
+    const bool f64 = m->prec == GPBO_PREC_F64;
+    const size_t tc_bytes = n_pad >= 2 * trtri_tc_min(n_pad, f64) ? trtri_tc_scratch(n_pad, f64) : 0;
+    const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
+                             sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
+    const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
+    const int chunks = (n_pad + TRMV_ROWS - 1) / TRMV_ROWS;
+    void *wsp = nullptr;
+    GPBO_TRY(ws_reserve(ctx, vec * (6 + chunks) + sync_bytes + inv_bytes, &wsp));
+    double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *u = r + n_pad;
+    double *part = ypad + 6 * (int64_t)n_pad;
+    int *sync = (int *)((char *)wsp + vec * (6 + chunks));
+    void *w2 = (void *)((char *)wsp + vec * (6 + chunks) + sync_bytes);
+
     // Right-looking blocked factorisation with a lookahead of one block column.  The chain that
     // every step waits on runs on the high-priority side stream and holds only 64 x 64 blocks:
     // the panel's first block row L_{kb+1,kb}, the update of diagonal block kb+1 by it, the
@@ -509,6 +601,50 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         k_chol_inv<<<NB / INV_WARPS, 32 * INV_WARPS, 0, side2>>>(m->L, n_pad, jb, m->Dinv);
         GPBO_LAUNCH_CHECK(ctx);
         GPBO_CUDA_TRY(cudaEventRecord(ev_inv, side2));
+        return GPBO_OK;
+    };
+    // The inverse L^-1 in two halves where n_pad / NB is a power of two (at least 4): once
+    // block column nblk / 2 - 1 is final, the leading half of L is, and a third stream takes
+    // the inverse's work that needs nothing else (the leading half's doubling levels and the
+    // top level's T = L21 X11) under the factorisation's remaining steps.  Its kernels share
+    // the SMs with the factorisation's (stream priority does not preempt), so they start where
+    // that cost least as measured (fit times at n = 2048, 4096, 8192): the FP64 inverse, and the
+    // FP32 one below 64 blocks, right after block column nblk / 2 - 1; the FP32 one from 64
+    // blocks with an eighth of the factorisation left, where its steps leave most SMs idle.
+    const bool split_inv = large && nblk >= 4 && (nblk & (nblk - 1)) == 0;
+    const int lead_kb = !f64 && nblk >= 64 ? 7 * nblk / 8 - 1 : nblk / 2 - 1;
+    cudaEvent_t ev_half = ctx->side_ev[8], ev_lead = ctx->side_ev[9];
+    GemmProb *probs = nullptr;
+    void *tcs = nullptr;
+    double *tmp64 = nullptr;
+    float *L32 = nullptr, *tmp32 = nullptr;
+    if (f64) {
+        tmp64 = (double *)w2;
+        probs = (GemmProb *)(tmp64 + sq);
+    } else {
+        L32 = (float *)w2;
+        tmp32 = L32 + sq;
+        probs = (GemmProb *)(tmp32 + sq);
+    }
+    if (tc_bytes) tcs = (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255);
+    auto inverse_lead = [&]() -> int {
+        cudaStream_t s3 = ctx->side3;
+        const int hb = nblk / 2;
+        GPBO_CUDA_TRY(cudaEventRecord(ev_half, st));
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(s3, ev_half, 0));
+        if (f64) {
+            k_linv_init_part<double><<<blocks_for(sq), 256, 0, s3>>>(m->Dinv, n_pad, m->Linv64, hb, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<double>(ctx, s3, m->L, m->Linv64, tmp64, n_pad, probs, tcs, 1));
+        } else {
+            k_cast_cols<double, float><<<blocks_for((int64_t)n_pad * hb * NB), 256, 0, s3>>>(m->L, n_pad, 0, hb * NB,
+                                                                                             L32);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_linv_init_part<float><<<blocks_for(sq), 256, 0, s3>>>(m->Dinv, n_pad, m->Linv32, hb, 1);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<float>(ctx, s3, L32, m->Linv32, tmp32, n_pad, probs, tcs, 1));
+        }
+        GPBO_CUDA_TRY(cudaEventRecord(ev_lead, s3));
         return GPBO_OK;
     };
     if (large) GPBO_TRY(inverse_on_side2(0));
@@ -556,6 +692,7 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
             else
                 k_chol_panel<<<(T - 1) * (NB / 4), 128, 0, st>>>(m->L, n_pad, kb, m->Dinv, 1);
             GPBO_LAUNCH_CHECK(ctx);
+            if (split_inv && kb == lead_kb) GPBO_TRY(inverse_lead());  // block columns 0 .. nblk / 2 - 1 are final
             if (!tc_col) {
                 k_chol_update_slab<<<(T - 1) * (NB / SLAB_ROWS), 256, 0, st>>>(m->L, n_pad, kb, 1, 1);
                 GPBO_LAUNCH_CHECK(ctx);
@@ -590,22 +727,6 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
     // A pivot that was not positive is reported by the status check at the end (the factor
     // carries on with 1 in its place, so what follows stays finite): no host round trip here.
 
-    // One workspace reservation for both branches below (they run concurrently).
-    const int max_probs = 2 * nblk + 2;
-    const int64_t sq = (int64_t)n_pad * n_pad;
-    const size_t vec = sizeof(double) * n_pad;
-    const bool f64 = m->prec == GPBO_PREC_F64;
-    const size_t tc_bytes = n_pad >= 2 * trtri_tc_min(n_pad, f64) ? trtri_tc_scratch(n_pad, f64) : 0;
-    const size_t inv_bytes = (m->prec == GPBO_PREC_F64 ? sizeof(double) * sq : sizeof(float) * 2 * sq) +
-                             sizeof(GemmProb) * 2 * max_probs + tc_bytes + 256;
-    const size_t sync_bytes = round_up64(sizeof(int) * (2 * (int64_t)nblk + 2), 256);
-    const int chunks = (n_pad + TRMV_ROWS - 1) / TRMV_ROWS;
-    void *wsp = nullptr;
-    GPBO_TRY(ws_reserve(ctx, vec * (6 + chunks) + sync_bytes + inv_bytes, &wsp));
-    double *ypad = (double *)wsp, *work = ypad + n_pad, *r = work + 2 * n_pad, *u = r + n_pad;
-    double *part = ypad + 6 * (int64_t)n_pad;
-    int *sync = (int *)((char *)wsp + vec * (6 + chunks));
-    void *w2 = (void *)((char *)wsp + vec * (6 + chunks) + sync_bytes);
 
     // alpha = K^-1 y with one step of iterative refinement, on the side stream: the FP64 solve
     // (latency-bound substitutions, beside the L^-1 products on the main stream) and the FP64
@@ -634,25 +755,38 @@ int fit_model(gpbo_ctx *ctx, gp_model *m, const double *X_dev, const double *y_d
         return GPBO_OK;
     };
 
-    // L^-1 for scoring
-    GemmProb *probs = nullptr;
+    // L^-1 for scoring (the trailing half where the leading one ran under the factorisation:
+    // its own problem list, so the two never share one)
+    const int hb = nblk / 2;
+    if (split_inv) GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_lead, 0));
     if (m->prec == GPBO_PREC_F64) {
-        double *tmp = (double *)w2;
-        probs = (GemmProb *)(tmp + sq);
-        k_linv_init<double><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv64);
-        GPBO_LAUNCH_CHECK(ctx);
-        void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
-        GPBO_TRY(trtri_levels<double>(ctx, m->L, m->Linv64, tmp, n_pad, probs, tcs));
+        if (split_inv) {
+            k_linv_init_part<double><<<blocks_for((int64_t)(nblk - hb) * NB * NB), 256, 0, st>>>(m->Dinv, n_pad,
+                                                                                                m->Linv64, hb, 2);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<double>(ctx, st, m->L, m->Linv64, tmp64, n_pad, probs + max_probs, tcs, 2));
+        } else {
+            k_linv_init<double><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv64);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<double>(ctx, st, m->L, m->Linv64, tmp64, n_pad, probs, tcs));
+        }
         GPBO_TRY(correction(m->Linv64));
     } else {
-        float *L32 = (float *)w2, *tmp = L32 + sq;
-        probs = (GemmProb *)(tmp + sq);
-        k_cast<double, float><<<blocks_for(sq), 256, 0, st>>>(m->L, sq, L32);
-        GPBO_LAUNCH_CHECK(ctx);
-        k_linv_init<float><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv32);
-        GPBO_LAUNCH_CHECK(ctx);
-        void *tcs = tc_bytes ? (void *)(((uintptr_t)(probs + 2 * max_probs) + 255) & ~(uintptr_t)255) : nullptr;
-        GPBO_TRY(trtri_levels<float>(ctx, L32, m->Linv32, tmp, n_pad, probs, tcs));
+        if (split_inv) {
+            k_cast_cols<double, float><<<blocks_for((int64_t)n_pad * (n_pad - hb * NB)), 256, 0, st>>>(
+                m->L, n_pad, hb * NB, n_pad, L32);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_linv_init_part<float><<<blocks_for((int64_t)(nblk - hb) * NB * NB), 256, 0, st>>>(m->Dinv, n_pad,
+                                                                                               m->Linv32, hb, 2);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<float>(ctx, st, L32, m->Linv32, tmp32, n_pad, probs + max_probs, tcs, 2));
+        } else {
+            k_cast<double, float><<<blocks_for(sq), 256, 0, st>>>(m->L, sq, L32);
+            GPBO_LAUNCH_CHECK(ctx);
+            k_linv_init<float><<<blocks_for(sq), 256, 0, st>>>(m->Dinv, n_pad, m->Linv32);
+            GPBO_LAUNCH_CHECK(ctx);
+            GPBO_TRY(trtri_levels<float>(ctx, st, L32, m->Linv32, tmp32, n_pad, probs, tcs));
+        }
         GPBO_TRY(correction(m->Linv32));
         if (m->prec == GPBO_PREC_BF16) {
             __nv_bfloat16 *hi = (__nv_bfloat16 *)m->Linv16;

@@ -69,7 +69,8 @@ struct BatchPlan {
     float tune_ms[3] = {-1.f, -1.f, -1.f};  // autotuner's times for 64, 128, 256
     cudaStream_t cap = nullptr;
     cudaStream_t cap2 = nullptr;     // second capture stream: lookahead column, alpha solve
-    cudaEvent_t ev[5] = {};          // fork / join events between the two capture streams
+    cudaStream_t cap3 = nullptr;     // third: the FP64 trailing updates beside the tensor-core ones
+    cudaEvent_t ev[7] = {};          // fork / join events between the capture streams
     int64_t kernels = 0;             // kernel nodes in the captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -290,6 +291,7 @@ static void free_plan(BatchPlan *pl)
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap) cudaStreamDestroy(pl->cap);
     if (pl->cap2) cudaStreamDestroy(pl->cap2);
+    if (pl->cap3) cudaStreamDestroy(pl->cap3);
     for (cudaEvent_t e : pl->ev)
         if (e) cudaEventDestroy(e);
     for (void *p : pl->allocs) cudaFree(p);
@@ -437,6 +439,7 @@ static int build_plan(gpbo_ctx *ctx, BatchPlan *pl, const gp_hyper *hyp)
         GPBO_CUDA_TRY(cudaMemcpy(pl->gemm_dev, all.data(), sizeof(GemmProb) * all.size(), cudaMemcpyHostToDevice));
     GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
     GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap2, cudaStreamNonBlocking));
+    GPBO_CUDA_TRY(cudaStreamCreateWithFlags(&pl->cap3, cudaStreamNonBlocking));
     for (cudaEvent_t &e : pl->ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return GPBO_OK;
 }
@@ -535,8 +538,9 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
         if (T > 1) b_chol_panel<<<dim3((T - 1) * (NB / 4), G), 128, 0, s2>>>(P, pl->L, pl->Dinv, kb + 1);
         GPBO_CUDA_TRY(cudaEventRecord(ev_panel, s2));
         if (T > 1) {
-            // problems with a tensor-core update at this step (the single-problem rule), then
-            // the FP64 update of the others
+            // problems with a tensor-core update at this step (the single-problem rule), and
+            // beside it, on the third capture stream, the FP64 update of the others (disjoint
+            // problems, so the two branches of the graph run concurrently)
             int max_rows = 0;
             int64_t max_tiles = 0;
             if (pl->tc_probs)
@@ -546,10 +550,14 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
                     max_rows = std::max(max_rows, t.n_pad - (kb + 2) * NB);
                     max_tiles = std::max(max_tiles, chol_tc_tiles(t.nblk, kb));
                 }
+            GPBO_CUDA_TRY(cudaEventRecord(pl->ev[5], st));
+            GPBO_CUDA_TRY(cudaStreamWaitEvent(pl->cap3, pl->ev[5], 0));
+            b_chol_update_slab<<<dim3((unsigned)((int64_t)T * (T - 1) / 2 * (NB / B_SLAB_ROWS)), G), 256, 0,
+                                 pl->cap3>>>(P, pl->L, kb, 2);
+            GPBO_CUDA_TRY(cudaEventRecord(pl->ev[6], pl->cap3));
             GPBO_TRY(chol_tc_update_batched(ctx, st, pl->tc_probs, G, kb, max_rows, max_tiles, pl->tc_slices,
                                             pl->tc_maps[0], pl->tc_maps[1]));
-            b_chol_update_slab<<<dim3((unsigned)((int64_t)T * (T - 1) / 2 * (NB / B_SLAB_ROWS)), G), 256, 0, st>>>(
-                P, pl->L, kb, 2);
+            GPBO_CUDA_TRY(cudaStreamWaitEvent(st, pl->ev[6], 0));
             GPBO_CUDA_TRY(cudaEventRecord(ev_rest, st));
         }
     }

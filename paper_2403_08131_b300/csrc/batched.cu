@@ -145,11 +145,29 @@ __global__ void __launch_bounds__(256) b_chol_update_slab(const BProb *P, double
     k_chol_update_slab_body<B_SLAB_ROWS>(L + p.off_sq, p.n_pad, kb, blockIdx.x, part, 0);
 }
 
-__global__ void b_zero_upper(const BProb *P, double *L)
+// Between the factorisation and the inverse's levels, one pass over each problem's n_pad^2
+// elements (grid-stride, so a small problem's share of the grid is not idle blocks): the blocks
+// of L above its block diagonal set to zero, L32 = (float) L, and the start of Linv32 (the
+// diagonal blocks' inverses from Dinv, zeros elsewhere); per element the arithmetic of
+// k_zero_upper_blocks, k_cast and k_linv_init.
+__global__ void b_prep_inverse(const BProb *P, double *L, float *L32, const double *Dinv, float *Linv)
 {
     const BProb &p = P[blockIdx.y];
-    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
-    k_zero_upper_blocks_body(L + p.off_sq, p.n_pad, blockIdx.x, 0);
+    const int n_pad = p.n_pad;
+    const int64_t sq = (int64_t)n_pad * n_pad;
+    double *Lp = L + p.off_sq;
+    float *L32p = L32 + p.off_sq, *Lip = Linv + p.off_sq;
+    const double *Dp = Dinv + p.off_dinv;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < sq; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / n_pad), j = (int)(t % n_pad), bi = i / NB, bj = j / NB;
+        double v = Lp[t];
+        if (bj > bi) {
+            v = 0.0;
+            Lp[t] = 0.0;
+        }
+        L32p[t] = (float)v;
+        Lip[t] = bi == bj ? (float)Dp[(int64_t)bi * NB * NB + (i % NB) * NB + (j % NB)] : 0.0f;
+    }
 }
 
 // vec arena per problem: [alpha64 | ypad | work (2 n_pad) | r | dlt]
@@ -219,20 +237,6 @@ __global__ void b_trmv_t_sum(const BProb *P, const double *rpart, double *vec, f
     const BProb &p = P[blockIdx.y];
     if ((int)(blockIdx.x * blockDim.x) >= p.n_pad) return;
     k_trmv_t_sum_body(rpart + p.off_rpart, p.n_pad, p.chunks, vec + p.off_vec, alpha32 + p.off_vec / 6, blockIdx.x);
-}
-
-__global__ void b_cast_L(const BProb *P, const double *L, float *L32)
-{
-    const BProb &p = P[blockIdx.y];
-    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
-    k_cast_body<double, float>(L + p.off_sq, (int64_t)p.n_pad * p.n_pad, L32 + p.off_sq, blockIdx.x, 0);
-}
-
-__global__ void b_linv_init(const BProb *P, const double *Dinv, float *Linv)
-{
-    const BProb &p = P[blockIdx.y];
-    if ((int64_t)blockIdx.x * blockDim.x >= (int64_t)p.n_pad * p.n_pad) return;
-    k_linv_init_body<float>(Dinv + p.off_dinv, p.n_pad, Linv + p.off_sq, blockIdx.x, 0);
 }
 
 // The recursion's GEMMs: problems in blockIdx.z, shared body with the single-problem path.
@@ -563,7 +567,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     }
     GPBO_CUDA_TRY(cudaEventRecord(ev_join, s2));
     GPBO_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));
-    b_zero_upper<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L);
+    b_prep_inverse<<<dim3(std::max(1u, gb(pl->max_sq) / 8), G), 256, 0, st>>>(P, pl->L, pl->L32, pl->Dinv, pl->Linv32);
     // alpha = K^-1 y' with one step of iterative refinement (as the single-problem path): the
     // FP64 solve and residual on the second stream, under the L^-1 products, then the
     // correction through L^-1; vec slots: 0 alpha, 1 ypad, 2-3 work, 4 r, 5 u
@@ -576,9 +580,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     for (int s = 0; s < NBL; ++s)
         b_bwd_step<<<dim3(std::max(1, NBL - 1 - s), G), 256, 0, s2>>>(P, pl->L, pl->Dinv, pl->vec, s, 0);
     b_residual<<<dim3((pl->max_npad + 7) / 8, G), 256, 0, s2>>>(P, pl->K, pl->vec);
-    // FP32 L^-1
-    b_cast_L<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->L, pl->L32);
-    b_linv_init<<<dim3(gb(pl->max_sq), G), 256, 0, st>>>(P, pl->Dinv, pl->Linv32);
+    // FP32 L^-1 (L32 and the start of Linv32 from b_prep_inverse)
     for (size_t l = 0; l < pl->lvl_first.size(); ++l) {
         if (pl->lvl_mm[l].y >= 128) {  // the single-problem path's rule: 128 x 128 tiles on large levels
             dim3 g((pl->lvl_mm[l].y + 127) / 128, (pl->lvl_mm[l].x + 127) / 128, pl->lvl_count[l]);

@@ -554,10 +554,19 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
                     max_rows = std::max(max_rows, t.n_pad - (kb + 2) * NB);
                     max_tiles = std::max(max_tiles, chol_tc_tiles(t.nblk, kb));
                 }
+            // the FP64 update's grid covers the largest problem it updates (the kernel skips the
+            // tensor-core ones by the same rule)
+            int64_t slab_tiles = 0;
+            for (int g = 0; g < G; ++g) {
+                const BProb &q = pl->probs[g];
+                const int64_t Tg = q.nblk - kb - 1;
+                if (Tg > 1 && !chol_tc_step(q.n_pad, q.nblk, kb)) slab_tiles = std::max(slab_tiles, Tg * (Tg - 1) / 2);
+            }
             GPBO_CUDA_TRY(cudaEventRecord(pl->ev[5], st));
             GPBO_CUDA_TRY(cudaStreamWaitEvent(pl->cap3, pl->ev[5], 0));
-            b_chol_update_slab<<<dim3((unsigned)((int64_t)T * (T - 1) / 2 * (NB / B_SLAB_ROWS)), G), 256, 0,
-                                 pl->cap3>>>(P, pl->L, kb, 2);
+            if (slab_tiles > 0)
+                b_chol_update_slab<<<dim3((unsigned)(slab_tiles * (NB / B_SLAB_ROWS)), G), 256, 0, pl->cap3>>>(
+                    P, pl->L, kb, 2);
             GPBO_CUDA_TRY(cudaEventRecord(pl->ev[6], pl->cap3));
             GPBO_TRY(chol_tc_update_batched(ctx, st, pl->tc_probs, G, kb, max_rows, max_tiles, pl->tc_slices,
                                             pl->tc_maps[0], pl->tc_maps[1]));

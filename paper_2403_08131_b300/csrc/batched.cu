@@ -28,6 +28,9 @@ struct BProb {
     int64_t off_X, off_y, off_xs, off_sq, off_dinv, off_vec, off_kst, off_mu, off_part, off_rpart;
     int part_count;
     int chunks;  // row chunks of the refinement's X^T u
+    // this call's device inputs (n x d, n), gathered into the arenas by the graph's first
+    // kernel; null when the host copied them (host inputs)
+    const double *X_src, *y_src;
 };
 
 struct BatchPlan {
@@ -83,6 +86,19 @@ __device__ __forceinline__ Lengthscales_inv ls_of(const double *lsinv, int g, in
     Lengthscales_inv ls;
     for (int k = 0; k < d; ++k) ls.inv[k] = lsinv[g * GPBO_MAX_D + k];
     return ls;
+}
+
+// The call's device inputs into the arenas (one launch for all problems instead of two copies
+// each); problems whose inputs the host copied have null sources.
+__global__ void b_load_inputs(const BProb *P, double *X, double *y)
+{
+    const BProb &p = P[blockIdx.y];
+    if (!p.X_src) return;
+    const int64_t nd = (int64_t)p.n * p.d;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nd + p.n; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < nd) X[p.off_X + t] = p.X_src[t];
+        else y[p.off_y + (t - nd)] = p.y_src[t - nd];
+    }
 }
 
 __global__ void __launch_bounds__(1024) b_standardize(const BProb *P, const double *y, double *ys, double *tau)
@@ -515,6 +531,7 @@ static int enqueue_step(gpbo_ctx *ctx, BatchPlan *pl, cudaStream_t st, float xi)
     const int G = pl->G;
     const BProb *P = pl->probs_dev;
     const size_t smem1 = sizeof(double) * NB * (NB + 1);
+    b_load_inputs<<<dim3(std::max(1u, gb(pl->max_dn + pl->max_npad) / 4), G), 256, 0, st>>>(P, pl->dX, pl->dy);
     b_standardize<<<G, 1024, 0, st>>>(P, pl->dy, pl->dys, pl->tau);
     b_scale_x<<<dim3(gb(pl->max_dn), G), 256, 0, st>>>(P, pl->dX, pl->lsinv, pl->Xs64, pl->Xs32);
     b_kmat<<<dim3(pl->max_npad / 32, pl->max_npad / 32, G), dim3(32, 8), 0, st>>>(P, pl->Xs64, pl->K);
@@ -701,12 +718,19 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
         ctx->batch_plan = pl;
     }
     // this call's inputs and seeds
-    const cudaMemcpyKind kind = (flags & GPBO_HOST_PTRS) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // (host inputs: one copy each here; device inputs: read by the graph's first kernel)
+    const bool host = flags & GPBO_HOST_PTRS;
     for (int g = 0; g < G; ++g) {
         BProb &p = pl->probs[g];
         p.seed = seed[g];
-        GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dX + p.off_X, X[g], sizeof(double) * p.n * p.d, kind, ctx->stream));
-        GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dy + p.off_y, y[g], sizeof(double) * p.n, kind, ctx->stream));
+        p.X_src = host ? nullptr : X[g];
+        p.y_src = host ? nullptr : y[g];
+        if (host) {
+            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dX + p.off_X, X[g], sizeof(double) * p.n * p.d, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dy + p.off_y, y[g], sizeof(double) * p.n, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+        }
     }
     GPBO_CUDA_TRY(cudaMemcpyAsync(pl->probs_dev, pl->probs.data(), sizeof(BProb) * G, cudaMemcpyHostToDevice, ctx->stream));
     if (!pl->exec) {

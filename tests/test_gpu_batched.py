@@ -144,3 +144,25 @@ def test_batched_large_problem_within_bars_small_one_bit_for_bit(ctx):
     check_argmax(int(out["argmax"][1]), ei, BAR["f32"])
     assert abs(out["ei_max"][1] - one["ei_max"]) <= BAR["f32"] * one["ei_max"]
     m.free()
+
+
+def test_batched_device_inputs_equal_host_inputs(ctx):
+    """Device inputs (read by the graph's first kernel) and host inputs (copied by the host
+    before the graph) give the same step bit for bit, on one plan, in either order."""
+    import torch
+
+    def dev(ps):
+        return [dict(pb, X=torch.from_numpy(pb["X"]).cuda(), y=torch.from_numpy(pb["y"]).cuda()) for pb in ps]
+
+    def same(a, b):
+        return (np.array_equal(a["argmax"], b["argmax"]) and np.array_equal(a["ei_max"], b["ei_max"])
+                and all(np.array_equal(x, z) for x, z in zip(a["x_next"], b["x_next"])))
+
+    _, probs_a = _problems(G=9, M=1536)
+    probs_b = [dict(pb, y=pb["y"][::-1].copy()) for pb in probs_a]   # same shapes, other values
+    host_a = ctx.search_step_batched(probs_a)
+    assert same(host_a, ctx.search_step_batched(dev(probs_a)))
+    host_b = ctx.search_step_batched(probs_b)
+    assert not same(host_a, host_b)
+    assert same(host_b, ctx.search_step_batched(dev(probs_b)))
+    assert same(host_a, ctx.search_step_batched(probs_a))

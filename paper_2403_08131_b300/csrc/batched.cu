@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) b_gemm128(const float *A, const float *B,
     k_gemm128_body(A, B, Cc, probs, alpha, tri_a, tri_b, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-__global__ void __launch_bounds__(256) b_xkern(const BProb *P, const float *Xs32, const float *alpha32, const double *lsinv,
+__global__ void __launch_bounds__(256, 4) b_xkern(const BProb *P, const float *Xs32, const float *alpha32, const double *lsinv,
                                                float *Kst, float *mu)
 {
     const BProb &p = P[blockIdx.y];

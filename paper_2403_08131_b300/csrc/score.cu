@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_xkern(const float *__restrict__ Xc, uin
 }
 
 template <typename Out>
-__global__ void __launch_bounds__(256) k_xkern32(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
+__global__ void __launch_bounds__(256, 4) k_xkern32(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
                                                  int d, const float *__restrict__ Xs, const float *__restrict__ alpha,
                                                  int n, int n_pad, float s2, Lengthscales_inv ls, Out *__restrict__ Kst,
                                                  float *__restrict__ mu)

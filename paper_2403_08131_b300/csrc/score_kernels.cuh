@@ -136,6 +136,9 @@ __device__ __forceinline__ float matern_fast(float r2, float s2)
 
 // Cross-kernel and mean for FP32 scoring: CTA = 256 threads = 64 candidates (8 per warp) x
 // blocks of 128 observations (4 per lane).  Dynamic shared memory: sizeof(float) (192 d + 128).
+// Its kernels are bounded to 64 registers (four CTAs per SM, no spills): 128 left two CTAs
+// per SM, too few warps to cover the shared-memory and MUFU latencies (the batched step
+// 17.97 -> 17.57 ms, 17.73 ms at three CTAs).
 template <typename Out>
 __device__ __forceinline__ void k_xkern32_body(const float *__restrict__ Xc, uint64_t seed, int64_t c0, int64_t C,
                                                  int d, const float *__restrict__ Xs, const float *__restrict__ alpha,

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256, BM == 256 ? 1 : 2) b_var(const BProb *P, 
 {
     const BProb &p = P[blockIdx.y];
     if ((int64_t)blockIdx.x * BM >= p.M) return;
-    k_var_f32_body<BM>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
+    k_var_f32_body<BM, true>(Kst + p.off_kst, p.M, 0, p.n_pad, Linv + p.off_sq, mu + p.off_mu, (float)p.s2, 0.0,
                        tau + blockIdx.y, xi, nullptr, nullptr, pei + p.off_part, pidx + p.off_part, 0, blockIdx.x);
 }
 

@@ -654,25 +654,127 @@ static int64_t count_kernel_nodes(cudaGraph_t g)
     return k;
 }
 
-static bool same_key(const BatchPlan *pl, int G, const int *n, const int *d, const int64_t *M, const gp_hyper *hyp,
+// The call's problems split by size into at most two plans whose graphs run concurrently, on
+// streams of low and high priority: the small problems' whole step (factorisation, inverse,
+// scoring) runs beside the large ones' factorisation, whose chain of latency-bound launches
+// leaves most SMs idle.  Each problem's kernels and arithmetic are those of one plan, so every
+// result is the same as with one plan.
+constexpr int B_SMALL_NPAD = 512;
+struct BatchSet {
+    // key
+    int G = 0;
+    double xi = 0.0;
+    std::vector<int> n, d;
+    std::vector<int64_t> M;
+    std::vector<double> key_hyp;
+    int tile_req = 0;
+    BatchPlan *pl[2] = {};       // [0]: problems of n_pad <= B_SMALL_NPAD, [1]: the others (either may be null)
+    std::vector<int> idx[2];     // each plan's problems' positions in the call
+    cudaStream_t st[2] = {};     // [0] lowest priority, [1] highest
+    cudaEvent_t ev[3] = {};      // fork, and each plan's end
+};
+
+static void free_set(BatchSet *bs)
+{
+    if (!bs) return;
+    for (int c = 0; c < 2; ++c) {
+        free_plan(bs->pl[c]);
+        if (bs->st[c]) cudaStreamDestroy(bs->st[c]);
+    }
+    for (cudaEvent_t e : bs->ev)
+        if (e) cudaEventDestroy(e);
+    delete bs;
+}
+
+static bool same_key(const BatchSet *bs, int G, const int *n, const int *d, const int64_t *M, const gp_hyper *hyp,
                      double xi)
 {
-    if (!pl || pl->G != G || pl->xi != xi) return false;
+    if (!bs || bs->G != G || bs->xi != xi) return false;
     std::vector<double> kh;
     for (int g = 0; g < G; ++g) {
-        if (pl->n[g] != n[g] || pl->d[g] != d[g] || pl->M[g] != M[g]) return false;
+        if (bs->n[g] != n[g] || bs->d[g] != d[g] || bs->M[g] != M[g]) return false;
         kh.push_back(hyp[g].signal_var);
         kh.push_back(hyp[g].noise_var);
         for (int k = 0; k < d[g]; ++k) kh.push_back(hyp[g].lengthscale[k]);
     }
-    return kh == pl->key_hyp;
+    return kh == bs->key_hyp;
+}
+
+// A new set for this call's shapes: the split, each part's plan (arenas, autotuned tile), the
+// streams and events.
+static int build_set(gpbo_ctx *ctx, BatchSet *bs, const gp_hyper *hyp)
+{
+    for (int g = 0; g < bs->G; ++g) bs->idx[round_up(bs->n[g], NB) <= B_SMALL_NPAD ? 0 : 1].push_back(g);
+    int lo = 0, hi = 0;
+    GPBO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    for (int c = 0; c < 2; ++c) {
+        GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&bs->st[c], cudaStreamNonBlocking, c == 0 ? lo : hi));
+        if (bs->idx[c].empty()) continue;
+        BatchPlan *pl = new BatchPlan();
+        bs->pl[c] = pl;
+        pl->G = (int)bs->idx[c].size();
+        pl->xi = bs->xi;
+        std::vector<gp_hyper> h;
+        for (int g : bs->idx[c]) {
+            pl->n.push_back(bs->n[g]);
+            pl->d.push_back(bs->d[g]);
+            pl->M.push_back(bs->M[g]);
+            h.push_back(hyp[g]);
+        }
+        pl->tile_req = bs->tile_req;
+        GPBO_TRY(build_plan(ctx, pl, h.data()));
+        if (pl->tile_req) set_tile(pl, pl->tile_req);
+        else GPBO_TRY(autotune(pl));
+    }
+    for (cudaEvent_t &e : bs->ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return GPBO_OK;
+}
+
+// Enqueue one plan's step on stream s: its inputs (host: a copy each; device: read by the
+// graph's first kernel), its problem table, and its graph (captured on first use).
+static int enqueue_plan(gpbo_ctx *ctx, BatchPlan *pl, const std::vector<int> &idx, cudaStream_t s,
+                        const double *const *X, const double *const *y, const uint64_t *seed, bool host)
+{
+    for (int k = 0; k < pl->G; ++k) {
+        const int g = idx[k];
+        BProb &p = pl->probs[k];
+        p.seed = seed[g];
+        p.X_src = host ? nullptr : X[g];
+        p.y_src = host ? nullptr : y[g];
+        if (host) {
+            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dX + p.off_X, X[g], sizeof(double) * p.n * p.d, cudaMemcpyHostToDevice, s));
+            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dy + p.off_y, y[g], sizeof(double) * p.n, cudaMemcpyHostToDevice, s));
+        }
+    }
+    GPBO_CUDA_TRY(cudaMemcpyAsync(pl->probs_dev, pl->probs.data(), sizeof(BProb) * pl->G, cudaMemcpyHostToDevice, s));
+    if (!pl->exec) {
+        // capture the step once; the probe table and arenas keep their addresses from here on
+        GPBO_CUDA_TRY(cudaStreamSynchronize(s));
+        GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double) * 2 * NB * (NB + 1))));
+        GPBO_CUDA_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+        int st = enqueue_step(ctx, pl, pl->cap, (float)pl->xi);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(pl->cap, &graph);
+        if (st != GPBO_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            note_cuda_error(e, "batched capture", __FILE__, __LINE__);
+            return st != GPBO_OK ? st : GPBO_ECUDA;
+        }
+        pl->graph = graph;
+        pl->kernels = count_kernel_nodes(graph);
+        GPBO_CUDA_TRY(cudaGraphInstantiate(&pl->exec, graph, 0));
+    }
+    GPBO_CUDA_TRY(cudaGraphLaunch(pl->exec, s));
+    ctx->launches += pl->kernels;
+    return GPBO_OK;
 }
 
 }  // namespace gpbo
 
 using namespace gpbo;
 
-static BatchPlan *g_last_plan_for_ctx(gpbo_ctx *ctx) { return (BatchPlan *)ctx->batch_plan; }
+static BatchSet *g_last_set_for_ctx(gpbo_ctx *ctx) { return (BatchSet *)ctx->batch_plan; }
 
 extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const double *const *y, const int *n,
                                    const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
@@ -689,77 +791,62 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
             if (!(hyp[g].lengthscale[k] > 0)) return GPBO_EINVAL;
     }
     GPBO_CUDA_TRY(cudaSetDevice(ctx->device));
-    BatchPlan *pl = g_last_plan_for_ctx(ctx);
-    if (!same_key(pl, G, n, d, M, hyp, xi) || pl->tile_req != ctx->batch_tile) {
+    BatchSet *bs = g_last_set_for_ctx(ctx);
+    if (!same_key(bs, G, n, d, M, hyp, xi) || bs->tile_req != ctx->batch_tile) {
         cudaStreamSynchronize(ctx->stream);
-        free_plan(pl);
+        free_set(bs);
         ctx->batch_plan = nullptr;
-        pl = new BatchPlan();
-        pl->G = G;
-        pl->xi = xi;
-        pl->n.assign(n, n + G);
-        pl->d.assign(d, d + G);
-        pl->M.assign(M, M + G);
+        bs = new BatchSet();
+        bs->G = G;
+        bs->xi = xi;
+        bs->n.assign(n, n + G);
+        bs->d.assign(d, d + G);
+        bs->M.assign(M, M + G);
         for (int g = 0; g < G; ++g) {
-            pl->key_hyp.push_back(hyp[g].signal_var);
-            pl->key_hyp.push_back(hyp[g].noise_var);
-            for (int k = 0; k < d[g]; ++k) pl->key_hyp.push_back(hyp[g].lengthscale[k]);
+            bs->key_hyp.push_back(hyp[g].signal_var);
+            bs->key_hyp.push_back(hyp[g].noise_var);
+            for (int k = 0; k < d[g]; ++k) bs->key_hyp.push_back(hyp[g].lengthscale[k]);
         }
-        pl->tile_req = ctx->batch_tile;
-        int st = build_plan(ctx, pl, hyp);
-        if (st == GPBO_OK) {
-            if (pl->tile_req) set_tile(pl, pl->tile_req);
-            else st = autotune(pl);
-        }
+        bs->tile_req = ctx->batch_tile;
+        const int st = build_set(ctx, bs, hyp);
         if (st != GPBO_OK) {
-            free_plan(pl);
+            free_set(bs);
             return st;
         }
-        ctx->batch_plan = pl;
+        ctx->batch_plan = bs;
     }
-    // this call's inputs and seeds
-    // (host inputs: one copy each here; device inputs: read by the graph's first kernel)
+    // both plans' steps, forked from and joined back into the context stream
     const bool host = flags & GPBO_HOST_PTRS;
-    for (int g = 0; g < G; ++g) {
-        BProb &p = pl->probs[g];
-        p.seed = seed[g];
-        p.X_src = host ? nullptr : X[g];
-        p.y_src = host ? nullptr : y[g];
-        if (host) {
-            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dX + p.off_X, X[g], sizeof(double) * p.n * p.d, cudaMemcpyHostToDevice,
-                                          ctx->stream));
-            GPBO_CUDA_TRY(cudaMemcpyAsync(pl->dy + p.off_y, y[g], sizeof(double) * p.n, cudaMemcpyHostToDevice,
-                                          ctx->stream));
-        }
+    GPBO_CUDA_TRY(cudaEventRecord(bs->ev[0], ctx->stream));
+    for (int c = 1; c >= 0; --c) {  // the large problems' step first, on the high-priority stream
+        if (!bs->pl[c]) continue;
+        GPBO_CUDA_TRY(cudaStreamWaitEvent(bs->st[c], bs->ev[0], 0));
+        GPBO_TRY(enqueue_plan(ctx, bs->pl[c], bs->idx[c], bs->st[c], X, y, seed, host));
+        GPBO_CUDA_TRY(cudaEventRecord(bs->ev[1 + c], bs->st[c]));
     }
-    GPBO_CUDA_TRY(cudaMemcpyAsync(pl->probs_dev, pl->probs.data(), sizeof(BProb) * G, cudaMemcpyHostToDevice, ctx->stream));
-    if (!pl->exec) {
-        // capture the step once; the probe table and arenas keep their addresses from here on
-        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-        GPBO_CUDA_TRY(cudaFuncSetAttribute(b_chol_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(double) * 2 * NB * (NB + 1))));
-        GPBO_CUDA_TRY(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
-        int st = enqueue_step(ctx, pl, pl->cap, (float)xi);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(pl->cap, &graph);
-        if (st != GPBO_OK || e != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            note_cuda_error(e, "batched capture", __FILE__, __LINE__);
-            return st != GPBO_OK ? st : GPBO_ECUDA;
-        }
-        pl->graph = graph;
-        pl->kernels = count_kernel_nodes(graph);
-        GPBO_CUDA_TRY(cudaGraphInstantiate(&pl->exec, graph, 0));
-    }
-    GPBO_CUDA_TRY(cudaGraphLaunch(pl->exec, ctx->stream));
-    ctx->launches += pl->kernels;
+    for (int c = 0; c < 2; ++c)
+        if (bs->pl[c]) GPBO_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, bs->ev[1 + c], 0));
     std::vector<double> be(G);
     std::vector<int64_t> bi(G);
     std::vector<float> xn((size_t)G * GPBO_MAX_D);
-    GPBO_CUDA_TRY(cudaMemcpyAsync(be.data(), pl->best_ei, sizeof(double) * G, cudaMemcpyDeviceToHost, ctx->stream));
-    GPBO_CUDA_TRY(cudaMemcpyAsync(bi.data(), pl->best_idx, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, ctx->stream));
-    GPBO_CUDA_TRY(cudaMemcpyAsync(xn.data(), pl->xnext, sizeof(float) * xn.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < 2; ++c) {
+        const BatchPlan *pl = bs->pl[c];
+        if (!pl) continue;
+        std::vector<double> pe(pl->G);
+        std::vector<int64_t> pi(pl->G);
+        std::vector<float> px((size_t)pl->G * GPBO_MAX_D);
+        GPBO_CUDA_TRY(cudaMemcpyAsync(pe.data(), pl->best_ei, sizeof(double) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
+        GPBO_CUDA_TRY(cudaMemcpyAsync(pi.data(), pl->best_idx, sizeof(int64_t) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
+        GPBO_CUDA_TRY(cudaMemcpyAsync(px.data(), pl->xnext, sizeof(float) * px.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        for (int k = 0; k < pl->G; ++k) {
+            const int g = bs->idx[c][k];
+            be[g] = pe[k];
+            bi[g] = pi[k];
+            std::copy(px.begin() + (size_t)k * GPBO_MAX_D, px.begin() + (size_t)(k + 1) * GPBO_MAX_D,
+                      xn.begin() + (size_t)g * GPBO_MAX_D);
+        }
+    }
     unsigned bits = 0;
     GPBO_TRY(take_device_status(ctx, &bits));
     if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
@@ -778,10 +865,12 @@ extern "C" int search_step_batched_tile(gpbo_ctx *ctx, int tile)
     return GPBO_OK;
 }
 
+// The tile of the plan with the larger problems (the one with most of the variance work).
 extern "C" int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3)
 {
     if (!ctx || !tile) return GPBO_EINVAL;
-    const BatchPlan *pl = (const BatchPlan *)ctx->batch_plan;
+    const BatchSet *bs = (const BatchSet *)ctx->batch_plan;
+    const BatchPlan *pl = bs ? (bs->pl[1] ? bs->pl[1] : bs->pl[0]) : nullptr;
     if (!pl) return GPBO_EINVAL;
     *tile = pl->var_bm;
     if (ms3)
@@ -790,5 +879,5 @@ extern "C" int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float 
 }
 
 namespace gpbo {
-void batch_plan_free(void *p) { free_plan((BatchPlan *)p); }
+void batch_plan_free(void *p) { free_set((BatchSet *)p); }
 }  // namespace gpbo

@@ -306,8 +306,11 @@ int search_step(gpbo_ctx *ctx, const double *X, const double *y, int n, int d, c
  *   x_next : host, G x 64 doubles; row g holds the d[g] coordinates of problem g's pick.
  *   ei_max : host, G.  argmax : host, G, may be NULL.
  * The first call for a set of shapes (G, n, d, M, hyperparameters, xi) builds device arenas
- * and captures the step into a CUDA graph held by the context; later calls with the same
- * shapes copy the new X, y and seeds and replay the graph.  Synchronises. */
+ * and captures the step into CUDA graphs held by the context; later calls with the same
+ * shapes take the new X, y and seeds and replay the graphs.  The problems that pad to at
+ * most 512 rows form a second plan whose graph runs beside the larger problems' on a
+ * lower-priority stream (its whole step under their factorisation); the split changes no
+ * result.  Synchronises. */
 int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const double *const *y, const int *n,
                         const int *d, const gp_hyper *hyp, const int64_t *M, const uint64_t *seed, double xi,
                         gpbo_prec prec, unsigned flags, double *x_next, double *ei_max, int64_t *argmax);
@@ -318,9 +321,11 @@ int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X, const doub
  * captures the fastest into the graph.  The tile changes no result: every candidate's sums
  * run in the same order.  Takes effect at the next search_step_batched call. */
 int search_step_batched_tile(gpbo_ctx *ctx, int tile);
-/* The current plan's tile and the autotuner's mean time per launch (ms) of the 64, 128 and
- * 256 tiles (negative when not measured).  GPBO_EINVAL before the first batched call. */
-int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3);
+/* The tile of the plan that holds the largest problems of the last batched call, and the
+ * autotuner's mean time per launch (ms) of its 64, 128 and 256 tiles (negative when not
+ * measured).  members: NULL, or host room for that call's G ints, set to 1 for the problems
+ * of that plan and 0 for the others.  GPBO_EINVAL before the first batched call. */
+int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3, int *members);
 
 /* ------------------------------------------------------------------ learned pre-screen
  * Not in the paper: a cheap surrogate of the GP posterior that pre-screens very large

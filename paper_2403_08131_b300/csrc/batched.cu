@@ -865,16 +865,21 @@ extern "C" int search_step_batched_tile(gpbo_ctx *ctx, int tile)
     return GPBO_OK;
 }
 
-// The tile of the plan with the larger problems (the one with most of the variance work).
-extern "C" int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3)
+// The plan with the larger problems (the one with most of the variance work).
+extern "C" int search_step_batched_tuning(const gpbo_ctx *ctx, int *tile, float *ms3, int *members)
 {
     if (!ctx || !tile) return GPBO_EINVAL;
     const BatchSet *bs = (const BatchSet *)ctx->batch_plan;
-    const BatchPlan *pl = bs ? (bs->pl[1] ? bs->pl[1] : bs->pl[0]) : nullptr;
+    const int c = bs && bs->pl[1] ? 1 : 0;
+    const BatchPlan *pl = bs ? bs->pl[c] : nullptr;
     if (!pl) return GPBO_EINVAL;
     *tile = pl->var_bm;
     if (ms3)
         for (int i = 0; i < 3; ++i) ms3[i] = pl->tune_ms[i];
+    if (members) {
+        for (int g = 0; g < bs->G; ++g) members[g] = 0;
+        for (int g : bs->idx[c]) members[g] = 1;
+    }
     return GPBO_OK;
 }
 

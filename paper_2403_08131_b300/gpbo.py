@@ -88,7 +88,7 @@ _step_batched = _sig("search_step_batched", C.c_int, [_P, C.c_int, C.POINTER(_P)
                                                      C.POINTER(GpHyper), _L, C.POINTER(C.c_uint64), C.c_double,
                                                      C.c_int, C.c_uint, _D, _D, _L])
 _batched_tile = _sig("search_step_batched_tile", C.c_int, [_P, C.c_int])
-_batched_tuning = _sig("search_step_batched_tuning", C.c_int, [_P, _I, C.POINTER(C.c_float)])
+_batched_tuning = _sig("search_step_batched_tuning", C.c_int, [_P, _I, C.POINTER(C.c_float), _I])
 _posterior_noalloc = _sig("gp_posterior_ei_noalloc", C.c_int, [_P, _P, _P, C.c_int64, C.c_uint64, C.c_double,
                                                                C.c_double, _P, _P, _P, _L, _D])
 _mlp_create = _sig("mlp_create", C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(_P)])
@@ -375,6 +375,7 @@ class Context:
         x_next = np.zeros((G, 64))
         ei_max = np.zeros(G)
         am = np.zeros(G, dtype=np.int64)
+        self._batched_G = G
         check(_step_batched(self._h, G, Xp, yp, ns.ctypes.data_as(_I), ds.ctypes.data_as(_I), hyps,
                             Ms.ctypes.data_as(_L), seeds, float(xi), PREC[prec], HOST_PTRS if host else 0,
                             x_next.ctypes.data_as(_D), ei_max.ctypes.data_as(_D), am.ctypes.data_as(_L)),
@@ -385,12 +386,16 @@ class Context:
         """Variance tile of the batched step (64, 128, 256), or 0 for the autotuner."""
         check(_batched_tile(self._h, int(tile)), "search_step_batched_tile")
 
-    def batched_tuning(self):
-        """(tile in use, {tile: autotuner ms per launch}) of the current batched plan."""
+    def batched_tuning(self, members=False):
+        """(tile in use, {tile: autotuner ms per launch}) of the batched plan that holds the
+        largest problems of the last call; with members=True also a boolean array over that
+        call's problems marking the ones in that plan."""
         t = C.c_int(0)
         ms = (C.c_float * 3)()
-        check(_batched_tuning(self._h, C.byref(t), ms), "search_step_batched_tuning")
-        return t.value, {k: float(v) for k, v in zip((64, 128, 256), ms) if v >= 0}
+        mem = np.zeros(max(getattr(self, "_batched_G", 0), 1), dtype=np.int32)
+        check(_batched_tuning(self._h, C.byref(t), ms, mem.ctypes.data_as(_I)), "search_step_batched_tuning")
+        out = (t.value, {k: float(v) for k, v in zip((64, 128, 256), ms) if v >= 0})
+        return out + (mem[:getattr(self, "_batched_G", 0)].astype(bool),) if members else out
 
     # ------------------------------------------------------------ screen
     def screen(self, block_dim=None, block_fn=None, noise_sd=0.0, seed=0, n_base=32, h=0.1, cutoff=0.25,

@@ -166,3 +166,17 @@ def test_batched_device_inputs_equal_host_inputs(ctx):
     assert not same(host_a, host_b)
     assert same(host_b, ctx.search_step_batched(dev(probs_b)))
     assert same(host_a, ctx.search_step_batched(probs_a))
+
+
+def test_batched_plan_members(ctx):
+    """The tuning report covers the plan of the largest problems: those that pad to more than
+    512 rows (the small ones run as a second, concurrent plan), or all of them if none do."""
+    subs, probs = _problems()
+    ctx.search_step_batched(probs)
+    tile, ms, big = ctx.batched_tuning(members=True)
+    npad = np.array([(w.n + 63) // 64 * 64 for w in subs])
+    expect = npad > 512 if (npad > 512).any() else np.ones(len(subs), dtype=bool)
+    assert np.array_equal(big, expect) and tile in ms
+    small = [pb for pb, w in zip(probs, subs) if (w.n + 63) // 64 * 64 <= 512][:3]
+    ctx.search_step_batched(small)
+    assert ctx.batched_tuning(members=True)[2].all()

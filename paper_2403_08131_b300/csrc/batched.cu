@@ -672,6 +672,7 @@ struct BatchSet {
     std::vector<int> idx[2];     // each plan's problems' positions in the call
     cudaStream_t st[2] = {};     // [0] lowest priority, [1] highest
     cudaEvent_t ev[3] = {};      // fork, and each plan's end
+    void *host = nullptr;        // pinned: per problem its best EI, index and x_next, then the status word
 };
 
 static void free_set(BatchSet *bs)
@@ -683,6 +684,7 @@ static void free_set(BatchSet *bs)
     }
     for (cudaEvent_t e : bs->ev)
         if (e) cudaEventDestroy(e);
+    if (bs->host) cudaFreeHost(bs->host);
     delete bs;
 }
 
@@ -698,6 +700,12 @@ static bool same_key(const BatchSet *bs, int G, const int *n, const int *d, cons
         for (int k = 0; k < d[g]; ++k) kh.push_back(hyp[g].lengthscale[k]);
     }
     return kh == bs->key_hyp;
+}
+
+// Pinned readback of a set: G best EIs, G indices, G x GPBO_MAX_D floats of x_next, the status.
+static size_t set_host_bytes(int G)
+{
+    return (sizeof(double) + sizeof(int64_t) + sizeof(float) * GPBO_MAX_D) * (size_t)G + 16;
 }
 
 // A new set for this call's shapes: the split, each part's plan (arenas, autotuned tile), the
@@ -727,6 +735,7 @@ static int build_set(gpbo_ctx *ctx, BatchSet *bs, const gp_hyper *hyp)
         else GPBO_TRY(autotune(pl));
     }
     for (cudaEvent_t &e : bs->ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    GPBO_CUDA_TRY(cudaMallocHost(&bs->host, set_host_bytes(bs->G)));
     return GPBO_OK;
 }
 
@@ -826,34 +835,35 @@ extern "C" int search_step_batched(gpbo_ctx *ctx, int G, const double *const *X,
     }
     for (int c = 0; c < 2; ++c)
         if (bs->pl[c]) GPBO_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, bs->ev[1 + c], 0));
-    std::vector<double> be(G);
-    std::vector<int64_t> bi(G);
-    std::vector<float> xn((size_t)G * GPBO_MAX_D);
+    // every plan's results and the status word into pinned memory, then one synchronisation
+    double *be = (double *)bs->host;
+    int64_t *bi = (int64_t *)(be + G);
+    float *xn = (float *)(bi + G);
+    unsigned *bits = (unsigned *)(xn + (size_t)G * GPBO_MAX_D);
+    int off = 0;
     for (int c = 0; c < 2; ++c) {
         const BatchPlan *pl = bs->pl[c];
         if (!pl) continue;
-        std::vector<double> pe(pl->G);
-        std::vector<int64_t> pi(pl->G);
-        std::vector<float> px((size_t)pl->G * GPBO_MAX_D);
-        GPBO_CUDA_TRY(cudaMemcpyAsync(pe.data(), pl->best_ei, sizeof(double) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
-        GPBO_CUDA_TRY(cudaMemcpyAsync(pi.data(), pl->best_idx, sizeof(int64_t) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
-        GPBO_CUDA_TRY(cudaMemcpyAsync(px.data(), pl->xnext, sizeof(float) * px.size(), cudaMemcpyDeviceToHost, ctx->stream));
-        GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-        for (int k = 0; k < pl->G; ++k) {
-            const int g = bs->idx[c][k];
-            be[g] = pe[k];
-            bi[g] = pi[k];
-            std::copy(px.begin() + (size_t)k * GPBO_MAX_D, px.begin() + (size_t)(k + 1) * GPBO_MAX_D,
-                      xn.begin() + (size_t)g * GPBO_MAX_D);
-        }
+        GPBO_CUDA_TRY(cudaMemcpyAsync(be + off, pl->best_ei, sizeof(double) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
+        GPBO_CUDA_TRY(cudaMemcpyAsync(bi + off, pl->best_idx, sizeof(int64_t) * pl->G, cudaMemcpyDeviceToHost, ctx->stream));
+        GPBO_CUDA_TRY(cudaMemcpyAsync(xn + (size_t)off * GPBO_MAX_D, pl->xnext, sizeof(float) * GPBO_MAX_D * pl->G,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        off += pl->G;
     }
-    unsigned bits = 0;
-    GPBO_TRY(take_device_status(ctx, &bits));
-    if (bits & DEV_NOTSPD) return GPBO_ENOTSPD;
-    for (int g = 0; g < G; ++g) {
-        ei_max[g] = be[g];
-        if (argmax) argmax[g] = bi[g];
-        for (int k = 0; k < GPBO_MAX_D; ++k) x_next[(size_t)g * GPBO_MAX_D + k] = k < d[g] ? (double)xn[(size_t)g * GPBO_MAX_D + k] : 0.0;
+    GPBO_CUDA_TRY(cudaMemcpyAsync(bits, ctx->dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    GPBO_CUDA_TRY(cudaMemsetAsync(ctx->dev_status, 0, sizeof(unsigned), ctx->stream));
+    GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (*bits & DEV_NOTSPD) return GPBO_ENOTSPD;
+    off = 0;
+    for (int c = 0; c < 2; ++c) {
+        if (!bs->pl[c]) continue;
+        for (size_t k = 0; k < bs->idx[c].size(); ++k, ++off) {
+            const int g = bs->idx[c][k];
+            ei_max[g] = be[off];
+            if (argmax) argmax[g] = bi[off];
+            for (int q = 0; q < GPBO_MAX_D; ++q)
+                x_next[(size_t)g * GPBO_MAX_D + q] = q < d[g] ? (double)xn[(size_t)off * GPBO_MAX_D + q] : 0.0;
+        }
     }
     return GPBO_OK;
 }

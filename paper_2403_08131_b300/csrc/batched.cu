@@ -34,11 +34,10 @@ struct BProb {
 };
 
 struct BatchPlan {
-    // key
+    // shapes (the set that owns the plan holds the key)
     int G = 0;
     std::vector<int> n, d;
     std::vector<int64_t> M;
-    std::vector<double> key_hyp;
     double xi = 0.0;     // baked into the captured graph
     // arenas
     BProb *probs_dev = nullptr;

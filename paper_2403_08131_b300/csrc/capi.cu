@@ -49,6 +49,7 @@ int ws_reserve(gpbo_ctx *ctx, size_t bytes, void **out)
             if (ctx->side) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side));
             if (ctx->side2) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side2));
             if (ctx->side3) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->side3));
+            if (ctx->mainf) GPBO_CUDA_TRY(cudaStreamSynchronize(ctx->mainf));
             GPBO_CUDA_TRY(cudaFree(ctx->ws));
             ctx->ws = nullptr;
             ctx->ws_size = 0;
@@ -68,6 +69,7 @@ int side_stream(gpbo_ctx *ctx, cudaStream_t *out)
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side2, cudaStreamNonBlocking, hi));
         GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->side3, cudaStreamNonBlocking, lo));
+        GPBO_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->mainf, cudaStreamNonBlocking, (lo + hi) / 2));
         for (cudaEvent_t &e : ctx->side_ev) GPBO_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     *out = ctx->side;
@@ -331,6 +333,10 @@ int gpbo_destroy(gpbo_ctx *ctx)
     if (ctx->side3) {
         cudaStreamSynchronize(ctx->side3);
         cudaStreamDestroy(ctx->side3);
+    }
+    if (ctx->mainf) {
+        cudaStreamSynchronize(ctx->mainf);
+        cudaStreamDestroy(ctx->mainf);
     }
     for (cudaEvent_t e : ctx->side_ev)
         if (e) cudaEventDestroy(e);

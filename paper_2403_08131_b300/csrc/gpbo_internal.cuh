@@ -99,8 +99,9 @@ struct gpbo_ctx {
     int batch_tile = 0;              // batched variance tile (0: autotune)
     cudaStream_t side = nullptr;     // high-priority streams for work overlapped inside a call
     cudaStream_t side2 = nullptr;
-    cudaStream_t side3 = nullptr;    // default priority: the fit's leading-half inverse under its factorisation
-    cudaEvent_t side_ev[10] = {};    // fork / join events between the streams
+    cudaStream_t side3 = nullptr;    // lowest priority: the fit's leading-half inverse under its factorisation
+    cudaStream_t mainf = nullptr;    // the fit's main-stream work, between the chain's priority and side3's
+    cudaEvent_t side_ev[12] = {};    // fork / join events between the streams
     gp_model *step_model = nullptr;  // search_step's model, kept for the next call of the same shape
     void *step_buf = nullptr;        // search_step's device staging
     size_t step_buf_bytes = 0;
